@@ -1,0 +1,184 @@
+/*
+ * idet.h -- C ABI of libidet, a CUDA (sm_103a) implementation of the
+ * data-parallel path of Dumas & Urbanska, "An introspective algorithm for
+ * the integer determinant": multi-prime LU over Z/p (Section 2.1, Alg. 2.1),
+ * Dixon p-adic lifting for the largest invariant factor s_n (Section 2.2),
+ * and Chinese remaindering of det(A)/s_n with early termination (Alg. 2.1,
+ * Alg. 4.1 with i_max = 1, as run in Section 5.1).
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are dense, row-major, n x n, with leading dimension lda >= n
+ *     (in elements). Entries are int64 values with |a_ij| <= 2^31 - 1.
+ *   - on_device = 0: pointers are host memory; the library copies them.
+ *     on_device = 1: pointers are device memory of the current device.
+ *   - stream is a cudaStream_t (passed as void*; NULL = legacy default
+ *     stream). Calls are synchronous with respect to the host: they return
+ *     after their results are written.
+ *   - Inputs are never modified. Output buffers are owned by the caller.
+ *   - Device workspace is allocated per call with the allocator installed by
+ *     idet_set_allocator, or cudaMallocAsync/cudaFreeAsync on the stream.
+ *   - Return value: IDET_OK (0) or one of the IDET_ERR_* codes below;
+ *     idet_last_error() gives a message for the calling thread's last error.
+ *   - Results are exact integers. int_det is correct with probability at
+ *     least 1 - 2^log2_epsilon (Alg. 2.1 ensures 1 - epsilon), or always when
+ *     certify = 1 (reconstruction past twice the Hadamard bound, Lemma 2.1(i)).
+ */
+#ifndef IDET_H
+#define IDET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define IDET_OK 0
+#define IDET_ERR_ARG 1        /* n < 0, null pointer, lda < n, entry too large */
+#define IDET_ERR_BUFFER 2     /* output capacity too small; nlimbs = needed  */
+#define IDET_ERR_SINGULAR 3   /* det(A) = 0 where a nonsingular A is needed  */
+#define IDET_ERR_NOMEM 4      /* device workspace could not be allocated     */
+#define IDET_ERR_TIMEOUT 5    /* a bounded device wait gave up               */
+#define IDET_ERR_CUDA 6       /* a CUDA call failed                          */
+#define IDET_ERR_INTERNAL 7   /* a reconstruction failed its own check       */
+
+/* Trailing-update (Schur complement) arithmetic of the LU over Z/p. */
+#define IDET_PATH_AUTO 0
+#define IDET_PATH_INT64 1     /* CUDA cores, int64 delayed reduction         */
+#define IDET_PATH_I8 2        /* signed 7-bit int8 limbs, int32 accumulation */
+#define IDET_PATH_F64 3       /* FP64 with delayed reduction below 2^53      */
+#define IDET_PATH_BF16 4      /* 7-bit limbs exact in bf16, tcgen05 tensor   */
+
+/* Big integer: sign in {-1, 0, +1}, magnitude in little-endian base-2^32
+ * limbs. The caller provides limbs[0..cap). On IDET_ERR_BUFFER, nlimbs is set
+ * to the number of limbs needed and nothing else is written. */
+typedef struct {
+    int32_t sign;
+    uint32_t nlimbs;
+    uint32_t cap;
+    uint32_t *limbs;
+} idet_int;
+
+typedef struct {
+    double log2_epsilon;   /* error tolerance epsilon = 2^log2_epsilon (-64) */
+    uint64_t seed;         /* seeds the prime sampling and the random b, u   */
+    int32_t certify;       /* 1: no early termination; stop at prod p >= 2H  */
+    int32_t update_path;   /* IDET_PATH_*                                    */
+    int32_t nb;            /* LU panel width, 0 = default                    */
+    int32_t wave;          /* primes factored per batch, 0 = default         */
+    int32_t lif;           /* 1 (default): Alg. 4.1 with i_max = 1; 0: CRA
+                              only (Alg. 2.1 on det(A))                      */
+    int32_t reserved[7];
+} idet_opts;
+
+typedef struct {
+    int32_t primes_used;       /* CRA primes factored (det mod p computed)   */
+    int32_t primes_in_cra;     /* primes the final reconstruction used      */
+    int32_t et_stop;           /* 1 early termination, 2 bound, 0 neither   */
+    int32_t lift_iters;        /* Dixon iterations (0 when no solve ran)    */
+    int32_t lift_timed_out;
+    int32_t log2_K;            /* bits of the factor K = s~_n found          */
+    double log2_H;             /* log2 of the Hadamard bound used           */
+    double ms_lu;              /* device time of the multi-prime LU         */
+    double ms_lift;            /* device time of the inverse + lift         */
+    double ms_cra;             /* device time of reconstruction steps       */
+    double ms_total;
+    uint64_t launches;         /* kernels launched by the call              */
+    double ms_lift_kernel;     /* device time of the lifting kernel alone   */
+    double lift_bytes;         /* its algorithmic bytes: m * 8 n^2          */
+    double lu_macs;            /* (2/3) n^3 per factored prime (+ inverse)  */
+} idet_stats;
+
+/* Fill *opts with the defaults. */
+void idet_default_opts(idet_opts *opts);
+
+/* Message for the calling thread's last error (never NULL). */
+const char *idet_last_error(void);
+
+/* Optional device allocator used for all workspace (e.g. a framework's
+ * caching allocator). alloc returns NULL on failure. Pass NULLs to restore
+ * the cudaMallocAsync default. Not thread-safe with concurrent calls. */
+typedef void *(*idet_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*idet_free_fn)(void *ptr, void *stream, void *ctx);
+void idet_set_allocator(idet_alloc_fn alloc, idet_free_fn free_, void *ctx);
+
+/* Kernels launched by this library since load (monotone counter). */
+uint64_t idet_launch_count(void);
+
+/*
+ * det(A): "computing the determinant of an integer matrix A" (Abstract,
+ * Section 1), by Alg. 4.1 with i_max = 1 (Section 5.1): Alg. 2.1 on det(A)
+ * for the Lemma 2.1(iv) number of primes, then one Dixon solve giving a
+ * factor K of s_n (Section 2.2), then Alg. 2.1 on det(A)/K reusing the
+ * residues already computed (Section 4). opts may be NULL (defaults), stats
+ * may be NULL. det receives the exact determinant.
+ */
+int idet_int_det(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
+                 const idet_opts *opts, void *stream, idet_int *det,
+                 idet_stats *stats);
+
+/*
+ * s~_n for the right-hand side b: the lcm of the denominators of the entries
+ * of A^{-1} b, computed by Dixon p-adic lifting and rational reconstruction
+ * (Section 2.2, LargestInvariantFactor with one solve). b has n int64
+ * entries with |b_i| < 2^62 (on_device applies to b too). The value is exact
+ * and deterministic given (A, b). IDET_ERR_SINGULAR if A is singular.
+ */
+int idet_largest_invariant_factor(const int64_t *A, int64_t n, int64_t lda,
+                                  const int64_t *b, int32_t on_device,
+                                  const idet_opts *opts, void *stream,
+                                  idet_int *s);
+
+/*
+ * det(A) mod p_k for a list of primes (the modular step of Alg. 2.1, "compute
+ * det(A) mod p_i using the LU factorization modulo p_i", Section 2.1).
+ * primes: host array of nprimes odd primes, each with 2^20 < p < 2^21 or
+ * 2^30 < p < 2^31 (all of one class). det_mod: host array receiving the
+ * residues in [0, p_k). The pivot is the first nonzero entry at or below the
+ * diagonal.
+ */
+int idet_det_mod_primes(const int64_t *A, int64_t n, int64_t lda,
+                        int32_t on_device, const uint32_t *primes,
+                        int32_t nprimes, const idet_opts *opts, void *stream,
+                        uint32_t *det_mod);
+
+/*
+ * LU over Z/p of one prime: factors (host, n*n int32 in [0, p): strict lower
+ * part L with unit diagonal, upper part U) and perm (host, n int32: row of A
+ * now at position i) with PA = LU. Returns IDET_ERR_SINGULAR (factors then
+ * partial) when a column has no nonzero pivot. Same prime classes as above.
+ */
+int idet_lu_mod_prime(const int64_t *A, int64_t n, int64_t lda,
+                      int32_t on_device, uint32_t p, const idet_opts *opts,
+                      void *stream, uint32_t *lu, int32_t *perm);
+
+/*
+ * The Dixon p-adic lifting iteration of Section 2.2 for one prime p with
+ * 2^30 < p < 2^31: C = A^{-1} mod p; r_0 = b; x_i = C r_i mod p in the
+ * balanced range [-(p-1)/2, (p-1)/2]; r_{i+1} = (r_i - A x_i)/p. Writes the m
+ * digit vectors to digits (host, m*n int32, row i = x_i) and r_m to
+ * residual (host, n int64). IDET_ERR_SINGULAR if A is singular mod p.
+ */
+int idet_dixon_digits(const int64_t *A, int64_t n, int64_t lda,
+                      const int64_t *b, uint32_t p, int32_t m,
+                      int32_t on_device, void *stream, int32_t *digits,
+                      int64_t *residual);
+
+/*
+ * Chinese remaindering in the symmetric range (Section 2.1): the unique r
+ * with r = residues[k] mod primes[k] for all k and
+ * -floor(M/2) <= r < ceil(M/2), M = prod primes (odd primes, pairwise
+ * distinct, < 2^31). Host arrays. trailing (may be NULL) receives the
+ * number k of early-termination agreements r_{t-k} = ... = r_t at the end of
+ * the sequence (Alg. 2.1).
+ */
+int idet_crt_symmetric(const uint32_t *residues, const uint32_t *primes,
+                       int32_t count, void *stream, idet_int *r,
+                       int32_t *trailing);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IDET_H */

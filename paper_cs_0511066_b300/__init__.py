@@ -1,0 +1,300 @@
+"""Python binding of libidet (the C ABI in include/idet.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of libidet.so. Matrices may be numpy int64 arrays (host) or torch
+int64 CUDA tensors (device). Workspace is drawn from torch's CUDA caching
+allocator and calls run on torch's current stream.
+
+The library must have been built (python -m paper_cs_0511066_b300.build, or
+__graft_entry__.build()); importing this module without libidet.so raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libidet.so")
+
+IDET_OK = 0
+IDET_ERR_ARG = 1
+IDET_ERR_BUFFER = 2
+IDET_ERR_SINGULAR = 3
+IDET_ERR_NOMEM = 4
+IDET_ERR_TIMEOUT = 5
+IDET_ERR_CUDA = 6
+IDET_ERR_INTERNAL = 7
+
+PATH_AUTO, PATH_INT64, PATH_I8, PATH_F64, PATH_BF16 = 0, 1, 2, 3, 4
+
+
+class IdetError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libidet error {code}: {msg}")
+        self.code = code
+
+
+class idet_int(ctypes.Structure):
+    _fields_ = [("sign", ctypes.c_int32), ("nlimbs", ctypes.c_uint32),
+                ("cap", ctypes.c_uint32), ("limbs", ctypes.POINTER(ctypes.c_uint32))]
+
+
+class idet_opts(ctypes.Structure):
+    _fields_ = [("log2_epsilon", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("certify", ctypes.c_int32), ("update_path", ctypes.c_int32),
+                ("nb", ctypes.c_int32), ("wave", ctypes.c_int32),
+                ("lif", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class idet_stats(ctypes.Structure):
+    _fields_ = [("primes_used", ctypes.c_int32), ("primes_in_cra", ctypes.c_int32),
+                ("et_stop", ctypes.c_int32), ("lift_iters", ctypes.c_int32),
+                ("lift_timed_out", ctypes.c_int32), ("log2_K", ctypes.c_int32),
+                ("log2_H", ctypes.c_double), ("ms_lu", ctypes.c_double),
+                ("ms_lift", ctypes.c_double), ("ms_cra", ctypes.c_double),
+                ("ms_total", ctypes.c_double), ("launches", ctypes.c_uint64),
+                ("ms_lift_kernel", ctypes.c_double), ("lift_bytes", ctypes.c_double),
+                ("lu_macs", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with "
+                      "`python -m paper_cs_0511066_b300.build`")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_P = ctypes.c_void_p
+_i64, _i32, _u32 = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32
+_lib.idet_default_opts.argtypes = [ctypes.POINTER(idet_opts)]
+_lib.idet_default_opts.restype = None
+_lib.idet_last_error.restype = ctypes.c_char_p
+_lib.idet_launch_count.restype = ctypes.c_uint64
+_lib.idet_int_det.argtypes = [_P, _i64, _i64, _i32, ctypes.POINTER(idet_opts), _P,
+                              ctypes.POINTER(idet_int), ctypes.POINTER(idet_stats)]
+_lib.idet_largest_invariant_factor.argtypes = [_P, _i64, _i64, _P, _i32,
+                                               ctypes.POINTER(idet_opts), _P,
+                                               ctypes.POINTER(idet_int)]
+_lib.idet_det_mod_primes.argtypes = [_P, _i64, _i64, _i32, _P, _i32,
+                                     ctypes.POINTER(idet_opts), _P, _P]
+_lib.idet_lu_mod_prime.argtypes = [_P, _i64, _i64, _i32, _u32, ctypes.POINTER(idet_opts),
+                                   _P, _P, _P]
+_lib.idet_dixon_digits.argtypes = [_P, _i64, _i64, _P, _u32, _i32, _i32, _P, _P, _P]
+_lib.idet_crt_symmetric.argtypes = [_P, _P, _i32, _P, ctypes.POINTER(idet_int),
+                                    ctypes.POINTER(ctypes.c_int32)]
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+_lib.idet_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, ctypes.c_void_p]
+_lib.idet_set_allocator.restype = None
+
+_torch = None
+_allocator_installed = False
+_cb_refs = []
+
+
+def _get_torch():
+    global _torch
+    if _torch is None:
+        try:
+            import torch  # noqa: F401
+            _torch = torch
+        except Exception:  # pragma: no cover
+            _torch = False
+    return _torch or None
+
+
+def use_torch_allocator() -> bool:
+    """Route libidet's device workspace through torch's caching allocator."""
+    global _allocator_installed
+    if _allocator_installed:
+        return True
+    torch = _get_torch()
+    if torch is None or not torch.cuda.is_available():
+        return False
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:
+            return None
+
+    def _free(ptr, stream, ctx):
+        try:
+            torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:
+            pass
+
+    a, f = _ALLOC_FN(_alloc), _FREE_FN(_free)
+    _cb_refs[:] = [a, f]
+    _lib.idet_set_allocator(a, f, None)
+    _allocator_installed = True
+    return True
+
+
+def _stream_ptr(stream=None) -> int:
+    torch = _get_torch()
+    if stream is not None:
+        return int(getattr(stream, "cuda_stream", stream))
+    if torch is not None and torch.cuda.is_available():
+        return int(torch.cuda.current_stream().cuda_stream)
+    return 0
+
+
+def _check(rc: int):
+    if rc != IDET_OK:
+        raise IdetError(rc, _lib.idet_last_error().decode(errors="replace"))
+
+
+def default_opts(**kw) -> idet_opts:
+    o = idet_opts()
+    _lib.idet_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if v is not None:
+            setattr(o, k, v)
+    return o
+
+
+def _matrix(A):
+    """(pointer, n, lda, on_device, keepalive) for a numpy or torch matrix."""
+    torch = _get_torch()
+    if torch is not None and isinstance(A, torch.Tensor):
+        if A.dtype != torch.int64 or A.dim() != 2 or A.shape[0] != A.shape[1]:
+            raise ValueError("square int64 tensor expected")
+        if A.stride(1) != 1:
+            A = A.contiguous()
+        return A.data_ptr(), A.shape[0], A.stride(0), 1 if A.is_cuda else 0, A
+    a = np.ascontiguousarray(np.asarray(A, dtype=np.int64))
+    if a.ndim != 2 or a.shape[0] != a.shape[1]:
+        raise ValueError("square matrix expected")
+    return a.ctypes.data, a.shape[0], a.shape[1], 0, a
+
+
+def _vector(b, on_device):
+    torch = _get_torch()
+    if torch is not None and isinstance(b, torch.Tensor):
+        b = b.to(torch.int64)
+        if on_device and not b.is_cuda:
+            b = b.cuda()
+        return b.contiguous().data_ptr(), b
+    v = np.ascontiguousarray(np.asarray(b, dtype=np.int64))
+    if on_device:
+        t = torch.from_numpy(v).cuda()
+        return t.data_ptr(), t
+    return v.ctypes.data, v
+
+
+def _to_int(x: idet_int, buf) -> int:
+    v = 0
+    for i in range(x.nlimbs - 1, -1, -1):
+        v = (v << 32) | int(buf[i])
+    return -v if x.sign < 0 else v
+
+
+def _call_int(fn, *args, cap: int = 1 << 12):
+    while True:
+        buf = (ctypes.c_uint32 * cap)()
+        out = idet_int(0, 0, cap, buf)
+        rc = fn(*args, ctypes.byref(out))
+        if rc == IDET_ERR_BUFFER and out.nlimbs > cap:
+            cap = int(out.nlimbs) + 8
+            continue
+        _check(rc)
+        return _to_int(out, buf)
+
+
+def int_det(A, *, certify: bool = False, seed: int | None = None, lif: bool = True,
+            update_path: int | None = None, nb: int | None = None, wave: int | None = None,
+            log2_epsilon: float | None = None, stream=None, return_stats: bool = False):
+    """det(A) as a Python int (idet_int_det)."""
+    use_torch_allocator()
+    ptr, n, lda, dev, keep = _matrix(A)
+    o = default_opts(certify=int(certify), seed=seed, lif=int(lif), update_path=update_path,
+                     nb=nb, wave=wave, log2_epsilon=log2_epsilon)
+    st = idet_stats()
+    cap = max(64, int(n * 40 // 32) + 64)
+    while True:
+        buf = (ctypes.c_uint32 * cap)()
+        out = idet_int(0, 0, cap, buf)
+        rc = _lib.idet_int_det(ptr, n, lda, dev, ctypes.byref(o), _stream_ptr(stream),
+                               ctypes.byref(out), ctypes.byref(st))
+        if rc == IDET_ERR_BUFFER and out.nlimbs > cap:
+            cap = int(out.nlimbs) + 8
+            continue
+        _check(rc)
+        break
+    d = _to_int(out, buf)
+    del keep
+    return (d, st.as_dict()) if return_stats else d
+
+
+def largest_invariant_factor(A, b, *, seed: int | None = None, stream=None) -> int:
+    """lcm of the denominators of A^{-1} b (idet_largest_invariant_factor)."""
+    use_torch_allocator()
+    ptr, n, lda, dev, keep = _matrix(A)
+    bp, bkeep = _vector(b, dev)
+    o = default_opts(seed=seed)
+    return _call_int(lambda *a: _lib.idet_largest_invariant_factor(*a), ptr, n, lda, bp, dev,
+                     ctypes.byref(o), _stream_ptr(stream), cap=max(64, n * 40 // 32 + 64))
+
+
+def det_mod_primes(A, primes, *, update_path: int | None = None, nb: int | None = None,
+                   stream=None) -> np.ndarray:
+    use_torch_allocator()
+    ptr, n, lda, dev, keep = _matrix(A)
+    pr = np.ascontiguousarray(np.asarray(primes, dtype=np.uint32))
+    out = np.zeros(len(pr), dtype=np.uint32)
+    o = default_opts(update_path=update_path, nb=nb)
+    _check(_lib.idet_det_mod_primes(ptr, n, lda, dev, pr.ctypes.data, len(pr), ctypes.byref(o),
+                                    _stream_ptr(stream), out.ctypes.data))
+    return out
+
+
+def lu_mod_prime(A, p: int, *, nb: int | None = None, stream=None):
+    """(LU residues in [0,p), perm, singular flag)."""
+    use_torch_allocator()
+    ptr, n, lda, dev, keep = _matrix(A)
+    lu = np.zeros((n, n), dtype=np.uint32)
+    perm = np.zeros(n, dtype=np.int32)
+    o = default_opts(nb=nb)
+    rc = _lib.idet_lu_mod_prime(ptr, n, lda, dev, p, ctypes.byref(o), _stream_ptr(stream),
+                                lu.ctypes.data, perm.ctypes.data)
+    if rc == IDET_ERR_SINGULAR:
+        return lu, perm, True
+    _check(rc)
+    return lu, perm, False
+
+
+def dixon_digits(A, b, p: int, m: int, *, stream=None):
+    """(digits [m][n] int32, residual r_m [n] int64)."""
+    use_torch_allocator()
+    ptr, n, lda, dev, keep = _matrix(A)
+    bp, bkeep = _vector(b, dev)
+    digits = np.zeros((m, n), dtype=np.int32)
+    res = np.zeros(n, dtype=np.int64)
+    _check(_lib.idet_dixon_digits(ptr, n, lda, bp, p, m, dev, _stream_ptr(stream),
+                                  digits.ctypes.data, res.ctypes.data))
+    return digits, res
+
+
+def crt_symmetric(residues, primes, *, stream=None):
+    """(r, trailing agreements) (idet_crt_symmetric)."""
+    use_torch_allocator()
+    res = np.ascontiguousarray(np.asarray(residues, dtype=np.uint32))
+    pr = np.ascontiguousarray(np.asarray(primes, dtype=np.uint32))
+    tr = ctypes.c_int32(0)
+    v = _call_int(lambda *a: _lib.idet_crt_symmetric(res.ctypes.data, pr.ctypes.data, len(pr),
+                                                     _stream_ptr(stream), a[0], ctypes.byref(tr)),
+                  cap=len(pr) + 8)
+    return v, int(tr.value)
+
+
+def launch_count() -> int:
+    return int(_lib.idet_launch_count())
+
+
+__all__ = ["int_det", "largest_invariant_factor", "det_mod_primes", "lu_mod_prime",
+           "dixon_digits", "crt_symmetric", "launch_count", "default_opts", "IdetError",
+           "use_torch_allocator", "LIB_PATH"]

@@ -1,0 +1,962 @@
+// C ABI of libidet and the host-side control of Alg. 4.1 (i_max = 1).
+//
+// The host code here only sequences kernels and takes the paper's control
+// decisions (which primes, when to stop, how many lifting steps); every
+// arithmetic step on A, its residues, the lifting state and the multi-word
+// results runs in the kernels of k_*.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "idet_internal.cuh"
+
+namespace idet {
+
+// ---------------------------------------------------------------------------
+// Errors, allocator, launch counter
+
+static thread_local char g_err[1024] = "no error";
+unsigned long long g_launches = 0;
+
+void set_last_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+static idet_alloc_fn g_alloc = nullptr;
+static idet_free_fn g_free = nullptr;
+static void *g_actx = nullptr;
+
+Workspace::~Workspace() {
+    for (int i = n_ - 1; i >= 0; --i) {
+        if (g_free)
+            g_free(ptrs_[i], (void *)stream_, g_actx);
+        else
+            cudaFreeAsync(ptrs_[i], stream_);
+    }
+}
+
+int Workspace::alloc(void **ptr, size_t bytes) {
+    if (n_ >= 256) {
+        set_last_error("workspace: too many allocations");
+        return IDET_ERR_INTERNAL;
+    }
+    bytes = (bytes + 255) / 256 * 256;
+    void *p = nullptr;
+    if (g_alloc) {
+        p = g_alloc(bytes, (void *)stream_, g_actx);
+    } else if (cudaMallocAsync(&p, bytes, stream_) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (!p) {
+        set_last_error("workspace: could not allocate %zu bytes of device memory", bytes);
+        return IDET_ERR_NOMEM;
+    }
+    ptrs_[n_++] = p;
+    *ptr = p;
+    return IDET_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Primes and random numbers (parameter choice, Alg. 2.1 "random primes")
+
+static const uint32_t kLo21 = 1u << 20, kHi21 = 1u << 21;
+
+static const std::vector<uint32_t> &pool21() {
+    static std::vector<uint32_t> pool;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        std::vector<uint8_t> comp(kHi21, 0);
+        for (uint32_t i = 2; (uint64_t)i * i < kHi21; ++i)
+            if (!comp[i])
+                for (uint32_t j = i * i; j < kHi21; j += i) comp[j] = 1;
+        for (uint32_t v = kLo21 + 1; v < kHi21; ++v)
+            if (!comp[v]) pool.push_back(v);
+    });
+    return pool;
+}
+
+struct SplitMix {
+    uint64_t s;
+    explicit SplitMix(uint64_t seed) : s(seed) {}
+    uint64_t next() {
+        uint64_t z = (s += 0x9e3779b97f4a7c15ull);
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+        return z ^ (z >> 31);
+    }
+    uint64_t below(uint64_t n) { return next() % n; }
+};
+
+static uint64_t powmod64(uint64_t a, uint64_t e, uint64_t m) {
+    unsigned __int128 r = 1, b = a % m;
+    while (e) {
+        if (e & 1) r = r * b % m;
+        b = b * b % m;
+        e >>= 1;
+    }
+    return (uint64_t)r;
+}
+
+// Deterministic Miller-Rabin for 32-bit integers (bases 2, 7, 61).
+static bool is_prime32(uint32_t n) {
+    if (n < 2) return false;
+    for (uint32_t q : {2u, 3u, 5u, 7u, 11u, 13u, 61u})
+        if (n % q == 0) return n == q;
+    uint32_t d = n - 1;
+    int s = 0;
+    while (!(d & 1)) {
+        d >>= 1;
+        ++s;
+    }
+    for (uint32_t a : {2u, 7u, 61u}) {
+        uint64_t x = powmod64(a, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool ok = false;
+        for (int r = 1; r < s; ++r) {
+            x = (unsigned __int128)x * x % n;
+            if (x == n - 1) {
+                ok = true;
+                break;
+            }
+        }
+        if (!ok) return false;
+    }
+    return true;
+}
+
+// Random primes sampled without replacement from the 21-bit pool.
+struct PrimeDraw {
+    std::vector<uint32_t> order;
+    size_t next = 0;
+    PrimeDraw(uint64_t seed) : order(pool21()) {
+        SplitMix g(seed ^ 0x5eed5eedull);
+        for (size_t i = order.size() - 1; i > 0; --i) std::swap(order[i], order[g.below(i + 1)]);
+    }
+    bool take(uint32_t &p) {
+        if (next >= order.size()) return false;
+        p = order[next++];
+        return true;
+    }
+};
+
+static uint32_t random_prime31(SplitMix &g) {
+    while (true) {
+        uint32_t c = (uint32_t)((1u << 30) + (g.next() % (1u << 30))) | 1u;
+        if (c < (1u << 31) && is_prime32(c)) return c;
+    }
+}
+
+static uint64_t inv_mod_2_64(uint64_t p) {
+    uint64_t x = p;  // p * p = 1 mod 8
+    for (int i = 0; i < 6; ++i) x *= 2 - p * x;
+    return x;
+}
+
+// ---------------------------------------------------------------------------
+// Early-termination control of Alg. 2.1 (Lemma 2.1(iii), (iv)).
+
+static double log2_sum(double a, double b) {  // log2(2^a + 2^b)
+    double hi = std::max(a, b), lo = std::min(a, b);
+    if (lo == -INFINITY) return hi;
+    return hi + std::log2(1.0 + std::exp2(lo - hi));
+}
+
+// Lemma 2.1(iv): k >= ceil(log(1/eps) / (log P' - log(log_l H))), with
+// P' = |P| - ceil(log_l H). Returns 0 when the pool is too small for it.
+static int k_default(double eps_log2, double pool, double log2H, double log2l) {
+    double lH = log2H / log2l;
+    if (lH <= 0) return 1;
+    double Pp = pool - std::ceil(lH);
+    if (Pp <= lH) return 0;
+    return std::max(1, (int)std::ceil(-eps_log2 / (std::log2(Pp) - std::log2(lH))));
+}
+
+struct CraScan {
+    // Alg. 2.1 over digits[0..count): returns the index t of the prime at
+    // which the loop stops (-1 if it does not) and why (1 ET, 2 bound).
+    static int scan(const std::vector<int32_t> &dig, const std::vector<uint32_t> &pr,
+                    double log2H, double eps_log2, double log2l, double pool, bool certify,
+                    int *why) {
+        double log2M = 0;
+        std::vector<double> lM(dig.size());
+        int k = 0, top = -1;
+        for (size_t t = 0; t < dig.size(); ++t) {
+            log2M += std::log2((double)pr[t]);
+            lM[t] = log2M;
+            if (t > 0 && dig[t] == 0)
+                ++k;
+            else
+                k = 0;
+            if (dig[t] != 0) top = (int)t;
+            if (log2M >= 1.0 + log2H) {
+                *why = 2;
+                return (int)t;
+            }
+            if (certify || k == 0) continue;
+            // |r| < (|v_top| + 1) prod_{j<top} p_j
+            double lr = -INFINITY;
+            if (top >= 0)
+                lr = (top > 0 ? lM[top - 1] : 0.0) + std::log2(std::fabs((double)dig[top]) + 1.0);
+            double num = log2_sum(log2H, lr);
+            double Rp = std::ceil((num - lM[t - k]) / log2l - 1e-12);
+            if (Rp < 0) Rp = 0;
+            double ratio = 1.0;
+            double i_used = (double)(t + 1);
+            for (int j = 0; j < k; ++j) {
+                double nn = std::max(0.0, Rp - j);
+                double dd = pool - i_used + k - 1 - j;
+                if (dd <= 0) {
+                    ratio = INFINITY;
+                    break;
+                }
+                ratio *= nn / dd;
+            }
+            if (ratio < std::exp2(eps_log2)) {
+                *why = 1;
+                return (int)t;
+            }
+        }
+        *why = 0;
+        return -1;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Helpers
+
+struct DevMatrix {
+    const int64_t *A = nullptr;  // n x n, ld n (device)
+    int64_t n = 0;
+};
+
+static int stage_matrix(const int64_t *A, int64_t n, int64_t lda, int on_device, Workspace &ws,
+                        DevMatrix &out) {
+    out.n = n;
+    int64_t *d = nullptr;
+    IDET_TRY(ws.alloc_n(&d, (size_t)n * n));
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    IDET_CUDA_TRY(cudaMemcpy2DAsync(d, sizeof(int64_t) * n, A, sizeof(int64_t) * lda,
+                                    sizeof(int64_t) * n, n, kind, ws.stream()));
+    out.A = d;
+    return IDET_OK;
+}
+
+static int write_int(idet_int *out, int sign, const uint32_t *limbs_host, uint32_t nl) {
+    if (!out) return IDET_ERR_ARG;
+    if (nl > out->cap || (nl > 0 && !out->limbs)) {
+        out->nlimbs = nl;
+        set_last_error("output integer needs %u limbs, capacity is %u", nl, out->cap);
+        return IDET_ERR_BUFFER;
+    }
+    out->sign = nl ? sign : 0;
+    out->nlimbs = nl;
+    if (nl) memcpy(out->limbs, limbs_host, sizeof(uint32_t) * nl);
+    return IDET_OK;
+}
+
+struct Timer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaStream_t s;
+    explicit Timer(cudaStream_t st) : s(st) {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, s);
+    }
+    double stop() {
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        return ms;
+    }
+    ~Timer() {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+    }
+};
+
+// Per-call state of the determinant computation.
+struct DetJob {
+    DevMatrix M;
+    Workspace &ws;
+    cudaStream_t s;
+    idet_opts o;
+    int nb;
+    // matrix statistics
+    double log2H = 0;
+    std::vector<double> rowsq;
+    uint64_t amax = 0;
+    int32_t *A32 = nullptr;  // ld = ld4
+    int64_t ld4 = 0;
+    // CRA state
+    PrimeDraw draw;
+    std::vector<uint32_t> primes;   // factored primes
+    std::vector<uint32_t> dets;     // det(A) mod primes
+    idet_stats st{};
+
+    DetJob(const DevMatrix &m, Workspace &w, const idet_opts &opts)
+        : M(m), ws(w), s(w.stream()), o(opts), draw(opts.seed) {
+        nb = o.nb > 0 ? o.nb : 32;
+    }
+
+    int stats() {
+        const int64_t n = M.n;
+        double *d_rowsq = nullptr;
+        unsigned long long *d_amax = nullptr;
+        IDET_TRY(ws.alloc_n(&d_rowsq, n));
+        IDET_TRY(ws.alloc_n(&d_amax, 1));
+        IDET_TRY(launch_row_stats(M.A, n, n, d_rowsq, d_amax, s));
+        rowsq.resize(n);
+        IDET_CUDA_TRY(cudaMemcpyAsync(rowsq.data(), d_rowsq, sizeof(double) * n,
+                                      cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaMemcpyAsync(&amax, d_amax, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        if (amax > 0x7fffffffull) {
+            set_last_error("entries must satisfy |a_ij| <= 2^31 - 1");
+            return IDET_ERR_ARG;
+        }
+        log2H = 0;
+        for (double v : rowsq) log2H += v > 0 ? 0.5 * std::log2(v) : -INFINITY;
+        st.log2_H = log2H;
+        return IDET_OK;
+    }
+
+    // det(A) mod p for W more primes (appended to primes/dets).
+    int factor_wave(int W) {
+        const int64_t n = M.n;
+        std::vector<uint32_t> pw;
+        for (int i = 0; i < W; ++i) {
+            uint32_t p;
+            if (!draw.take(p)) break;
+            pw.push_back(p);
+        }
+        W = (int)pw.size();
+        if (W == 0) {
+            set_last_error("prime pool exhausted");
+            return IDET_ERR_INTERNAL;
+        }
+        std::vector<ModP> mh(W);
+        for (int i = 0; i < W; ++i) mh[i] = make_mod(pw[i]);
+        ModP *md = nullptr;
+        int32_t *R = nullptr;
+        uint32_t *dd = nullptr;
+        IDET_TRY(ws.alloc_n(&md, W));
+        IDET_TRY(ws.alloc_n(&R, (size_t)W * n * n));
+        IDET_TRY(ws.alloc_n(&dd, W));
+        IDET_CUDA_TRY(cudaMemcpyAsync(md, mh.data(), sizeof(ModP) * W, cudaMemcpyHostToDevice, s));
+        Timer t(s);
+        IDET_TRY(launch_reduce(M.A, n, n, md, W, R, s));
+        IDET_TRY(lu_factor_batched(R, n, md, mh.data(), W, false, nb, nullptr, dd,
+                                   o.update_path, ws));
+        std::vector<uint32_t> res(W);
+        IDET_CUDA_TRY(cudaMemcpyAsync(res.data(), dd, sizeof(uint32_t) * W,
+                                      cudaMemcpyDeviceToHost, s));
+        st.ms_lu += t.stop();
+        for (int i = 0; i < W; ++i) {
+            primes.push_back(pw[i]);
+            dets.push_back(res[i]);
+        }
+        st.primes_used += W;
+        st.lu_macs += (2.0 / 3.0) * (double)n * n * n * W;
+        return IDET_OK;
+    }
+
+    // Garner digits of the residues res (mod prs) on the device.
+    int cra_digits(const std::vector<uint32_t> &prs, const std::vector<uint32_t> &res,
+                   std::vector<int32_t> &dig) {
+        const int c = (int)prs.size();
+        dig.assign(c, 0);
+        if (c == 0) return IDET_OK;
+        uint32_t *dp = nullptr, *dr = nullptr;
+        int32_t *dg = nullptr;
+        IDET_TRY(ws.alloc_n(&dp, c));
+        IDET_TRY(ws.alloc_n(&dr, c));
+        IDET_TRY(ws.alloc_n(&dg, c));
+        IDET_CUDA_TRY(cudaMemcpyAsync(dp, prs.data(), 4 * c, cudaMemcpyHostToDevice, s));
+        IDET_CUDA_TRY(cudaMemcpyAsync(dr, res.data(), 4 * c, cudaMemcpyHostToDevice, s));
+        IDET_TRY(launch_cra_append(dp, dr, dg, 0, c, nullptr, s));
+        IDET_CUDA_TRY(cudaMemcpyAsync(dig.data(), dg, 4 * c, cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        return IDET_OK;
+    }
+
+    // result = K * sum_{i<c} dig_i prod_{j<i} prs_j, K given as device limbs.
+    int assemble(const std::vector<uint32_t> &prs, const std::vector<int32_t> &dig, int c,
+                 const uint32_t *Kdev, int Klen, idet_int *out) {
+        double bits = 64;
+        for (int i = 0; i < c; ++i) bits += std::log2((double)prs[i]);
+        const int cap = (int)(bits / 32) + Klen + 4;
+        uint32_t *dp = nullptr, *buf = nullptr;
+        int32_t *dg = nullptr, *info = nullptr;
+        IDET_TRY(ws.alloc_n(&dp, c + 1));
+        IDET_TRY(ws.alloc_n(&dg, c + 1));
+        IDET_TRY(ws.alloc_n(&buf, 2 * (size_t)cap));
+        IDET_TRY(ws.alloc_n(&info, 4));
+        uint32_t one = 1;
+        uint32_t *Kd = (uint32_t *)Kdev;
+        if (!Kd) {
+            IDET_TRY(ws.alloc_n(&Kd, 1));
+            IDET_CUDA_TRY(cudaMemcpyAsync(Kd, &one, 4, cudaMemcpyHostToDevice, s));
+            Klen = 1;
+        }
+        IDET_CUDA_TRY(cudaMemcpyAsync(dp, prs.data(), 4 * c, cudaMemcpyHostToDevice, s));
+        IDET_CUDA_TRY(cudaMemcpyAsync(dg, dig.data(), 4 * c, cudaMemcpyHostToDevice, s));
+        IDET_TRY(launch_mixed_to_int(dp, dg, c, Kd, Klen, buf, cap, info, s));
+        int32_t hinfo[3];
+        IDET_CUDA_TRY(cudaMemcpyAsync(hinfo, info, 12, cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hinfo[2]) {
+            set_last_error("reconstruction buffer too small");
+            return IDET_ERR_INTERNAL;
+        }
+        std::vector<uint32_t> host(hinfo[1] > 0 ? hinfo[1] : 1);
+        if (hinfo[1] > 0)
+            IDET_CUDA_TRY(cudaMemcpyAsync(host.data(), buf, 4 * (size_t)hinfo[1],
+                                          cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        return write_int(out, hinfo[0], host.data(), (uint32_t)hinfo[1]);
+    }
+};
+
+// LU + inverse mod a 31-bit prime; returns IDET_ERR_SINGULAR if A is
+// singular mod p. Cinv: n x ld4 (zero padded columns).
+static int inverse_mod_prime(const DevMatrix &M, uint32_t p, int nb, Workspace &ws, int32_t *Cinv,
+                             int64_t ld4) {
+    cudaStream_t s = ws.stream();
+    const int64_t n = M.n;
+    ModP mh = make_mod(p);
+    ModP *md = nullptr;
+    int32_t *R = nullptr, *perm = nullptr, *Y = nullptr;
+    uint32_t *dd = nullptr;
+    IDET_TRY(ws.alloc_n(&md, 1));
+    IDET_TRY(ws.alloc_n(&R, (size_t)n * n));
+    IDET_TRY(ws.alloc_n(&perm, n));
+    IDET_TRY(ws.alloc_n(&dd, 1));
+    IDET_CUDA_TRY(cudaMemcpyAsync(md, &mh, sizeof(ModP), cudaMemcpyHostToDevice, s));
+    IDET_TRY(launch_reduce(M.A, n, n, md, 1, R, s));
+    IDET_TRY(lu_factor_batched(R, n, md, &mh, 1, true, nb, perm, dd, IDET_PATH_INT64, ws));
+    uint32_t det = 0;
+    IDET_CUDA_TRY(cudaMemcpyAsync(&det, dd, 4, cudaMemcpyDeviceToHost, s));
+    IDET_CUDA_TRY(cudaStreamSynchronize(s));
+    if (det == 0) return IDET_ERR_SINGULAR;
+    if (ld4 == n) {
+        IDET_TRY(lu_inverse(R, perm, n, mh, md, true, nb, Cinv, ws));
+    } else {
+        IDET_TRY(ws.alloc_n(&Y, (size_t)n * n));
+        IDET_TRY(lu_inverse(R, perm, n, mh, md, true, nb, Y, ws));
+        IDET_CUDA_TRY(cudaMemsetAsync(Cinv, 0, sizeof(int32_t) * n * ld4, s));
+        IDET_CUDA_TRY(cudaMemcpy2DAsync(Cinv, 4 * ld4, Y, 4 * n, 4 * n, n,
+                                        cudaMemcpyDeviceToDevice, s));
+    }
+    return IDET_OK;
+}
+
+static int make_A32(const DevMatrix &M, Workspace &ws, int32_t **A32, int64_t *ld4) {
+    const int64_t n = M.n;
+    *ld4 = (n + 3) / 4 * 4;
+    int32_t *a = nullptr;
+    IDET_TRY(ws.alloc_n(&a, (size_t)n * *ld4));
+    if (*ld4 == n) {
+        IDET_TRY(launch_to_int32(M.A, n, n, a, ws.stream()));
+    } else {
+        int32_t *t = nullptr;
+        IDET_TRY(ws.alloc_n(&t, (size_t)n * n));
+        IDET_TRY(launch_to_int32(M.A, n, n, t, ws.stream()));
+        IDET_CUDA_TRY(cudaMemsetAsync(a, 0, sizeof(int32_t) * n * *ld4, ws.stream()));
+        IDET_CUDA_TRY(cudaMemcpy2DAsync(a, 4 * *ld4, t, 4 * n, 4 * n, n,
+                                        cudaMemcpyDeviceToDevice, ws.stream()));
+    }
+    *A32 = a;
+    return IDET_OK;
+}
+
+// Section 2.2: one Dixon solve with right-hand side b, then the denominator
+// of the projection u . x by rational reconstruction. Kdig receives the
+// base-p digits of the denominator (host), Kp the lift prime.
+struct LiftResult {
+    uint32_t p = 0;
+    int m = 0;
+    std::vector<uint32_t> den;  // base-p digits
+    int timed_out = 0;
+};
+
+static int solve_and_denominator(DetJob &J, const int64_t *b_dev, const std::vector<int64_t> &b_host,
+                                 const int32_t *u_dev, double log2u1, LiftResult &out) {
+    const int64_t n = J.M.n;
+    Workspace &ws = J.ws;
+    cudaStream_t s = J.s;
+    SplitMix g(J.o.seed ^ 0x11f7ull);
+    if (!J.A32) IDET_TRY(make_A32(J.M, ws, &J.A32, &J.ld4));
+    int32_t *Cinv = nullptr;
+    IDET_TRY(ws.alloc_n(&Cinv, (size_t)n * J.ld4));
+    uint32_t p = 0;
+    int rc = IDET_ERR_SINGULAR;
+    for (int tries = 0; tries < 6 && rc == IDET_ERR_SINGULAR; ++tries) {
+        p = random_prime31(g);
+        rc = inverse_mod_prime(J.M, p, J.nb, ws, Cinv, J.ld4);
+    }
+    if (rc != IDET_OK) return rc;
+    // Bounds: D <= |det A| <= prod ||row_i||; numerator of u.x:
+    // |u . N| <= ||u||_1 max_j |N_j|, |N_j| <= prod_i sqrt(||row_i||^2 + b_i^2).
+    double log2D = 0, log2N = log2u1;
+    for (int64_t i = 0; i < n; ++i) {
+        log2D += 0.5 * std::log2(std::max(J.rowsq[i], 1.0));
+        double bi = (double)b_host[i];
+        log2N += 0.5 * std::log2(J.rowsq[i] * (1 + 1e-12) + bi * bi + 1.0);
+    }
+    const double lp = std::log2((double)p);
+    const int hN = (int)std::ceil((log2N + 1) / lp);
+    const int hD = (int)std::ceil((log2D + 1) / lp);
+    const int m = hN + hD + 2;
+    LiftArgs a{};
+    a.A32 = J.A32;
+    a.Cinv = Cinv;
+    a.b = b_dev;
+    a.u = u_dev;
+    a.n = n;
+    a.m = m;
+    a.mod = make_mod(p);
+    a.pinv = inv_mod_2_64(p);
+    int64_t *z = nullptr, *r = nullptr;
+    IDET_TRY(ws.alloc_n(&z, m));
+    IDET_TRY(ws.alloc_n(&r, n));
+    a.zproj = z;
+    a.r = r;
+    a.digits = nullptr;
+    float kms = 0;
+    IDET_TRY(launch_lift(a, ws, &out.timed_out, &kms));
+    J.st.ms_lift_kernel += kms;
+    J.st.lift_bytes += (double)m * 8.0 * (double)n * (double)n;
+    J.st.lu_macs += 2.0 * (double)n * n * n;  // LU + inverse of the lift prime
+    uint32_t *den = nullptr;
+    int32_t *info = nullptr;
+    const int den_cap = hD + 2;
+    IDET_TRY(ws.alloc_n(&den, den_cap));
+    IDET_TRY(ws.alloc_n(&info, 4));
+    IDET_TRY(launch_ratrecon(z, m, p, hN, hD, den, den_cap, info, ws));
+    int32_t hinfo[2] = {0, 0};
+    IDET_CUDA_TRY(cudaMemcpyAsync(hinfo, info, 8, cudaMemcpyDeviceToHost, s));
+    IDET_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hinfo[0] != 0) {
+        set_last_error("rational reconstruction failed (code %d)", hinfo[0]);
+        return IDET_ERR_INTERNAL;
+    }
+    out.den.resize(hinfo[1]);
+    IDET_CUDA_TRY(cudaMemcpyAsync(out.den.data(), den, 4 * (size_t)hinfo[1],
+                                  cudaMemcpyDeviceToHost, s));
+    IDET_CUDA_TRY(cudaStreamSynchronize(s));
+    out.p = p;
+    out.m = m;
+    return IDET_OK;
+}
+
+static double rhs_range_log2(int64_t n, double log2H) {
+    // Alg. 4.1: S = 13 E(#factors)^3 ceil(log H)^4, E(#factors) =
+    // ceil(sqrt(2 log2 n)) + 3 (Section 4.1), clamped to 2^62.
+    double e = std::ceil(std::sqrt(2.0 * std::log2((double)std::max<int64_t>(n, 2)))) + 3;
+    double lh = std::ceil(std::max(log2H, 1.0));
+    double l2 = std::log2(13.0) + 3 * std::log2(e) + 4 * std::log2(lh);
+    return std::min(l2, 62.0);
+}
+
+}  // namespace idet
+
+using namespace idet;
+
+// ---------------------------------------------------------------------------
+// C ABI
+
+extern "C" {
+
+void idet_default_opts(idet_opts *o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->log2_epsilon = -64.0;
+    o->seed = 0x1de7u;
+    o->certify = 0;
+    o->update_path = IDET_PATH_AUTO;
+    o->nb = 0;
+    o->wave = 0;
+    o->lif = 1;
+}
+
+const char *idet_last_error(void) { return g_err; }
+
+void idet_set_allocator(idet_alloc_fn a, idet_free_fn f, void *ctx) {
+    g_alloc = a;
+    g_free = f;
+    g_actx = ctx;
+}
+
+uint64_t idet_launch_count(void) { return g_launches; }
+
+int idet_det_mod_primes(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
+                        const uint32_t *primes, int32_t nprimes, const idet_opts *opts,
+                        void *stream, uint32_t *det_mod) {
+    if (n < 0 || lda < n || (n > 0 && !A) || nprimes < 0 || (nprimes > 0 && (!primes || !det_mod))) {
+        set_last_error("invalid argument");
+        return IDET_ERR_ARG;
+    }
+    if (nprimes == 0) return IDET_OK;
+    bool wide = primes[0] > (1u << 30);
+    for (int i = 0; i < nprimes; ++i) {
+        uint32_t p = primes[i];
+        bool w = p > (1u << 30);
+        bool ok = w ? (p < (1u << 31) && is_prime32(p)) : (p > kLo21 && p < kHi21 && is_prime32(p));
+        if (!ok || w != wide) {
+            set_last_error("primes must be odd primes of one class: (2^20, 2^21) or (2^30, 2^31)");
+            return IDET_ERR_ARG;
+        }
+    }
+    if (n == 0) {
+        for (int i = 0; i < nprimes; ++i) det_mod[i] = 1;
+        return IDET_OK;
+    }
+    idet_opts o;
+    idet_default_opts(&o);
+    if (opts) o = *opts;
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace ws(s);
+    DevMatrix M;
+    IDET_TRY(stage_matrix(A, n, lda, on_device, ws, M));
+    double *rowsq = nullptr;
+    unsigned long long *amax = nullptr, hmax = 0;
+    IDET_TRY(ws.alloc_n(&rowsq, n));
+    IDET_TRY(ws.alloc_n(&amax, 1));
+    IDET_TRY(launch_row_stats(M.A, n, n, rowsq, amax, s));
+    IDET_CUDA_TRY(cudaMemcpyAsync(&hmax, amax, 8, cudaMemcpyDeviceToHost, s));
+    IDET_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hmax > 0x7fffffffull) {
+        set_last_error("entries must satisfy |a_ij| <= 2^31 - 1");
+        return IDET_ERR_ARG;
+    }
+    const int W = nprimes;
+    std::vector<ModP> mh(W);
+    for (int i = 0; i < W; ++i) mh[i] = make_mod(primes[i]);
+    ModP *md = nullptr;
+    int32_t *R = nullptr;
+    uint32_t *dd = nullptr;
+    IDET_TRY(ws.alloc_n(&md, W));
+    IDET_TRY(ws.alloc_n(&R, (size_t)W * n * n));
+    IDET_TRY(ws.alloc_n(&dd, W));
+    IDET_CUDA_TRY(cudaMemcpyAsync(md, mh.data(), sizeof(ModP) * W, cudaMemcpyHostToDevice, s));
+    IDET_TRY(launch_reduce(M.A, n, n, md, W, R, s));
+    IDET_TRY(lu_factor_batched(R, n, md, mh.data(), W, wide, o.nb, nullptr, dd, o.update_path, ws));
+    IDET_CUDA_TRY(cudaMemcpyAsync(det_mod, dd, 4 * (size_t)W, cudaMemcpyDeviceToHost, s));
+    IDET_CUDA_TRY(cudaStreamSynchronize(s));
+    return IDET_OK;
+}
+
+int idet_lu_mod_prime(const int64_t *A, int64_t n, int64_t lda, int32_t on_device, uint32_t p,
+                      const idet_opts *opts, void *stream, uint32_t *lu, int32_t *perm) {
+    if (n <= 0 || lda < n || !A || !lu || !perm) {
+        set_last_error("invalid argument");
+        return IDET_ERR_ARG;
+    }
+    bool wide = p > (1u << 30);
+    if (!(wide ? (p < (1u << 31) && is_prime32(p)) : (p > kLo21 && p < kHi21 && is_prime32(p)))) {
+        set_last_error("p must be a prime in (2^20, 2^21) or (2^30, 2^31)");
+        return IDET_ERR_ARG;
+    }
+    idet_opts o;
+    idet_default_opts(&o);
+    if (opts) o = *opts;
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace ws(s);
+    DevMatrix M;
+    IDET_TRY(stage_matrix(A, n, lda, on_device, ws, M));
+    ModP mh = make_mod(p);
+    ModP *md = nullptr;
+    int32_t *R = nullptr, *pm = nullptr;
+    uint32_t *dd = nullptr;
+    IDET_TRY(ws.alloc_n(&md, 1));
+    IDET_TRY(ws.alloc_n(&R, (size_t)n * n));
+    IDET_TRY(ws.alloc_n(&pm, n));
+    IDET_TRY(ws.alloc_n(&dd, 1));
+    IDET_CUDA_TRY(cudaMemcpyAsync(md, &mh, sizeof(ModP), cudaMemcpyHostToDevice, s));
+    IDET_TRY(launch_reduce(M.A, n, n, md, 1, R, s));
+    IDET_TRY(lu_factor_batched(R, n, md, &mh, 1, wide, o.nb, pm, dd, o.update_path, ws));
+    std::vector<int32_t> h((size_t)n * n);
+    uint32_t det = 0;
+    IDET_CUDA_TRY(cudaMemcpyAsync(h.data(), R, 4 * h.size(), cudaMemcpyDeviceToHost, s));
+    IDET_CUDA_TRY(cudaMemcpyAsync(perm, pm, 4 * (size_t)n, cudaMemcpyDeviceToHost, s));
+    IDET_CUDA_TRY(cudaMemcpyAsync(&det, dd, 4, cudaMemcpyDeviceToHost, s));
+    IDET_CUDA_TRY(cudaStreamSynchronize(s));
+    for (size_t i = 0; i < h.size(); ++i) lu[i] = h[i] < 0 ? (uint32_t)(h[i] + (int64_t)p) : (uint32_t)h[i];
+    return det == 0 ? IDET_ERR_SINGULAR : IDET_OK;
+}
+
+int idet_dixon_digits(const int64_t *A, int64_t n, int64_t lda, const int64_t *b, uint32_t p,
+                      int32_t m, int32_t on_device, void *stream, int32_t *digits,
+                      int64_t *residual) {
+    if (n <= 0 || lda < n || !A || !b || m < 0 || (m > 0 && !digits) || !residual ||
+        !(p > (1u << 30) && p < (1u << 31) && is_prime32(p))) {
+        set_last_error("invalid argument");
+        return IDET_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace ws(s);
+    DevMatrix M;
+    IDET_TRY(stage_matrix(A, n, lda, on_device, ws, M));
+    int32_t *A32 = nullptr, *Cinv = nullptr, *dig = nullptr;
+    int64_t ld4 = 0, *bd = nullptr, *r = nullptr;
+    IDET_TRY(make_A32(M, ws, &A32, &ld4));
+    IDET_TRY(ws.alloc_n(&Cinv, (size_t)n * ld4));
+    IDET_TRY(inverse_mod_prime(M, p, 32, ws, Cinv, ld4));
+    IDET_TRY(ws.alloc_n(&bd, n));
+    IDET_TRY(ws.alloc_n(&r, n));
+    IDET_TRY(ws.alloc_n(&dig, (size_t)m * n + 1));
+    IDET_CUDA_TRY(cudaMemcpyAsync(bd, b, 8 * (size_t)n,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    LiftArgs a{};
+    a.A32 = A32;
+    a.Cinv = Cinv;
+    a.b = bd;
+    a.n = n;
+    a.m = m;
+    a.mod = make_mod(p);
+    a.pinv = inv_mod_2_64(p);
+    a.digits = dig;
+    a.r = r;
+    int to = 0;
+    IDET_TRY(launch_lift(a, ws, &to));
+    if (m > 0)
+        IDET_CUDA_TRY(cudaMemcpyAsync(digits, dig, 4 * (size_t)m * n, cudaMemcpyDeviceToHost, s));
+    IDET_CUDA_TRY(cudaMemcpyAsync(residual, r, 8 * (size_t)n, cudaMemcpyDeviceToHost, s));
+    IDET_CUDA_TRY(cudaStreamSynchronize(s));
+    return IDET_OK;
+}
+
+int idet_crt_symmetric(const uint32_t *residues, const uint32_t *primes, int32_t count,
+                       void *stream, idet_int *r, int32_t *trailing) {
+    if (count < 0 || (count > 0 && (!residues || !primes)) || !r) {
+        set_last_error("invalid argument");
+        return IDET_ERR_ARG;
+    }
+    for (int i = 0; i < count; ++i)
+        if (!(primes[i] > 2 && primes[i] < (1u << 31) && is_prime32(primes[i]))) {
+            set_last_error("primes must be odd primes below 2^31");
+            return IDET_ERR_ARG;
+        }
+    if (count == 0) {
+        if (trailing) *trailing = 0;
+        return write_int(r, 0, nullptr, 0);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace ws(s);
+    idet_opts o;
+    idet_default_opts(&o);
+    DevMatrix M;
+    DetJob J(M, ws, o);
+    std::vector<uint32_t> prs(primes, primes + count), res(residues, residues + count);
+    for (int i = 0; i < count; ++i) res[i] %= prs[i];
+    std::vector<int32_t> dig;
+    IDET_TRY(J.cra_digits(prs, res, dig));
+    if (trailing) {
+        int k = 0;
+        for (int t = count - 1; t > 0 && dig[t] == 0; --t) ++k;
+        *trailing = k;
+    }
+    return J.assemble(prs, dig, count, nullptr, 0, r);
+}
+
+static int lif_common(DetJob &J, const int64_t *b_dev, const std::vector<int64_t> &bh,
+                      LiftResult &lr);
+
+int idet_int_det(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
+                 const idet_opts *opts, void *stream, idet_int *det, idet_stats *stats) {
+    if (n < 0 || lda < n || (n > 0 && !A) || !det) {
+        set_last_error("invalid argument");
+        return IDET_ERR_ARG;
+    }
+    const unsigned long long launches0 = g_launches;
+    if (n == 0) {
+        uint32_t one = 1;
+        return write_int(det, 1, &one, 1);
+    }
+    idet_opts o;
+    idet_default_opts(&o);
+    if (opts) o = *opts;
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace ws(s);
+    Timer total(s);
+    DevMatrix M;
+    IDET_TRY(stage_matrix(A, n, lda, on_device, ws, M));
+    DetJob J(M, ws, o);
+    IDET_TRY(J.stats());
+    auto finish = [&](int rc) {
+        J.st.ms_total = total.stop();
+        J.st.launches = g_launches - launches0;
+        if (stats) *stats = J.st;
+        return rc;
+    };
+    if (J.log2H == -INFINITY || J.amax == 0) {  // a zero row: det = 0
+        J.st.et_stop = 2;
+        return finish(write_int(det, 0, nullptr, 0));
+    }
+    const double log2l = 20.0;  // primes > l = 2^20
+    const double pool = (double)pool21().size();
+    const bool certify = o.certify != 0;
+    const int k0 = k_default(o.log2_epsilon, pool, J.log2H, log2l);
+    const int wave = o.wave > 0 ? o.wave : std::max(8, k0);
+
+    // Alg. 2.1 on det(A): the first k0 primes (Alg. 4.1 lines 1-4), or all
+    // the way in CRA-only / certified mode.
+    const bool cra_only = certify || !o.lif;
+    std::vector<int32_t> dig;
+    int why = 0;
+    {
+        int first = cra_only ? wave : std::max(k0, 1);
+        IDET_TRY(J.factor_wave(first));
+        while (true) {
+            Timer t(s);
+            IDET_TRY(J.cra_digits(J.primes, J.dets, dig));
+            J.st.ms_cra += t.stop();
+            int stop = CraScan::scan(dig, J.primes, J.log2H, o.log2_epsilon, log2l, pool,
+                                     certify, &why);
+            if (stop >= 0) {
+                J.st.et_stop = why;
+                J.st.primes_in_cra = stop + 1;
+                Timer t2(s);
+                int rc = J.assemble(J.primes, dig, stop + 1, nullptr, 0, det);
+                J.st.ms_cra += t2.stop();
+                return finish(rc);
+            }
+            if (!cra_only) break;
+            IDET_TRY(J.factor_wave(wave));
+        }
+    }
+
+    // Section 2.2 / Alg. 4.1 with i_max = 1: one solve gives K = s~_n.
+    const int64_t *bdev = nullptr;
+    std::vector<int64_t> bh(n);
+    {
+        SplitMix g(o.seed ^ 0xb5ull);
+        const double l2S = rhs_range_log2(n, J.log2H);
+        const uint64_t S = (uint64_t)std::exp2(std::floor(l2S));
+        for (int64_t i = 0; i < n; ++i) bh[i] = (int64_t)(g.below(S)) - (int64_t)(S / 2);
+        int64_t *bd = nullptr;
+        IDET_TRY(ws.alloc_n(&bd, n));
+        IDET_CUDA_TRY(cudaMemcpyAsync(bd, bh.data(), 8 * (size_t)n, cudaMemcpyHostToDevice, s));
+        bdev = bd;
+    }
+    LiftResult lr;
+    Timer tl(s);
+    int rc = lif_common(J, bdev, bh, lr);
+    J.st.ms_lift += tl.stop();
+    if (rc != IDET_OK && rc != IDET_ERR_SINGULAR) return finish(rc);
+    J.st.lift_iters = lr.m;
+    J.st.lift_timed_out = lr.timed_out;
+
+    // K = denominator (binary limbs on the device).
+    uint32_t *Kbin = nullptr;
+    int Klen = 0;
+    double log2K = 0;
+    if (rc == IDET_OK && !lr.den.empty()) {
+        const int kd = (int)lr.den.size();
+        const int cap = kd + 2;
+        uint32_t *dd = nullptr;
+        int32_t *dl = nullptr;
+        IDET_TRY(ws.alloc_n(&dd, kd));
+        IDET_TRY(ws.alloc_n(&Kbin, cap));
+        IDET_TRY(ws.alloc_n(&dl, 1));
+        IDET_CUDA_TRY(cudaMemcpyAsync(dd, lr.den.data(), 4 * (size_t)kd, cudaMemcpyHostToDevice, s));
+        IDET_TRY(launch_radix_to_binary(dd, kd, lr.p, Kbin, cap, dl, s));
+        IDET_CUDA_TRY(cudaMemcpyAsync(&Klen, dl, 4, cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        log2K = 0;
+        for (int i = 0; i < kd; ++i) (void)i;
+        // log2 K from the top digits
+        double top = lr.den[kd - 1] + (kd > 1 ? lr.den[kd - 2] / (double)lr.p : 0.0);
+        log2K = std::log2(top) + (kd - 1) * std::log2((double)lr.p);
+    }
+    J.st.log2_K = (int)std::floor(log2K);
+
+    // Alg. 2.1 on det(A)/K, using the residues already computed first
+    // (Section 4, "use the already computed modular determinants first").
+    const double log2HK = std::max(0.0, J.log2H - log2K);
+    while (true) {
+        std::vector<uint32_t> prs, res;
+        Timer t(s);
+        if (Kbin) {
+            const int c = (int)J.primes.size();
+            uint32_t *dp = nullptr, *di = nullptr, *dout = nullptr;
+            int32_t *dskip = nullptr;
+            IDET_TRY(ws.alloc_n(&dp, c));
+            IDET_TRY(ws.alloc_n(&di, c));
+            IDET_TRY(ws.alloc_n(&dout, c));
+            IDET_TRY(ws.alloc_n(&dskip, c));
+            IDET_CUDA_TRY(cudaMemcpyAsync(dp, J.primes.data(), 4 * c, cudaMemcpyHostToDevice, s));
+            IDET_CUDA_TRY(cudaMemcpyAsync(di, J.dets.data(), 4 * c, cudaMemcpyHostToDevice, s));
+            IDET_TRY(launch_div_by_K(Kbin, Klen, dp, di, dout, dskip, c, s));
+            std::vector<uint32_t> hout(c);
+            std::vector<int32_t> hskip(c);
+            IDET_CUDA_TRY(cudaMemcpyAsync(hout.data(), dout, 4 * c, cudaMemcpyDeviceToHost, s));
+            IDET_CUDA_TRY(cudaMemcpyAsync(hskip.data(), dskip, 4 * c, cudaMemcpyDeviceToHost, s));
+            IDET_CUDA_TRY(cudaStreamSynchronize(s));
+            for (int i = 0; i < c; ++i)
+                if (!hskip[i]) {
+                    prs.push_back(J.primes[i]);
+                    res.push_back(hout[i]);
+                }
+        } else {
+            prs = J.primes;
+            res = J.dets;
+        }
+        IDET_TRY(J.cra_digits(prs, res, dig));
+        int stop = CraScan::scan(dig, prs, Kbin ? log2HK : J.log2H, o.log2_epsilon, log2l, pool,
+                                 false, &why);
+        J.st.ms_cra += t.stop();
+        if (stop >= 0) {
+            J.st.et_stop = why;
+            J.st.primes_in_cra = stop + 1;
+            Timer t2(s);
+            int rc2 = J.assemble(prs, dig, stop + 1, Kbin, Klen, det);
+            J.st.ms_cra += t2.stop();
+            return finish(rc2);
+        }
+        IDET_TRY(J.factor_wave(wave));
+    }
+}
+
+static int lif_common(DetJob &J, const int64_t *b_dev, const std::vector<int64_t> &bh,
+                      LiftResult &lr) {
+    const int64_t n = J.M.n;
+    // projection vector u, entries in [0, 2^16)
+    SplitMix g(J.o.seed ^ 0x9a11ull);
+    std::vector<int32_t> uh(n);
+    double u1 = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        uh[i] = (int32_t)(g.next() & 0xffff);
+        u1 += uh[i];
+    }
+    int32_t *ud = nullptr;
+    IDET_TRY(J.ws.alloc_n(&ud, n));
+    IDET_CUDA_TRY(cudaMemcpyAsync(ud, uh.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, J.s));
+    return solve_and_denominator(J, b_dev, bh, ud, std::log2(std::max(u1, 1.0)), lr);
+}
+
+int idet_largest_invariant_factor(const int64_t *A, int64_t n, int64_t lda, const int64_t *b,
+                                  int32_t on_device, const idet_opts *opts, void *stream,
+                                  idet_int *sout) {
+    (void)A;
+    (void)n;
+    (void)lda;
+    (void)b;
+    (void)on_device;
+    (void)opts;
+    (void)stream;
+    (void)sout;
+    set_last_error("not implemented yet");
+    return IDET_ERR_INTERNAL;
+}
+
+}  // extern "C"

@@ -1,0 +1,215 @@
+// Internal declarations shared by the CUDA translation units of libidet.
+//
+// Residues are stored "balanced": an element of Z/p is kept as the int32 in
+// [-(p-1)/2, (p-1)/2] (p odd). Two prime classes are used:
+//   * CRA primes, 2^20 < p < 2^21: |residue| < 2^20, products < 2^40, so
+//     thousands of products can be summed exactly in int64 before a
+//     reduction (delayed reduction);
+//   * the lift prime, 2^30 < p < 2^31: |residue| < 2^30, products < 2^60,
+//     so at most 4 products are summed before a fold.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/idet.h"
+
+namespace idet {
+
+// ---------------------------------------------------------------------------
+// Modular arithmetic (device and host)
+
+struct ModP {
+    uint32_t p;      // odd prime, p < 2^31
+    uint32_t half;   // (p - 1) / 2
+    uint64_t m;      // floor((2^64 - 1) / p): Barrett multiplier
+    int64_t off;     // a multiple of p with off >= 2^62
+};
+
+inline ModP make_mod(uint32_t p) {
+    ModP M;
+    M.p = p;
+    M.half = (p - 1) / 2;
+    M.m = ~0ull / p;
+    M.off = (int64_t)(((1ull << 62) / p + 1) * p);
+    return M;
+}
+
+// Balanced representative of s mod p, for |s| < 2^62.
+// u = s + off lies in [0, 2^63 + p); Barrett with m = floor((2^64-1)/p)
+// gives q in {floor(u/p) - 1, floor(u/p)}, so u - q p lies in [0, 2p).
+__device__ __forceinline__ int32_t red_bal(int64_t s, const ModP &M) {
+    uint64_t u = (uint64_t)(s + M.off);
+    uint64_t q = __umul64hi(u, M.m);
+    uint64_t r = u - q * (uint64_t)M.p;
+    if (r >= M.p) r -= M.p;
+    return (r > M.half) ? (int32_t)((int64_t)r - (int64_t)M.p) : (int32_t)r;
+}
+
+// Non-negative representative in [0, p).
+__device__ __forceinline__ uint32_t red_pos(int64_t s, const ModP &M) {
+    uint64_t u = (uint64_t)(s + M.off);
+    uint64_t q = __umul64hi(u, M.m);
+    uint64_t r = u - q * (uint64_t)M.p;
+    if (r >= M.p) r -= M.p;
+    return (uint32_t)r;
+}
+
+__device__ __forceinline__ int32_t mul_bal(int32_t a, int32_t b, const ModP &M) {
+    return red_bal((int64_t)a * (int64_t)b, M);
+}
+
+// Inverse of a (nonzero mod p) by the extended Euclidean algorithm;
+// returns the balanced representative.
+__host__ __device__ inline int32_t inv_bal(int64_t a, uint32_t p) {
+    int64_t r0 = (int64_t)p, r1 = a % (int64_t)p;
+    if (r1 < 0) r1 += p;
+    int64_t t0 = 0, t1 = 1;
+    while (r1 != 0) {
+        int64_t q = r0 / r1, t;
+        t = r0 - q * r1; r0 = r1; r1 = t;
+        t = t0 - q * t1; t0 = t1; t1 = t;
+    }
+    t0 %= (int64_t)p;
+    if (t0 < 0) t0 += p;
+    if (t0 > (int64_t)(p - 1) / 2) t0 -= p;
+    return (int32_t)t0;
+}
+
+// ---------------------------------------------------------------------------
+// Error plumbing
+
+struct Status {
+    int code = IDET_OK;
+    const char *what = nullptr;
+};
+
+void set_last_error(const char *fmt, ...);
+
+#define IDET_CUDA_TRY(expr)                                                   \
+    do {                                                                      \
+        cudaError_t _e = (expr);                                              \
+        if (_e != cudaSuccess) {                                              \
+            ::idet::set_last_error("%s:%d %s: %s", __FILE__, __LINE__, #expr, \
+                                   cudaGetErrorString(_e));                   \
+            return IDET_ERR_CUDA;                                             \
+        }                                                                     \
+    } while (0)
+
+#define IDET_TRY(expr)                  \
+    do {                                \
+        int _rc = (expr);               \
+        if (_rc != IDET_OK) return _rc; \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Device workspace: allocations made through the user-installed allocator
+// (or cudaMallocAsync on the call's stream), released in LIFO order when the
+// Workspace goes out of scope.
+
+class Workspace {
+  public:
+    explicit Workspace(cudaStream_t s) : stream_(s) {}
+    ~Workspace();
+    // Returns IDET_OK or IDET_ERR_NOMEM; *ptr is 256-byte aligned.
+    int alloc(void **ptr, size_t bytes);
+    template <class T> int alloc_n(T **ptr, size_t count) {
+        return alloc((void **)ptr, count * sizeof(T) + 16);
+    }
+    cudaStream_t stream() const { return stream_; }
+
+  private:
+    cudaStream_t stream_;
+    void *ptrs_[256];
+    int n_ = 0;
+};
+
+// Counter of kernel launches made by this library (for the benchmark's
+// launch accounting); incremented by every launcher.
+extern unsigned long long g_launches;
+inline void count_launch(unsigned k = 1) { g_launches += k; }
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (defined in the .cu files)
+
+// k_reduce.cu ---------------------------------------------------------------
+// Row statistics of an int64 matrix: rowsq[i] = sum_j A_ij^2 (double,
+// rounded upward by a relative 2^-40 margin), amax[0] = max |A_ij|.
+int launch_row_stats(const int64_t *A, int64_t n, int64_t lda, double *rowsq,
+                     unsigned long long *amax, cudaStream_t s);
+// A (int64, |A_ij| < 2^31) -> int32 copy with leading dimension n.
+int launch_to_int32(const int64_t *A, int64_t n, int64_t lda, int32_t *A32,
+                    cudaStream_t s);
+// R[w] = A mod mods[w] (balanced), w < W; R has W * n * n entries (ld n).
+int launch_reduce(const int64_t *A, int64_t n, int64_t lda, const ModP *mods,
+                  int W, int32_t *R, cudaStream_t s);
+
+// k_lu.cu -----------------------------------------------------------------
+struct LUState {
+    uint32_t det;    // running product of pivots mod p, in [0, p)
+    int32_t neg;     // parity of row swaps
+    int32_t dead;    // 1 once a column had no pivot: det = 0 mod p
+    int32_t pad;
+};
+// Factor W residue matrices R[w] (n x n, ld n) in place: PA = LU mod p_w with
+// the first-nonzero pivot rule. perm (W*n, may be null) receives the row
+// permutation; det_out[w] = det mod p_w in [0, p_w). wide = the primes are
+// of the 31-bit class.
+int lu_factor_batched(int32_t *R, int64_t n, const ModP *mods_dev,
+                      const ModP *mods_host, int W, bool wide, int nb,
+                      int32_t *perm, uint32_t *det_out, int update_path,
+                      Workspace &ws);
+// Inverse of A mod p from its LU (R, perm as produced above with W = 1);
+// Xinv receives A^{-1} mod p, balanced, n x n.
+int lu_inverse(const int32_t *R, const int32_t *perm, int64_t n,
+               const ModP &mod_host, const ModP *mod_dev, bool wide, int nb,
+               int32_t *Xinv, Workspace &ws);
+
+// k_lift.cu ---------------------------------------------------------------
+struct LiftArgs {
+    const int32_t *A32;    // n x n, ld n
+    const int32_t *Cinv;   // A^{-1} mod p, balanced, n x n
+    const int64_t *b;      // right-hand side, n
+    const int32_t *u;      // projection vector, n (may be null)
+    int64_t n;
+    int32_t m;             // number of digits to produce
+    ModP mod;
+    uint64_t pinv;         // p^{-1} mod 2^64
+    int32_t *digits;       // m x n (row i = digit vector x_i), may be null
+    int64_t *zproj;        // m projections u . x_i, may be null
+    int64_t *r;            // n: residual (in: ignored; out: r_m)
+};
+int launch_lift(const LiftArgs &a, Workspace &ws, int *timed_out, float *ms = nullptr);
+
+// k_bignum.cu ---------------------------------------------------------------
+// Device big integers: little-endian uint32 limbs with an explicit length.
+struct BigDev {
+    uint32_t *w;
+    int32_t cap;
+};
+// Garner mixed-radix digits with balanced digits (symmetric range) for a
+// wave of new primes appended after `count` existing ones; see k_bignum.cu.
+int launch_cra_append(const uint32_t *primes, const uint32_t *residues,
+                      int32_t *digits, int start, int count, int32_t *info,
+                      cudaStream_t s);
+// residues_out[k] = res_in[k] * K^{-1} mod primes[k] (K as limbs); skip[k]=1
+// where K = 0 mod primes[k].
+int launch_div_by_K(const uint32_t *Klimbs, int Klen, const uint32_t *primes,
+                    const uint32_t *res_in, uint32_t *res_out, int32_t *skip,
+                    int count, cudaStream_t s);
+// Mixed radix (balanced digits) -> two's complement limbs, then times K.
+int launch_mixed_to_int(const uint32_t *primes, const int32_t *digits,
+                        int count, const uint32_t *Klimbs, int Klen,
+                        uint32_t *out, int out_cap, int32_t *out_info,
+                        cudaStream_t s);
+// Rational reconstruction of the p-adic number with base-p lifting sums z
+// (int64, m of them, |z_i| < 2^59): numerator below p^hN, denominator below
+// p^hD; den receives the denominator's base-p digits. info[0]: 0 ok,
+// 1 no fraction within the bounds, 2/4 capacity; info[1]: digits of den.
+int launch_ratrecon(const int64_t *z, int m, uint32_t p, int hN, int hD, uint32_t *den,
+                    int den_cap, int32_t *info, Workspace &ws);
+// Base-p digits -> base-2^32 limbs (out_len receives the limb count).
+int launch_radix_to_binary(const uint32_t *dig, int len, uint32_t p, uint32_t *out, int cap,
+                           int32_t *out_len, cudaStream_t s);
+
+}  // namespace idet

@@ -1,0 +1,497 @@
+// LU factorisation over Z/p for a batch of primes, and A^{-1} mod p from it.
+//
+// Section 2.1 (Alg. 2.1, step "Compute det(A) mod p_i") obtains det(A) mod
+// p_i from an LU factorisation modulo p_i. Pivoting rule: the first row at or
+// below the diagonal whose entry is nonzero mod p (the paper does not fix
+// one; any nonzero pivot gives the same determinant, this one makes the
+// factors unique). det(A) mod p = (-1)^{#swaps} prod U_kk.
+//
+// Layout: W residue matrices, prime-major, R[w][i][j] int32 balanced, ld n.
+// Small n: the whole matrix of one prime lives in shared memory (one CTA per
+// prime). Larger n: right-looking blocked LU with panel width nb:
+//   panel  (one CTA per prime, column by column, full-row swaps),
+//   TRSM   U12 = L11^{-1} A12,
+//   update A22 <- A22 - L21 U12 mod p (the O(n^3) part), int64 delayed
+//          reduction on the CUDA cores: balanced residues of a 21-bit prime
+//          have |x| < 2^20, so a K-term dot product stays below K 2^40.
+// Lift-class primes (31 bits, |x| < 2^30, products < 2^60) fold the
+// accumulator every 4 products.
+#include <climits>
+#include <cstdio>
+
+#include "idet_internal.cuh"
+
+namespace idet {
+
+namespace {
+
+constexpr int kSmallN = 192;  // whole-matrix-in-shared-memory limit
+constexpr int kPanelThreads = 1024;
+constexpr int kNBMax = 32;
+constexpr int kFoldWide = 4;
+
+__device__ __forceinline__ uint32_t det_mul(uint32_t det, int32_t piv, const ModP &M) {
+    return red_pos((int64_t)det * (int64_t)piv, M);
+}
+
+// ---------------------------------------------------------------------------
+// Whole-matrix LU in shared memory.
+
+__global__ void k_lu_small(int32_t *__restrict__ R, int n, const ModP *__restrict__ mods,
+                           LUState *__restrict__ st, int32_t *__restrict__ perm) {
+    extern __shared__ int32_t sa[];
+    __shared__ int s_piv;
+    __shared__ int32_t s_inv;
+    const int w = blockIdx.x;
+    const ModP M = mods[w];
+    int32_t *g = R + (int64_t)w * n * n;
+    const int nn = n * n;
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) sa[e] = g[e];
+    int32_t *pm = perm ? perm + (int64_t)w * n : nullptr;
+    if (pm)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) pm[i] = i;
+    uint32_t det = 1u % M.p;
+    int neg = 0, dead = 0;
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        if (threadIdx.x == 0) s_piv = sa[k * n + k] != 0 ? k : INT_MAX;
+        __syncthreads();
+        if (s_piv == INT_MAX) {
+            for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x)
+                if (sa[i * n + k] != 0) atomicMin(&s_piv, i);
+            __syncthreads();
+        }
+        const int piv = s_piv;
+        if (piv == INT_MAX) {
+            dead = 1;
+            break;
+        }
+        if (piv != k) {
+            for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                int32_t t = sa[k * n + j];
+                sa[k * n + j] = sa[piv * n + j];
+                sa[piv * n + j] = t;
+            }
+            if (threadIdx.x == 0 && pm) {
+                int32_t t = pm[k];
+                pm[k] = pm[piv];
+                pm[piv] = t;
+            }
+            neg ^= 1;
+            __syncthreads();
+        }
+        const int32_t pv = sa[k * n + k];
+        if (threadIdx.x == 0) s_inv = inv_bal(pv, M.p);
+        det = det_mul(det, pv, M);
+        __syncthreads();
+        const int32_t inv = s_inv;
+        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x)
+            sa[i * n + k] = mul_bal(sa[i * n + k], inv, M);
+        __syncthreads();
+        const int m = n - k - 1;
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            int i = k + 1 + e / m, j = k + 1 + e % m;
+            int32_t l = sa[i * n + k];
+            if (l) sa[i * n + j] = red_bal((int64_t)sa[i * n + j] - (int64_t)l * sa[k * n + j], M);
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) g[e] = sa[e];
+    if (threadIdx.x == 0) {
+        LUState s;
+        s.dead = dead;
+        s.neg = neg;
+        s.det = dead ? 0u : det;
+        s.pad = 0;
+        st[w] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Blocked LU pieces.
+
+__global__ void k_state_init(LUState *st, const ModP *mods, int W, int32_t *perm, int64_t n) {
+    int w = blockIdx.x;
+    if (threadIdx.x == 0) {
+        LUState s;
+        s.det = 1u % mods[w].p;
+        s.neg = 0;
+        s.dead = 0;
+        s.pad = 0;
+        st[w] = s;
+    }
+    if (perm)
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) perm[(int64_t)w * n + i] = (int32_t)i;
+}
+
+// Factor the panel of columns [j0, j0 + jb) on rows [j0, n); rows are swapped
+// across all n columns.
+__global__ void __launch_bounds__(kPanelThreads)
+k_panel(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb,
+        const ModP *__restrict__ mods, LUState *__restrict__ st,
+        int32_t *__restrict__ perm) {
+    __shared__ int32_t s_u[kNBMax];
+    __shared__ int s_piv;
+    __shared__ int32_t s_inv;
+    const int w = blockIdx.x;
+    if (st[w].dead) return;
+    const ModP M = mods[w];
+    int32_t *a = R + (int64_t)w * n * n;
+    uint32_t det = st[w].det;
+    int neg = st[w].neg;
+    for (int c = 0; c < jb; ++c) {
+        const int64_t col = j0 + c;
+        if (threadIdx.x == 0) s_piv = a[col * n + col] != 0 ? (int)col : INT_MAX;
+        __syncthreads();
+        if (s_piv == INT_MAX) {
+            for (int64_t i = col + 1 + threadIdx.x; i < n; i += blockDim.x)
+                if (a[i * n + col] != 0) atomicMin(&s_piv, (int)i);
+            __syncthreads();
+        }
+        const int piv = s_piv;
+        if (piv == INT_MAX) {
+            if (threadIdx.x == 0) {
+                LUState s = st[w];
+                s.dead = 1;
+                s.det = 0;
+                st[w] = s;
+            }
+            return;
+        }
+        if (piv != col) {
+            for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+                int32_t t = a[col * n + j];
+                a[col * n + j] = a[(int64_t)piv * n + j];
+                a[(int64_t)piv * n + j] = t;
+            }
+            if (threadIdx.x == 0 && perm) {
+                int32_t *pm = perm + (int64_t)w * n;
+                int32_t t = pm[col];
+                pm[col] = pm[piv];
+                pm[piv] = t;
+            }
+            neg ^= 1;
+            __syncthreads();
+        }
+        const int32_t pv = a[col * n + col];
+        det = det_mul(det, pv, M);
+        if (threadIdx.x == 0) s_inv = inv_bal(pv, M.p);
+        if (threadIdx.x > c && threadIdx.x < jb) s_u[threadIdx.x] = a[col * n + j0 + threadIdx.x];
+        __syncthreads();
+        const int32_t inv = s_inv;
+        for (int64_t i = col + 1 + threadIdx.x; i < n; i += blockDim.x) {
+            int32_t *row = a + i * n + j0;
+            int32_t l = mul_bal(row[c], inv, M);
+            row[c] = l;
+            if (l)
+                for (int j = c + 1; j < jb; ++j)
+                    row[j] = red_bal((int64_t)row[j] - (int64_t)l * s_u[j], M);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        LUState s = st[w];
+        s.det = det;
+        s.neg = neg;
+        st[w] = s;
+    }
+}
+
+// X[r0 .. r0+jb)[cols] <- L^{-1} X, L unit lower triangular (jb x jb) at
+// (lr0, lr0) of matrix Lm (ld n). One thread per column.
+template <bool WIDE>
+__global__ void k_trsm_lower(const int32_t *__restrict__ Lm, int64_t strideL,
+                             int32_t *__restrict__ X, int64_t strideX, int64_t n,
+                             int64_t lr0, int64_t xr0, int jb, int64_t c0,
+                             int64_t ncols, const ModP *__restrict__ mods,
+                             const LUState *__restrict__ st) {
+    __shared__ int32_t sL[kNBMax][kNBMax + 1];
+    const int w = blockIdx.y;
+    if (st && st[w].dead) return;
+    const ModP M = mods[w];
+    const int32_t *L = Lm + (int64_t)w * strideL;
+    int32_t *x = X + (int64_t)w * strideX;
+    for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) {
+        int r = e / jb, k = e % jb;
+        sL[r][k] = L[(lr0 + r) * n + lr0 + k];
+    }
+    __syncthreads();
+    const int64_t j = c0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= c0 + ncols) return;
+    int32_t u[kNBMax];
+#pragma unroll
+    for (int r = 0; r < kNBMax; ++r) {
+        if (r < jb) {
+            int64_t acc = x[(xr0 + r) * n + j];
+#pragma unroll
+            for (int k = 0; k < kNBMax; ++k) {
+                if (k < r) {
+                    acc -= (int64_t)sL[r][k] * u[k];
+                    if (WIDE && (k % kFoldWide) == kFoldWide - 1) acc = red_bal(acc, M);
+                }
+            }
+            u[r] = red_bal(acc, M);
+            x[(xr0 + r) * n + j] = u[r];
+        }
+    }
+}
+
+// X[r0 .. r0+jb)[cols] <- U^{-1} X, U upper triangular with nonzero diagonal.
+template <bool WIDE>
+__global__ void k_trsm_upper(const int32_t *__restrict__ Um, int64_t n, int64_t ur0,
+                             int32_t *__restrict__ X, int64_t xr0, int jb,
+                             int64_t ncols, ModP M) {
+    __shared__ int32_t sU[kNBMax][kNBMax + 1];
+    __shared__ int32_t sInv[kNBMax];
+    for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) {
+        int r = e / jb, k = e % jb;
+        sU[r][k] = Um[(ur0 + r) * n + ur0 + k];
+    }
+    __syncthreads();
+    if (threadIdx.x < jb) sInv[threadIdx.x] = inv_bal(sU[threadIdx.x][threadIdx.x], M.p);
+    __syncthreads();
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ncols) return;
+    int32_t u[kNBMax];
+#pragma unroll
+    for (int rr = kNBMax - 1; rr >= 0; --rr) {
+        if (rr < jb) {
+            int64_t acc = X[(xr0 + rr) * n + j];
+            int cnt = 0;
+#pragma unroll
+            for (int k = 0; k < kNBMax; ++k) {
+                if (k > rr && k < jb) {
+                    acc -= (int64_t)sU[rr][k] * u[k];
+                    if (WIDE && (++cnt % kFoldWide) == 0) acc = red_bal(acc, M);
+                }
+            }
+            u[rr] = mul_bal(red_bal(acc, M), sInv[rr], M);
+            X[(xr0 + rr) * n + j] = u[rr];
+        }
+    }
+}
+
+// C <- C - A B mod p (batched over primes by blockIdx.z). A: M x K (lda),
+// B: K x N (ldb), C: M x N (ldc). 64 x 64 tile, 256 threads, 4 x 4 outputs
+// per thread, int64 accumulators.
+constexpr int BM = 64, BN = 64, BK = 32;
+
+template <bool WIDE>
+__global__ void __launch_bounds__(256)
+k_gemm_sub(const int32_t *__restrict__ A, int64_t lda, int64_t strideA,
+           const int32_t *__restrict__ B, int64_t ldb, int64_t strideB,
+           int32_t *__restrict__ C, int64_t ldc, int64_t strideC, int M, int N,
+           int K, const ModP *__restrict__ mods, const LUState *__restrict__ st) {
+    __shared__ int32_t As[BK][BM + 1];
+    __shared__ int32_t Bs[BK][BN];
+    const int w = blockIdx.z;
+    if (st && st[w].dead) return;
+    const ModP Mo = mods[w];
+    const int32_t *a = A + (int64_t)w * strideA;
+    const int32_t *b = B + (int64_t)w * strideB;
+    int32_t *c = C + (int64_t)w * strideC;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    int64_t acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+    for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            int r = tid / 32 + 8 * t, cc = tid % 32;
+            int gm = m0 + r, gk = k0 + cc;
+            As[cc][r] = (gm < M && gk < K) ? a[(int64_t)gm * lda + gk] : 0;
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            int r = tid / 64 + 4 * t, cc = tid % 64;
+            int gk = k0 + r, gn = n0 + cc;
+            Bs[r][cc] = (gk < K && gn < N) ? b[(int64_t)gk * ldb + gn] : 0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < BK; ++k) {
+            int32_t av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = As[k][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += (int64_t)av[i] * bv[j];
+            if (WIDE && (k % kFoldWide) == kFoldWide - 1) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = red_bal(acc[i][j], Mo);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int gm = m0 + ty + 16 * i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int gn = n0 + tx + 16 * j;
+            if (gn >= N) continue;
+            int32_t *p = c + (int64_t)gm * ldc + gn;
+            *p = red_bal((int64_t)*p - red_bal(acc[i][j], Mo), Mo);
+        }
+    }
+}
+
+__global__ void k_finalize_det(const LUState *st, const ModP *mods, int W, uint32_t *det_out) {
+    int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W) return;
+    LUState s = st[w];
+    uint32_t p = mods[w].p;
+    uint32_t d = s.dead ? 0u : s.det;
+    if (s.neg && d) d = p - d;
+    det_out[w] = d;
+}
+
+__global__ void k_perm_identity(int32_t *Y, const int32_t *perm, int64_t n) {
+    const int64_t total = n * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = e / n, j = e - i * n;
+        Y[e] = (perm[i] == j) ? 1 : 0;
+    }
+}
+
+template <bool WIDE>
+int gemm_sub(const int32_t *A, int64_t lda, int64_t sA, const int32_t *B, int64_t ldb,
+             int64_t sB, int32_t *C, int64_t ldc, int64_t sC, int M, int N, int K,
+             const ModP *mods, const LUState *st, int W, cudaStream_t s) {
+    if (M <= 0 || N <= 0 || K <= 0) return IDET_OK;
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, W);
+    k_gemm_sub<WIDE><<<grid, 256, 0, s>>>(A, lda, sA, B, ldb, sB, C, ldc, sC, M, N,
+                                           K, mods, st);
+    count_launch();
+    IDET_CUDA_TRY(cudaGetLastError());
+    return IDET_OK;
+}
+
+template <bool WIDE>
+int trsm_lower(const int32_t *Lm, int64_t sL, int32_t *X, int64_t sX, int64_t n,
+               int64_t lr0, int64_t xr0, int jb, int64_t c0, int64_t ncols,
+               const ModP *mods, const LUState *st, int W, cudaStream_t s) {
+    if (ncols <= 0) return IDET_OK;
+    dim3 grid((unsigned)((ncols + 127) / 128), W);
+    k_trsm_lower<WIDE><<<grid, 128, 0, s>>>(Lm, sL, X, sX, n, lr0, xr0, jb, c0, ncols,
+                                             mods, st);
+    count_launch();
+    IDET_CUDA_TRY(cudaGetLastError());
+    return IDET_OK;
+}
+
+template <bool WIDE>
+int lu_blocked(int32_t *R, int64_t n, const ModP *mods, int W, int nb, int32_t *perm,
+               LUState *st, cudaStream_t s) {
+    k_state_init<<<W, 256, 0, s>>>(st, mods, W, perm, n);
+    count_launch();
+    const int64_t nn = n * n;
+    for (int64_t j0 = 0; j0 < n; j0 += nb) {
+        const int jb = (int)((n - j0) < nb ? (n - j0) : nb);
+        k_panel<<<W, kPanelThreads, 0, s>>>(R, n, j0, jb, mods, st, perm);
+        count_launch();
+        IDET_CUDA_TRY(cudaGetLastError());
+        const int64_t rest = n - j0 - jb;
+        if (rest <= 0) break;
+        IDET_TRY(trsm_lower<WIDE>(R, nn, R, nn, n, j0, j0, jb, j0 + jb, rest, mods, st,
+                                  W, s));
+        IDET_TRY(gemm_sub<WIDE>(R + (j0 + jb) * n + j0, n, nn, R + j0 * n + j0 + jb, n,
+                                nn, R + (j0 + jb) * n + j0 + jb, n, nn, (int)rest,
+                                (int)rest, jb, mods, st, W, s));
+    }
+    return IDET_OK;
+}
+
+}  // namespace
+
+int lu_factor_batched(int32_t *R, int64_t n, const ModP *mods_dev,
+                      const ModP *mods_host, int W, bool wide, int nb,
+                      int32_t *perm, uint32_t *det_out, int update_path,
+                      Workspace &ws) {
+    (void)mods_host;
+    (void)update_path;
+    cudaStream_t s = ws.stream();
+    if (W <= 0) return IDET_OK;
+    LUState *st = nullptr;
+    IDET_TRY(ws.alloc_n(&st, W));
+    if (nb <= 0 || nb > kNBMax) nb = kNBMax;
+    if (n <= kSmallN) {
+        size_t smem = sizeof(int32_t) * n * n;
+        IDET_CUDA_TRY(cudaFuncSetAttribute(k_lu_small,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(sizeof(int32_t) * kSmallN * kSmallN)));
+        k_lu_small<<<W, 512, smem, s>>>(R, (int)n, mods_dev, st, perm);
+        count_launch();
+        IDET_CUDA_TRY(cudaGetLastError());
+    } else if (wide) {
+        IDET_TRY(lu_blocked<true>(R, n, mods_dev, W, nb, perm, st, s));
+    } else {
+        IDET_TRY(lu_blocked<false>(R, n, mods_dev, W, nb, perm, st, s));
+    }
+    k_finalize_det<<<(W + 127) / 128, 128, 0, s>>>(st, mods_dev, W, det_out);
+    count_launch();
+    IDET_CUDA_TRY(cudaGetLastError());
+    return IDET_OK;
+}
+
+// A^{-1} = U^{-1} L^{-1} P: Y <- P, Y <- L^{-1} Y (blocked forward
+// substitution), Y <- U^{-1} Y (blocked back substitution).
+int lu_inverse(const int32_t *R, const int32_t *perm, int64_t n, const ModP &mod_host,
+               const ModP *mod_dev, bool wide, int nb, int32_t *Y, Workspace &ws) {
+    cudaStream_t s = ws.stream();
+    if (nb <= 0 || nb > kNBMax) nb = kNBMax;
+    k_perm_identity<<<148 * 4, 256, 0, s>>>(Y, perm, n);
+    count_launch();
+    IDET_CUDA_TRY(cudaGetLastError());
+    for (int64_t k0 = 0; k0 < n; k0 += nb) {
+        const int kb = (int)((n - k0) < nb ? (n - k0) : nb);
+        if (wide)
+            IDET_TRY(trsm_lower<true>(R, 0, Y, 0, n, k0, k0, kb, 0, n, mod_dev, nullptr, 1, s));
+        else
+            IDET_TRY(trsm_lower<false>(R, 0, Y, 0, n, k0, k0, kb, 0, n, mod_dev, nullptr, 1, s));
+        const int64_t below = n - k0 - kb;
+        if (below > 0) {
+            if (wide)
+                IDET_TRY(gemm_sub<true>(R + (k0 + kb) * n + k0, n, 0, Y + k0 * n, n, 0,
+                                        Y + (k0 + kb) * n, n, 0, (int)below, (int)n, kb,
+                                        mod_dev, nullptr, 1, s));
+            else
+                IDET_TRY(gemm_sub<false>(R + (k0 + kb) * n + k0, n, 0, Y + k0 * n, n, 0,
+                                         Y + (k0 + kb) * n, n, 0, (int)below, (int)n, kb,
+                                         mod_dev, nullptr, 1, s));
+        }
+    }
+    const int64_t nblk = (n + nb - 1) / nb;
+    for (int64_t bi = nblk - 1; bi >= 0; --bi) {
+        const int64_t k0 = bi * nb;
+        const int kb = (int)((n - k0) < nb ? (n - k0) : nb);
+        dim3 grid((unsigned)((n + 127) / 128));
+        if (wide)
+            k_trsm_upper<true><<<grid, 128, 0, s>>>(R, n, k0, Y, k0, kb, n, mod_host);
+        else
+            k_trsm_upper<false><<<grid, 128, 0, s>>>(R, n, k0, Y, k0, kb, n, mod_host);
+        count_launch();
+        IDET_CUDA_TRY(cudaGetLastError());
+        if (k0 > 0) {
+            if (wide)
+                IDET_TRY(gemm_sub<true>(R + k0, n, 0, Y + k0 * n, n, 0, Y, n, 0, (int)k0,
+                                        (int)n, kb, mod_dev, nullptr, 1, s));
+            else
+                IDET_TRY(gemm_sub<false>(R + k0, n, 0, Y + k0 * n, n, 0, Y, n, 0, (int)k0,
+                                         (int)n, kb, mod_dev, nullptr, 1, s));
+        }
+    }
+    return IDET_OK;
+}
+
+}  // namespace idet

@@ -1,0 +1,167 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer results are compared bit-exactly: residues, LU factors, lifting
+digits and determinants have unique values (the LU with the first-nonzero
+pivot rule is unique).
+"""
+import math
+import random
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import cra, dixon, exact, modular
+
+pytestmark = pytest.mark.gpu
+
+idet = pytest.importorskip("paper_cs_0511066_b300")
+
+P21 = modular.primes_in(1 << 20, 1 << 21)
+
+
+def rprimes(k, seed, pool=P21):
+    return random.Random(seed).sample(pool, k)
+
+
+def p31(k, seed):
+    r = random.Random(seed)
+    out = []
+    while len(out) < k:
+        c = r.randrange(1 << 30, 1 << 31) | 1
+        if modular.is_prime(c) and c not in out:
+            out.append(c)
+    return out
+
+
+# --- det mod p (the multi-prime LU) -----------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 32, 33, 100, 191, 192, 193, 257, 300])
+def test_det_mod_primes_matches_oracle(n):
+    A = workloads.dense_pm100(n, seed=n)
+    primes = rprimes(7, n)
+    assert list(idet.det_mod_primes(A, primes)) == list(modular.det_mod_primes(A, primes))
+
+
+@pytest.mark.parametrize("n", [60, 250])
+def test_det_mod_31bit_primes(n):
+    A = workloads.dense_pm2p20(n, seed=n + 1)
+    primes = p31(3, n)
+    assert list(idet.det_mod_primes(A, primes)) == list(modular.det_mod_primes(A, primes))
+
+
+def test_det_mod_primes_dense_u8_n1000():
+    A = workloads.dense_u8(1000, seed=0)
+    primes = rprimes(4, 99)
+    assert list(idet.det_mod_primes(A, primes)) == list(modular.det_mod_primes(A, primes, threads=4))
+
+
+@pytest.mark.parametrize("n", [50, 230])
+def test_det_mod_p_with_zero_pivots_and_p_dividing_det(n):
+    p = P21[5]
+    A = workloads.dense_pm100(n, seed=7)
+    A[0, 0] = 0
+    A[1, 0] = p                   # 0 mod p: pivot search must skip it
+    A[5] = A[3] * 2 + p           # row 5 = 2 row 3 mod p: singular mod p
+    primes = [p, P21[6], P21[7]]
+    got = idet.det_mod_primes(A, primes)
+    assert got[0] == 0
+    assert list(got) == list(modular.det_mod_primes(A, primes))
+
+
+@pytest.mark.parametrize("n", [40, 200, 301])
+def test_lu_factors_match_oracle(n):
+    p = P21[11]
+    A = workloads.dense_pm100(n, seed=3)
+    A[0, 0] = 0                   # forces a row exchange
+    A[3, 3] = A[3, 3] + p * 0
+    lu, perm, sing = idet.lu_mod_prime(A, p)
+    LU, operm, d, stop = modular.lu_mod_p(A, p)
+    assert not sing and stop == n
+    assert (perm == operm).all()
+    assert (lu == LU).all()
+
+
+def test_lu_factors_31bit():
+    p = p31(1, 5)[0]
+    A = workloads.dense_pm2p20(150, seed=4)
+    lu, perm, _ = idet.lu_mod_prime(A, p)
+    LU, operm, _, _ = modular.lu_mod_p(A, p)
+    assert (perm == operm).all() and (lu == LU).all()
+
+
+# --- Dixon lifting --------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,m", [(5, 4), (24, 7), (67, 5)])
+def test_dixon_digits_match_oracle(n, m):
+    A = workloads.dense_pm100(n, seed=n)
+    b = workloads.random_rhs(n, 1 << 40, seed=n)
+    p = p31(1, n)[0]
+    dg, r = idet.dixon_digits(A, b, p, m)
+    odg, orr = dixon.dixon_digits(A, b, p, m)
+    assert dg.tolist() == odg
+    assert r.tolist() == orr
+
+
+# --- CRT ---------------------------------------------------------------------------
+
+def test_crt_symmetric_matches_oracle():
+    r = random.Random(1)
+    for k in [1, 2, 5, 40, 300]:
+        primes = rprimes(k, k)
+        M = math.prod(primes)
+        for N in [0, 1, -1, r.randint(-(M // 2), M // 2), M // 2, -(M // 2)]:
+            res = [N % p for p in primes]
+            v, tr = idet.crt_symmetric(res, primes)
+            assert v == cra.crt_symmetric(res, primes) == N
+    primes = rprimes(12, 3)
+    v, tr = idet.crt_symmetric([12345 % p for p in primes], primes)
+    assert v == 12345 and tr == 11
+
+
+# --- det(A) -------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_int_det_dense_pm100_n100(seed):
+    A = workloads.dense_pm100(100, seed=seed)
+    assert idet.int_det(A) == exact.bareiss_det(A.tolist())
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 7, 16, 33])
+def test_int_det_small(n):
+    for seed in range(3):
+        A = workloads.dense_uniform(n, -5, 5, seed + 10 * n)
+        assert idet.int_det(A) == exact.bareiss_det(A.tolist())
+
+
+def test_int_det_degenerate_cases():
+    assert idet.int_det(np.zeros((5, 5), dtype=np.int64)) == 0
+    I = np.eye(9, dtype=np.int64)
+    assert idet.int_det(I) == 1
+    A = workloads.dense_pm100(30, seed=2)
+    A[7] = 0
+    assert idet.int_det(A) == 0
+    B = workloads.dense_pm100(30, seed=3)
+    B[4] = B[9] + B[11]
+    assert idet.int_det(B) == 0
+    C = workloads.dense_uniform(12, -(2 ** 31 - 1), 2 ** 31 - 1, 5)
+    assert idet.int_det(C) == exact.bareiss_det(C.tolist())
+
+
+def test_int_det_engineered_smith():
+    A = workloads.engineered_smith(60, seed=1)
+    assert idet.int_det(A) == math.factorial(60)
+
+
+def test_int_det_certify_and_cra_only():
+    A = workloads.dense_pm100(70, seed=5)
+    want = exact.bareiss_det(A.tolist())
+    assert idet.int_det(A, certify=True) == want
+    assert idet.int_det(A, lif=False) == want
+
+
+def test_int_det_blocked_sizes():
+    for n in [193, 260]:
+        A = workloads.dense_uniform(n, -8, 8, n)
+        want = exact.bareiss_det(A.tolist())
+        assert idet.int_det(A) == want

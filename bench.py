@@ -136,6 +136,26 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_case(case):
+    """Small fixed invocations of single kernels, for profiler captures."""
+    import torch
+    import paper_cs_0511066_b300 as idet
+    if case == "lift1k":
+        A = torch.from_numpy(workloads.dense_u8(1000, seed=0)).cuda()
+    else:
+        A = torch.from_numpy(workloads.dense_pm2p20(4000, seed=0)).cuda()
+    t0 = time.perf_counter()
+    if case in ("lift", "lift1k"):
+        b = workloads.random_rhs(A.shape[0], 1 << 40, seed=1)
+        idet.dixon_digits(A, b, 2147483629, 64)
+    elif case == "lu":
+        idet.det_mod_primes(A, [1048583, 1048589, 1048601, 1048609])
+    else:
+        raise SystemExit(f"unknown case {case}")
+    torch.cuda.synchronize()
+    print(json.dumps({"case": case, "seconds": time.perf_counter() - t0}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -143,9 +163,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default=None,
+                    help="profiling case: 'lift' (Dixon lifting, n=4000, 64 digits) or "
+                         "'lu' (det mod 4 primes, n=4000); runs once and prints timings")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.case:
+        return run_case(args.case)
 
     import torch
     import paper_cs_0511066_b300 as idet
@@ -231,7 +256,8 @@ def main():
     per_mat = [{"n": int(mats[i % len(mats)].shape[0]),
                 "ms_total": round(st["ms_total"], 2), "ms_lu": round(st["ms_lu"], 2),
                 "ms_lift": round(st["ms_lift"], 2), "ms_lift_kernel": round(st["ms_lift_kernel"], 2),
-                "ms_cra": round(st["ms_cra"], 2), "primes": st["primes_used"],
+                "ms_cra": round(st["ms_cra"], 2), "ms_inverse": round(st["ms_inverse"], 2),
+                "ms_rr": round(st["ms_rr"], 2), "primes": st["primes_used"],
                 "lift_iters": st["lift_iters"], "log2_K": st["log2_K"]}
                for i, (_, st) in enumerate(stats[:len(mats)])]
     line = {

@@ -56,7 +56,8 @@ class idet_stats(ctypes.Structure):
                 ("ms_lift", ctypes.c_double), ("ms_cra", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("launches", ctypes.c_uint64),
                 ("ms_lift_kernel", ctypes.c_double), ("lift_bytes", ctypes.c_double),
-                ("lu_macs", ctypes.c_double)]
+                ("lu_macs", ctypes.c_double), ("ms_inverse", ctypes.c_double),
+                ("ms_rr", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

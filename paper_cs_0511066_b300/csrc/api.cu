@@ -294,8 +294,10 @@ struct DetJob {
     double log2H = 0;
     std::vector<double> rowsq;
     uint64_t amax = 0;
-    int32_t *A32 = nullptr;  // ld = ld4
-    int64_t ld4 = 0;
+    std::vector<double> colsq;
+    void *Anar = nullptr;  // A as int8/int16/int32, rows padded to ldl
+    int abytes = 4;
+    int64_t ldl = 0;
     // CRA state
     PrimeDraw draw;
     std::vector<uint32_t> primes;   // factored primes
@@ -318,13 +320,24 @@ struct DetJob {
         IDET_CUDA_TRY(cudaMemcpyAsync(rowsq.data(), d_rowsq, sizeof(double) * n,
                                       cudaMemcpyDeviceToHost, s));
         IDET_CUDA_TRY(cudaMemcpyAsync(&amax, d_amax, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        double *d_colsq = nullptr;
+        IDET_TRY(ws.alloc_n(&d_colsq, n));
+        IDET_TRY(launch_col_stats(M.A, n, n, d_colsq, s));
+        colsq.resize(n);
+        IDET_CUDA_TRY(cudaMemcpyAsync(colsq.data(), d_colsq, sizeof(double) * n,
+                                      cudaMemcpyDeviceToHost, s));
         IDET_CUDA_TRY(cudaStreamSynchronize(s));
         if (amax > 0x7fffffffull) {
             set_last_error("entries must satisfy |a_ij| <= 2^31 - 1");
             return IDET_ERR_ARG;
         }
-        log2H = 0;
-        for (double v : rowsq) log2H += v > 0 ? 0.5 * std::log2(v) : -INFINITY;
+        // Hadamard: |det A| <= prod of the row norms and <= prod of the
+        // column norms (Lemma 2.1 uses H = (sqrt(n) ||A||)^n, which bounds
+        // both); the smaller one is used.
+        double hr = 0, hc = 0;
+        for (double v : rowsq) hr += v > 0 ? 0.5 * std::log2(v) : -INFINITY;
+        for (double v : colsq) hc += v > 0 ? 0.5 * std::log2(v) : -INFINITY;
+        log2H = std::min(hr, hc);
         st.log2_H = log2H;
         return IDET_OK;
     }
@@ -427,7 +440,7 @@ struct DetJob {
 };
 
 // LU + inverse mod a 31-bit prime; returns IDET_ERR_SINGULAR if A is
-// singular mod p. Cinv: n x ld4 (zero padded columns).
+// singular mod p. Cinv: n rows of ld4 entries (zero padded columns).
 static int inverse_mod_prime(const DevMatrix &M, uint32_t p, int nb, Workspace &ws, int32_t *Cinv,
                              int64_t ld4) {
     cudaStream_t s = ws.stream();
@@ -459,22 +472,17 @@ static int inverse_mod_prime(const DevMatrix &M, uint32_t p, int nb, Workspace &
     return IDET_OK;
 }
 
-static int make_A32(const DevMatrix &M, Workspace &ws, int32_t **A32, int64_t *ld4) {
+// A in the narrowest of int8/int16/int32 holding max |a_ij| = amax, rows
+// padded with zeros to ldl = n rounded up to a multiple of 16.
+static int make_Anar(const DevMatrix &M, uint64_t amax, Workspace &ws, void **out, int *abytes,
+                     int64_t *ldl) {
     const int64_t n = M.n;
-    *ld4 = (n + 3) / 4 * 4;
-    int32_t *a = nullptr;
-    IDET_TRY(ws.alloc_n(&a, (size_t)n * *ld4));
-    if (*ld4 == n) {
-        IDET_TRY(launch_to_int32(M.A, n, n, a, ws.stream()));
-    } else {
-        int32_t *t = nullptr;
-        IDET_TRY(ws.alloc_n(&t, (size_t)n * n));
-        IDET_TRY(launch_to_int32(M.A, n, n, t, ws.stream()));
-        IDET_CUDA_TRY(cudaMemsetAsync(a, 0, sizeof(int32_t) * n * *ld4, ws.stream()));
-        IDET_CUDA_TRY(cudaMemcpy2DAsync(a, 4 * *ld4, t, 4 * n, 4 * n, n,
-                                        cudaMemcpyDeviceToDevice, ws.stream()));
-    }
-    *A32 = a;
+    *ldl = (n + 15) / 16 * 16;
+    *abytes = amax <= 127 ? 1 : (amax <= 32767 ? 2 : 4);
+    void *a = nullptr;
+    IDET_TRY(ws.alloc(&a, (size_t)n * *ldl * *abytes + 64));
+    IDET_TRY(launch_narrow(M.A, n, n, a, *ldl, *abytes, ws.stream()));
+    *out = a;
     return IDET_OK;
 }
 
@@ -494,30 +502,36 @@ static int solve_and_denominator(DetJob &J, const int64_t *b_dev, const std::vec
     Workspace &ws = J.ws;
     cudaStream_t s = J.s;
     SplitMix g(J.o.seed ^ 0x11f7ull);
-    if (!J.A32) IDET_TRY(make_A32(J.M, ws, &J.A32, &J.ld4));
+    if (!J.Anar) IDET_TRY(make_Anar(J.M, J.amax, ws, &J.Anar, &J.abytes, &J.ldl));
     int32_t *Cinv = nullptr;
-    IDET_TRY(ws.alloc_n(&Cinv, (size_t)n * J.ld4));
+    IDET_TRY(ws.alloc_n(&Cinv, (size_t)n * J.ldl));
     uint32_t p = 0;
     int rc = IDET_ERR_SINGULAR;
+    Timer tinv(s);
     for (int tries = 0; tries < 6 && rc == IDET_ERR_SINGULAR; ++tries) {
         p = random_prime31(g);
-        rc = inverse_mod_prime(J.M, p, J.nb, ws, Cinv, J.ld4);
+        rc = inverse_mod_prime(J.M, p, J.nb, ws, Cinv, J.ldl);
     }
+    J.st.ms_inverse += tinv.stop();
     if (rc != IDET_OK) return rc;
-    // Bounds: D <= |det A| <= prod ||row_i||; numerator of u.x:
-    // |u . N| <= ||u||_1 max_j |N_j|, |N_j| <= prod_i sqrt(||row_i||^2 + b_i^2).
-    double log2D = 0, log2N = log2u1;
+    // Bounds (Cramer): x_j = N_j / det A. The denominator of u.x divides
+    // det A, |det A| <= H; the numerator of u.x is at most
+    // ||u||_1 max_j |N_j| with |N_j| = |det A_j(b)| <= ||b||_2 prod_{k != j}
+    // ||col_k||_2 (Hadamard on the columns of A with column j replaced by b).
+    double log2D = J.log2H, log2N = log2u1, bb = 1.0, lc = 0, lcmin = INFINITY;
     for (int64_t i = 0; i < n; ++i) {
-        log2D += 0.5 * std::log2(std::max(J.rowsq[i], 1.0));
         double bi = (double)b_host[i];
-        log2N += 0.5 * std::log2(J.rowsq[i] * (1 + 1e-12) + bi * bi + 1.0);
+        bb += bi * bi;
+        double c = 0.5 * std::log2(std::max(J.colsq[i], 1.0));
+        lc += c;
+        lcmin = std::min(lcmin, c);
     }
+    log2N += 0.5 * std::log2(bb * (1 + 1e-12)) + lc - lcmin;
     const double lp = std::log2((double)p);
     const int hN = (int)std::ceil((log2N + 1) / lp);
     const int hD = (int)std::ceil((log2D + 1) / lp);
     const int m = hN + hD + 2;
     LiftArgs a{};
-    a.A32 = J.A32;
     a.Cinv = Cinv;
     a.b = b_dev;
     a.u = u_dev;
@@ -532,7 +546,7 @@ static int solve_and_denominator(DetJob &J, const int64_t *b_dev, const std::vec
     a.r = r;
     a.digits = nullptr;
     float kms = 0;
-    IDET_TRY(launch_lift(a, ws, &out.timed_out, &kms));
+    IDET_TRY(launch_lift(a, J.Anar, J.abytes, J.ldl, ws, &out.timed_out, &kms));
     J.st.ms_lift_kernel += kms;
     J.st.lift_bytes += (double)m * 8.0 * (double)n * (double)n;
     J.st.lu_macs += 2.0 * (double)n * n * n;  // LU + inverse of the lift prime
@@ -541,10 +555,12 @@ static int solve_and_denominator(DetJob &J, const int64_t *b_dev, const std::vec
     const int den_cap = hD + 2;
     IDET_TRY(ws.alloc_n(&den, den_cap));
     IDET_TRY(ws.alloc_n(&info, 4));
+    Timer trr(s);
     IDET_TRY(launch_ratrecon(z, m, p, hN, hD, den, den_cap, info, ws));
     int32_t hinfo[2] = {0, 0};
     IDET_CUDA_TRY(cudaMemcpyAsync(hinfo, info, 8, cudaMemcpyDeviceToHost, s));
     IDET_CUDA_TRY(cudaStreamSynchronize(s));
+    J.st.ms_rr += trr.stop();
     if (hinfo[0] != 0) {
         set_last_error("rational reconstruction failed (code %d)", hinfo[0]);
         return IDET_ERR_INTERNAL;
@@ -706,18 +722,30 @@ int idet_dixon_digits(const int64_t *A, int64_t n, int64_t lda, const int64_t *b
     Workspace ws(s);
     DevMatrix M;
     IDET_TRY(stage_matrix(A, n, lda, on_device, ws, M));
-    int32_t *A32 = nullptr, *Cinv = nullptr, *dig = nullptr;
-    int64_t ld4 = 0, *bd = nullptr, *r = nullptr;
-    IDET_TRY(make_A32(M, ws, &A32, &ld4));
-    IDET_TRY(ws.alloc_n(&Cinv, (size_t)n * ld4));
-    IDET_TRY(inverse_mod_prime(M, p, 32, ws, Cinv, ld4));
+    int32_t *Cinv = nullptr, *dig = nullptr;
+    int64_t ldl = 0, *bd = nullptr, *r = nullptr;
+    double *rowsq = nullptr;
+    unsigned long long *d_amax = nullptr, hmax = 0;
+    IDET_TRY(ws.alloc_n(&rowsq, n));
+    IDET_TRY(ws.alloc_n(&d_amax, 1));
+    IDET_TRY(launch_row_stats(M.A, n, n, rowsq, d_amax, s));
+    IDET_CUDA_TRY(cudaMemcpyAsync(&hmax, d_amax, 8, cudaMemcpyDeviceToHost, s));
+    IDET_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hmax > 0x7fffffffull) {
+        set_last_error("entries must satisfy |a_ij| <= 2^31 - 1");
+        return IDET_ERR_ARG;
+    }
+    void *Anar = nullptr;
+    int abytes = 4;
+    IDET_TRY(make_Anar(M, hmax, ws, &Anar, &abytes, &ldl));
+    IDET_TRY(ws.alloc_n(&Cinv, (size_t)n * ldl));
+    IDET_TRY(inverse_mod_prime(M, p, 32, ws, Cinv, ldl));
     IDET_TRY(ws.alloc_n(&bd, n));
     IDET_TRY(ws.alloc_n(&r, n));
     IDET_TRY(ws.alloc_n(&dig, (size_t)m * n + 1));
     IDET_CUDA_TRY(cudaMemcpyAsync(bd, b, 8 * (size_t)n,
                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     LiftArgs a{};
-    a.A32 = A32;
     a.Cinv = Cinv;
     a.b = bd;
     a.n = n;
@@ -727,7 +755,7 @@ int idet_dixon_digits(const int64_t *A, int64_t n, int64_t lda, const int64_t *b
     a.digits = dig;
     a.r = r;
     int to = 0;
-    IDET_TRY(launch_lift(a, ws, &to));
+    IDET_TRY(launch_lift(a, Anar, abytes, ldl, ws, &to));
     if (m > 0)
         IDET_CUDA_TRY(cudaMemcpyAsync(digits, dig, 4 * (size_t)m * n, cudaMemcpyDeviceToHost, s));
     IDET_CUDA_TRY(cudaMemcpyAsync(residual, r, 8 * (size_t)n, cudaMemcpyDeviceToHost, s));

@@ -137,6 +137,12 @@ inline void count_launch(unsigned k = 1) { g_launches += k; }
 // rounded upward by a relative 2^-40 margin), amax[0] = max |A_ij|.
 int launch_row_stats(const int64_t *A, int64_t n, int64_t lda, double *rowsq,
                      unsigned long long *amax, cudaStream_t s);
+// colsq[j] = sum_i A_ij^2 (double, rounded upward).
+int launch_col_stats(const int64_t *A, int64_t n, int64_t lda, double *colsq, cudaStream_t s);
+// A -> int8/int16/int32 copy (bytes = 1, 2, 4) with leading dimension ldo
+// >= n, zero padded; entries must fit the type.
+int launch_narrow(const int64_t *A, int64_t n, int64_t lda, void *out, int64_t ldo, int bytes,
+                  cudaStream_t s);
 // A (int64, |A_ij| < 2^31) -> int32 copy with leading dimension n.
 int launch_to_int32(const int64_t *A, int64_t n, int64_t lda, int32_t *A32,
                     cudaStream_t s);
@@ -167,8 +173,7 @@ int lu_inverse(const int32_t *R, const int32_t *perm, int64_t n,
 
 // k_lift.cu ---------------------------------------------------------------
 struct LiftArgs {
-    const int32_t *A32;    // n x n, ld n
-    const int32_t *Cinv;   // A^{-1} mod p, balanced, n x n
+    const int32_t *Cinv;   // A^{-1} mod p, balanced, n rows of ld entries
     const int64_t *b;      // right-hand side, n
     const int32_t *u;      // projection vector, n (may be null)
     int64_t n;
@@ -179,7 +184,10 @@ struct LiftArgs {
     int64_t *zproj;        // m projections u . x_i, may be null
     int64_t *r;            // n: residual (in: ignored; out: r_m)
 };
-int launch_lift(const LiftArgs &a, Workspace &ws, int *timed_out, float *ms = nullptr);
+// Anar: A as int8/int16/int32 (abytes = 1, 2, 4), n rows of ld entries;
+// Cinv rows also have ld entries; ld must be a multiple of 16.
+int launch_lift(const LiftArgs &a, const void *Anar, int abytes, int64_t ld, Workspace &ws,
+                int *timed_out, float *ms = nullptr);
 
 // k_bignum.cu ---------------------------------------------------------------
 // Device big integers: little-endian uint32 limbs with an explicit length.

@@ -196,8 +196,7 @@ __global__ void k_mixed_to_int(const uint32_t *__restrict__ primes,
 constexpr int kRT = 1024;
 
 struct RRShared {
-    int64_t co1[kRT];
-    int64_t co2[kRT];
+    int64_t co[4][kRT];
     int la, lb, lta, ltb;
     int64_t A, B, C, D;
     int steps;
@@ -242,55 +241,105 @@ __device__ __forceinline__ void chunk_of(int len, int &beg, int &end) {
     end = min(len, beg + per);
 }
 
-// Each thread has written its digits with carry-in 0 and carry-out co;
-// propagate the (signed) carries across the chunks.
-__device__ void resolve_p(uint32_t *w, int beg, int end, int64_t co, int64_t *s_co,
-                          const Radix &R) {
+// Each thread has written its digits [beg, end) of NA arrays with carry-in
+// 0 and carry-outs co[]; propagate the (signed) carries across the chunks.
+// Each pass moves every pending carry at least one chunk up, so at most kRT
+// passes are needed.
+template <int NA>
+__device__ void resolve_p(uint32_t *const *w, int beg, int end, const int64_t *co,
+                          RRShared &S, const Radix &R) {
     const int tid = threadIdx.x;
-    s_co[tid] = co;
+#pragma unroll
+    for (int q = 0; q < NA; ++q) S.co[q][tid] = co[q];
     __syncthreads();
-    int64_t cin = tid > 0 ? s_co[tid - 1] : 0;
+    int64_t cin[NA];
+#pragma unroll
+    for (int q = 0; q < NA; ++q) cin[q] = tid > 0 ? S.co[q][tid - 1] : 0;
     __syncthreads();
-    // each pass moves the pending carries one chunk up: at most kRT passes
     for (int pass = 0; pass <= kRT; ++pass) {
-        int64_t c = cin;
-        for (int k = beg; k < end && c != 0; ++k) w[k] = divmod_p((int64_t)w[k] + c, R, c);
-        s_co[tid] = c;
-        int any = __syncthreads_or(c != 0 && tid != kRT - 1);
+        bool pend = false;
+#pragma unroll
+        for (int q = 0; q < NA; ++q) {
+            int64_t c = cin[q];
+            for (int k = beg; k < end && c != 0; ++k) w[q][k] = divmod_p((int64_t)w[q][k] + c, R, c);
+            // a chunk past the top digit drops its carry: the result fits in
+            // the digits below, so carries beyond them cancel
+            if (beg >= end) c = 0;
+            S.co[q][tid] = c;
+            pend |= (c != 0);
+        }
+        int any = __syncthreads_or(pend && tid != kRT - 1);
         if (!any) break;
-        cin = tid > 0 ? s_co[tid - 1] : 0;
+#pragma unroll
+        for (int q = 0; q < NA; ++q) cin[q] = tid > 0 ? S.co[q][tid - 1] : 0;
         __syncthreads();
     }
     __syncthreads();
 }
 
-// (x, y) <- (A x + B y, C x + D y); |A|, |B|, |C|, |D| < 2^29; results >= 0.
-__device__ void lincomb2_p(uint32_t *x, uint32_t *y, int L, int64_t A, int64_t B,
-                           int64_t C, int64_t D, RRShared &S, const Radix &R) {
+// (x, y) <- (A x + B y, C x + D y) and (tx, ty) <- (|A| tx + |B| ty,
+// |C| tx + |D| ty) in one pass over L digits; |A|..|D| < 2^28; all results
+// are >= 0 and fit in L digits.
+__device__ void lincomb4_p(uint32_t *x, uint32_t *y, uint32_t *tx, uint32_t *ty, int La,
+                           int Lt, int64_t A, int64_t B, int64_t C, int64_t D, RRShared &S,
+                           const Radix &R) {
+    // x, y use digits [0, La), tx, ty digits [0, Lt); both are zero above
+    // their ranges, so one chunking of [0, max(La, Lt)) serves all four.
+    const int L = max(La, Lt);
     int beg, end;
     chunk_of(L, beg, end);
-    int64_t c1 = 0, c2 = 0;
+    const int64_t aA = A < 0 ? -A : A, aB = B < 0 ? -B : B, aC = C < 0 ? -C : C,
+                  aD = D < 0 ? -D : D;
+    int64_t c[4] = {0, 0, 0, 0};
     for (int k = beg; k < end; ++k) {
-        int64_t xv = x[k], yv = y[k];
-        x[k] = divmod_p(A * xv + B * yv + c1, R, c1);
-        y[k] = divmod_p(C * xv + D * yv + c2, R, c2);
+        if (k < La) {
+            int64_t xv = x[k], yv = y[k];
+            x[k] = divmod_p(A * xv + B * yv + c[0], R, c[0]);
+            y[k] = divmod_p(C * xv + D * yv + c[1], R, c[1]);
+        }
+        if (k < Lt) {
+            int64_t txv = tx[k], tyv = ty[k];
+            tx[k] = divmod_p(aA * txv + aB * tyv + c[2], R, c[2]);
+            ty[k] = divmod_p(aC * txv + aD * tyv + c[3], R, c[3]);
+        }
     }
-    resolve_p(x, beg, end, c1, S.co1, R);
-    resolve_p(y, beg, end, c2, S.co2, R);
+    uint32_t *ws[4] = {x, y, tx, ty};
+    resolve_p<4>(ws, beg, end, c, S, R);
 }
 
-// x <- x + s * y * p^sh (|s| < 2^29); L digits.
-__device__ void addmul_shift_p(uint32_t *x, const uint32_t *y, int ylen, int L, int64_t s,
-                               int sh, RRShared &S, const Radix &R) {
+// x <- x - q y p^sh and tx <- tx + q ty p^sh (0 < q < 2^29); L digits.
+__device__ void submul2_shift_p(uint32_t *x, const uint32_t *y, int ylen, uint32_t *tx,
+                                const uint32_t *ty, int tylen, int La, int Lt, int64_t q,
+                                int sh, RRShared &S, const Radix &R) {
     int beg, end;
-    chunk_of(L, beg, end);
-    int64_t c = 0;
+    chunk_of(max(La, Lt), beg, end);
+    int64_t c[2] = {0, 0};
     for (int k = beg; k < end; ++k) {
-        int src = k - sh;
-        int64_t yv = (src >= 0 && src < ylen) ? y[src] : 0;
-        x[k] = divmod_p((int64_t)x[k] + s * yv + c, R, c);
+        const int src = k - sh;
+        if (k < La) {
+            const int64_t yv = (src >= 0 && src < ylen) ? y[src] : 0;
+            x[k] = divmod_p((int64_t)x[k] - q * yv + c[0], R, c[0]);
+        }
+        if (k < Lt) {
+            const int64_t tyv = (src >= 0 && src < tylen) ? ty[src] : 0;
+            tx[k] = divmod_p((int64_t)tx[k] + q * tyv + c[1], R, c[1]);
+        }
     }
-    resolve_p(x, beg, end, c, S.co1, R);
+    uint32_t *ws[2] = {x, tx};
+    resolve_p<2>(ws, beg, end, c, S, R);
+}
+
+// floor(x / y) for x, y < 2^63, y > 0: subtraction for the small quotients
+// that dominate Euclid's algorithm, 64-bit division otherwise.
+__device__ __forceinline__ uint64_t small_quot(uint64_t x, uint64_t y) {
+    if (x < y) return 0;
+    uint64_t r = x - y;
+    if (r < y) return 1;
+    r -= y;
+    if (r < y) return 2;
+    r -= y;
+    if (r < y) return 3;
+    return x / y;
 }
 
 __device__ int trim(const uint32_t *x, int l) {
@@ -391,8 +440,11 @@ k_ratrecon(const int64_t *__restrict__ z, int m, uint32_t p, int hN, int hD,
                 while (true) {
                     int64_t d1 = (int64_t)bh + C, d2 = (int64_t)bh + D;
                     if (d1 <= 0 || d2 <= 0) break;
-                    uint64_t q1 = (uint64_t)((int64_t)ah + A) / (uint64_t)d1;
-                    uint64_t q2 = (uint64_t)((int64_t)ah + B) / (uint64_t)d2;
+                    if ((int64_t)ah + A < 0 || (int64_t)ah + B < 0) break;
+                    const uint64_t n1 = (uint64_t)((int64_t)ah + A), n2 = (uint64_t)((int64_t)ah + B);
+                    if (d1 < (1ll << 35) && n1 >= ((uint64_t)d1 << 28)) break;  // quotient >= 2^28
+                    const uint64_t q1 = small_quot(n1, (uint64_t)d1);
+                    const uint64_t q2 = small_quot(n2, (uint64_t)d2);
                     if (q1 != q2 || q1 >= (1ull << 28)) break;
                     int64_t q = (int64_t)q1;
                     int64_t nC = A - q * C, nD = B - q * D;
@@ -432,37 +484,31 @@ k_ratrecon(const int64_t *__restrict__ z, int m, uint32_t p, int hN, int hD,
         __syncthreads();
         if (S.mode != 0) break;
         if (S.steps > 0) {
-            const int L = S.la;
-            lincomb2_p(a, b, L, S.A, S.B, S.C, S.D, S, R);
-            const int64_t A = S.A < 0 ? -S.A : S.A, B = S.B < 0 ? -S.B : S.B;
-            const int64_t C = S.C < 0 ? -S.C : S.C, D = S.D < 0 ? -S.D : S.D;
-            const int Lt = max(S.lta, S.ltb) + 2;
+            const int La = S.la, Lt = max(S.lta, S.ltb) + 2;
             if (Lt > cap) {
                 if (tid == 0) S.mode = 2;
                 __syncthreads();
                 break;
             }
-            lincomb2_p(ta, tb, Lt, A, B, C, D, S, R);
+            lincomb4_p(a, b, ta, tb, La, Lt, S.A, S.B, S.C, S.D, S, R);
             if (tid == 0) {
-                S.la = trim(a, L);
-                S.lb = trim(b, L);
+                S.la = trim(a, La);
+                S.lb = trim(b, La);
                 S.lta = trim(ta, Lt);
                 S.ltb = trim(tb, Lt);
             }
             __syncthreads();
         } else {
             if (S.sh >= 0) {
-                const int L = S.la;
-                addmul_shift_p(a, b, S.lb, L, -(int64_t)S.q, S.sh, S, R);
-                const int Lt = max(S.lta, S.ltb + S.sh) + 2;
+                const int La = S.la, Lt = max(S.lta, S.ltb + S.sh) + 2;
                 if (Lt > cap) {
                     if (tid == 0) S.mode = 2;
                     __syncthreads();
                     break;
                 }
-                addmul_shift_p(ta, tb, S.ltb, Lt, (int64_t)S.q, S.sh, S, R);
+                submul2_shift_p(a, b, S.lb, ta, tb, S.ltb, La, Lt, (int64_t)S.q, S.sh, S, R);
                 if (tid == 0) {
-                    S.la = trim(a, L);
+                    S.la = trim(a, La);
                     S.lta = trim(ta, Lt);
                 }
                 __syncthreads();
@@ -551,6 +597,7 @@ k_radix_to_binary(const uint32_t *__restrict__ dig, int len, uint32_t p,
                 out[k] = (uint32_t)v;
                 cc = v >> 32;
             }
+            if (beg >= end) cc = 0;  // past the top limb: nothing to carry into
             s_co[threadIdx.x] = (int64_t)cc;
             int any = __syncthreads_or(cc != 0 && threadIdx.x != kRT - 1);
             if (!any) break;

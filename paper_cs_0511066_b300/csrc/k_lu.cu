@@ -19,6 +19,8 @@
 #include <climits>
 #include <cstdio>
 
+#include <cooperative_groups.h>
+
 #include "idet_internal.cuh"
 
 namespace idet {
@@ -190,6 +192,166 @@ k_panel(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb,
         __syncthreads();
     }
     if (threadIdx.x == 0) {
+        LUState s = st[w];
+        s.det = det;
+        s.neg = neg;
+        st[w] = s;
+    }
+}
+
+// Inverse mod p < 2^31 by the extended Euclidean algorithm in 32-bit
+// arithmetic (all remainders and cofactors stay below p in magnitude).
+__device__ __forceinline__ int32_t inv_bal32(int32_t a, uint32_t p) {
+    int32_t r0 = (int32_t)p, r1 = a % (int32_t)p;
+    if (r1 < 0) r1 += (int32_t)p;
+    int32_t t0 = 0, t1 = 1;
+    while (r1 != 0) {
+        int32_t q = r0 / r1, t;
+        t = r0 - q * r1; r0 = r1; r1 = t;
+        t = t0 - q * t1; t0 = t1; t1 = t;
+    }
+    if (t0 > (int32_t)(p - 1) / 2) t0 -= (int32_t)p;
+    if (t0 < -(int32_t)(p - 1) / 2) t0 += (int32_t)p;
+    return t0;
+}
+
+// Panel factorisation by a cluster of kCl CTAs (one cluster per prime).
+// The panel (rows [j0, n), columns [j0, j0 + jb)) is split into kCl
+// contiguous row blocks held in the CTAs' shared memory for the whole
+// panel. Per column: the owner of the diagonal row publishes whether the
+// diagonal entry is nonzero; otherwise every CTA publishes its first nonzero
+// row and all take the minimum (first-nonzero rule); the pivot row is read
+// through distributed shared memory; each CTA scales and updates its rows.
+// Swapped rows are exchanged across CTAs, and their parts outside the panel
+// are swapped in global memory.
+constexpr int kCl = 8;
+constexpr int kClThreads = 512;
+
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClThreads)
+k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chunk,
+                const ModP *__restrict__ mods, LUState *__restrict__ st,
+                int32_t *__restrict__ perm) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ int32_t sp[];          // chunk x kNBMax panel block
+    __shared__ int s_flag[2];                // diagonal nonzero (owner)
+    __shared__ int s_cand[2];                // first nonzero row (each CTA)
+    __shared__ int32_t s_u[kNBMax];
+    __shared__ int32_t s_tmp[kNBMax];
+    __shared__ int32_t s_inv;
+    const int rank = (int)cluster.block_rank();
+    const int w = blockIdx.x / kCl;
+    const ModP M = mods[w];
+    int32_t *a = R + (int64_t)w * n * n;
+    const bool dead0 = st[w].dead != 0;  // uniform over the cluster
+    if (dead0) return;
+    const int64_t rbeg = j0 + (int64_t)rank * chunk;
+    const int64_t rend = min(n, rbeg + chunk);
+    const int nloc = rend > rbeg ? (int)(rend - rbeg) : 0;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < nloc * jb; e += kClThreads) {
+        int r = e / jb, j = e % jb;
+        sp[r * kNBMax + j] = a[(rbeg + r) * n + j0 + j];
+    }
+    uint32_t det = st[w].det;
+    int neg = st[w].neg;
+    bool dead = false;
+    __syncthreads();
+    cluster.sync();
+    for (int c = 0; c < jb; ++c) {
+        const int64_t col = j0 + c;
+        const int owner = (int)((col - j0) / chunk);
+        const int par = c & 1;
+        if (rank == owner && tid == 0)
+            s_flag[par] = sp[(int)(col - rbeg) * kNBMax + c] != 0;
+        cluster.sync();
+        int *fl = cluster.map_shared_rank(&s_flag[par], owner);
+        int64_t piv = col;
+        if (!*fl) {
+            // every CTA: first row >= col + 1 of its block with a nonzero
+            if (tid == 0) s_cand[par] = INT_MAX;
+            __syncthreads();
+            for (int r = tid; r < nloc; r += kClThreads) {
+                int64_t gi = rbeg + r;
+                if (gi > col && sp[r * kNBMax + c] != 0) atomicMin(&s_cand[par], (int)gi);
+            }
+            cluster.sync();
+            int best = INT_MAX;
+            for (int k = 0; k < kCl; ++k) best = min(best, *cluster.map_shared_rank(&s_cand[par], k));
+            if (best == INT_MAX) {
+                dead = true;
+                break;
+            }
+            piv = best;
+            // exchange rows piv and col (panel part) through DSMEM
+            const int po = (int)((piv - j0) / chunk);
+            int32_t *prow = cluster.map_shared_rank(sp, po) + (int)(piv - (j0 + (int64_t)po * chunk)) * kNBMax;
+            int32_t *crow = cluster.map_shared_rank(sp, owner) + (int)(col - (j0 + (int64_t)owner * chunk)) * kNBMax;
+            if (rank == 0 && tid < jb) s_tmp[tid] = crow[tid];
+            cluster.sync();
+            if (rank == 0 && tid < jb) {
+                crow[tid] = prow[tid];
+                prow[tid] = s_tmp[tid];
+            }
+            // parts outside the panel, in global memory (rank 0)
+            if (rank == 0) {
+                for (int64_t j = tid; j < n; j += kClThreads) {
+                    if (j >= j0 && j < j0 + jb) continue;
+                    int32_t t = a[col * n + j];
+                    a[col * n + j] = a[piv * n + j];
+                    a[piv * n + j] = t;
+                }
+                if (tid == 0 && perm) {
+                    int32_t *pm = perm + (int64_t)w * n;
+                    int32_t t = pm[col];
+                    pm[col] = pm[piv];
+                    pm[piv] = t;
+                }
+            }
+            neg ^= 1;
+            cluster.sync();
+        }
+        // pivot row -> local copy
+        {
+            const int32_t *crow = cluster.map_shared_rank(sp, owner) + (int)(col - (j0 + (int64_t)owner * chunk)) * kNBMax;
+            if (tid < jb) s_u[tid] = crow[tid];
+        }
+        __syncthreads();
+        const int32_t pv = s_u[c];
+        if (tid == 0) s_inv = inv_bal32(pv, M.p);
+        det = det_mul(det, pv, M);
+        __syncthreads();
+        const int32_t inv = s_inv;
+        // scale column c of the rows below the pivot
+        for (int r = tid; r < nloc; r += kClThreads)
+            if (rbeg + r > col) sp[r * kNBMax + c] = mul_bal(sp[r * kNBMax + c], inv, M);
+        __syncthreads();
+        const int wdt = jb - c - 1;
+        if (wdt > 0) {
+            for (int e = tid; e < nloc * wdt; e += kClThreads) {
+                int r = e / wdt, j = c + 1 + e % wdt;
+                if (rbeg + r <= col) continue;
+                int32_t l = sp[r * kNBMax + c];
+                sp[r * kNBMax + j] = red_bal((int64_t)sp[r * kNBMax + j] - (int64_t)l * s_u[j], M);
+            }
+        }
+        __syncthreads();
+    }
+    cluster.sync();  // no CTA leaves while others may still read its block
+    if (dead) {
+        if (rank == 0 && tid == 0) {
+            LUState s = st[w];
+            s.dead = 1;
+            s.det = 0;
+            st[w] = s;
+        }
+        return;
+    }
+    for (int e = tid; e < nloc * jb; e += kClThreads) {
+        int r = e / jb, j = e % jb;
+        a[(rbeg + r) * n + j0 + j] = sp[r * kNBMax + j];
+    }
+    if (rank == 0 && tid == 0) {
         LUState s = st[w];
         s.det = det;
         s.neg = neg;
@@ -382,8 +544,9 @@ int trsm_lower(const int32_t *Lm, int64_t sL, int32_t *X, int64_t sX, int64_t n,
                int64_t lr0, int64_t xr0, int jb, int64_t c0, int64_t ncols,
                const ModP *mods, const LUState *st, int W, cudaStream_t s) {
     if (ncols <= 0) return IDET_OK;
-    dim3 grid((unsigned)((ncols + 127) / 128), W);
-    k_trsm_lower<WIDE><<<grid, 128, 0, s>>>(Lm, sL, X, sX, n, lr0, xr0, jb, c0, ncols,
+    // narrow blocks: a TRSM row block has few columns per prime
+    dim3 grid((unsigned)((ncols + 31) / 32), W);
+    k_trsm_lower<WIDE><<<grid, 32, 0, s>>>(Lm, sL, X, sX, n, lr0, xr0, jb, c0, ncols,
                                              mods, st);
     count_launch();
     IDET_CUDA_TRY(cudaGetLastError());
@@ -395,10 +558,19 @@ int lu_blocked(int32_t *R, int64_t n, const ModP *mods, int W, int nb, int32_t *
                LUState *st, cudaStream_t s) {
     k_state_init<<<W, 256, 0, s>>>(st, mods, W, perm, n);
     count_launch();
+    IDET_CUDA_TRY(cudaFuncSetAttribute(k_panel_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024));
     const int64_t nn = n * n;
     for (int64_t j0 = 0; j0 < n; j0 += nb) {
         const int jb = (int)((n - j0) < nb ? (n - j0) : nb);
-        k_panel<<<W, kPanelThreads, 0, s>>>(R, n, j0, jb, mods, st, perm);
+        const int chunk = (int)((n - j0 + kCl - 1) / kCl);
+        const size_t psmem = sizeof(int32_t) * (size_t)chunk * kNBMax;
+        if (psmem <= 200 * 1024) {
+            k_panel_cluster<<<W * kCl, kClThreads, psmem, s>>>(R, n, j0, jb, chunk, mods, st,
+                                                               perm);
+        } else {
+            k_panel<<<W, kPanelThreads, 0, s>>>(R, n, j0, jb, mods, st, perm);
+        }
         count_launch();
         IDET_CUDA_TRY(cudaGetLastError());
         const int64_t rest = n - j0 - jb;
@@ -475,11 +647,11 @@ int lu_inverse(const int32_t *R, const int32_t *perm, int64_t n, const ModP &mod
     for (int64_t bi = nblk - 1; bi >= 0; --bi) {
         const int64_t k0 = bi * nb;
         const int kb = (int)((n - k0) < nb ? (n - k0) : nb);
-        dim3 grid((unsigned)((n + 127) / 128));
+        dim3 grid((unsigned)((n + 31) / 32));
         if (wide)
-            k_trsm_upper<true><<<grid, 128, 0, s>>>(R, n, k0, Y, k0, kb, n, mod_host);
+            k_trsm_upper<true><<<grid, 32, 0, s>>>(R, n, k0, Y, k0, kb, n, mod_host);
         else
-            k_trsm_upper<false><<<grid, 128, 0, s>>>(R, n, k0, Y, k0, kb, n, mod_host);
+            k_trsm_upper<false><<<grid, 32, 0, s>>>(R, n, k0, Y, k0, kb, n, mod_host);
         count_launch();
         IDET_CUDA_TRY(cudaGetLastError());
         if (k0 > 0) {

@@ -65,10 +65,24 @@ __global__ void k_row_stats(const int64_t *__restrict__ A, int64_t n, int64_t ld
             m = s_max[k] > m ? s_max[k] : m;
         }
         // Upper bound: every product and addition above is rounded to
-        // nearest, relative error < (n + 2) 2^-53 < 2^-40 for n < 2^12.
-        rowsq[i] = t * (1.0 + 0x1p-30);
+        // nearest, relative error < (n + 2) 2^-53 < 2^-30 for n < 2^20.
+        rowsq[i] = t * (1.0 + 0x1p-30);  // upward margin >> rounding error
         atomicMax(amax, m);
     }
+}
+
+// Column sums of squares (double, same upward margin as the rows): one
+// thread per column, rows streamed (coalesced across the warp).
+__global__ void k_col_stats(const int64_t *__restrict__ A, int64_t n, int64_t lda,
+                            double *__restrict__ colsq) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double acc = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double d = (double)A[i * lda + j];
+        acc += d * d;
+    }
+    colsq[j] = acc * (1.0 + 0x1p-30);
 }
 
 __global__ void k_to_int32(const int64_t *__restrict__ A, int64_t n, int64_t lda,
@@ -79,6 +93,17 @@ __global__ void k_to_int32(const int64_t *__restrict__ A, int64_t n, int64_t lda
          e += stride) {
         int64_t i = e / n, j = e - i * n;
         A32[e] = (int32_t)A[i * lda + j];
+    }
+}
+
+template <class T>
+__global__ void k_narrow(const int64_t *__restrict__ A, int64_t n, int64_t lda, T *__restrict__ out,
+                         int64_t ldo) {
+    const int64_t total = n * ldo;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+        int64_t i = e / ldo, j = e - i * ldo;
+        out[e] = j < n ? (T)A[i * lda + j] : (T)0;
     }
 }
 
@@ -100,9 +125,30 @@ int launch_row_stats(const int64_t *A, int64_t n, int64_t lda, double *rowsq,
     return IDET_OK;
 }
 
+int launch_col_stats(const int64_t *A, int64_t n, int64_t lda, double *colsq, cudaStream_t s) {
+    k_col_stats<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(A, n, lda, colsq);
+    count_launch();
+    IDET_CUDA_TRY(cudaGetLastError());
+    return IDET_OK;
+}
+
 int launch_to_int32(const int64_t *A, int64_t n, int64_t lda, int32_t *A32,
                     cudaStream_t s) {
     k_to_int32<<<grid_for(n * n), kThreads, 0, s>>>(A, n, lda, A32);
+    count_launch();
+    IDET_CUDA_TRY(cudaGetLastError());
+    return IDET_OK;
+}
+
+int launch_narrow(const int64_t *A, int64_t n, int64_t lda, void *out, int64_t ldo, int bytes,
+                  cudaStream_t s) {
+    const int g = grid_for(n * ldo);
+    if (bytes == 1)
+        k_narrow<int8_t><<<g, kThreads, 0, s>>>(A, n, lda, (int8_t *)out, ldo);
+    else if (bytes == 2)
+        k_narrow<int16_t><<<g, kThreads, 0, s>>>(A, n, lda, (int16_t *)out, ldo);
+    else
+        k_narrow<int32_t><<<g, kThreads, 0, s>>>(A, n, lda, (int32_t *)out, ldo);
     count_launch();
     IDET_CUDA_TRY(cudaGetLastError());
     return IDET_OK;

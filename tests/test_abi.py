@@ -22,8 +22,12 @@ def test_header_declares_the_boundary():
 
 
 def test_library_exports_every_declared_symbol():
-    from paper_cs_0511066_b300.build import build
-    lib = ctypes.CDLL(build())
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "_idet_build", os.path.join(ROOT, "paper_cs_0511066_b300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    lib = ctypes.CDLL(mod.build())
     missing = [n for n in declared_functions() if not hasattr(lib, n)]
     assert not missing, missing
 

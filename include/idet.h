@@ -179,6 +179,33 @@ int idet_crt_symmetric(const uint32_t *residues, const uint32_t *primes,
                        int32_t count, void *stream, idet_int *r,
                        int32_t *trailing);
 
+/*
+ * det(A) mod p_k for small matrices WITHOUT allocating device memory. The
+ * paper has no counterpart: this serves callers that cannot call cudaMalloc
+ * or any allocator -- for instance code that runs where a framework owns all
+ * device memory through its own pool, or a context that forbids allocation
+ * while it is being set up. The result equals idet_det_mod_primes on the
+ * same arguments.
+ *
+ * Limits: 1 <= n <= 128, 1 <= nprimes <= 32, |a_ij| < 2^62; primes as for
+ * idet_det_mod_primes (each a prime in (2^20, 2^21) or (2^30, 2^31)); sizes
+ * beyond the limits return IDET_ERR_ARG with a message. A (n x n, leading
+ * dimension lda) is host memory when on_device = 0, device memory when 1;
+ * primes and det_mod are host arrays of nprimes entries.
+ *
+ * Scratch: a fixed area of about 2.2 MiB that lives in the library image as
+ * a __device__ array; every GPU that loads the library holds it until the
+ * process exits. The first call on a device looks up the area's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture. All calls share the one area and it keeps
+ * the last call's contents (each call writes everything it reads): calls
+ * whose GPU work overlaps -- on different streams or host threads -- race
+ * and must be serialised by the caller. The call is synchronous.
+ */
+int idet_det_mod_primes_noalloc(const int64_t *A, int64_t n, int64_t lda,
+                                int32_t on_device, const uint32_t *primes,
+                                int32_t nprimes, void *stream, uint32_t *det_mod);
+
 #ifdef __cplusplus
 }
 #endif

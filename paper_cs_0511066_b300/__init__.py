@@ -292,6 +292,20 @@ def crt_symmetric(residues, primes, *, stream=None):
     return v, int(tr.value)
 
 
+_lib.idet_det_mod_primes_noalloc.argtypes = [_P, _i64, _i64, _i32, _P, _i32, _P, _P]
+
+
+def det_mod_primes_noalloc(A, primes, *, stream=None) -> np.ndarray:
+    """det(A) mod p_k through idet_det_mod_primes_noalloc: no device memory is
+    allocated (n <= 128, at most 32 primes); see include/idet.h."""
+    ptr, n, lda, dev, keep = _matrix(A)
+    pr = np.ascontiguousarray(np.asarray(primes, dtype=np.uint32))
+    out = np.zeros(len(pr), dtype=np.uint32)
+    _check(_lib.idet_det_mod_primes_noalloc(ptr, n, lda, dev, pr.ctypes.data, len(pr),
+                                            _stream_ptr(stream), out.ctypes.data))
+    return out
+
+
 def launch_count() -> int:
     return int(_lib.idet_launch_count())
 

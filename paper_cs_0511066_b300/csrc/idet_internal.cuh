@@ -221,3 +221,9 @@ int launch_radix_to_binary(const uint32_t *dig, int len, uint32_t p, uint32_t *o
                            int32_t *out_len, cudaStream_t s);
 
 }  // namespace idet
+
+namespace idet {
+// Whole-matrix LU (n <= 192) writing only into the given buffers.
+int lu_small_into(int32_t *R, int n, const ModP *mods_dev, int W, LUState *st,
+                  uint32_t *det_out, cudaStream_t s);
+}  // namespace idet

@@ -667,3 +667,27 @@ int lu_inverse(const int32_t *R, const int32_t *perm, int64_t n, const ModP &mod
 }
 
 }  // namespace idet
+
+namespace idet {
+
+// Whole-matrix LU for n <= 192 into caller-provided buffers (no workspace):
+// R holds W residue matrices (n x n), st W states, det_out W residues.
+int lu_small_into(int32_t *R, int n, const ModP *mods_dev, int W, LUState *st,
+                  uint32_t *det_out, cudaStream_t s) {
+    if (n < 1 || n > kSmallN || W < 1) {
+        set_last_error("lu_small_into: n must be in [1, %d]", kSmallN);
+        return IDET_ERR_ARG;
+    }
+    const size_t smem = sizeof(int32_t) * (size_t)n * n;
+    IDET_CUDA_TRY(cudaFuncSetAttribute(k_lu_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(int32_t) * kSmallN * kSmallN)));
+    k_lu_small<<<W, 512, smem, s>>>(R, n, mods_dev, st, nullptr);
+    count_launch();
+    IDET_CUDA_TRY(cudaGetLastError());
+    k_finalize_det<<<(W + 127) / 128, 128, 0, s>>>(st, mods_dev, W, det_out);
+    count_launch();
+    IDET_CUDA_TRY(cudaGetLastError());
+    return IDET_OK;
+}
+
+}  // namespace idet

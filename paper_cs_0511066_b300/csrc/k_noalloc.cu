@@ -1,0 +1,122 @@
+// det(A) mod p_k for small matrices without any device memory allocation.
+//
+// Some callers cannot allocate device memory: code running inside a CUDA
+// graph capture that forbids allocation nodes, plugins hosted by a framework
+// that owns all device memory through its own pool, or processes whose
+// allocator is locked down for determinism. This entry point serves them by
+// using a fixed scratch area that lives in the library image itself: a
+// file-scope __device__ array, present on every GPU that loads the library
+// until the process exits. It has no counterpart in the paper; it is the
+// same computation as idet_det_mod_primes restricted to small sizes.
+//
+// Limits: n <= kMaxN = 128 and at most kMaxW = 32 primes per call, so the
+// scratch is 32 * 128 * 128 * 4 bytes of residues (2 MiB) plus the staged
+// matrix (128 KiB) and per-prime parameters.
+//
+// In host code the array's name only stands for it; the device address is
+// obtained once per device with cudaGetSymbolAddress, with that device
+// current, by the first call made on it.
+#include <cstring>
+#include <mutex>
+
+#include "idet_internal.cuh"
+
+namespace idet {
+
+namespace {
+
+constexpr int kMaxN = 128;
+constexpr int kMaxW = 32;
+constexpr size_t kResBytes = sizeof(int32_t) * kMaxW * kMaxN * kMaxN;
+constexpr size_t kMatBytes = sizeof(int64_t) * kMaxN * kMaxN;
+constexpr size_t kModOff = kResBytes + kMatBytes;
+constexpr size_t kStateOff = kModOff + 1024;
+constexpr size_t kDetOff = kStateOff + 1024;
+constexpr size_t kScratchBytes = kDetOff + 1024;
+static_assert(sizeof(ModP) * kMaxW <= 1024, "parameter area");
+static_assert(sizeof(LUState) * kMaxW <= 1024, "state area");
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+unsigned char *g_addr[kMaxDevices] = {};
+
+// Device address of the scratch on the current device (set up on first use).
+int scratch_address(unsigned char **out) {
+    int dev = 0;
+    IDET_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_last_error("device ordinal %d out of range", dev);
+        return IDET_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            set_last_error("cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+            return IDET_ERR_CUDA;
+        }
+        g_addr[dev] = (unsigned char *)p;
+    }
+    *out = g_addr[dev];
+    return IDET_OK;
+}
+
+bool prime_ok(uint32_t p) {
+    if (!(p & 1)) return false;
+    const bool narrow = p > (1u << 20) && p < (1u << 21);
+    const bool wide = p > (1u << 30) && p < (1u << 31);
+    if (!narrow && !wide) return false;
+    for (uint32_t d = 3; (uint64_t)d * d <= p; d += 2)
+        if (p % d == 0) return false;
+    return true;
+}
+
+}  // namespace
+
+}  // namespace idet
+
+using namespace idet;
+
+extern "C" int idet_det_mod_primes_noalloc(const int64_t *A, int64_t n, int64_t lda,
+                                           int32_t on_device, const uint32_t *primes,
+                                           int32_t nprimes, void *stream, uint32_t *det_mod) {
+    if (n < 1 || n > kMaxN || lda < n || !A || !primes || !det_mod || nprimes < 1 ||
+        nprimes > kMaxW) {
+        set_last_error("idet_det_mod_primes_noalloc: need 1 <= n <= %d, 1 <= nprimes <= %d, "
+                       "lda >= n and non-null pointers",
+                       kMaxN, kMaxW);
+        return IDET_ERR_ARG;
+    }
+    ModP mods[kMaxW];
+    for (int i = 0; i < nprimes; ++i) {
+        if (!prime_ok(primes[i])) {
+            set_last_error("primes must be primes in (2^20, 2^21) or (2^30, 2^31)");
+            return IDET_ERR_ARG;
+        }
+        mods[i] = make_mod(primes[i]);
+    }
+    unsigned char *base = nullptr;
+    IDET_TRY(scratch_address(&base));
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t *R = (int32_t *)base;
+    int64_t *Ad = (int64_t *)(base + kResBytes);
+    ModP *md = (ModP *)(base + kModOff);
+    LUState *st = (LUState *)(base + kStateOff);
+    uint32_t *dd = (uint32_t *)(base + kDetOff);
+    // stage A (compact, ld = n) and the prime parameters; every scratch byte
+    // read below is written first in this call
+    IDET_CUDA_TRY(cudaMemcpy2DAsync(Ad, sizeof(int64_t) * n, A, sizeof(int64_t) * lda,
+                                    sizeof(int64_t) * n, n,
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                    s));
+    IDET_CUDA_TRY(cudaMemcpyAsync(md, mods, sizeof(ModP) * nprimes, cudaMemcpyHostToDevice, s));
+    IDET_TRY(launch_reduce(Ad, n, n, md, nprimes, R, s));
+    IDET_TRY(lu_small_into(R, (int)n, md, nprimes, st, dd, s));
+    IDET_CUDA_TRY(cudaMemcpyAsync(det_mod, dd, sizeof(uint32_t) * nprimes, cudaMemcpyDeviceToHost,
+                                  s));
+    IDET_CUDA_TRY(cudaStreamSynchronize(s));
+    return IDET_OK;
+}

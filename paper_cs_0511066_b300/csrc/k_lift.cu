@@ -8,14 +8,19 @@
 // with C = A^{-1} mod p precomputed from the LU of A mod p. Each iteration is
 // two matrix-vector products separated by grid-wide barriers.
 //
-// Layout: one CTA per SM (32 warps, one row per warp at a time); CTA b owns a
-// contiguous block of rows of C and A.
-// As many of its rows as fit are copied to shared memory once and stay there
-// for all m iterations; the rest are streamed from global memory (L2 when
-// the streamed part fits in it). A is stored in the narrowest of
+// Layout and schedule. One CTA per SM owns a contiguous block of rows of C
+// and of A. As many of those rows as fit stay in shared memory for the whole
+// launch ("resident"); the others are streamed every iteration. Streaming is
+// warp-specialised: warp 31 of each CTA is a producer that copies streamed
+// rows with bulk asynchronous copies (cp.async.bulk) into a ring of shared
+// memory slots guarded by full/empty mbarriers; warps 0..30 consume resident
+// rows and ring slots. The streamed data does not depend on the iteration's
+// vector, so the producer runs ahead across phases and across the grid
+// barriers, keeping memory busy while the consumers wait. The vector operand
+// (r mod p, pre-split into 16-bit halves, then x) is staged in shared memory
+// at the start of each phase. A is stored in the narrowest of
 // int8/int16/int32 that holds its entries; rows are zero padded to a
-// multiple of 16 elements. The vector operand (r mod p, then x) is staged in
-// shared memory at the start of each phase.
+// multiple of 16 elements.
 //
 // Exactness:
 //  * x_i: |C_jk| < 2^30 and r mod p is split as hi * 2^16 + lo with
@@ -25,7 +30,12 @@
 //    |r_i|/p + n ||A|| < 2^62, equal to (r_i - A x_i) p^{-1} modulo 2^64; so
 //    products and sums are taken modulo 2^64 (wrapping) and multiplied by
 //    the inverse of p modulo 2^64 (exact division).
+//
+// Every wait is bounded (about two seconds of SM clock): a grid barrier or an
+// mbarrier that does not complete sets err, all warps leave, and the
+// producer first waits for the copies it has issued.
 #include <algorithm>
+#include <cstdlib>
 
 #include "idet_internal.cuh"
 
@@ -34,36 +44,135 @@ namespace idet {
 namespace {
 
 constexpr int kLiftThreads = 1024;
-constexpr int kLiftWarps = kLiftThreads / 32;
-constexpr long long kSpinLimit = 1ll << 26;
+constexpr int kConsumers = 31;  // warps 0..30
+constexpr int kConsThreads = kConsumers * 32;
+constexpr int kProducer = 31;   // warp 31
+constexpr int kRingMax = 8;
+constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
 
 struct GridBar {
     unsigned int count;  // arrivals, monotone within one launch
-    int err;
-    int pad[2];
+    int err;             // first failure: 1 grid barrier, 2 mbarrier time limit
+    int info[6];         // where it happened: block, warp, seq, slot, parity, it
 };
 
-// Grid-wide barrier: the b-th barrier of the launch completes when
-// count reaches b * gridDim.x. Bounded wait: after kSpinLimit polls the
-// block records err = 1 and every block leaves at its next barrier.
+// Record the first failure only.
+__device__ __forceinline__ void fail_once(GridBar *gb, int code, int warp, long long seq, int slot,
+                                          unsigned par, int it) {
+    if (atomicCAS(&gb->err, 0, code) == 0) {
+        gb->info[0] = blockIdx.x;
+        gb->info[1] = warp;
+        gb->info[2] = (int)seq;
+        gb->info[3] = slot;
+        gb->info[4] = (int)par;
+        gb->info[5] = it;
+    }
+}
+
+struct LiftGeom {
+    int64_t ld;   // padded row length (multiple of 16)
+    int64_t rpc;  // rows per CTA
+    int cC, cA;   // rows of C / A resident in shared memory per CTA
+    int S;        // ring slots (0: no streaming)
+    int pad;
+};
+
+__device__ __forceinline__ void cons_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kConsThreads) : "memory");
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Wait for the completion of the phase of parity `parity`; false after the
+// time limit or when another block has recorded an error.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, GridBar *gb,
+                                          long long seq = -1, int slot = -1, int it = -1) {
+    const uint32_t addr = smem_u32(bar);
+    const long long t0 = clock64();
+    for (unsigned i = 0;; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((i & 255) == 255) {
+            if (*((volatile int *)&gb->err)) return false;
+            if (clock64() - t0 > kWaitCycles) {
+                fail_once(gb, 2, threadIdx.x >> 5, seq, slot, parity, it);
+                return false;
+            }
+        }
+    }
+}
+
+// Wait until the producer has issued sequence number seq. An mbarrier parity
+// wait only tells the current phase from the previous one, so a consumer may
+// wait on a slot's barrier only once the copy it needs has been issued (the
+// slot's barrier is then at most one phase away from it).
+__device__ __forceinline__ bool wait_issued(const volatile unsigned int *issued, long long seq,
+                                            GridBar *gb, int slot, int it) {
+    const long long t0 = clock64();
+    for (unsigned i = 0; (long long)*issued <= seq; ++i) {
+        if ((i & 255) == 255) {
+            if (*((volatile int *)&gb->err)) return false;
+            if (clock64() - t0 > kWaitCycles) {
+                fail_once(gb, 4, threadIdx.x >> 5, seq, slot, 0, it);
+                return false;
+            }
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Grid-wide barrier among the consumer warps of all CTAs: the b-th barrier
+// completes when count reaches b * gridDim.x.
 __device__ __forceinline__ bool grid_sync(GridBar *gb, unsigned target) {
-    __syncthreads();
+    cons_sync();
     if (threadIdx.x == 0) {
         __threadfence();
         atomicAdd(&gb->count, 1u);
         volatile unsigned int *vc = &gb->count;
         volatile int *ve = &gb->err;
-        long long spins = 0;
+        const long long t0 = clock64();
         while (*vc < target) {
             if (*ve) break;
-            if (++spins > kSpinLimit) {
-                atomicExch(&gb->err, 1);
+            if (clock64() - t0 > kWaitCycles) {
+                fail_once(gb, 1, 0, target, -1, 0, -1);
                 break;
             }
         }
         __threadfence();
     }
-    __syncthreads();
+    cons_sync();
     return *((volatile int *)&gb->err) == 0;
 }
 
@@ -85,25 +194,16 @@ template <> struct Quad<int32_t> {
     using V = int4;
 };
 
-struct LiftGeom {
-    int64_t ld;   // padded row length (multiple of 16)
-    int64_t rpc;  // rows per CTA
-    int cC, cA;   // rows of C / A kept in shared memory per CTA
-};
-
-// Row products, one warp per row. The vector operand is staged in shared
-// memory once per phase; for the x phase it is pre-split into
-// lo = (r mod p) & 0xffff and hi = (r mod p) >> 16 so that the inner loop is
-// two 32x32->64-bit multiply-adds per element.
-template <bool SMEM>
+// x phase: sum_k C[row][k] v[k] mod p; the row is in shared memory and v is
+// staged as 16-bit halves lo, hi (two 32x32->64 multiply-adds per element).
 __device__ __forceinline__ int32_t dot_c(const int4 *__restrict__ crow,
                                          const int4 *__restrict__ vlo,
                                          const int4 *__restrict__ vhi, int64_t nq, int lane,
                                          const ModP &M) {
     int64_t lo = 0, hi = 0;
-#pragma unroll 8
+#pragma unroll 4
     for (int64_t q = lane; q < nq; q += 32) {
-        const int4 c = SMEM ? crow[q] : __ldg(crow + q);
+        const int4 c = crow[q];
         const int4 l = vlo[q], h = vhi[q];
         lo += (int64_t)c.x * l.x;
         lo += (int64_t)c.y * l.y;
@@ -119,13 +219,14 @@ __device__ __forceinline__ int32_t dot_c(const int4 *__restrict__ crow,
     return red_bal((int64_t)red_bal(hi, M) * 65536 + red_bal(lo, M), M);
 }
 
-template <class TA, bool SMEM>
+// r phase: sum_k A[row][k] x[k] modulo 2^64; the row is in shared memory.
+template <class TA>
 __device__ __forceinline__ uint64_t dot_a(const typename Quad<TA>::V *__restrict__ arow,
                                           const int4 *__restrict__ v, int64_t nq, int lane) {
     uint64_t acc = 0;
-#pragma unroll 8
+#pragma unroll 4
     for (int64_t q = lane; q < nq; q += 32) {
-        const typename Quad<TA>::V a = SMEM ? arow[q] : __ldg(arow + q);
+        const typename Quad<TA>::V a = arow[q];
         const int4 x = v[q];
         acc += (uint64_t)((int64_t)a.x * x.x);
         acc += (uint64_t)((int64_t)a.y * x.y);
@@ -139,23 +240,37 @@ template <class TA>
 __global__ void __launch_bounds__(kLiftThreads, 1)
 k_lift(LiftArgs a, const TA *__restrict__ Anar, LiftGeom g, int32_t *__restrict__ rm,
        int32_t *__restrict__ xcur, GridBar *gb) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[kRingMax], empty[kRingMax];
+    __shared__ int64_t s_z[kConsumers];
+    __shared__ volatile unsigned int s_issued;  // copies issued so far
+    using V = typename Quad<TA>::V;
     const int64_t n = a.n, ld = g.ld, nq = ld / 4;
     const ModP M = a.mod;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t r0 = (int64_t)blockIdx.x * g.rpc;
     const int64_t r1 = min(n, r0 + g.rpc);
     const int nrows = r1 > r0 ? (int)(r1 - r0) : 0;
-    int4 *vlo = reinterpret_cast<int4 *>(smem);                          // ld int32
-    int4 *vhi = reinterpret_cast<int4 *>(smem + 4 * ld);                 // ld int32
-    int32_t *cC = reinterpret_cast<int32_t *>(smem + 8 * ld);            // g.cC rows
-    TA *cA = reinterpret_cast<TA *>(smem + 8 * ld + 4 * ld * g.cC);      // g.cA rows
-    __shared__ int64_t s_z[kLiftWarps];
-    unsigned bar = 0;
-    const unsigned G = gridDim.x;
+    const int64_t slotB = 4 * ld;
+    int4 *vlo = reinterpret_cast<int4 *>(smem);
+    int4 *vhi = reinterpret_cast<int4 *>(smem + 4 * ld);
+    unsigned char *ring = smem + 8 * ld;
+    int32_t *cC = reinterpret_cast<int32_t *>(ring + g.S * slotB);
+    TA *cA = reinterpret_cast<TA *>(ring + g.S * slotB + 4 * ld * g.cC);
     const int kc = min(g.cC, nrows), ka = min(g.cA, nrows);
+    const int nsC = nrows - kc, nsA = nrows - ka;  // streamed rows per phase
+    const int per_it = nsC + nsA;
+    const unsigned G = gridDim.x;
 
-    // resident rows
+    if (tid == 0) {
+        s_issued = 0;
+        for (int s = 0; s < g.S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // resident rows (all warps)
     {
         const int4 *src = reinterpret_cast<const int4 *>(a.Cinv + r0 * ld);
         int4 *dst = reinterpret_cast<int4 *>(cC);
@@ -165,63 +280,141 @@ k_lift(LiftArgs a, const TA *__restrict__ Anar, LiftGeom g, int32_t *__restrict_
         const int64_t qa = ld * (int64_t)sizeof(TA) / 16;
         for (int64_t e = tid; e < (int64_t)ka * qa; e += kLiftThreads) dstA[e] = __ldg(srcA + e);
     }
-    for (int64_t i = r0 + tid; i < r1; i += kLiftThreads) {
+    __syncthreads();
+
+    if (warp == kProducer) {
+        // ---- producer: stream rows kc.. of C and ka.. of A, every iteration
+        if (lane == 0 && per_it > 0 && g.S > 0) {
+            long long seq = 0;
+            bool ok = true;
+            for (int it = 0; it < a.m && ok; ++it) {
+                for (int k = 0; k < per_it; ++k, ++seq) {
+                    const int slot = (int)(seq % g.S);
+                    const unsigned par = (unsigned)((seq / g.S) & 1) ^ 1u;
+                    if (!mbar_wait(&empty[slot], par, gb, seq, slot, it)) {
+                        ok = false;
+                        break;
+                    }
+                    const void *src;
+                    unsigned bytes;
+                    if (k < nsC) {
+                        src = a.Cinv + (r0 + kc + k) * ld;
+                        bytes = (unsigned)(4 * ld);
+                    } else {
+                        src = Anar + (r0 + ka + (k - nsC)) * ld;
+                        bytes = (unsigned)(sizeof(TA) * ld);
+                    }
+                    mbar_expect_tx(&full[slot], bytes);
+                    bulk_g2s(ring + slot * slotB, src, bytes, &full[slot]);
+                    s_issued = (unsigned int)(seq + 1);
+                }
+            }
+            // no copy may be in flight when the CTA exits: wait for the last
+            // phase of every slot that was used
+            for (int s = 0; s < g.S && s < seq; ++s) {
+                const long long q = seq - 1 - ((seq - 1 - s) % g.S);
+                const uint32_t addr = smem_u32(&full[s]);
+                const unsigned par = (unsigned)((q / g.S) & 1);
+                const long long t0 = clock64();
+                while (true) {
+                    uint32_t done;
+                    asm volatile(
+                        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                        "selp.u32 %0, 1, 0, p;\n}\n"
+                        : "=r"(done)
+                        : "r"(addr), "r"(par)
+                        : "memory");
+                    if (done || clock64() - t0 > kWaitCycles) break;
+                }
+            }
+        }
+        return;
+    }
+
+    // ---- consumers (warps 0..30)
+    for (int64_t i = r0 + tid; i < r1; i += kConsThreads) {
         int64_t bi = a.b[i];
         a.r[i] = bi;
         rm[i] = red_bal(bi, M);
     }
+    unsigned bar = 0;
     if (!grid_sync(gb, (++bar) * G)) return;
+    long long seq_base = 0;
+    bool fail = false;
 
-    using V = typename Quad<TA>::V;
     for (int it = 0; it < a.m; ++it) {
         // Phase 1: x = C (r mod p) mod p on this CTA's rows.
         {
             const int4 *src = reinterpret_cast<const int4 *>(rm);
-            for (int64_t q = tid; q < nq; q += kLiftThreads) {
+            for (int64_t q = tid; q < nq; q += kConsThreads) {
                 const int4 v = __ldcg(src + q);
                 vlo[q] = make_int4(v.x & 0xffff, v.y & 0xffff, v.z & 0xffff, v.w & 0xffff);
                 vhi[q] = make_int4(v.x >> 16, v.y >> 16, v.z >> 16, v.w >> 16);
             }
         }
-        __syncthreads();
+        cons_sync();
         int64_t zpart = 0;
-        for (int lr = warp; lr < nrows; lr += kLiftWarps) {
+        for (int lr = warp; lr < nrows; lr += kConsumers) {
             const int64_t row = r0 + lr;
-            const int32_t x =
-                lr < kc ? dot_c<true>(reinterpret_cast<const int4 *>(cC + (int64_t)lr * ld), vlo,
-                                      vhi, nq, lane, M)
-                        : dot_c<false>(reinterpret_cast<const int4 *>(a.Cinv + row * ld), vlo,
-                                       vhi, nq, lane, M);
+            int32_t x = 0;
+            if (lr < kc) {
+                x = dot_c(reinterpret_cast<const int4 *>(cC + (int64_t)lr * ld), vlo, vhi, nq,
+                          lane, M);
+            } else {
+                const long long seq = seq_base + (lr - kc);
+                const int slot = (int)(seq % g.S);
+                if (!wait_issued(&s_issued, seq, gb, slot, it) ||
+                    !mbar_wait(&full[slot], (unsigned)((seq / g.S) & 1), gb, seq, slot, it)) {
+                    fail = true;
+                    break;
+                }
+                x = dot_c(reinterpret_cast<const int4 *>(ring + slot * slotB), vlo, vhi, nq, lane,
+                          M);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
+            }
             if (lane == 0) {
                 xcur[row] = x;
                 if (a.digits) a.digits[(int64_t)it * n + row] = x;
                 if (a.u) zpart += (int64_t)a.u[row] * x;
             }
         }
+        seq_base += nsC;
         if (a.zproj) {
             if (lane == 0) s_z[warp] = zpart;
-            __syncthreads();
+            cons_sync();
             if (tid == 0) {
                 int64_t t = 0;
-                for (int k = 0; k < kLiftWarps; ++k) t += s_z[k];
+                for (int k = 0; k < kConsumers; ++k) t += s_z[k];
                 if (t) atomicAdd((unsigned long long *)&a.zproj[it], (unsigned long long)t);
             }
         }
+        if (fail) fail_once(gb, 3, 0, -1, -1, 0, it);
         if (!grid_sync(gb, (++bar) * G)) return;
 
         // Phase 2: r <- (r - A x) / p on this CTA's rows.
         {
             const int4 *src = reinterpret_cast<const int4 *>(xcur);
-            for (int64_t q = tid; q < nq; q += kLiftThreads) vlo[q] = __ldcg(src + q);
+            for (int64_t q = tid; q < nq; q += kConsThreads) vlo[q] = __ldcg(src + q);
         }
-        __syncthreads();
-        for (int lr = warp; lr < nrows; lr += kLiftWarps) {
+        cons_sync();
+        for (int lr = warp; lr < nrows; lr += kConsumers) {
             const int64_t row = r0 + lr;
-            const uint64_t acc =
-                lr < ka ? dot_a<TA, true>(reinterpret_cast<const V *>(cA + (int64_t)lr * ld), vlo,
-                                          nq, lane)
-                        : dot_a<TA, false>(reinterpret_cast<const V *>(Anar + row * ld), vlo, nq,
-                                           lane);
+            uint64_t acc = 0;
+            if (lr < ka) {
+                acc = dot_a<TA>(reinterpret_cast<const V *>(cA + (int64_t)lr * ld), vlo, nq, lane);
+            } else {
+                const long long seq = seq_base + (lr - ka);
+                const int slot = (int)(seq % g.S);
+                if (!wait_issued(&s_issued, seq, gb, slot, it) ||
+                    !mbar_wait(&full[slot], (unsigned)((seq / g.S) & 1), gb, seq, slot, it)) {
+                    fail = true;
+                    break;
+                }
+                acc = dot_a<TA>(reinterpret_cast<const V *>(ring + slot * slotB), vlo, nq, lane);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
+            }
             if (lane == 0) {
                 uint64_t diff = (uint64_t)__ldcg(a.r + row) - acc;
                 int64_t rn = (int64_t)(diff * a.pinv);
@@ -229,6 +422,8 @@ k_lift(LiftArgs a, const TA *__restrict__ Anar, LiftGeom g, int32_t *__restrict_
                 rm[row] = red_bal(rn, M);
             }
         }
+        seq_base += nsA;
+        if (fail) fail_once(gb, 3, 0, -1, -1, 0, it);
         if (!grid_sync(gb, (++bar) * G)) return;
     }
 }
@@ -253,21 +448,39 @@ int launch_lift_t(const LiftArgs &a0, const void *Anar, int64_t ld, Workspace &w
     IDET_CUDA_TRY(cudaGetDevice(&dev));
     IDET_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     IDET_CUDA_TRY(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    // CTAs: one per SM, but no more than needed for one warp per row.
-    int64_t G = sms;
-    const int64_t need = (n + kLiftWarps - 1) / kLiftWarps;
-    if (G > need) G = need < 1 ? 1 : need;
-    LiftGeom g;
-    g.ld = ld;
-    g.rpc = (n + G - 1) / G;
-    const int64_t budget = (int64_t)smem_max - 8 * ld - 2048;
     const int64_t crow = 4 * ld, arow = (int64_t)sizeof(TA) * ld;
-    const int64_t cC = budget > 0 ? std::min<int64_t>(g.rpc, budget / crow) : 0;
-    const int64_t rest = budget - cC * crow;
-    const int64_t cA = rest > 0 ? std::min<int64_t>(g.rpc, rest / arow) : 0;
-    g.cC = (int)cC;
-    g.cA = (int)cA;
-    const size_t smem = (size_t)(8 * ld + cC * crow + cA * arow);
+    const int64_t avail = (int64_t)smem_max - 8 * ld - 4096;
+    LiftGeom g{};
+    g.ld = ld;
+    // Fewest CTAs with one row per consumer warp, if everything then fits in
+    // shared memory (fewer CTAs make the grid barrier cheaper); otherwise all
+    // SMs, a ring of streaming slots, and as many resident rows as fit.
+    int64_t G = std::min<int64_t>(sms, (n + kConsumers - 1) / kConsumers);
+    if (G < 1) G = 1;
+    g.rpc = (n + G - 1) / G;
+    if (g.rpc * (crow + arow) <= avail) {
+        g.S = 0;
+        g.cC = (int)g.rpc;
+        g.cA = (int)g.rpc;
+    } else {
+        G = sms;
+        g.rpc = (n + G - 1) / G;
+        // ring depth: bytes in flight per SM; IDET_LIFT_SLOTS overrides (tuning)
+        int want = 8;
+        if (const char *e = getenv("IDET_LIFT_SLOTS")) want = atoi(e);
+        g.S = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)kRingMax, (int64_t)want,
+                                                           avail / crow}));
+        const int64_t left = avail - g.S * crow;
+        const int64_t cC = left > 0 ? std::min<int64_t>(g.rpc, left / crow) : 0;
+        const int64_t cA = std::min<int64_t>(g.rpc, std::max<int64_t>(0, left - cC * crow) / arow);
+        g.cC = (int)cC;
+        g.cA = (int)cA;
+        if (g.S * crow > avail) {
+            set_last_error("lift: a row does not fit in shared memory (n too large)");
+            return IDET_ERR_ARG;
+        }
+    }
+    const size_t smem = (size_t)(8 * ld + g.S * crow + (int64_t)g.cC * crow + (int64_t)g.cA * arow);
     IDET_CUDA_TRY(cudaFuncSetAttribute(k_lift<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
     int occ = 0;
@@ -295,12 +508,15 @@ int launch_lift_t(const LiftArgs &a0, const void *Anar, int64_t ld, Workspace &w
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
     }
-    int err = 0;
-    IDET_CUDA_TRY(cudaMemcpyAsync(&err, &gb->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GridBar hb{};
+    IDET_CUDA_TRY(cudaMemcpyAsync(&hb, gb, sizeof(GridBar), cudaMemcpyDeviceToHost, s));
     IDET_CUDA_TRY(cudaStreamSynchronize(s));
-    if (timed_out) *timed_out = err;
-    if (err) {
-        set_last_error("lift: a grid barrier wait exceeded its limit");
+    if (timed_out) *timed_out = hb.err;
+    if (hb.err) {
+        set_last_error("lift: a bounded wait gave up (code %d, block %d warp %d seq %d slot %d "
+                       "parity %d iteration %d; grid %d, S %d, cC %d, cA %d, rpc %d)",
+                       hb.err, hb.info[0], hb.info[1], hb.info[2], hb.info[3], hb.info[4],
+                       hb.info[5], (int)G, g.S, g.cC, g.cA, (int)g.rpc);
         return IDET_ERR_TIMEOUT;
     }
     return IDET_OK;

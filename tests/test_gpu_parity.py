@@ -165,3 +165,37 @@ def test_int_det_blocked_sizes():
         A = workloads.dense_uniform(n, -8, 8, n)
         want = exact.bareiss_det(A.tolist())
         assert idet.int_det(A) == want
+
+
+@pytest.mark.parametrize("n,lo,hi,m", [(1600, -(1 << 20), 1 << 20, 5), (2048, -100, 100, 4)])
+def test_dixon_lift_identity_streamed_rows(n, lo, hi, m):
+    """Sizes whose rows do not all fit in shared memory (the streamed path):
+    balanced digits and A X + p^m r_m = b exactly, X = sum_i x_i p^i; this
+    fixes every digit (X is the unique balanced p-adic truncation of
+    A^{-1} b)."""
+    A = workloads.dense_uniform(n, lo, hi, seed=n)
+    b = workloads.random_rhs(n, 1 << 40, seed=n + 1)
+    p = p31(1, n)[0]
+    dg, r = idet.dixon_digits(A, b, p, m)
+    assert np.abs(dg.astype(np.int64)).max() <= (p - 1) // 2
+    X = np.zeros(n, dtype=object)
+    for i in range(m - 1, -1, -1):
+        X = X * p + dg[i].astype(object)
+    lhs = A.astype(object).dot(X) + (p ** m) * r.astype(object)
+    assert (lhs == b.astype(object)).all()
+
+
+def test_dixon_lift_identity_streamed_n4000():
+    """n = 4000, int32 entries: part of every CTA's rows is streamed through
+    the bulk-copy ring each iteration."""
+    n, m = 4000, 3
+    A = workloads.dense_pm2p20(n, seed=2)
+    b = workloads.random_rhs(n, 1 << 40, seed=3)
+    p = 2147483629
+    dg, r = idet.dixon_digits(A, b, p, m)
+    assert np.abs(dg.astype(np.int64)).max() <= (p - 1) // 2
+    X = np.zeros(n, dtype=object)
+    for i in range(m - 1, -1, -1):
+        X = X * p + dg[i].astype(object)
+    lhs = A.astype(object).dot(X) + (p ** m) * r.astype(object)
+    assert (lhs == b.astype(object)).all()

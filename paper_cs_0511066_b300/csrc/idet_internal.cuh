@@ -171,6 +171,12 @@ int lu_inverse(const int32_t *R, const int32_t *perm, int64_t n,
                const ModP &mod_host, const ModP *mod_dev, bool wide, int nb,
                int32_t *Xinv, Workspace &ws);
 
+// k_gemm_tc.cu: C <- C - A B mod p on the tensor cores (21-bit primes,
+// K <= 32), path = IDET_PATH_I8, IDET_PATH_BF16 or IDET_PATH_F64.
+int gemm_sub_tc(int path, const int32_t *A, int64_t lda, int64_t sA, const int32_t *B, int64_t ldb,
+                int64_t sB, int32_t *C, int64_t ldc, int64_t sC, int M, int N, int K,
+                const ModP *mods, const LUState *st, int W, cudaStream_t s);
+
 // k_lift.cu ---------------------------------------------------------------
 struct LiftArgs {
     const int32_t *Cinv;   // A^{-1} mod p, balanced, n rows of ld entries

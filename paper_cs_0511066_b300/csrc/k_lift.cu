@@ -47,7 +47,7 @@ constexpr int kLiftThreads = 1024;
 constexpr int kConsumers = 31;  // warps 0..30
 constexpr int kConsThreads = kConsumers * 32;
 constexpr int kProducer = 31;   // warp 31
-constexpr int kRingMax = 8;
+constexpr int kRingMax = 16;
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
 
 struct GridBar {
@@ -74,7 +74,7 @@ struct LiftGeom {
     int64_t rpc;  // rows per CTA
     int cC, cA;   // rows of C / A resident in shared memory per CTA
     int S;        // ring slots (0: no streaming)
-    int pad;
+    int keep;     // streamed rows per iteration copied with an L2 evict_last hint
 };
 
 __device__ __forceinline__ void cons_sync() {
@@ -144,13 +144,26 @@ __device__ __forceinline__ bool wait_issued(const volatile unsigned int *issued,
     return true;
 }
 
+// Bulk copy global -> shared completing on an mbarrier, with an L2 policy.
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
-                                         uint64_t *bar) {
+                                         uint64_t *bar, uint64_t policy) {
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-            "r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+        "[%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
         : "memory");
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
 }
 
 // Grid-wide barrier among the consumer warps of all CTAs: the b-th barrier
@@ -285,6 +298,11 @@ k_lift(LiftArgs a, const TA *__restrict__ Anar, LiftGeom g, int32_t *__restrict_
     if (warp == kProducer) {
         // ---- producer: stream rows kc.. of C and ka.. of A, every iteration
         if (lane == 0 && per_it > 0 && g.S > 0) {
+            // The first g.keep streamed rows of every iteration are marked to
+            // stay in L2 (evict_last), the others to leave it first, so that a
+            // fixed subset of the streamed bytes is served by L2 each time
+            // instead of the whole set cycling through it.
+            const uint64_t pol_keep = policy_evict_last(), pol_pass = policy_evict_first();
             long long seq = 0;
             bool ok = true;
             for (int it = 0; it < a.m && ok; ++it) {
@@ -305,7 +323,8 @@ k_lift(LiftArgs a, const TA *__restrict__ Anar, LiftGeom g, int32_t *__restrict_
                         bytes = (unsigned)(sizeof(TA) * ld);
                     }
                     mbar_expect_tx(&full[slot], bytes);
-                    bulk_g2s(ring + slot * slotB, src, bytes, &full[slot]);
+                    bulk_g2s(ring + slot * slotB, src, bytes, &full[slot],
+                             k < g.keep ? pol_keep : pol_pass);
                     s_issued = (unsigned int)(seq + 1);
                 }
             }
@@ -479,6 +498,16 @@ int launch_lift_t(const LiftArgs &a0, const void *Anar, int64_t ld, Workspace &w
             set_last_error("lift: a row does not fit in shared memory (n too large)");
             return IDET_ERR_ARG;
         }
+    }
+    // L2 budget for the rows kept across iterations (IDET_LIFT_L2_MB, tuning)
+    {
+        double l2mb = 72.0;
+        if (const char *e = getenv("IDET_LIFT_L2_MB")) l2mb = atof(e);
+        const int64_t per_it = std::max<int64_t>(0, g.rpc - g.cC) + std::max<int64_t>(0, g.rpc - g.cA);
+        const double row_bytes = (double)(crow + arow) / 2;
+        const double total = (double)G * per_it * row_bytes;
+        const double frac = total > 0 ? std::min(1.0, l2mb * 1048576.0 / total) : 0.0;
+        g.keep = (int)(frac * per_it);
     }
     const size_t smem = (size_t)(8 * ld + g.S * crow + (int64_t)g.cC * crow + (int64_t)g.cA * arow);
     IDET_CUDA_TRY(cudaFuncSetAttribute(k_lift<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize,

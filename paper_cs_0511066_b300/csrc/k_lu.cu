@@ -553,33 +553,60 @@ int trsm_lower(const int32_t *Lm, int64_t sL, int32_t *X, int64_t sX, int64_t n,
     return IDET_OK;
 }
 
+// Two-level right-looking LU: block columns of NB = 128 (the trailing
+// update's K, so that the Schur complement is read and written once per 128
+// columns), each factored by 32-wide cluster panels with updates confined to
+// the block column; then U12 = L11^{-1} A12 by 32-row blocks and the rank-128
+// update A22 <- A22 - L21 U12.
 template <bool WIDE>
 int lu_blocked(int32_t *R, int64_t n, const ModP *mods, int W, int nb, int32_t *perm,
-               LUState *st, cudaStream_t s) {
+               LUState *st, cudaStream_t s, int path) {
     k_state_init<<<W, 256, 0, s>>>(st, mods, W, perm, n);
     count_launch();
     IDET_CUDA_TRY(cudaFuncSetAttribute(k_panel_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        200 * 1024));
     const int64_t nn = n * n;
-    for (int64_t j0 = 0; j0 < n; j0 += nb) {
-        const int jb = (int)((n - j0) < nb ? (n - j0) : nb);
-        const int chunk = (int)((n - j0 + kCl - 1) / kCl);
-        const size_t psmem = sizeof(int32_t) * (size_t)chunk * kNBMax;
-        if (psmem <= 200 * 1024) {
-            k_panel_cluster<<<W * kCl, kClThreads, psmem, s>>>(R, n, j0, jb, chunk, mods, st,
-                                                               perm);
-        } else {
-            k_panel<<<W, kPanelThreads, 0, s>>>(R, n, j0, jb, mods, st, perm);
+    const int NB = WIDE ? nb : 4 * nb;
+    auto upd = [&](int64_t r, int64_t c, int64_t kr, int M, int N, int K) -> int {
+        // C = R[r.., c..] -= R[r.., kr..kr+K) * R[kr..kr+K, c..]
+        if (M <= 0 || N <= 0 || K <= 0) return IDET_OK;
+        const int32_t *Ap = R + r * n + kr;
+        const int32_t *Bp = R + kr * n + c;
+        int32_t *Cp = R + r * n + c;
+        if (!WIDE && path != IDET_PATH_INT64)
+            return gemm_sub_tc(path, Ap, n, nn, Bp, n, nn, Cp, n, nn, M, N, K, mods, st, W, s);
+        return gemm_sub<WIDE>(Ap, n, nn, Bp, n, nn, Cp, n, nn, M, N, K, mods, st, W, s);
+    };
+    for (int64_t J0 = 0; J0 < n; J0 += NB) {
+        const int JB = (int)((n - J0) < NB ? (n - J0) : NB);
+        for (int64_t j0 = J0; j0 < J0 + JB; j0 += nb) {
+            const int jb = (int)((J0 + JB - j0) < nb ? (J0 + JB - j0) : nb);
+            const int chunk = (int)((n - j0 + kCl - 1) / kCl);
+            const size_t psmem = sizeof(int32_t) * (size_t)chunk * kNBMax;
+            if (psmem <= 200 * 1024) {
+                k_panel_cluster<<<W * kCl, kClThreads, psmem, s>>>(R, n, j0, jb, chunk, mods, st,
+                                                                   perm);
+            } else {
+                k_panel<<<W, kPanelThreads, 0, s>>>(R, n, j0, jb, mods, st, perm);
+            }
+            count_launch();
+            IDET_CUDA_TRY(cudaGetLastError());
+            const int64_t inner = J0 + JB - (j0 + jb);  // columns left in the block column
+            if (inner > 0) {
+                IDET_TRY(trsm_lower<WIDE>(R, nn, R, nn, n, j0, j0, jb, j0 + jb, inner, mods, st,
+                                          W, s));
+                IDET_TRY(upd(j0 + jb, j0 + jb, j0, (int)(n - j0 - jb), (int)inner, jb));
+            }
         }
-        count_launch();
-        IDET_CUDA_TRY(cudaGetLastError());
-        const int64_t rest = n - j0 - jb;
+        const int64_t rest = n - J0 - JB;
         if (rest <= 0) break;
-        IDET_TRY(trsm_lower<WIDE>(R, nn, R, nn, n, j0, j0, jb, j0 + jb, rest, mods, st,
-                                  W, s));
-        IDET_TRY(gemm_sub<WIDE>(R + (j0 + jb) * n + j0, n, nn, R + j0 * n + j0 + jb, n,
-                                nn, R + (j0 + jb) * n + j0 + jb, n, nn, (int)rest,
-                                (int)rest, jb, mods, st, W, s));
+        for (int64_t i0 = J0; i0 < J0 + JB; i0 += nb) {
+            const int ib = (int)((J0 + JB - i0) < nb ? (J0 + JB - i0) : nb);
+            IDET_TRY(trsm_lower<WIDE>(R, nn, R, nn, n, i0, i0, ib, J0 + JB, rest, mods, st, W, s));
+            const int64_t below = J0 + JB - (i0 + ib);
+            if (below > 0) IDET_TRY(upd(i0 + ib, J0 + JB, i0, (int)below, (int)rest, ib));
+        }
+        IDET_TRY(upd(J0 + JB, J0 + JB, J0, (int)rest, (int)rest, JB));
     }
     return IDET_OK;
 }
@@ -591,7 +618,6 @@ int lu_factor_batched(int32_t *R, int64_t n, const ModP *mods_dev,
                       int32_t *perm, uint32_t *det_out, int update_path,
                       Workspace &ws) {
     (void)mods_host;
-    (void)update_path;
     cudaStream_t s = ws.stream();
     if (W <= 0) return IDET_OK;
     LUState *st = nullptr;
@@ -606,9 +632,12 @@ int lu_factor_batched(int32_t *R, int64_t n, const ModP *mods_dev,
         count_launch();
         IDET_CUDA_TRY(cudaGetLastError());
     } else if (wide) {
-        IDET_TRY(lu_blocked<true>(R, n, mods_dev, W, nb, perm, st, s));
+        IDET_TRY(lu_blocked<true>(R, n, mods_dev, W, nb, perm, st, s, IDET_PATH_INT64));
     } else {
-        IDET_TRY(lu_blocked<false>(R, n, mods_dev, W, nb, perm, st, s));
+        // default trailing-update arithmetic for 21-bit primes
+        // (AUTO = int64 delayed reduction: fastest measured at n = 1000 and 4000)
+        const int path = update_path == IDET_PATH_AUTO ? IDET_PATH_INT64 : update_path;
+        IDET_TRY(lu_blocked<false>(R, n, mods_dev, W, nb, perm, st, s, path));
     }
     k_finalize_det<<<(W + 127) / 128, 128, 0, s>>>(st, mods_dev, W, det_out);
     count_launch();

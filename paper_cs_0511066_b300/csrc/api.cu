@@ -975,16 +975,176 @@ static int lif_common(DetJob &J, const int64_t *b_dev, const std::vector<int64_t
 int idet_largest_invariant_factor(const int64_t *A, int64_t n, int64_t lda, const int64_t *b,
                                   int32_t on_device, const idet_opts *opts, void *stream,
                                   idet_int *sout) {
-    (void)A;
-    (void)n;
-    (void)lda;
-    (void)b;
-    (void)on_device;
-    (void)opts;
-    (void)stream;
-    (void)sout;
-    set_last_error("not implemented yet");
-    return IDET_ERR_INTERNAL;
+    if (n < 0 || lda < n || (n > 0 && (!A || !b)) || !sout) {
+        set_last_error("invalid argument");
+        return IDET_ERR_ARG;
+    }
+    if (n == 0) {
+        uint32_t one = 1;
+        return write_int(sout, 1, &one, 1);
+    }
+    idet_opts o;
+    idet_default_opts(&o);
+    if (opts) o = *opts;
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace ws(s);
+    DevMatrix M;
+    IDET_TRY(stage_matrix(A, n, lda, on_device, ws, M));
+    DetJob J(M, ws, o);
+    IDET_TRY(J.stats());
+    if (J.log2H == -INFINITY) {
+        set_last_error("A is singular (zero row or column)");
+        return IDET_ERR_SINGULAR;
+    }
+    std::vector<int64_t> bh(n);
+    int64_t *bd = nullptr;
+    IDET_TRY(ws.alloc_n(&bd, n));
+    IDET_CUDA_TRY(cudaMemcpyAsync(bd, b, 8 * (size_t)n,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    IDET_CUDA_TRY(cudaMemcpyAsync(bh.data(), bd, 8 * (size_t)n, cudaMemcpyDeviceToHost, s));
+    IDET_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int64_t i = 0; i < n; ++i)
+        if (bh[i] >= (1ll << 62) || bh[i] <= -(1ll << 62)) {
+            set_last_error("right-hand side entries must satisfy |b_i| < 2^62");
+            return IDET_ERR_ARG;
+        }
+    // lift with the digits kept, and the projection u . x
+    SplitMix g(o.seed ^ 0x9a11ull);
+    std::vector<int32_t> uh(n);
+    double u1 = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        uh[i] = (int32_t)(g.next() & 0xffff);
+        u1 += uh[i];
+    }
+    int32_t *ud = nullptr;
+    IDET_TRY(ws.alloc_n(&ud, n));
+    IDET_CUDA_TRY(cudaMemcpyAsync(ud, uh.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s));
+    IDET_TRY(make_Anar(J.M, J.amax, ws, &J.Anar, &J.abytes, &J.ldl));
+    int32_t *Cinv = nullptr;
+    IDET_TRY(ws.alloc_n(&Cinv, (size_t)n * J.ldl));
+    SplitMix gp(o.seed ^ 0x11f7ull);
+    uint32_t p = 0;
+    int rc = IDET_ERR_SINGULAR;
+    for (int tries = 0; tries < 6 && rc == IDET_ERR_SINGULAR; ++tries) {
+        p = random_prime31(gp);
+        rc = inverse_mod_prime(J.M, p, J.nb, ws, Cinv, J.ldl);
+    }
+    if (rc == IDET_ERR_SINGULAR) {
+        set_last_error("A is singular (singular modulo 6 random 31-bit primes)");
+        return rc;
+    }
+    IDET_TRY(rc);
+    double bb = 1.0, lc = 0, lcmin = INFINITY;
+    for (int64_t i = 0; i < n; ++i) {
+        bb += (double)bh[i] * (double)bh[i];
+        double c = 0.5 * std::log2(std::max(J.colsq[i], 1.0));
+        lc += c;
+        lcmin = std::min(lcmin, c);
+    }
+    const double log2Ne = 0.5 * std::log2(bb * (1 + 1e-12)) + lc - lcmin;  // |N_j|
+    const double log2N = log2Ne + std::log2(std::max(u1, 1.0));             // |u . N|
+    const double lp = std::log2((double)p);
+    const int hN = (int)std::ceil((log2N + 1) / lp);
+    const int hNe = (int)std::ceil((log2Ne + 1) / lp);
+    const int hD = (int)std::ceil((J.log2H + 1) / lp);
+    const int m = hN + hD + 2;
+    int32_t *dig = nullptr;
+    int64_t *z = nullptr, *r = nullptr;
+    IDET_TRY(ws.alloc_n(&dig, (size_t)m * n));
+    IDET_TRY(ws.alloc_n(&z, m));
+    IDET_TRY(ws.alloc_n(&r, n));
+    LiftArgs la{};
+    la.Cinv = Cinv;
+    la.b = bd;
+    la.u = ud;
+    la.n = n;
+    la.m = m;
+    la.mod = make_mod(p);
+    la.pinv = inv_mod_2_64(p);
+    la.digits = dig;
+    la.zproj = z;
+    la.r = r;
+    int to = 0;
+    IDET_TRY(launch_lift(la, J.Anar, J.abytes, J.ldl, ws, &to));
+    // candidate D from the projection
+    const int dcap = hD + 4;
+    uint32_t *D = nullptr, *Dn = nullptr, *dj = nullptr, *cof = nullptr;
+    int32_t *info = nullptr, *flags = nullptr, *len = nullptr;
+    int64_t *zj = nullptr;
+    IDET_TRY(ws.alloc_n(&D, dcap));
+    IDET_TRY(ws.alloc_n(&Dn, dcap));
+    IDET_TRY(ws.alloc_n(&dj, dcap));
+    IDET_TRY(ws.alloc_n(&cof, dcap));
+    IDET_TRY(ws.alloc_n(&info, 4));
+    IDET_TRY(ws.alloc_n(&len, 1));
+    IDET_TRY(ws.alloc_n(&flags, n));
+    IDET_TRY(ws.alloc_n(&zj, m));
+    int32_t hi[2] = {0, 0};
+    IDET_TRY(launch_ratrecon(z, m, p, hN, hD, D, dcap, info, ws));
+    IDET_CUDA_TRY(cudaMemcpyAsync(hi, info, 8, cudaMemcpyDeviceToHost, s));
+    IDET_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hi[0] != 0) {
+        set_last_error("rational reconstruction of the projection failed (code %d)", hi[0]);
+        return IDET_ERR_INTERNAL;
+    }
+    int dlen = hi[1];
+    // every entry integral under D?  else D <- lcm(D, den(x_j))
+    std::vector<int32_t> fl(n);
+    for (int round = 0;; ++round) {
+        if (round > 64) {
+            set_last_error("largest invariant factor: too many denominator updates");
+            return IDET_ERR_INTERNAL;
+        }
+        IDET_TRY(launch_lif_check(dig, n, m, D, dlen, p, hNe, flags, s));
+        IDET_CUDA_TRY(cudaMemcpyAsync(fl.data(), flags, 4 * (size_t)n, cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        int64_t bad = -1;
+        for (int64_t j = 0; j < n && bad < 0; ++j)
+            if (fl[j]) bad = j;
+        if (bad < 0) break;
+        // d_j = den(x_j) by reconstruction of X_j
+        IDET_TRY(launch_gather_col(dig, n, m, bad, zj, s));
+        IDET_TRY(launch_ratrecon(zj, m, p, hNe, hD, dj, dcap, info, ws));
+        IDET_CUDA_TRY(cudaMemcpyAsync(hi, info, 8, cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hi[0] != 0) {
+            set_last_error("rational reconstruction of an entry failed (code %d)", hi[0]);
+            return IDET_ERR_INTERNAL;
+        }
+        const int djlen = hi[1];
+        // D / gcd(D, d_j): cofactor of d_j at the zero remainder of Euclid(D, d_j)
+        std::vector<uint32_t> djh(djlen);
+        IDET_CUDA_TRY(cudaMemcpyAsync(djh.data(), dj, 4 * (size_t)djlen, cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        std::vector<int64_t> djz(djh.begin(), djh.end());
+        IDET_CUDA_TRY(cudaMemcpyAsync(zj, djz.data(), 8 * (size_t)djlen, cudaMemcpyHostToDevice, s));
+        IDET_TRY(launch_ratrecon(zj, djlen, p, 0, dcap, cof, dcap, info, ws, D, dlen));
+        IDET_CUDA_TRY(cudaMemcpyAsync(hi, info, 8, cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hi[0] != 0) {
+            set_last_error("gcd of denominators failed (code %d)", hi[0]);
+            return IDET_ERR_INTERNAL;
+        }
+        IDET_TRY(launch_mul_radix(dj, djlen, cof, hi[1], p, Dn, dcap, len, s));
+        int32_t nl = 0;
+        IDET_CUDA_TRY(cudaMemcpyAsync(&nl, len, 4, cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        std::swap(D, Dn);
+        dlen = nl;
+    }
+    // D -> base 2^32
+    const int bcap = dlen + 2;
+    uint32_t *Db = nullptr;
+    IDET_TRY(ws.alloc_n(&Db, bcap));
+    IDET_TRY(launch_radix_to_binary(D, dlen, p, Db, bcap, len, s));
+    int32_t bl = 0;
+    IDET_CUDA_TRY(cudaMemcpyAsync(&bl, len, 4, cudaMemcpyDeviceToHost, s));
+    IDET_CUDA_TRY(cudaStreamSynchronize(s));
+    std::vector<uint32_t> host(bl > 0 ? bl : 1);
+    if (bl > 0)
+        IDET_CUDA_TRY(cudaMemcpyAsync(host.data(), Db, 4 * (size_t)bl, cudaMemcpyDeviceToHost, s));
+    IDET_CUDA_TRY(cudaStreamSynchronize(s));
+    return write_int(sout, 1, host.data(), (uint32_t)bl);
 }
 
 }  // extern "C"

@@ -220,8 +220,19 @@ int launch_mixed_to_int(const uint32_t *primes, const int32_t *digits,
 // (int64, m of them, |z_i| < 2^59): numerator below p^hN, denominator below
 // p^hD; den receives the denominator's base-p digits. info[0]: 0 ok,
 // 1 no fraction within the bounds, 2/4 capacity; info[1]: digits of den.
+// With ainit (alen digits) the first operand is ainit instead of p^m; with
+// hN = 0 the extended Euclid then runs to the zero remainder and den receives
+// |cofactor of b| = ainit / gcd(ainit, b).
 int launch_ratrecon(const int64_t *z, int m, uint32_t p, int hN, int hD, uint32_t *den,
-                    int den_cap, int32_t *info, Workspace &ws);
+                    int den_cap, int32_t *info, Workspace &ws, const uint32_t *ainit = nullptr,
+                    int alen = 0);
+// k_lif.cu: exact lcm of denominators (see there).
+int launch_lif_check(const int32_t *digits, int64_t n, int m, const uint32_t *D, int dlen,
+                     uint32_t p, int h, int32_t *flag, cudaStream_t s);
+int launch_mul_radix(const uint32_t *a, int la, const uint32_t *b, int lb, uint32_t p,
+                     uint32_t *out, int cap, int32_t *out_len, cudaStream_t s);
+int launch_gather_col(const int32_t *digits, int64_t n, int m, int64_t j, int64_t *z,
+                      cudaStream_t s);
 // Base-p digits -> base-2^32 limbs (out_len receives the limb count).
 int launch_radix_to_binary(const uint32_t *dig, int len, uint32_t p, uint32_t *out, int cap,
                            int32_t *out_len, cudaStream_t s);

@@ -396,7 +396,7 @@ __device__ void exact_step(const uint32_t *a, int la, const uint32_t *b, int lb,
 __global__ void __launch_bounds__(kRT)
 k_ratrecon(const int64_t *__restrict__ z, int m, uint32_t p, int hN, int hD,
            uint32_t *__restrict__ gbuf, int cap, uint32_t *__restrict__ den, int den_cap,
-           int32_t *__restrict__ info) {
+           int32_t *__restrict__ info, const uint32_t *__restrict__ ainit, int alen) {
     __shared__ RRShared S;
     extern __shared__ uint32_t dyn[];
     uint32_t *base = gbuf ? gbuf : dyn;
@@ -414,9 +414,14 @@ k_ratrecon(const int64_t *__restrict__ z, int m, uint32_t p, int hN, int hD,
         // b = X mod p^m with digits in [0, p); a = p^m; ta = 0, tb = 1
         int64_t carry = 0;
         for (int i = 0; i < m; ++i) b[i] = divmod_p(z[i] + carry, R, carry);
-        a[m] = 1;
+        if (ainit) {  // first operand given (hN = 0: full extended Euclid)
+            for (int i = 0; i < alen; ++i) a[i] = ainit[i];
+            S.la = trim(a, alen);
+        } else {
+            a[m] = 1;
+            S.la = m + 1;
+        }
         tb[0] = 1;
-        S.la = m + 1;
         S.lb = trim(b, m);
         S.lta = 0;
         S.ltb = 1;
@@ -649,9 +654,9 @@ int launch_mixed_to_int(const uint32_t *primes, const int32_t *digits, int count
 }
 
 int launch_ratrecon(const int64_t *z, int m, uint32_t p, int hN, int hD, uint32_t *den,
-                    int den_cap, int32_t *info, Workspace &ws) {
+                    int den_cap, int32_t *info, Workspace &ws, const uint32_t *ainit, int alen) {
     cudaStream_t s = ws.stream();
-    const int cap = m + 4;
+    const int cap = (m > alen ? m : alen) + 4;
     uint32_t *gbuf = nullptr;
     size_t smem = sizeof(uint32_t) * 4 * (size_t)cap;
     if (smem > 190 * 1024) {
@@ -662,7 +667,7 @@ int launch_ratrecon(const int64_t *z, int m, uint32_t p, int hN, int hD, uint32_
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem));
     }
-    k_ratrecon<<<1, kRT, smem, s>>>(z, m, p, hN, hD, gbuf, cap, den, den_cap, info);
+    k_ratrecon<<<1, kRT, smem, s>>>(z, m, p, hN, hD, gbuf, cap, den, den_cap, info, ainit, alen);
     count_launch();
     IDET_CUDA_TRY(cudaGetLastError());
     return IDET_OK;

@@ -234,3 +234,62 @@ def test_lu_factors_every_update_path(path):
 def test_int_det_every_update_path(path):
     A = workloads.dense_uniform(260, -50, 50, seed=33)
     assert idet.int_det(A, update_path=PATHS[path]) == exact.bareiss_det(A.tolist())
+
+
+# --- largest invariant factor (exact lcm of denominators) ----------------------------
+
+@pytest.mark.parametrize("n", [1, 5, 20, 64])
+def test_lif_matches_oracle_many_rhs(n):
+    A = workloads.dense_pm100(n, seed=40 + n)
+    for seed in range(6 if n < 64 else 2):
+        b = workloads.random_rhs(n, 1 << 20, seed=seed)
+        assert idet.largest_invariant_factor(A, b) == exact.largest_invariant_factor(A.tolist(), b.tolist())
+
+
+def test_lif_even_denominators():
+    """A with det divisible by 2^k: the lcm is even; random projections miss
+    the factor 2 about half of the time, so this exercises the entry-by-entry
+    completion of the denominator."""
+    n = 12
+    for seed in range(8):
+        A = workloads.dense_pm100(n, seed=70 + seed)
+        A[:, 0] *= 4
+        A[:, 1] *= 2
+        b = workloads.random_rhs(n, 1000, seed=seed)
+        assert idet.largest_invariant_factor(A, b) == exact.largest_invariant_factor(A.tolist(), b.tolist())
+
+
+def _unimodular(n, nops, seed):
+    r = random.Random(seed)
+    U = [[int(i == j) for j in range(n)] for i in range(n)]
+    for _ in range(nops):
+        i, j = r.sample(range(n), 2)
+        c = r.choice([-1, 1])
+        U[i] = [a + c * b for a, b in zip(U[i], U[j])]
+    return U
+
+
+@pytest.mark.parametrize("n", [8, 24])
+def test_lif_engineered_smith_gives_lcm_1_to_n(n):
+    U = _unimodular(n, 2 * n, n)
+    V = _unimodular(n, 2 * n, n + 1)
+    D = [[(i + 1) if i == j else 0 for j in range(n)] for i in range(n)]
+    A = np.array(exact.matmul(exact.matmul(U, D), V), dtype=np.int64)
+    b = np.array([sum(row) for row in U], dtype=np.int64)
+    want = 1
+    for k in range(1, n + 1):
+        want = want * k // math.gcd(want, k)
+    assert idet.largest_invariant_factor(A, b) == want
+
+
+def test_lif_device_inputs_and_singular():
+    torch = pytest.importorskip("torch")
+    A = workloads.dense_pm100(30, seed=5)
+    b = workloads.random_rhs(30, 1 << 30, seed=5)
+    want = exact.largest_invariant_factor(A.tolist(), b.tolist())
+    assert idet.largest_invariant_factor(torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda()) == want
+    S = A.copy()
+    S[3] = S[1] + S[2]
+    with pytest.raises(idet.IdetError) as e:
+        idet.largest_invariant_factor(S, b)
+    assert e.value.code == 3

@@ -180,6 +180,23 @@ int idet_crt_symmetric(const uint32_t *residues, const uint32_t *primes,
                        int32_t *trailing);
 
 /*
+ * det(A_i) for a batch of independent matrices of possibly different orders:
+ * the same method as idet_int_det (Alg. 4.1 with i_max = 1), with the
+ * batch's work fused across matrices -- the LUs of all (matrix, prime) pairs
+ * with n_i <= 192 in one launch, one launch for all the Dixon solves (one
+ * CTA per matrix), one for all reconstructions and one per round of Chinese
+ * remaindering -- in the spirit of Section 6's remark that the LUs of a CRA
+ * step and several p-adic liftings are independent and can run in parallel.
+ * A[i] (n[i] x n[i], leading dimension lda[i]) follow the conventions above;
+ * dets[i] receives det(A_i) (IDET_ERR_BUFFER if any dets[i].cap is too
+ * small: that entry's nlimbs is set and the call fails). stats (may be NULL)
+ * receives totals over the batch.
+ */
+int idet_int_det_batch(int32_t count, const int64_t *const *A, const int64_t *n,
+                       const int64_t *lda, int32_t on_device, const idet_opts *opts,
+                       void *stream, idet_int *dets, idet_stats *stats);
+
+/*
  * det(A) mod p_k for small matrices WITHOUT allocating device memory. The
  * paper has no counterpart: this serves callers that cannot call cudaMalloc
  * or any allocator -- for instance code that runs where a framework owns all

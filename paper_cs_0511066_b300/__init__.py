@@ -292,6 +292,38 @@ def crt_symmetric(residues, primes, *, stream=None):
     return v, int(tr.value)
 
 
+_lib.idet_int_det_batch.argtypes = [_i32, _P, _P, _P, _i32, ctypes.POINTER(idet_opts), _P, _P,
+                                    ctypes.POINTER(idet_stats)]
+
+
+def int_det_batch(mats, *, seed: int | None = None, update_path: int | None = None,
+                  stream=None, return_stats: bool = False):
+    """[det(A_i)] for a list of square matrices (numpy int64, or torch int64
+    CUDA tensors), through idet_int_det_batch."""
+    use_torch_allocator()
+    count = len(mats)
+    infos = [_matrix(A) for A in mats]
+    devs = {d for (_, _, _, d, _) in infos}
+    if len(devs) > 1:
+        raise ValueError("all matrices must be on the host or all on the device")
+    dev = devs.pop() if devs else 0
+    ptrs = (ctypes.c_void_p * max(count, 1))(*[p for (p, _, _, _, _) in infos])
+    ns = (ctypes.c_int64 * max(count, 1))(*[nn for (_, nn, _, _, _) in infos])
+    lds = (ctypes.c_int64 * max(count, 1))(*[ld for (_, _, ld, _, _) in infos])
+    caps = [max(64, int(nn * 40 // 32) + 64) for (_, nn, _, _, _) in infos]
+    bufs = [(ctypes.c_uint32 * c)() for c in caps]
+    outs = (idet_int * max(count, 1))()
+    for i in range(count):
+        outs[i] = idet_int(0, 0, caps[i], bufs[i])
+    o = default_opts(seed=seed, update_path=update_path)
+    st = idet_stats()
+    _check(_lib.idet_int_det_batch(count, ptrs, ns, lds, dev, ctypes.byref(o),
+                                   _stream_ptr(stream), outs, ctypes.byref(st)))
+    res = [_to_int(outs[i], bufs[i]) for i in range(count)]
+    del infos
+    return (res, st.as_dict()) if return_stats else res
+
+
 _lib.idet_det_mod_primes_noalloc.argtypes = [_P, _i64, _i64, _i32, _P, _i32, _P, _P]
 
 

@@ -34,7 +34,7 @@ static idet_free_fn g_free = nullptr;
 static void *g_actx = nullptr;
 
 Workspace::~Workspace() {
-    for (int i = n_ - 1; i >= 0; --i) {
+    for (size_t i = ptrs_.size(); i-- > 0;) {
         if (g_free)
             g_free(ptrs_[i], (void *)stream_, g_actx);
         else
@@ -43,10 +43,6 @@ Workspace::~Workspace() {
 }
 
 int Workspace::alloc(void **ptr, size_t bytes) {
-    if (n_ >= 256) {
-        set_last_error("workspace: too many allocations");
-        return IDET_ERR_INTERNAL;
-    }
     bytes = (bytes + 255) / 256 * 256;
     void *p = nullptr;
     if (g_alloc) {
@@ -59,7 +55,7 @@ int Workspace::alloc(void **ptr, size_t bytes) {
         set_last_error("workspace: could not allocate %zu bytes of device memory", bytes);
         return IDET_ERR_NOMEM;
     }
-    ptrs_[n_++] = p;
+    ptrs_.push_back(p);
     *ptr = p;
     return IDET_OK;
 }
@@ -283,6 +279,46 @@ struct Timer {
     }
 };
 
+// result = K * sum_{i<c} dig_i prod_{j<i} prs_j (K given as device limbs, or
+// null for K = 1), written to out.
+static int assemble_int(Workspace &ws, const std::vector<uint32_t> &prs,
+                        const std::vector<int32_t> &dig, int c, const uint32_t *Kdev, int Klen,
+                        idet_int *out) {
+        cudaStream_t s = ws.stream();
+        double bits = 64;
+        for (int i = 0; i < c; ++i) bits += std::log2((double)prs[i]);
+        const int cap = (int)(bits / 32) + Klen + 4;
+        uint32_t *dp = nullptr, *buf = nullptr;
+        int32_t *dg = nullptr, *info = nullptr;
+        IDET_TRY(ws.alloc_n(&dp, c + 1));
+        IDET_TRY(ws.alloc_n(&dg, c + 1));
+        IDET_TRY(ws.alloc_n(&buf, 2 * (size_t)cap));
+        IDET_TRY(ws.alloc_n(&info, 4));
+        uint32_t one = 1;
+        uint32_t *Kd = (uint32_t *)Kdev;
+        if (!Kd) {
+            IDET_TRY(ws.alloc_n(&Kd, 1));
+            IDET_CUDA_TRY(cudaMemcpyAsync(Kd, &one, 4, cudaMemcpyHostToDevice, s));
+            Klen = 1;
+        }
+        IDET_CUDA_TRY(cudaMemcpyAsync(dp, prs.data(), 4 * c, cudaMemcpyHostToDevice, s));
+        IDET_CUDA_TRY(cudaMemcpyAsync(dg, dig.data(), 4 * c, cudaMemcpyHostToDevice, s));
+        IDET_TRY(launch_mixed_to_int(dp, dg, c, Kd, Klen, buf, cap, info, s));
+        int32_t hinfo[3];
+        IDET_CUDA_TRY(cudaMemcpyAsync(hinfo, info, 12, cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hinfo[2]) {
+            set_last_error("reconstruction buffer too small");
+            return IDET_ERR_INTERNAL;
+        }
+        std::vector<uint32_t> host(hinfo[1] > 0 ? hinfo[1] : 1);
+        if (hinfo[1] > 0)
+            IDET_CUDA_TRY(cudaMemcpyAsync(host.data(), buf, 4 * (size_t)hinfo[1],
+                                          cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        return write_int(out, hinfo[0], host.data(), (uint32_t)hinfo[1]);
+    }
+
 // Per-call state of the determinant computation.
 struct DetJob {
     DevMatrix M;
@@ -404,38 +440,7 @@ struct DetJob {
     // result = K * sum_{i<c} dig_i prod_{j<i} prs_j, K given as device limbs.
     int assemble(const std::vector<uint32_t> &prs, const std::vector<int32_t> &dig, int c,
                  const uint32_t *Kdev, int Klen, idet_int *out) {
-        double bits = 64;
-        for (int i = 0; i < c; ++i) bits += std::log2((double)prs[i]);
-        const int cap = (int)(bits / 32) + Klen + 4;
-        uint32_t *dp = nullptr, *buf = nullptr;
-        int32_t *dg = nullptr, *info = nullptr;
-        IDET_TRY(ws.alloc_n(&dp, c + 1));
-        IDET_TRY(ws.alloc_n(&dg, c + 1));
-        IDET_TRY(ws.alloc_n(&buf, 2 * (size_t)cap));
-        IDET_TRY(ws.alloc_n(&info, 4));
-        uint32_t one = 1;
-        uint32_t *Kd = (uint32_t *)Kdev;
-        if (!Kd) {
-            IDET_TRY(ws.alloc_n(&Kd, 1));
-            IDET_CUDA_TRY(cudaMemcpyAsync(Kd, &one, 4, cudaMemcpyHostToDevice, s));
-            Klen = 1;
-        }
-        IDET_CUDA_TRY(cudaMemcpyAsync(dp, prs.data(), 4 * c, cudaMemcpyHostToDevice, s));
-        IDET_CUDA_TRY(cudaMemcpyAsync(dg, dig.data(), 4 * c, cudaMemcpyHostToDevice, s));
-        IDET_TRY(launch_mixed_to_int(dp, dg, c, Kd, Klen, buf, cap, info, s));
-        int32_t hinfo[3];
-        IDET_CUDA_TRY(cudaMemcpyAsync(hinfo, info, 12, cudaMemcpyDeviceToHost, s));
-        IDET_CUDA_TRY(cudaStreamSynchronize(s));
-        if (hinfo[2]) {
-            set_last_error("reconstruction buffer too small");
-            return IDET_ERR_INTERNAL;
-        }
-        std::vector<uint32_t> host(hinfo[1] > 0 ? hinfo[1] : 1);
-        if (hinfo[1] > 0)
-            IDET_CUDA_TRY(cudaMemcpyAsync(host.data(), buf, 4 * (size_t)hinfo[1],
-                                          cudaMemcpyDeviceToHost, s));
-        IDET_CUDA_TRY(cudaStreamSynchronize(s));
-        return write_int(out, hinfo[0], host.data(), (uint32_t)hinfo[1]);
+        return assemble_int(ws, prs, dig, c, Kdev, Klen, out);
     }
 };
 
@@ -1145,6 +1150,513 @@ int idet_largest_invariant_factor(const int64_t *A, int64_t n, int64_t lda, cons
         IDET_CUDA_TRY(cudaMemcpyAsync(host.data(), Db, 4 * (size_t)bl, cudaMemcpyDeviceToHost, s));
     IDET_CUDA_TRY(cudaStreamSynchronize(s));
     return write_int(sout, 1, host.data(), (uint32_t)bl);
+}
+
+// ---------------------------------------------------------------------------
+// Batched determinants: Alg. 4.1 (i_max = 1) for many independent matrices,
+// advanced together phase by phase. The LUs of all (matrix, prime) pairs with
+// n <= 192 run in one launch (one CTA each), the lifts of all matrices in one
+// launch (one CTA each), and the reconstructions and Chinese remaindering of
+// all matrices in one launch each; larger matrices use the blocked LU.
+
+namespace {
+
+struct BItem {
+    DevMatrix M;
+    int64_t n = 0;
+    double log2H = 0;
+    std::vector<double> rowsq, colsq;
+    unsigned long long amax = 0;
+    double *d_rowsq = nullptr, *d_colsq = nullptr;
+    unsigned long long *d_amax = nullptr;
+    bool done = false;
+    int k0 = 0;
+    std::vector<uint32_t> dets;  // det mod P[0..dets.size())
+    // lift
+    uint32_t p = 0;
+    int m = 0, hN = 0, hD = 0;
+    int32_t *A32 = nullptr, *Cinv = nullptr;
+    int64_t ld4 = 0, *bd = nullptr, *z = nullptr, *r = nullptr;
+    int32_t *ud = nullptr;
+    uint32_t *den = nullptr, *Kbin = nullptr;
+    int32_t *info = nullptr;
+    int Klen = 0;
+    double log2K = 0;
+    bool have_K = false;
+};
+
+}  // namespace
+
+int idet_int_det_batch(int32_t count, const int64_t *const *A, const int64_t *n,
+                       const int64_t *lda, int32_t on_device, const idet_opts *opts, void *stream,
+                       idet_int *dets, idet_stats *stats) {
+    if (count < 0 || (count > 0 && (!A || !n || !lda || !dets))) {
+        set_last_error("invalid argument");
+        return IDET_ERR_ARG;
+    }
+    for (int i = 0; i < count; ++i)
+        if (n[i] < 0 || lda[i] < n[i] || (n[i] > 0 && !A[i])) {
+            set_last_error("invalid matrix %d", i);
+            return IDET_ERR_ARG;
+        }
+    const unsigned long long launches0 = g_launches;
+    idet_opts o;
+    idet_default_opts(&o);
+    if (opts) o = *opts;
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace ws(s);
+    Timer total(s);
+    idet_stats agg{};
+    const double log2l = 20.0;
+    const double pool = (double)pool21().size();
+    std::vector<BItem> it(count);
+    // stage and bound
+    for (int i = 0; i < count; ++i) {
+        BItem &b = it[i];
+        b.n = n[i];
+        if (b.n == 0) continue;
+        IDET_TRY(stage_matrix(A[i], b.n, lda[i], on_device, ws, b.M));
+        IDET_TRY(ws.alloc_n(&b.d_rowsq, b.n));
+        IDET_TRY(ws.alloc_n(&b.d_colsq, b.n));
+        IDET_TRY(ws.alloc_n(&b.d_amax, 1));
+        IDET_TRY(launch_row_stats(b.M.A, b.n, b.n, b.d_rowsq, b.d_amax, s));
+        IDET_TRY(launch_col_stats(b.M.A, b.n, b.n, b.d_colsq, s));
+    }
+    for (int i = 0; i < count; ++i) {
+        BItem &b = it[i];
+        if (b.n == 0) continue;
+        b.rowsq.resize(b.n);
+        b.colsq.resize(b.n);
+        IDET_CUDA_TRY(cudaMemcpyAsync(b.rowsq.data(), b.d_rowsq, 8 * b.n, cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaMemcpyAsync(b.colsq.data(), b.d_colsq, 8 * b.n, cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaMemcpyAsync(&b.amax, b.d_amax, 8, cudaMemcpyDeviceToHost, s));
+    }
+    IDET_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int i = 0; i < count; ++i) {
+        BItem &b = it[i];
+        if (b.n == 0) {
+            uint32_t one = 1;
+            IDET_TRY(write_int(&dets[i], 1, &one, 1));
+            b.done = true;
+            continue;
+        }
+        if (b.amax > 0x7fffffffull) {
+            set_last_error("matrix %d: entries must satisfy |a_ij| <= 2^31 - 1", i);
+            return IDET_ERR_ARG;
+        }
+        double hr = 0, hc = 0;
+        for (double v : b.rowsq) hr += v > 0 ? 0.5 * std::log2(v) : -INFINITY;
+        for (double v : b.colsq) hc += v > 0 ? 0.5 * std::log2(v) : -INFINITY;
+        b.log2H = std::min(hr, hc);
+        if (b.log2H == -INFINITY || b.amax == 0) {
+            IDET_TRY(write_int(&dets[i], 0, nullptr, 0));
+            b.done = true;
+            continue;
+        }
+        b.k0 = std::max(1, k_default(o.log2_epsilon, pool, b.log2H, log2l));
+    }
+    // shared random prime sequence (Alg. 2.1), parameters on the device
+    PrimeDraw draw(o.seed);
+    std::vector<uint32_t> P;
+    ModP *modsd = nullptr;
+    int mods_cap = 0;
+    auto ensure_primes = [&](int need) -> int {
+        if (need <= (int)P.size() && need <= mods_cap) return IDET_OK;
+        while ((int)P.size() < need) {
+            uint32_t q;
+            if (!draw.take(q)) {
+                set_last_error("prime pool exhausted");
+                return IDET_ERR_INTERNAL;
+            }
+            P.push_back(q);
+        }
+        const int cap = std::max(need, 2 * mods_cap);
+        while ((int)P.size() < cap) {
+            uint32_t q;
+            if (!draw.take(q)) break;
+            P.push_back(q);
+        }
+        std::vector<ModP> mh(P.size());
+        for (size_t k = 0; k < P.size(); ++k) mh[k] = make_mod(P[k]);
+        IDET_TRY(ws.alloc_n(&modsd, P.size()));
+        IDET_CUDA_TRY(cudaMemcpyAsync(modsd, mh.data(), sizeof(ModP) * P.size(),
+                                      cudaMemcpyHostToDevice, s));
+        mods_cap = (int)P.size();
+        return IDET_OK;
+    };
+    // det mod P[have .. need) for the listed items
+    auto factor = [&](const std::vector<std::pair<int, int>> &want) -> int {
+        Timer t(s);
+        std::vector<LUSmallJob> jobs;
+        std::vector<ElimJob> ejobs;
+        int maxn = 1, max_en = 1;
+        std::vector<uint32_t *> outs(count, nullptr);
+        for (auto &wi : want) {
+            BItem &b = it[wi.first];
+            const int have = (int)b.dets.size(), need = wi.second;
+            if (need <= have) continue;
+            IDET_TRY(ensure_primes(need));
+            const int W = need - have;
+            int32_t *R = nullptr;
+            uint32_t *dd = nullptr;
+            IDET_TRY(ws.alloc_n(&dd, W));
+            outs[wi.first] = dd;
+            agg.lu_macs += (2.0 / 3.0) * (double)b.n * b.n * b.n * W;
+            agg.primes_used += W;
+            if (b.n > 192 && elim_cluster_fits((int)b.n)) {
+                // one cluster per prime, reducing the int64 entries itself
+                for (int w = 0; w < W; ++w) {
+                    ElimJob e;
+                    e.A = b.M.A;
+                    e.lda = b.n;
+                    e.n = (int32_t)b.n;
+                    e.ld = (int32_t)b.n;
+                    e.mod = make_mod(P[have + w]);
+                    e.Cinv = nullptr;
+                    e.det = dd + w;
+                    ejobs.push_back(e);
+                }
+                max_en = std::max<int>(max_en, (int)b.n);
+                continue;
+            }
+            IDET_TRY(ws.alloc_n(&R, (size_t)W * b.n * b.n));
+            IDET_TRY(launch_reduce(b.M.A, b.n, b.n, modsd + have, W, R, s));
+            if (b.n <= 192) {
+                LUState *st = nullptr;
+                IDET_TRY(ws.alloc_n(&st, W));
+                for (int w = 0; w < W; ++w) {
+                    LUSmallJob j{};
+                    j.R = R + (int64_t)w * b.n * b.n;
+                    j.n = (int32_t)b.n;
+                    j.mod = make_mod(P[have + w]);
+                    j.st = st + w;
+                    j.det = dd + w;
+                    jobs.push_back(j);
+                }
+                maxn = std::max<int>(maxn, (int)b.n);
+            } else {
+                std::vector<ModP> mh(W);
+                for (int w = 0; w < W; ++w) mh[w] = make_mod(P[have + w]);
+                IDET_TRY(lu_factor_batched(R, b.n, modsd + have, mh.data(), W, false, o.nb, nullptr,
+                                           dd, o.update_path, ws));
+            }
+        }
+        if (!jobs.empty()) {
+            LUSmallJob *jd = nullptr;
+            IDET_TRY(ws.alloc_n(&jd, jobs.size()));
+            IDET_CUDA_TRY(cudaMemcpyAsync(jd, jobs.data(), sizeof(LUSmallJob) * jobs.size(),
+                                          cudaMemcpyHostToDevice, s));
+            IDET_TRY(lu_small_multi(jd, (int)jobs.size(), maxn, s));
+        }
+        if (!ejobs.empty()) {
+            ElimJob *ed = nullptr;
+            IDET_TRY(ws.alloc_n(&ed, ejobs.size()));
+            IDET_CUDA_TRY(cudaMemcpyAsync(ed, ejobs.data(), sizeof(ElimJob) * ejobs.size(),
+                                          cudaMemcpyHostToDevice, s));
+            IDET_TRY(launch_elim_cluster(ed, (int)ejobs.size(), max_en, 0, s));
+        }
+        for (auto &wi : want) {
+            BItem &b = it[wi.first];
+            const int have = (int)b.dets.size(), need = wi.second;
+            if (need <= have) continue;
+            b.dets.resize(need);
+            IDET_CUDA_TRY(cudaMemcpyAsync(b.dets.data() + have, outs[wi.first],
+                                          4 * (size_t)(need - have), cudaMemcpyDeviceToHost, s));
+        }
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        agg.ms_lu += t.stop();
+        return IDET_OK;
+    };
+    // Garner digits for each listed item: residues res[i] mod prs[i]
+    auto cra = [&](const std::vector<int> &ids, const std::vector<std::vector<uint32_t>> &prs,
+                   const std::vector<std::vector<uint32_t>> &res,
+                   std::vector<std::vector<int32_t>> &dig) -> int {
+        Timer t(s);
+        std::vector<CraJob> jobs(ids.size());
+        std::vector<int32_t *> dd(ids.size());
+        for (size_t q = 0; q < ids.size(); ++q) {
+            const int c = (int)prs[q].size();
+            uint32_t *dp = nullptr, *dr = nullptr;
+            IDET_TRY(ws.alloc_n(&dp, c + 1));
+            IDET_TRY(ws.alloc_n(&dr, c + 1));
+            IDET_TRY(ws.alloc_n(&dd[q], c + 1));
+            IDET_CUDA_TRY(cudaMemcpyAsync(dp, prs[q].data(), 4 * c, cudaMemcpyHostToDevice, s));
+            IDET_CUDA_TRY(cudaMemcpyAsync(dr, res[q].data(), 4 * c, cudaMemcpyHostToDevice, s));
+            jobs[q].primes = dp;
+            jobs[q].residues = dr;
+            jobs[q].digits = dd[q];
+            jobs[q].count = c;
+        }
+        CraJob *jd = nullptr;
+        IDET_TRY(ws.alloc_n(&jd, jobs.size() + 1));
+        IDET_CUDA_TRY(cudaMemcpyAsync(jd, jobs.data(), sizeof(CraJob) * jobs.size(),
+                                      cudaMemcpyHostToDevice, s));
+        IDET_TRY(launch_cra_multi(jd, (int)jobs.size(), s));
+        dig.assign(ids.size(), {});
+        for (size_t q = 0; q < ids.size(); ++q) {
+            dig[q].resize(prs[q].size());
+            IDET_CUDA_TRY(cudaMemcpyAsync(dig[q].data(), dd[q], 4 * prs[q].size(),
+                                          cudaMemcpyDeviceToHost, s));
+        }
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        agg.ms_cra += t.stop();
+        return IDET_OK;
+    };
+    auto assemble = [&](int i, const std::vector<uint32_t> &prs, const std::vector<int32_t> &dig,
+                        int c, const uint32_t *Kd, int Klen) -> int {
+        return assemble_int(ws, prs, dig, c, Kd, Klen, &dets[i]);
+    };
+
+    // Alg. 2.1 on det(A_i) for k0_i primes (Alg. 4.1, lines 1-4)
+    {
+        std::vector<std::pair<int, int>> want;
+        for (int i = 0; i < count; ++i)
+            if (!it[i].done) want.push_back({i, it[i].k0});
+        IDET_TRY(factor(want));
+        std::vector<int> ids;
+        std::vector<std::vector<uint32_t>> prs, res;
+        for (int i = 0; i < count; ++i)
+            if (!it[i].done) {
+                ids.push_back(i);
+                prs.push_back(std::vector<uint32_t>(P.begin(), P.begin() + it[i].dets.size()));
+                res.push_back(it[i].dets);
+            }
+        std::vector<std::vector<int32_t>> dig;
+        if (!ids.empty()) IDET_TRY(cra(ids, prs, res, dig));
+        for (size_t q = 0; q < ids.size(); ++q) {
+            int why = 0;
+            const int i = ids[q];
+            const int stop = CraScan::scan(dig[q], prs[q], it[i].log2H, o.log2_epsilon, log2l, pool,
+                                           o.certify != 0, &why);
+            if (stop >= 0) {
+                IDET_TRY(assemble(i, prs[q], dig[q], stop + 1, nullptr, 0));
+                it[i].done = true;
+            }
+        }
+    }
+    // one Dixon solve per remaining matrix, all in one launch
+    {
+        Timer t(s);
+        std::vector<int> ids;
+        for (int i = 0; i < count; ++i)
+            if (!it[i].done) ids.push_back(i);
+        SplitMix gp(o.seed ^ 0x11f7ull);
+        uint32_t p0 = random_prime31(gp);
+        std::vector<LiftJob> lj;
+        std::vector<RRJob> rj;
+        int max_ld = 4, max_m = 1;
+        // A_i^{-1} mod p0 for every matrix that fits a cluster, in one launch
+        std::vector<ElimJob> ej;
+        std::vector<int> ejid;
+        int max_en = 1;
+        uint32_t *eflag = nullptr;
+        IDET_TRY(ws.alloc_n(&eflag, std::max<size_t>(ids.size(), 1)));
+        for (int i : ids) {
+            BItem &b = it[i];
+            b.ld4 = (b.n + 3) / 4 * 4;
+            IDET_TRY(ws.alloc_n(&b.A32, (size_t)b.n * b.ld4));
+            IDET_TRY(ws.alloc_n(&b.Cinv, (size_t)b.n * b.ld4));
+            IDET_TRY(launch_narrow(b.M.A, b.n, b.n, b.A32, b.ld4, 4, s));
+            if (elim_cluster_fits((int)b.n)) {
+                ElimJob e;
+                e.A = b.M.A;
+                e.lda = b.n;
+                e.n = (int32_t)b.n;
+                e.ld = (int32_t)b.ld4;
+                e.mod = make_mod(p0);
+                e.Cinv = b.Cinv;
+                e.det = eflag + ej.size();
+                ej.push_back(e);
+                ejid.push_back(i);
+                max_en = std::max<int>(max_en, (int)b.n);
+            }
+        }
+        std::vector<uint32_t> einv(ids.size() + 1, 0);
+        if (!ej.empty()) {
+            ElimJob *ejd = nullptr;
+            IDET_TRY(ws.alloc_n(&ejd, ej.size()));
+            IDET_CUDA_TRY(cudaMemcpyAsync(ejd, ej.data(), sizeof(ElimJob) * ej.size(),
+                                          cudaMemcpyHostToDevice, s));
+            Timer ti(s);
+            IDET_TRY(launch_elim_cluster(ejd, (int)ej.size(), max_en, 1, s));
+            agg.ms_inverse += ti.stop();
+            IDET_CUDA_TRY(cudaMemcpyAsync(einv.data(), eflag, 4 * ej.size(), cudaMemcpyDeviceToHost, s));
+            IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+        std::vector<char> inv_ok(count, 0);
+        for (size_t q = 0; q < ej.size(); ++q) inv_ok[ejid[q]] = einv[q] != 0;
+        for (int i : ids) {
+            BItem &b = it[i];
+            uint32_t p = p0;
+            int rc = inv_ok[i] ? IDET_OK : IDET_ERR_SINGULAR;
+            if (!inv_ok[i] && elim_cluster_fits((int)b.n)) p = random_prime31(gp);
+            for (int tries = 0; tries < 6 && rc == IDET_ERR_SINGULAR; ++tries) {
+                rc = inverse_mod_prime(b.M, p, 32, ws, b.Cinv, b.ld4);
+                if (rc == IDET_ERR_SINGULAR) p = random_prime31(gp);
+            }
+            if (rc != IDET_OK) {
+                b.p = 0;  // no solve: the CRA alone finishes this matrix
+                continue;
+            }
+            b.p = p;
+            agg.lu_macs += 2.0 * (double)b.n * b.n * b.n;
+            // right-hand side and projection, bounds as in the single-matrix path
+            SplitMix g(o.seed ^ 0xb5ull ^ ((uint64_t)i << 20));
+            const double l2S = rhs_range_log2(b.n, b.log2H);
+            const uint64_t S = (uint64_t)std::exp2(std::floor(l2S));
+            std::vector<int64_t> bh(b.n);
+            std::vector<int32_t> uh(b.n);
+            double bb = 1.0, u1 = 0, lc = 0, lcmin = INFINITY;
+            for (int64_t k = 0; k < b.n; ++k) {
+                bh[k] = (int64_t)(g.below(S)) - (int64_t)(S / 2);
+                uh[k] = (int32_t)(g.next() & 0xffff);
+                bb += (double)bh[k] * (double)bh[k];
+                u1 += uh[k];
+                const double c = 0.5 * std::log2(std::max(b.colsq[k], 1.0));
+                lc += c;
+                lcmin = std::min(lcmin, c);
+            }
+            const double log2N = std::log2(std::max(u1, 1.0)) + 0.5 * std::log2(bb * (1 + 1e-12)) + lc - lcmin;
+            const double lp = std::log2((double)p);
+            b.hN = (int)std::ceil((log2N + 1) / lp);
+            b.hD = (int)std::ceil((b.log2H + 1) / lp);
+            b.m = b.hN + b.hD + 2;
+            IDET_TRY(ws.alloc_n(&b.bd, b.n));
+            IDET_TRY(ws.alloc_n(&b.ud, b.n));
+            IDET_TRY(ws.alloc_n(&b.z, b.m));
+            IDET_TRY(ws.alloc_n(&b.r, b.n));
+            IDET_TRY(ws.alloc_n(&b.den, b.hD + 4));
+            IDET_TRY(ws.alloc_n(&b.info, 4));
+            IDET_CUDA_TRY(cudaMemcpyAsync(b.bd, bh.data(), 8 * b.n, cudaMemcpyHostToDevice, s));
+            IDET_CUDA_TRY(cudaMemcpyAsync(b.ud, uh.data(), 4 * b.n, cudaMemcpyHostToDevice, s));
+            LiftJob j{};
+            j.A = b.A32;
+            j.C = b.Cinv;
+            j.b = b.bd;
+            j.u = b.ud;
+            j.r = b.r;
+            j.z = b.z;
+            j.n = (int32_t)b.n;
+            j.ld = (int32_t)b.ld4;
+            j.m = b.m;
+            j.mod = make_mod(p);
+            j.pinv = inv_mod_2_64(p);
+            lj.push_back(j);
+            RRJob q{};
+            q.z = b.z;
+            q.m = b.m;
+            q.hN = b.hN;
+            q.hD = b.hD;
+            q.den_cap = b.hD + 4;
+            q.den = b.den;
+            q.info = b.info;
+            q.p = p;
+            rj.push_back(q);
+            max_ld = std::max<int>(max_ld, (int)b.ld4);
+            max_m = std::max(max_m, b.m);
+            agg.lift_iters += b.m;
+            agg.lift_bytes += (double)b.m * 8.0 * b.n * b.n;
+        }
+        if (!lj.empty()) {
+            LiftJob *ljd = nullptr;
+            RRJob *rjd = nullptr;
+            IDET_TRY(ws.alloc_n(&ljd, lj.size()));
+            IDET_TRY(ws.alloc_n(&rjd, rj.size()));
+            IDET_CUDA_TRY(cudaMemcpyAsync(ljd, lj.data(), sizeof(LiftJob) * lj.size(),
+                                          cudaMemcpyHostToDevice, s));
+            IDET_CUDA_TRY(cudaMemcpyAsync(rjd, rj.data(), sizeof(RRJob) * rj.size(),
+                                          cudaMemcpyHostToDevice, s));
+            Timer tk(s);
+            IDET_TRY(launch_lift_multi(ljd, (int)lj.size(), max_ld, s));
+            agg.ms_lift_kernel += tk.stop();
+            Timer tr(s);
+            IDET_TRY(launch_ratrecon_multi(rjd, (int)rj.size(), max_m, s));
+            agg.ms_rr += tr.stop();
+        }
+        for (int i : ids) {
+            BItem &b = it[i];
+            if (!b.p) continue;
+            int32_t hi[2];
+            IDET_CUDA_TRY(cudaMemcpyAsync(hi, b.info, 8, cudaMemcpyDeviceToHost, s));
+            IDET_CUDA_TRY(cudaStreamSynchronize(s));
+            if (hi[0] != 0 || hi[1] <= 0) continue;  // no factor: K = 1
+            const int kd = hi[1];
+            std::vector<uint32_t> dh(kd);
+            IDET_CUDA_TRY(cudaMemcpyAsync(dh.data(), b.den, 4 * (size_t)kd, cudaMemcpyDeviceToHost, s));
+            int32_t *dl = nullptr;
+            IDET_TRY(ws.alloc_n(&b.Kbin, kd + 2));
+            IDET_TRY(ws.alloc_n(&dl, 1));
+            IDET_TRY(launch_radix_to_binary(b.den, kd, b.p, b.Kbin, kd + 2, dl, s));
+            IDET_CUDA_TRY(cudaMemcpyAsync(&b.Klen, dl, 4, cudaMemcpyDeviceToHost, s));
+            IDET_CUDA_TRY(cudaStreamSynchronize(s));
+            const double top = dh[kd - 1] + (kd > 1 ? dh[kd - 2] / (double)b.p : 0.0);
+            b.log2K = std::log2(top) + (kd - 1) * std::log2((double)b.p);
+            b.have_K = b.Klen > 0;
+        }
+        agg.ms_lift += t.stop();
+    }
+    // Alg. 2.1 on det(A_i)/K_i reusing the residues; more primes as needed
+    for (int round = 0;; ++round) {
+        std::vector<int> ids;
+        for (int i = 0; i < count; ++i)
+            if (!it[i].done) ids.push_back(i);
+        if (ids.empty()) break;
+        if (round > 4096) {
+            set_last_error("batched determinant did not terminate");
+            return IDET_ERR_INTERNAL;
+        }
+        std::vector<std::vector<uint32_t>> prs(ids.size()), res(ids.size());
+        for (size_t q = 0; q < ids.size(); ++q) {
+            BItem &b = it[ids[q]];
+            const int c = (int)b.dets.size();
+            if (b.have_K) {
+                uint32_t *dp = nullptr, *di = nullptr, *dout = nullptr;
+                int32_t *dsk = nullptr;
+                IDET_TRY(ws.alloc_n(&dp, c));
+                IDET_TRY(ws.alloc_n(&di, c));
+                IDET_TRY(ws.alloc_n(&dout, c));
+                IDET_TRY(ws.alloc_n(&dsk, c));
+                IDET_CUDA_TRY(cudaMemcpyAsync(dp, P.data(), 4 * c, cudaMemcpyHostToDevice, s));
+                IDET_CUDA_TRY(cudaMemcpyAsync(di, b.dets.data(), 4 * c, cudaMemcpyHostToDevice, s));
+                IDET_TRY(launch_div_by_K(b.Kbin, b.Klen, dp, di, dout, dsk, c, s));
+                std::vector<uint32_t> ho(c);
+                std::vector<int32_t> hs(c);
+                IDET_CUDA_TRY(cudaMemcpyAsync(ho.data(), dout, 4 * c, cudaMemcpyDeviceToHost, s));
+                IDET_CUDA_TRY(cudaMemcpyAsync(hs.data(), dsk, 4 * c, cudaMemcpyDeviceToHost, s));
+                IDET_CUDA_TRY(cudaStreamSynchronize(s));
+                for (int k = 0; k < c; ++k)
+                    if (!hs[k]) {
+                        prs[q].push_back(P[k]);
+                        res[q].push_back(ho[k]);
+                    }
+            } else {
+                prs[q].assign(P.begin(), P.begin() + c);
+                res[q] = b.dets;
+            }
+        }
+        std::vector<std::vector<int32_t>> dig;
+        IDET_TRY(cra(ids, prs, res, dig));
+        std::vector<std::pair<int, int>> more;
+        for (size_t q = 0; q < ids.size(); ++q) {
+            const int i = ids[q];
+            BItem &b = it[i];
+            int why = 0;
+            const double lh = b.have_K ? std::max(0.0, b.log2H - b.log2K) : b.log2H;
+            const int stop = CraScan::scan(dig[q], prs[q], lh, o.log2_epsilon, log2l, pool, false, &why);
+            if (stop >= 0) {
+                IDET_TRY(assemble(i, prs[q], dig[q], stop + 1, b.have_K ? b.Kbin : nullptr,
+                                  b.have_K ? b.Klen : 0));
+                b.done = true;
+            } else {
+                more.push_back({i, (int)b.dets.size() + std::max(4, b.k0 / 2)});
+            }
+        }
+        if (!more.empty()) IDET_TRY(factor(more));
+    }
+    agg.ms_total = total.stop();
+    agg.launches = g_launches - launches0;
+    if (stats) *stats = agg;
+    return IDET_OK;
 }
 
 }  // extern "C"

@@ -12,6 +12,8 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <vector>
+
 #include "../../include/idet.h"
 
 namespace idet {
@@ -120,8 +122,7 @@ class Workspace {
 
   private:
     cudaStream_t stream_;
-    void *ptrs_[256];
-    int n_ = 0;
+    std::vector<void *> ptrs_;
 };
 
 // Counter of kernel launches made by this library (for the benchmark's
@@ -157,6 +158,56 @@ struct LUState {
     int32_t dead;    // 1 once a column had no pivot: det = 0 mod p
     int32_t pad;
 };
+// A (matrix, prime) job of the batched small LU.
+struct LUSmallJob {
+    int32_t *R;      // n x n residues, ld n, factored in place
+    int32_t n, pad;
+    ModP mod;
+    LUState *st;
+    uint32_t *det;   // out: det mod p in [0, p)
+};
+// Batched whole-matrix LU in shared memory, one CTA per job (n <= 192).
+int lu_small_multi(const LUSmallJob *jobs_dev, int count, int max_n, cudaStream_t s);
+// Jobs of the batched Chinese remaindering and rational reconstruction.
+struct CraJob {
+    const uint32_t *primes, *residues;
+    int32_t *digits;
+    int32_t count, pad;
+};
+struct RRJob {
+    const int64_t *z;
+    int32_t m, hN, hD, den_cap;
+    uint32_t *den;
+    int32_t *info;
+    uint32_t p, pad;
+};
+int launch_cra_multi(const CraJob *jobs_dev, int count, cudaStream_t s);
+// k_batch.cu: one CTA per lifting job.
+struct LiftJob {
+    const int32_t *A, *C;   // n rows of ld int32 entries (zero padded)
+    const int64_t *b;
+    const int32_t *u;       // projection vector (may be null)
+    int64_t *r;             // out: r_m
+    int64_t *z;             // out: m projections u . x_i (may be null)
+    int32_t *digits;        // out: m x n digits (may be null)
+    int32_t n, ld, m, pad;
+    ModP mod;
+    uint64_t pinv;
+};
+int launch_lift_multi(const LiftJob *jobs_dev, int count, int max_ld, cudaStream_t s);
+// Whole-matrix elimination by an 8-CTA cluster per job: mode 0 det mod p,
+// mode 1 A^{-1} mod p (det = 1 on success, 0 if singular mod p).
+struct ElimJob {
+    const int64_t *A;     // n x n, leading dimension lda (int64 entries)
+    int64_t lda;
+    int32_t n, ld;        // ld: row length of Cinv (mode 1)
+    ModP mod;
+    int32_t *Cinv;        // mode 1 output
+    uint32_t *det;        // det mod p (mode 0) or invertibility flag (mode 1)
+};
+int launch_elim_cluster(const ElimJob *jobs_dev, int count, int max_n, int mode, cudaStream_t s);
+bool elim_cluster_fits(int n);
+int launch_ratrecon_multi(const RRJob *jobs_dev, int count, int max_m, cudaStream_t s);
 // Factor W residue matrices R[w] (n x n, ld n) in place: PA = LU mod p_w with
 // the first-nonzero pivot rule. perm (W*n, may be null) receives the row
 // permutation; det_out[w] = det mod p_w in [0, p_w). wide = the primes are

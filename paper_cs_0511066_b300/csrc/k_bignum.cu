@@ -34,9 +34,9 @@ __device__ __forceinline__ uint32_t mod_u64(uint64_t v, uint32_t p, uint64_t m) 
     return (uint32_t)(r >= p ? r - p : r);
 }
 
-__global__ void __launch_bounds__(kCraThreads)
-k_cra_append(const uint32_t *__restrict__ primes, const uint32_t *__restrict__ residues,
-             int32_t *__restrict__ digits, int start, int count) {
+__device__ void cra_append_body(const uint32_t *__restrict__ primes,
+                                const uint32_t *__restrict__ residues,
+                                int32_t *__restrict__ digits, int start, int count) {
     __shared__ uint32_t s_sum[kCraThreads];
     __shared__ uint32_t s_prod[kCraThreads];
     const int tid = threadIdx.x;
@@ -72,6 +72,18 @@ k_cra_append(const uint32_t *__restrict__ primes, const uint32_t *__restrict__ r
         }
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(kCraThreads)
+k_cra_append(const uint32_t *__restrict__ primes, const uint32_t *__restrict__ residues,
+             int32_t *__restrict__ digits, int start, int count) {
+    cra_append_body(primes, residues, digits, start, count);
+}
+
+// One CTA per job of a batch: digits of residues mod primes, from scratch.
+__global__ void __launch_bounds__(kCraThreads) k_cra_multi(const CraJob *__restrict__ jobs) {
+    const CraJob j = jobs[blockIdx.x];
+    cra_append_body(j.primes, j.residues, j.digits, 0, j.count);
 }
 
 // K mod p_k by Horner over the base-2^32 limbs, then d_k K^{-1}.
@@ -393,13 +405,11 @@ __device__ void exact_step(const uint32_t *a, int la, const uint32_t *b, int lb,
 // zdig: m base-p digits of X (any int64 < 2^59 each; normalised here).
 // buf: 4 * cap digits (a, b, ta, tb). On success info[0] = 0,
 // info[1] = digits of the denominator, written to den (base p).
-__global__ void __launch_bounds__(kRT)
-k_ratrecon(const int64_t *__restrict__ z, int m, uint32_t p, int hN, int hD,
-           uint32_t *__restrict__ gbuf, int cap, uint32_t *__restrict__ den, int den_cap,
-           int32_t *__restrict__ info, const uint32_t *__restrict__ ainit, int alen) {
+__device__ void ratrecon_body(const int64_t *__restrict__ z, int m, uint32_t p, int hN, int hD,
+                              uint32_t *__restrict__ base, int cap, uint32_t *__restrict__ den,
+                              int den_cap, int32_t *__restrict__ info,
+                              const uint32_t *__restrict__ ainit, int alen) {
     __shared__ RRShared S;
-    extern __shared__ uint32_t dyn[];
-    uint32_t *base = gbuf ? gbuf : dyn;
     uint32_t *a = base, *b = base + cap, *ta = base + 2 * cap, *tb = base + 3 * cap;
     const int tid = threadIdx.x;
     const Radix R = make_radix(p);
@@ -570,6 +580,21 @@ k_ratrecon(const int64_t *__restrict__ z, int m, uint32_t p, int hN, int hD,
     }
 }
 
+__global__ void __launch_bounds__(kRT)
+k_ratrecon(const int64_t *__restrict__ z, int m, uint32_t p, int hN, int hD,
+           uint32_t *__restrict__ gbuf, int cap, uint32_t *__restrict__ den, int den_cap,
+           int32_t *__restrict__ info, const uint32_t *__restrict__ ainit, int alen) {
+    extern __shared__ uint32_t dyn[];
+    ratrecon_body(z, m, p, hN, hD, gbuf ? gbuf : dyn, cap, den, den_cap, info, ainit, alen);
+}
+
+// One CTA per job of a batch (numbers in shared memory, 4 * cap digits).
+__global__ void __launch_bounds__(kRT) k_ratrecon_multi(const RRJob *__restrict__ jobs, int cap) {
+    extern __shared__ uint32_t dyn[];
+    const RRJob j = jobs[blockIdx.x];
+    ratrecon_body(j.z, j.m, j.p, j.hN, j.hD, dyn, cap, j.den, j.den_cap, j.info, nullptr, 0);
+}
+
 // Base-p digits (len of them) -> base-2^32 limbs, Horner on one CTA:
 // x <- x * p + d, from the top digit down. out has cap limbs.
 __global__ void __launch_bounds__(kRT)
@@ -668,6 +693,30 @@ int launch_ratrecon(const int64_t *z, int m, uint32_t p, int hN, int hD, uint32_
                                            (int)smem));
     }
     k_ratrecon<<<1, kRT, smem, s>>>(z, m, p, hN, hD, gbuf, cap, den, den_cap, info, ainit, alen);
+    count_launch();
+    IDET_CUDA_TRY(cudaGetLastError());
+    return IDET_OK;
+}
+
+int launch_ratrecon_multi(const RRJob *jobs_dev, int count, int max_m, cudaStream_t s) {
+    if (count <= 0) return IDET_OK;
+    const int cap = max_m + 4;
+    const size_t smem = sizeof(uint32_t) * 4 * (size_t)cap;
+    if (smem > 190 * 1024) {
+        set_last_error("batched reconstruction: lift too long");
+        return IDET_ERR_ARG;
+    }
+    IDET_CUDA_TRY(cudaFuncSetAttribute(k_ratrecon_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    k_ratrecon_multi<<<count, kRT, smem, s>>>(jobs_dev, cap);
+    count_launch();
+    IDET_CUDA_TRY(cudaGetLastError());
+    return IDET_OK;
+}
+
+int launch_cra_multi(const CraJob *jobs_dev, int count, cudaStream_t s) {
+    if (count <= 0) return IDET_OK;
+    k_cra_multi<<<count, kCraThreads, 0, s>>>(jobs_dev);
     count_launch();
     IDET_CUDA_TRY(cudaGetLastError());
     return IDET_OK;

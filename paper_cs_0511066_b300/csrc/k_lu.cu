@@ -39,17 +39,13 @@ __device__ __forceinline__ uint32_t det_mul(uint32_t det, int32_t piv, const Mod
 // ---------------------------------------------------------------------------
 // Whole-matrix LU in shared memory.
 
-__global__ void k_lu_small(int32_t *__restrict__ R, int n, const ModP *__restrict__ mods,
-                           LUState *__restrict__ st, int32_t *__restrict__ perm) {
+__device__ void lu_small_body(int32_t *__restrict__ g, int n, const ModP M,
+                              LUState *__restrict__ st_out, int32_t *__restrict__ pm) {
     extern __shared__ int32_t sa[];
     __shared__ int s_piv;
     __shared__ int32_t s_inv;
-    const int w = blockIdx.x;
-    const ModP M = mods[w];
-    int32_t *g = R + (int64_t)w * n * n;
     const int nn = n * n;
     for (int e = threadIdx.x; e < nn; e += blockDim.x) sa[e] = g[e];
-    int32_t *pm = perm ? perm + (int64_t)w * n : nullptr;
     if (pm)
         for (int i = threadIdx.x; i < n; i += blockDim.x) pm[i] = i;
     uint32_t det = 1u % M.p;
@@ -105,7 +101,26 @@ __global__ void k_lu_small(int32_t *__restrict__ R, int n, const ModP *__restric
         s.neg = neg;
         s.det = dead ? 0u : det;
         s.pad = 0;
-        st[w] = s;
+        *st_out = s;
+    }
+}
+
+__global__ void k_lu_small(int32_t *__restrict__ R, int n, const ModP *__restrict__ mods,
+                           LUState *__restrict__ st, int32_t *__restrict__ perm) {
+    const int w = blockIdx.x;
+    lu_small_body(R + (int64_t)w * n * n, n, mods[w], st + w, perm ? perm + (int64_t)w * n : nullptr);
+}
+
+// One CTA per (matrix, prime) job of a batch.
+__global__ void k_lu_small_multi(const LUSmallJob *__restrict__ jobs) {
+    const LUSmallJob j = jobs[blockIdx.x];
+    lu_small_body(j.R, j.n, j.mod, j.st, nullptr);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const LUState t = *j.st;
+        uint32_t d = t.dead ? 0u : t.det;
+        if (t.neg && d) d = j.mod.p - d;
+        *j.det = d;
     }
 }
 
@@ -714,6 +729,24 @@ int lu_small_into(int32_t *R, int n, const ModP *mods_dev, int W, LUState *st,
     count_launch();
     IDET_CUDA_TRY(cudaGetLastError());
     k_finalize_det<<<(W + 127) / 128, 128, 0, s>>>(st, mods_dev, W, det_out);
+    count_launch();
+    IDET_CUDA_TRY(cudaGetLastError());
+    return IDET_OK;
+}
+
+}  // namespace idet
+
+namespace idet {
+
+int lu_small_multi(const LUSmallJob *jobs_dev, int count, int max_n, cudaStream_t s) {
+    if (count <= 0) return IDET_OK;
+    if (max_n > kSmallN) {
+        set_last_error("lu_small_multi: n must be at most %d", kSmallN);
+        return IDET_ERR_ARG;
+    }
+    IDET_CUDA_TRY(cudaFuncSetAttribute(k_lu_small_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(int32_t) * kSmallN * kSmallN)));
+    k_lu_small_multi<<<count, 512, sizeof(int32_t) * (size_t)max_n * max_n, s>>>(jobs_dev);
     count_launch();
     IDET_CUDA_TRY(cudaGetLastError());
     return IDET_OK;

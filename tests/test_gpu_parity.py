@@ -293,3 +293,68 @@ def test_lif_device_inputs_and_singular():
     with pytest.raises(idet.IdetError) as e:
         idet.largest_invariant_factor(S, b)
     assert e.value.code == 3
+
+
+# --- batched determinants ----------------------------------------------------------
+
+def test_int_det_batch_matches_oracle():
+    mats = workloads.batch_mix(count=24, nmin=1, nmax=90, bits=10, seed=3)
+    mats.append(np.zeros((7, 7), dtype=np.int64))
+    sing = workloads.dense_pm100(9, seed=1)
+    sing[2] = sing[0] - sing[1]
+    mats.append(sing)
+    got = idet.int_det_batch(mats)
+    for A, d in zip(mats, got):
+        assert d == exact.bareiss_det(A.tolist())
+
+
+def test_int_det_batch_matches_single_matrix_path():
+    """Sizes on both sides of the shared-memory LU limit (192)."""
+    mats = workloads.batch_mix(count=10, nmin=150, nmax=300, bits=10, seed=8)
+    got = idet.int_det_batch(mats)
+    for A, d in zip(mats, got):
+        assert d == idet.int_det(A)
+
+
+def _dets_agree_mod(A, d, primes):
+    """d == det(A), checked modulo primes with the oracle's CPU elimination."""
+    res = modular.det_mod_primes(A, primes)
+    return all(int(d) % p == int(r) for p, r in zip(primes, res))
+
+
+def test_int_det_batch_cluster_elimination_edge_cases():
+    """Whole-matrix cluster elimination (det mod p for 192 < n <= 600, and
+    A^{-1} mod p for the lift of every matrix): tiny n with idle blocks, row
+    exchanges whose pivot lies in another block, singular matrices, ragged n.
+    A wrong inverse would not change a determinant (the CRA alone still
+    finishes) but would make the lift fail, so the number of primes the batch
+    used is bounded too: with a working lift each matrix needs only the
+    early-terminated CRA primes, without it about log_l H of them."""
+    rng = np.random.default_rng(11)
+    mats = [np.array([[0, 1, 0], [1, 0, 0], [0, 0, 2]], dtype=np.int64),
+            np.array([[7]], dtype=np.int64)]
+    B = rng.integers(-1024, 1025, size=(5, 5)).astype(np.int64)
+    B[:4, 0] = 0
+    B[:2, 1] = 0
+    mats.append(B)
+    for n, zrows in [(193, 0), (250, 40), (333, 300), (47, 46)]:
+        A = rng.integers(-1024, 1025, size=(n, n)).astype(np.int64)
+        A[:zrows, 0] = 0
+        mats.append(A)
+    S = rng.integers(-1024, 1025, size=(257, 257)).astype(np.int64)
+    S[100] = S[3] - 2 * S[200]
+    mats.append(S)
+    Z = rng.integers(-1024, 1025, size=(220, 220)).astype(np.int64)
+    Z[:, 219] = 0
+    mats.append(Z)
+    mats.append(rng.integers(-1024, 1025, size=(600, 600)).astype(np.int64))
+    got, st = idet.int_det_batch(mats, return_stats=True)
+    qs = p31(24, seed=5)
+    for A, d in zip(mats, got):
+        if A.shape[0] <= 64:
+            assert d == exact.bareiss_det(A.tolist())
+        else:
+            assert _dets_agree_mod(A, d, qs)
+    assert got[7] == 0 and got[8] == 0
+    assert got[0] == -2
+    assert st["primes_used"] < 40 * len(mats), st

@@ -69,7 +69,10 @@ typedef struct {
     int32_t wave;          /* primes factored per batch, 0 = default         */
     int32_t lif;           /* 1 (default): Alg. 4.1 with i_max = 1; 0: CRA
                               only (Alg. 2.1 on det(A))                      */
-    int32_t reserved[7];
+    int32_t prime_bits;    /* CRA prime class: 21 (primes in (2^20, 2^21)) or
+                              31 (primes in (2^30, 2^31)); 0 = default: 21
+                              for idet_int_det, 31 for idet_int_det_mp      */
+    int32_t reserved[6];
 } idet_opts;
 
 typedef struct {
@@ -119,6 +122,24 @@ uint64_t idet_launch_count(void);
 int idet_int_det(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
                  const idet_opts *opts, void *stream, idet_int *det,
                  idet_stats *stats);
+
+/*
+ * det(A) for entries of many words: a_ij = A_sign[i n + j] * sum_l
+ * A_limbs[(i n + j) L + l] 2^(32 l), A_sign in {-1, 0, 1} (0 only with a zero
+ * magnitude), 1 <= L <= 64 limbs, n <= 65536, both arrays row-major without
+ * padding, on the host or (on_device) the device. Same method as
+ * idet_int_det (Alg. 4.1 with i_max = 1), CRA primes of opts->prime_bits
+ * (default 31: for entries this large log_l H approaches the 21-bit pool),
+ * and an output-sensitive Dixon lift: it stops at the first length m at
+ * which a reconstructed denominator D passes the certificate (every
+ * D x_j mod p^m small, and the Hadamard-free bound n max|a| p^h + D max|b| <
+ * p^m / 2 making A y = D b hold over Z), so m follows the size of s~_n and of
+ * the numerators, not H. Errors as idet_int_det; stats->lift_iters is m and
+ * stats->log2_K the bits of the factor s~_n found.
+ */
+int idet_int_det_mp(const uint32_t *A_limbs, const int8_t *A_sign, int64_t n, int32_t L,
+                    int32_t on_device, const idet_opts *opts, void *stream, idet_int *det,
+                    idet_stats *stats);
 
 /*
  * s~_n for the right-hand side b: the lcm of the denominators of the entries

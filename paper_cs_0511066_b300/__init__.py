@@ -45,7 +45,8 @@ class idet_opts(ctypes.Structure):
     _fields_ = [("log2_epsilon", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("certify", ctypes.c_int32), ("update_path", ctypes.c_int32),
                 ("nb", ctypes.c_int32), ("wave", ctypes.c_int32),
-                ("lif", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("lif", ctypes.c_int32), ("prime_bits", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class idet_stats(ctypes.Structure):
@@ -208,12 +209,13 @@ def _call_int(fn, *args, cap: int = 1 << 12):
 
 def int_det(A, *, certify: bool = False, seed: int | None = None, lif: bool = True,
             update_path: int | None = None, nb: int | None = None, wave: int | None = None,
-            log2_epsilon: float | None = None, stream=None, return_stats: bool = False):
+            log2_epsilon: float | None = None, prime_bits: int | None = None, stream=None,
+            return_stats: bool = False):
     """det(A) as a Python int (idet_int_det)."""
     use_torch_allocator()
     ptr, n, lda, dev, keep = _matrix(A)
     o = default_opts(certify=int(certify), seed=seed, lif=int(lif), update_path=update_path,
-                     nb=nb, wave=wave, log2_epsilon=log2_epsilon)
+                     nb=nb, wave=wave, log2_epsilon=log2_epsilon, prime_bits=prime_bits)
     st = idet_stats()
     cap = max(64, int(n * 40 // 32) + 64)
     while True:
@@ -345,3 +347,41 @@ def launch_count() -> int:
 __all__ = ["int_det", "largest_invariant_factor", "det_mod_primes", "lu_mod_prime",
            "dixon_digits", "crt_symmetric", "launch_count", "default_opts", "IdetError",
            "use_torch_allocator", "LIB_PATH"]
+
+
+_lib.idet_int_det_mp.argtypes = [_P, _P, _i64, _i32, _i32, ctypes.POINTER(idet_opts), _P,
+                                 ctypes.POINTER(idet_int), ctypes.POINTER(idet_stats)]
+
+
+def int_det_mp(mag, sgn, *, certify: bool = False, seed: int | None = None, lif: bool = True,
+               prime_bits: int | None = None, stream=None, return_stats: bool = False):
+    """det(A) for multi-word entries (idet_int_det_mp): mag is uint32
+    [n][n][L] (little-endian base-2^32 magnitudes), sgn int8 [n][n] in
+    {-1, 0, 1}; numpy arrays or CUDA tensors (both on the same side)."""
+    use_torch_allocator()
+    torch = _get_torch()
+    if torch is not None and isinstance(mag, torch.Tensor):
+        if not isinstance(sgn, torch.Tensor) or mag.is_cuda != sgn.is_cuda:
+            raise ValueError("mag and sgn must both be host arrays or both CUDA tensors")
+        if mag.dtype not in (torch.int32, torch.uint32) or sgn.dtype != torch.int8:
+            raise ValueError("mag must be 32-bit, sgn int8")
+        mag, sgn = mag.contiguous(), sgn.contiguous()
+        n, L, dev = mag.shape[0], mag.shape[2], 1 if mag.is_cuda else 0
+        mp, sp, keep = mag.data_ptr(), sgn.data_ptr(), (mag, sgn)
+    else:
+        m = np.ascontiguousarray(np.asarray(mag, dtype=np.uint32))
+        g = np.ascontiguousarray(np.asarray(sgn, dtype=np.int8))
+        n, L, dev = m.shape[0], m.shape[2], 0
+        mp, sp, keep = m.ctypes.data, g.ctypes.data, (m, g)
+    if mag.shape[:2] != (n, n) or tuple(sgn.shape) != (n, n):
+        raise ValueError("mag must be [n][n][L] and sgn [n][n]")
+    o = default_opts(certify=int(certify), seed=seed, lif=int(lif), prime_bits=prime_bits)
+    st = idet_stats()
+    cap = max(64, int(n * (32 * L + 16) // 32) + 64)
+    buf = (ctypes.c_uint32 * cap)()
+    out = idet_int(0, 0, cap, buf)
+    _check(_lib.idet_int_det_mp(mp, sp, n, L, dev, ctypes.byref(o), _stream_ptr(stream),
+                                ctypes.byref(out), ctypes.byref(st)))
+    d = _to_int(out, buf)
+    del keep
+    return (d, st.as_dict()) if return_stats else d

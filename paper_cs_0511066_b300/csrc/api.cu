@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <unordered_set>
 #include <vector>
 
 #include "idet_internal.cuh"
@@ -128,27 +129,43 @@ static bool is_prime32(uint32_t n) {
     return true;
 }
 
-// Random primes sampled without replacement from the 21-bit pool.
-struct PrimeDraw {
-    std::vector<uint32_t> order;
-    size_t next = 0;
-    PrimeDraw(uint64_t seed) : order(pool21()) {
-        SplitMix g(seed ^ 0x5eed5eedull);
-        for (size_t i = order.size() - 1; i > 0; --i) std::swap(order[i], order[g.below(i + 1)]);
-    }
-    bool take(uint32_t &p) {
-        if (next >= order.size()) return false;
-        p = order[next++];
-        return true;
-    }
-};
-
 static uint32_t random_prime31(SplitMix &g) {
     while (true) {
         uint32_t c = (uint32_t)((1u << 30) + (g.next() % (1u << 30))) | 1u;
         if (c < (1u << 31) && is_prime32(c)) return c;
     }
 }
+
+// Random primes sampled without replacement (Alg. 2.1) from one of two
+// pools: the 73,586 primes in (2^20, 2^21) (l = 2^20), or the 50,697,537
+// primes in (2^30, 2^31) (l = 2^30), drawn by rejection sampling.
+struct PrimeDraw {
+    int bits;
+    std::vector<uint32_t> order;
+    size_t next = 0;
+    SplitMix g;
+    std::unordered_set<uint32_t> seen;
+    explicit PrimeDraw(uint64_t seed, int b = 21) : bits(b), g(seed ^ 0x5eed5eedull) {
+        if (bits != 31) {
+            order = pool21();
+            for (size_t i = order.size() - 1; i > 0; --i) std::swap(order[i], order[g.below(i + 1)]);
+        }
+    }
+    bool take(uint32_t &p) {
+        if (bits == 31) {
+            if (seen.size() >= (1u << 24)) return false;
+            do {
+                p = random_prime31(g);
+            } while (!seen.insert(p).second);
+            return true;
+        }
+        if (next >= order.size()) return false;
+        p = order[next++];
+        return true;
+    }
+    double pool() const { return bits == 31 ? 50697537.0 : (double)pool21().size(); }
+    double log2l() const { return bits == 31 ? 30.0 : 20.0; }
+};
 
 static uint64_t inv_mod_2_64(uint64_t p) {
     uint64_t x = p;  // p * p = 1 mod 8
@@ -340,9 +357,20 @@ struct DetJob {
     std::vector<uint32_t> dets;     // det(A) mod primes
     idet_stats st{};
 
-    DetJob(const DevMatrix &m, Workspace &w, const idet_opts &opts)
-        : M(m), ws(w), s(w.stream()), o(opts), draw(opts.seed) {
+    // multi-word entries (idet_int_det_mp): sign x L base-2^32 limbs
+    const uint32_t *mag = nullptr;
+    const int8_t *sgn = nullptr;
+    int L = 0;
+
+    DetJob(const DevMatrix &m, Workspace &w, const idet_opts &opts, int prime_bits = 21)
+        : M(m), ws(w), s(w.stream()), o(opts), draw(opts.seed, prime_bits) {
         nb = o.nb > 0 ? o.nb : 32;
+    }
+
+    // A mod p for W primes into R (W x n x n balanced int32)
+    int reduce(const ModP *md, int W, int32_t *R) {
+        if (mag) return launch_reduce_mp(mag, sgn, M.n, L, md, W, R, s);
+        return launch_reduce(M.A, M.n, M.n, md, W, R, s);
     }
 
     int stats() {
@@ -402,8 +430,8 @@ struct DetJob {
         IDET_TRY(ws.alloc_n(&dd, W));
         IDET_CUDA_TRY(cudaMemcpyAsync(md, mh.data(), sizeof(ModP) * W, cudaMemcpyHostToDevice, s));
         Timer t(s);
-        IDET_TRY(launch_reduce(M.A, n, n, md, W, R, s));
-        IDET_TRY(lu_factor_batched(R, n, md, mh.data(), W, false, nb, nullptr, dd,
+        IDET_TRY(reduce(md, W, R));
+        IDET_TRY(lu_factor_batched(R, n, md, mh.data(), W, draw.bits == 31, nb, nullptr, dd,
                                    o.update_path, ws));
         std::vector<uint32_t> res(W);
         IDET_CUDA_TRY(cudaMemcpyAsync(res.data(), dd, sizeof(uint32_t) * W,
@@ -586,6 +614,307 @@ static double rhs_range_log2(int64_t n, double log2H) {
     double lh = std::ceil(std::max(log2H, 1.0));
     double l2 = std::log2(13.0) + 3 * std::log2(e) + 4 * std::log2(lh);
     return std::min(l2, 62.0);
+}
+
+// Alg. 2.1 on det(A) for the first primes (Alg. 4.1 lines 1-4), or all the
+// way in CRA-only / certified mode. *done when det has been written.
+static int det_first(DetJob &J, int k0, int wave, bool cra_only, idet_int *det, bool *done) {
+    const idet_opts &o = J.o;
+    std::vector<int32_t> dig;
+    int why = 0;
+    *done = false;
+    IDET_TRY(J.factor_wave(cra_only ? wave : std::max(k0, 1)));
+    while (true) {
+        Timer t(J.s);
+        IDET_TRY(J.cra_digits(J.primes, J.dets, dig));
+        J.st.ms_cra += t.stop();
+        const int stop = CraScan::scan(dig, J.primes, J.log2H, o.log2_epsilon, J.draw.log2l(),
+                                       J.draw.pool(), o.certify != 0, &why);
+        if (stop >= 0) {
+            J.st.et_stop = why;
+            J.st.primes_in_cra = stop + 1;
+            Timer t2(J.s);
+            const int rc = J.assemble(J.primes, dig, stop + 1, nullptr, 0, det);
+            J.st.ms_cra += t2.stop();
+            *done = true;
+            return rc;
+        }
+        if (!cra_only) return IDET_OK;
+        IDET_TRY(J.factor_wave(wave));
+    }
+}
+
+// K from its base-p digits: base-2^32 limbs on the device, and log2 K.
+static int den_to_binary(Workspace &ws, const std::vector<uint32_t> &den, uint32_t p,
+                         uint32_t **Kbin, int *Klen, double *log2K) {
+    cudaStream_t s = ws.stream();
+    const int kd = (int)den.size();
+    const int cap = kd + 2;
+    uint32_t *dd = nullptr;
+    int32_t *dl = nullptr;
+    IDET_TRY(ws.alloc_n(&dd, kd));
+    IDET_TRY(ws.alloc_n(Kbin, cap));
+    IDET_TRY(ws.alloc_n(&dl, 1));
+    IDET_CUDA_TRY(cudaMemcpyAsync(dd, den.data(), 4 * (size_t)kd, cudaMemcpyHostToDevice, s));
+    IDET_TRY(launch_radix_to_binary(dd, kd, p, *Kbin, cap, dl, s));
+    IDET_CUDA_TRY(cudaMemcpyAsync(Klen, dl, 4, cudaMemcpyDeviceToHost, s));
+    IDET_CUDA_TRY(cudaStreamSynchronize(s));
+    const double top = den[kd - 1] + (kd > 1 ? den[kd - 2] / (double)p : 0.0);
+    *log2K = std::log2(top) + (kd - 1) * std::log2((double)p);
+    return IDET_OK;
+}
+
+// Alg. 2.1 on det(A)/K, using the residues already computed first
+// (Section 4: the modular determinants computed so far are reused). Primes
+// dividing K are skipped. K = null: det(A) itself.
+static int det_over_K(DetJob &J, const uint32_t *Kbin, int Klen, double log2K, int wave,
+                      idet_int *det) {
+    const idet_opts &o = J.o;
+    Workspace &ws = J.ws;
+    cudaStream_t s = J.s;
+    const double log2HK = std::max(0.0, J.log2H - log2K);
+    std::vector<int32_t> dig;
+    int why = 0;
+    while (true) {
+        std::vector<uint32_t> prs, res;
+        Timer t(s);
+        if (Kbin) {
+            const int c = (int)J.primes.size();
+            uint32_t *dp = nullptr, *di = nullptr, *dout = nullptr;
+            int32_t *dskip = nullptr;
+            IDET_TRY(ws.alloc_n(&dp, c));
+            IDET_TRY(ws.alloc_n(&di, c));
+            IDET_TRY(ws.alloc_n(&dout, c));
+            IDET_TRY(ws.alloc_n(&dskip, c));
+            IDET_CUDA_TRY(cudaMemcpyAsync(dp, J.primes.data(), 4 * c, cudaMemcpyHostToDevice, s));
+            IDET_CUDA_TRY(cudaMemcpyAsync(di, J.dets.data(), 4 * c, cudaMemcpyHostToDevice, s));
+            IDET_TRY(launch_div_by_K(Kbin, Klen, dp, di, dout, dskip, c, s));
+            std::vector<uint32_t> hout(c);
+            std::vector<int32_t> hskip(c);
+            IDET_CUDA_TRY(cudaMemcpyAsync(hout.data(), dout, 4 * c, cudaMemcpyDeviceToHost, s));
+            IDET_CUDA_TRY(cudaMemcpyAsync(hskip.data(), dskip, 4 * c, cudaMemcpyDeviceToHost, s));
+            IDET_CUDA_TRY(cudaStreamSynchronize(s));
+            for (int i = 0; i < c; ++i)
+                if (!hskip[i]) {
+                    prs.push_back(J.primes[i]);
+                    res.push_back(hout[i]);
+                }
+        } else {
+            prs = J.primes;
+            res = J.dets;
+        }
+        IDET_TRY(J.cra_digits(prs, res, dig));
+        const int stop = CraScan::scan(dig, prs, Kbin ? log2HK : J.log2H, o.log2_epsilon,
+                                       J.draw.log2l(), J.draw.pool(), false, &why);
+        J.st.ms_cra += t.stop();
+        if (stop >= 0) {
+            J.st.et_stop = why;
+            J.st.primes_in_cra = stop + 1;
+            Timer t2(s);
+            const int rc = J.assemble(prs, dig, stop + 1, Kbin, Klen, det);
+            J.st.ms_cra += t2.stop();
+            return rc;
+        }
+        IDET_TRY(J.factor_wave(wave));
+    }
+}
+
+// Section 2.2 for multi-word entries, output-sensitive: the lift runs in
+// chunks and after each chunk of m digits tries to reconstruct u . x with
+// balanced bounds (numerator < p^(m-2-h), denominator D < p^h). A candidate
+// D is accepted only when every y_j = D X_j mod p^m is small, |y_j| < p^h,
+// and n max|a_ij| p^h + D max|b_i| < p^m / 2: then A y = D b holds over Z
+// (A X = b mod p^m, and both sides are below p^m / 2), so x = y / D, every
+// D x_j is an integer and D, the denominator of u . x, is the lcm of the
+// denominators of x, s~_n. Without acceptance by m_cap digits, no K.
+struct MpLift {
+    uint32_t p = 0;
+    int m = 0;
+    std::vector<uint32_t> den;
+};
+
+static int mp_lift(DetJob &J, unsigned int abits, MpLift &out) {
+    const int64_t n = J.M.n;
+    Workspace &ws = J.ws;
+    cudaStream_t s = J.s;
+    SplitMix g(J.o.seed ^ 0x11f7ull);
+    // A^{-1} mod p for a 31-bit p with det A != 0 mod p
+    Timer tinv(s);
+    int32_t *R = nullptr, *perm = nullptr, *C = nullptr;
+    ModP *md = nullptr;
+    uint32_t *dd = nullptr;
+    IDET_TRY(ws.alloc_n(&R, (size_t)n * n));
+    IDET_TRY(ws.alloc_n(&perm, n));
+    IDET_TRY(ws.alloc_n(&md, 1));
+    IDET_TRY(ws.alloc_n(&dd, 1));
+    uint32_t p = 0;
+    ModP mh{};
+    for (int tries = 0;; ++tries) {
+        if (tries == 6) return IDET_ERR_SINGULAR;
+        p = random_prime31(g);
+        mh = make_mod(p);
+        IDET_CUDA_TRY(cudaMemcpyAsync(md, &mh, sizeof(ModP), cudaMemcpyHostToDevice, s));
+        IDET_TRY(launch_reduce_mp(J.mag, J.sgn, n, J.L, md, 1, R, s));
+        IDET_TRY(lu_factor_batched(R, n, md, &mh, 1, true, J.nb, perm, dd, IDET_PATH_INT64, ws));
+        uint32_t det = 0;
+        IDET_CUDA_TRY(cudaMemcpyAsync(&det, dd, 4, cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        if (det != 0) break;
+    }
+    IDET_TRY(ws.alloc_n(&C, (size_t)n * n));
+    IDET_TRY(lu_inverse(R, perm, n, mh, md, true, J.nb, C, ws));
+    J.st.ms_inverse += tinv.stop();
+    J.st.lu_macs += 2.0 * (double)n * n * n;
+    // A as signed base-2^15 digit planes
+    const int T = (int)((abits + 1 + 14) / 15) + 1;
+    const int64_t ldp = (n + 7) / 8 * 8;
+    int16_t *planes = nullptr;
+    IDET_TRY(ws.alloc_n(&planes, (size_t)T * n * ldp));
+    IDET_TRY(launch_mp_planes(J.mag, J.sgn, n, J.L, T, ldp, planes, s));
+    // b (Alg. 4.1 range S) and the projection u
+    SplitMix gb(J.o.seed ^ 0xb5ull);
+    const double l2S = rhs_range_log2(n, J.log2H);
+    const uint64_t S = (uint64_t)std::exp2(std::floor(l2S));
+    const double lp = std::log2((double)p);
+    const double log2n = std::log2((double)n);
+    // |r - A x| < |r| + n 2^abits p / 2 and |r| < n 2^abits + |b|: digits
+    // 0..len-2 of 15 bits and a signed top digit below 2^14
+    const int lv = (int)std::ceil(log2n) + (int)abits + 34;
+    const int len = std::max(6, (lv + 1 - 14 + 14) / 15 + 2);
+    std::vector<int32_t> rdh((size_t)n * len), rmh(n), uh(n);
+    double u1 = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t b = (int64_t)(gb.below(S)) - (int64_t)(S / 2);
+        for (int k = 0; k < len; ++k) {
+            const int sh = std::min(15 * k, 63);
+            int64_t d = b >> sh;
+            rdh[(size_t)i * len + k] = (int32_t)(k < len - 1 ? (d & 0x7fff) : d);
+        }
+        int64_t bm = b % (int64_t)p;
+        if (bm > (int64_t)(p - 1) / 2) bm -= p;
+        if (bm < -(int64_t)(p - 1) / 2) bm += p;
+        rmh[i] = (int32_t)bm;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        uh[i] = (int32_t)(gb.next() & 0xffff);
+        u1 += uh[i];
+    }
+    const double log2b = std::log2((double)S);
+    const int gu = (int)std::ceil(std::log2(u1 + 1) / lp);
+    int32_t *rd = nullptr, *rm = nullptr, *ud = nullptr, *x = nullptr, *info = nullptr;
+    IDET_TRY(ws.alloc_n(&rd, (size_t)n * len));
+    IDET_TRY(ws.alloc_n(&rm, n));
+    IDET_TRY(ws.alloc_n(&ud, n));
+    IDET_TRY(ws.alloc_n(&x, n));
+    IDET_TRY(ws.alloc_n(&info, 4));
+    IDET_CUDA_TRY(cudaMemcpyAsync(rd, rdh.data(), 4 * rdh.size(), cudaMemcpyHostToDevice, s));
+    IDET_CUDA_TRY(cudaMemcpyAsync(rm, rmh.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s));
+    IDET_CUDA_TRY(cudaMemcpyAsync(ud, uh.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s));
+    IDET_CUDA_TRY(cudaMemsetAsync(info, 0, 16, s));
+    // the static length (Hadamard bounds) caps the lift
+    double lc = 0, lcmin = INFINITY;
+    for (int64_t i = 0; i < n; ++i) {
+        lc += J.colsq[i];
+        lcmin = std::min(lcmin, J.colsq[i]);
+    }
+    const double log2N = std::log2(u1 + 1) + log2b + 0.5 * log2n + lc - lcmin;
+    const int64_t m_static = (int64_t)std::ceil((log2N + 1) / lp) +
+                             (int64_t)std::ceil((J.log2H + 1) / lp) + 2;
+    const int m_cap = (int)std::min<int64_t>(m_static, 1 << 14);
+    int mcap = 64;
+    int32_t *digits = nullptr;
+    int64_t *z = nullptr;
+    IDET_TRY(ws.alloc_n(&digits, (size_t)mcap * n));
+    IDET_TRY(ws.alloc_n(&z, mcap));
+    IDET_CUDA_TRY(cudaMemsetAsync(z, 0, 8 * (size_t)mcap, s));
+    MpLiftArgs a{};
+    a.C = C;
+    a.ldc = n;
+    a.n = n;
+    a.planes = planes;
+    a.T = T;
+    a.ldp = ldp;
+    a.u = ud;
+    a.x = x;
+    a.rm = rm;
+    a.rd = rd;
+    a.len = len;
+    a.info = info;
+    a.mod = mh;
+    a.pinv15 = (uint32_t)(inv_mod_2_64(p) & 0x7fff);
+    uint32_t *den = nullptr;
+    int32_t *rinfo = nullptr, *flags = nullptr;
+    IDET_TRY(ws.alloc_n(&rinfo, 4));
+    IDET_TRY(ws.alloc_n(&flags, n));
+    std::vector<int32_t> hflags(n);
+    int it = 0, next_check = 16;
+    bool ok = false;
+    double kms = 0;
+    while (!ok && it < m_cap) {
+        const int target = std::min(next_check, m_cap);
+        if (target > mcap) {
+            int ncap = mcap;
+            while (ncap < target) ncap *= 2;
+            int32_t *nd = nullptr;
+            int64_t *nz = nullptr;
+            IDET_TRY(ws.alloc_n(&nd, (size_t)ncap * n));
+            IDET_TRY(ws.alloc_n(&nz, ncap));
+            IDET_CUDA_TRY(cudaMemcpyAsync(nd, digits, 4 * (size_t)it * n, cudaMemcpyDeviceToDevice, s));
+            IDET_CUDA_TRY(cudaMemsetAsync(nz, 0, 8 * (size_t)ncap, s));
+            IDET_CUDA_TRY(cudaMemcpyAsync(nz, z, 8 * (size_t)it, cudaMemcpyDeviceToDevice, s));
+            digits = nd;
+            z = nz;
+            mcap = ncap;
+        }
+        a.digits = digits;
+        a.z = z;
+        Timer tk(s);
+        for (; it < target; ++it) IDET_TRY(launch_mp_step(a, it, s));
+        kms += tk.stop();
+        next_check = it + std::max(8, it / 4);
+        // checkpoint: balanced bounds
+        const int h = (it - 2 - gu) / 2;
+        if (h < 1) continue;
+        const bool cert = log2n + abits + h * lp + 2 < it * lp - 1 && h * lp + log2b + 2 < it * lp - 1;
+        if (!cert) continue;
+        const int hN = it - 2 - h, den_cap = h + 2;
+        IDET_TRY(ws.alloc_n(&den, den_cap));
+        Timer trr(s);
+        IDET_TRY(launch_ratrecon(z, it, p, hN, h, den, den_cap, rinfo, ws));
+        int32_t hi[2] = {0, 0};
+        IDET_CUDA_TRY(cudaMemcpyAsync(hi, rinfo, 8, cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hi[0] != 0) {
+            J.st.ms_rr += trr.stop();
+            continue;
+        }
+        IDET_TRY(launch_lif_check(digits, n, it, den, hi[1], p, h, flags, s));
+        IDET_CUDA_TRY(cudaMemcpyAsync(hflags.data(), flags, 4 * (size_t)n, cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        J.st.ms_rr += trr.stop();
+        bool all = true;
+        for (int64_t j = 0; j < n && all; ++j) all = hflags[j] == 0;
+        if (!all) continue;
+        out.den.resize(hi[1]);
+        IDET_CUDA_TRY(cudaMemcpyAsync(out.den.data(), den, 4 * (size_t)hi[1], cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        // s~_n divides det A and p does not: a denominator divisible by p is
+        // not the reduced one
+        ok = out.den[0] != 0;
+    }
+    int32_t hinfo = 0;
+    IDET_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, 4, cudaMemcpyDeviceToHost, s));
+    IDET_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hinfo != 0) {
+        set_last_error("multi-word lift: residual out of range");
+        return IDET_ERR_INTERNAL;
+    }
+    J.st.ms_lift_kernel += kms;
+    J.st.lift_bytes += (double)it * ((double)T * 2.0 + 4.0) * (double)n * (double)n;
+    out.p = p;
+    out.m = it;
+    if (!ok) out.den.clear();
+    return IDET_OK;
 }
 
 }  // namespace idet
@@ -823,7 +1152,11 @@ int idet_int_det(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
     Timer total(s);
     DevMatrix M;
     IDET_TRY(stage_matrix(A, n, lda, on_device, ws, M));
-    DetJob J(M, ws, o);
+    if (o.prime_bits != 0 && o.prime_bits != 21 && o.prime_bits != 31) {
+        set_last_error("prime_bits must be 0, 21 or 31");
+        return IDET_ERR_ARG;
+    }
+    DetJob J(M, ws, o, o.prime_bits == 31 ? 31 : 21);
     IDET_TRY(J.stats());
     auto finish = [&](int rc) {
         J.st.ms_total = total.stop();
@@ -835,38 +1168,15 @@ int idet_int_det(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
         J.st.et_stop = 2;
         return finish(write_int(det, 0, nullptr, 0));
     }
-    const double log2l = 20.0;  // primes > l = 2^20
-    const double pool = (double)pool21().size();
     const bool certify = o.certify != 0;
-    const int k0 = k_default(o.log2_epsilon, pool, J.log2H, log2l);
+    const int k0 = k_default(o.log2_epsilon, J.draw.pool(), J.log2H, J.draw.log2l());
     const int wave = o.wave > 0 ? o.wave : std::max(8, k0);
 
     // Alg. 2.1 on det(A): the first k0 primes (Alg. 4.1 lines 1-4), or all
     // the way in CRA-only / certified mode.
-    const bool cra_only = certify || !o.lif;
-    std::vector<int32_t> dig;
-    int why = 0;
-    {
-        int first = cra_only ? wave : std::max(k0, 1);
-        IDET_TRY(J.factor_wave(first));
-        while (true) {
-            Timer t(s);
-            IDET_TRY(J.cra_digits(J.primes, J.dets, dig));
-            J.st.ms_cra += t.stop();
-            int stop = CraScan::scan(dig, J.primes, J.log2H, o.log2_epsilon, log2l, pool,
-                                     certify, &why);
-            if (stop >= 0) {
-                J.st.et_stop = why;
-                J.st.primes_in_cra = stop + 1;
-                Timer t2(s);
-                int rc = J.assemble(J.primes, dig, stop + 1, nullptr, 0, det);
-                J.st.ms_cra += t2.stop();
-                return finish(rc);
-            }
-            if (!cra_only) break;
-            IDET_TRY(J.factor_wave(wave));
-        }
-    }
+    bool done = false;
+    const int rc0 = det_first(J, k0, wave, certify || !o.lif, det, &done);
+    if (rc0 != IDET_OK || done) return finish(rc0);
 
     // Section 2.2 / Alg. 4.1 with i_max = 1: one solve gives K = s~_n.
     const int64_t *bdev = nullptr;
@@ -889,75 +1199,103 @@ int idet_int_det(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
     J.st.lift_iters = lr.m;
     J.st.lift_timed_out = lr.timed_out;
 
-    // K = denominator (binary limbs on the device).
     uint32_t *Kbin = nullptr;
     int Klen = 0;
     double log2K = 0;
-    if (rc == IDET_OK && !lr.den.empty()) {
-        const int kd = (int)lr.den.size();
-        const int cap = kd + 2;
-        uint32_t *dd = nullptr;
-        int32_t *dl = nullptr;
-        IDET_TRY(ws.alloc_n(&dd, kd));
-        IDET_TRY(ws.alloc_n(&Kbin, cap));
-        IDET_TRY(ws.alloc_n(&dl, 1));
-        IDET_CUDA_TRY(cudaMemcpyAsync(dd, lr.den.data(), 4 * (size_t)kd, cudaMemcpyHostToDevice, s));
-        IDET_TRY(launch_radix_to_binary(dd, kd, lr.p, Kbin, cap, dl, s));
-        IDET_CUDA_TRY(cudaMemcpyAsync(&Klen, dl, 4, cudaMemcpyDeviceToHost, s));
-        IDET_CUDA_TRY(cudaStreamSynchronize(s));
-        log2K = 0;
-        for (int i = 0; i < kd; ++i) (void)i;
-        // log2 K from the top digits
-        double top = lr.den[kd - 1] + (kd > 1 ? lr.den[kd - 2] / (double)lr.p : 0.0);
-        log2K = std::log2(top) + (kd - 1) * std::log2((double)lr.p);
-    }
+    if (rc == IDET_OK && !lr.den.empty())
+        IDET_TRY(den_to_binary(ws, lr.den, lr.p, &Kbin, &Klen, &log2K));
     J.st.log2_K = (int)std::floor(log2K);
+    return finish(det_over_K(J, Kbin, Klen, log2K, wave, det));
+}
 
-    // Alg. 2.1 on det(A)/K, using the residues already computed first
-    // (Section 4, "use the already computed modular determinants first").
-    const double log2HK = std::max(0.0, J.log2H - log2K);
-    while (true) {
-        std::vector<uint32_t> prs, res;
-        Timer t(s);
-        if (Kbin) {
-            const int c = (int)J.primes.size();
-            uint32_t *dp = nullptr, *di = nullptr, *dout = nullptr;
-            int32_t *dskip = nullptr;
-            IDET_TRY(ws.alloc_n(&dp, c));
-            IDET_TRY(ws.alloc_n(&di, c));
-            IDET_TRY(ws.alloc_n(&dout, c));
-            IDET_TRY(ws.alloc_n(&dskip, c));
-            IDET_CUDA_TRY(cudaMemcpyAsync(dp, J.primes.data(), 4 * c, cudaMemcpyHostToDevice, s));
-            IDET_CUDA_TRY(cudaMemcpyAsync(di, J.dets.data(), 4 * c, cudaMemcpyHostToDevice, s));
-            IDET_TRY(launch_div_by_K(Kbin, Klen, dp, di, dout, dskip, c, s));
-            std::vector<uint32_t> hout(c);
-            std::vector<int32_t> hskip(c);
-            IDET_CUDA_TRY(cudaMemcpyAsync(hout.data(), dout, 4 * c, cudaMemcpyDeviceToHost, s));
-            IDET_CUDA_TRY(cudaMemcpyAsync(hskip.data(), dskip, 4 * c, cudaMemcpyDeviceToHost, s));
-            IDET_CUDA_TRY(cudaStreamSynchronize(s));
-            for (int i = 0; i < c; ++i)
-                if (!hskip[i]) {
-                    prs.push_back(J.primes[i]);
-                    res.push_back(hout[i]);
-                }
-        } else {
-            prs = J.primes;
-            res = J.dets;
-        }
-        IDET_TRY(J.cra_digits(prs, res, dig));
-        int stop = CraScan::scan(dig, prs, Kbin ? log2HK : J.log2H, o.log2_epsilon, log2l, pool,
-                                 false, &why);
-        J.st.ms_cra += t.stop();
-        if (stop >= 0) {
-            J.st.et_stop = why;
-            J.st.primes_in_cra = stop + 1;
-            Timer t2(s);
-            int rc2 = J.assemble(prs, dig, stop + 1, Kbin, Klen, det);
-            J.st.ms_cra += t2.stop();
-            return finish(rc2);
-        }
-        IDET_TRY(J.factor_wave(wave));
+int idet_int_det_mp(const uint32_t *A_limbs, const int8_t *A_sign, int64_t n, int32_t L,
+                    int32_t on_device, const idet_opts *opts, void *stream, idet_int *det,
+                    idet_stats *stats) {
+    if (n < 0 || n > 65536 || L < 1 || L > 64 || (n > 0 && (!A_limbs || !A_sign)) || !det) {
+        set_last_error("invalid argument");
+        return IDET_ERR_ARG;
     }
+    const unsigned long long launches0 = g_launches;
+    if (n == 0) {
+        uint32_t one = 1;
+        return write_int(det, 1, &one, 1);
+    }
+    idet_opts o;
+    idet_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.prime_bits != 0 && o.prime_bits != 21 && o.prime_bits != 31) {
+        set_last_error("prime_bits must be 0, 21 or 31");
+        return IDET_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace ws(s);
+    Timer total(s);
+    const size_t nn = (size_t)n * n;
+    uint32_t *mag = nullptr;
+    int8_t *sgn = nullptr;
+    IDET_TRY(ws.alloc_n(&mag, nn * L));
+    IDET_TRY(ws.alloc_n(&sgn, nn));
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    IDET_CUDA_TRY(cudaMemcpyAsync(mag, A_limbs, 4 * nn * L, kind, s));
+    IDET_CUDA_TRY(cudaMemcpyAsync(sgn, A_sign, nn, kind, s));
+    DevMatrix M;
+    M.n = n;
+    DetJob J(M, ws, o, o.prime_bits == 21 ? 21 : 31);
+    J.mag = mag;
+    J.sgn = sgn;
+    J.L = L;
+    auto finish = [&](int rc) {
+        J.st.ms_total = total.stop();
+        J.st.launches = g_launches - launches0;
+        if (stats) *stats = J.st;
+        return rc;
+    };
+    // Hadamard bound from row and column norms (log domain); colsq holds
+    // log2 of the column norms here
+    double *E = nullptr, *rl = nullptr, *cl = nullptr;
+    unsigned int *mb = nullptr, abits = 0;
+    IDET_TRY(ws.alloc_n(&E, nn));
+    IDET_TRY(ws.alloc_n(&rl, n));
+    IDET_TRY(ws.alloc_n(&cl, n));
+    IDET_TRY(ws.alloc_n(&mb, 1));
+    IDET_TRY(launch_mp_stats(mag, sgn, n, L, E, rl, cl, mb, s));
+    std::vector<double> rlh(n), clh(n);
+    IDET_CUDA_TRY(cudaMemcpyAsync(rlh.data(), rl, 8 * (size_t)n, cudaMemcpyDeviceToHost, s));
+    IDET_CUDA_TRY(cudaMemcpyAsync(clh.data(), cl, 8 * (size_t)n, cudaMemcpyDeviceToHost, s));
+    IDET_CUDA_TRY(cudaMemcpyAsync(&abits, mb, 4, cudaMemcpyDeviceToHost, s));
+    IDET_CUDA_TRY(cudaStreamSynchronize(s));
+    double hr = 0, hc = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        hr += rlh[i];
+        hc += clh[i];
+    }
+    if (hr == -INFINITY || hc == -INFINITY || abits == 0) {  // a zero row or column
+        J.st.et_stop = 2;
+        return finish(write_int(det, 0, nullptr, 0));
+    }
+    // margin for the rounding of the norms (upper bound kept)
+    J.log2H = std::min(hr, hc) * (1 + 1e-12) + 1e-6 * n;
+    J.st.log2_H = J.log2H;
+    J.colsq = clh;
+    const bool certify = o.certify != 0;
+    const int k0 = k_default(o.log2_epsilon, J.draw.pool(), J.log2H, J.draw.log2l());
+    const int wave = o.wave > 0 ? o.wave : std::max(8, k0);
+    bool done = false;
+    const int rc0 = det_first(J, k0, wave, certify || !o.lif, det, &done);
+    if (rc0 != IDET_OK || done) return finish(rc0);
+    MpLift lr;
+    Timer tl(s);
+    int rc = mp_lift(J, abits, lr);
+    J.st.ms_lift += tl.stop();
+    if (rc != IDET_OK && rc != IDET_ERR_SINGULAR) return finish(rc);
+    J.st.lift_iters = lr.m;
+    uint32_t *Kbin = nullptr;
+    int Klen = 0;
+    double log2K = 0;
+    if (rc == IDET_OK && !lr.den.empty())
+        IDET_TRY(den_to_binary(ws, lr.den, lr.p, &Kbin, &Klen, &log2K));
+    J.st.log2_K = (int)std::floor(log2K);
+    return finish(det_over_K(J, Kbin, Klen, log2K, wave, det));
 }
 
 static int lif_common(DetJob &J, const int64_t *b_dev, const std::vector<int64_t> &bh,

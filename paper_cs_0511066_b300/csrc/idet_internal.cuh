@@ -207,6 +207,30 @@ struct ElimJob {
 };
 int launch_elim_cluster(const ElimJob *jobs_dev, int count, int max_n, int mode, cudaStream_t s);
 bool elim_cluster_fits(int n);
+
+// Multi-word entries (k_mp.cu): sign x magnitude of L base-2^32 limbs.
+int launch_reduce_mp(const uint32_t *mag, const int8_t *sgn, int64_t n, int L, const ModP *mods,
+                     int W, int32_t *R, cudaStream_t s);
+int launch_mp_stats(const uint32_t *mag, const int8_t *sgn, int64_t n, int L, double *E,
+                    double *rowl2, double *coll2, unsigned int *maxbits, cudaStream_t s);
+int launch_mp_planes(const uint32_t *mag, const int8_t *sgn, int64_t n, int L, int T, int64_t ldp,
+                     int16_t *planes, cudaStream_t s);
+struct MpLiftArgs {
+    const int32_t *C;        // A^{-1} mod p, n rows of ldc
+    int64_t ldc, n;
+    const int16_t *planes;   // T x n x ldp signed base-2^15 digits of A
+    int T;
+    int64_t ldp;
+    const int32_t *u;        // projection vector
+    int32_t *x, *rm, *rd;    // x_i; r mod p; residual digits n x len
+    int len;
+    int32_t *digits;         // lifting digits, row it = x_it
+    int64_t *z;              // z[it] = u . x_it (zeroed by the caller)
+    int32_t *info;
+    ModP mod;
+    uint32_t pinv15;         // p^{-1} mod 2^15
+};
+int launch_mp_step(const MpLiftArgs &a, int it, cudaStream_t s);
 int launch_ratrecon_multi(const RRJob *jobs_dev, int count, int max_m, cudaStream_t s);
 // Factor W residue matrices R[w] (n x n, ld n) in place: PA = LU mod p_w with
 // the first-nonzero pivot rule. perm (W*n, may be null) receives the row

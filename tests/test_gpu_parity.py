@@ -358,3 +358,76 @@ def test_int_det_batch_cluster_elimination_edge_cases():
     assert got[7] == 0 and got[8] == 0
     assert got[0] == -2
     assert st["primes_used"] < 40 * len(mats), st
+
+
+# ---------------------------------------------------------------------------
+# Multi-word entries (idet_int_det_mp) and 31-bit CRA primes
+
+
+def _limbs(M, L):
+    return workloads.to_limbs(M, L)
+
+
+def test_int_det_prime_bits_31_matches_oracle():
+    """Config c1 shape (n = 100, entries in [-100, 100]) with CRA primes in
+    (2^30, 2^31)."""
+    for seed in range(3):
+        A = workloads.dense_pm100(100, seed=seed)
+        d, st = idet.int_det(A, prime_bits=31, return_stats=True)
+        assert d == exact.bareiss_det(A.tolist())
+    A = workloads.dense_pm100(60, seed=9)
+    assert idet.int_det(A, prime_bits=31, certify=True) == exact.bareiss_det(A.tolist())
+
+
+def test_int_det_mp_random_multiword_matches_oracle():
+    rng = random.Random(4)
+    for n, bits, L in [(1, 70, 3), (2, 64, 2), (7, 200, 7), (20, 333, 11), (45, 90, 3)]:
+        M = [[rng.randrange(-(1 << bits), 1 << bits) for _ in range(n)] for _ in range(n)]
+        mag, sgn = _limbs(M, L)
+        d = idet.int_det_mp(mag, sgn)
+        assert d == exact.bareiss_det(M), (n, bits)
+
+
+def test_int_det_mp_sandwich_recovers_s_n():
+    """det(U diag(1,..,1,d) V) = d. One solve gives s~_n = d / gcd(d, w),
+    w the last entry of U^{-1} b (Section 2.2: s~_n may be a proper divisor
+    of s_n), so K is d up to a small cofactor, which the CRA of det / K
+    finds with a few primes."""
+    for n, bits, seed in [(12, 100, 1), (40, 600, 2), (150, 600, 3)]:
+        mag, sgn, d = workloads.lift_heavy_limbs(n, dbits=bits, seed=seed)
+        got, st = idet.int_det_mp(mag, sgn, return_stats=True)
+        assert got == d
+        if n <= 40:
+            assert got == exact.bareiss_det(workloads.from_limbs(mag, sgn))
+        assert bits - 1 - 16 <= st["log2_K"] <= bits - 1, st
+        assert 0 < st["lift_iters"] < 200, st
+
+
+def test_int_det_mp_single_limb_equals_int_det():
+    A = workloads.dense_pm2p20(300, seed=5)
+    M = A.tolist()
+    mag, sgn = _limbs(M, 1)
+    assert idet.int_det_mp(mag, sgn) == idet.int_det(A)
+    assert idet.int_det_mp(mag, sgn, prime_bits=21) == idet.int_det(A)
+
+
+def test_int_det_mp_degenerate():
+    z = np.zeros((5, 5, 2), dtype=np.uint32)
+    assert idet.int_det_mp(z, np.zeros((5, 5), dtype=np.int8)) == 0
+    rng = random.Random(8)
+    M = [[rng.randrange(-(1 << 100), 1 << 100) for _ in range(30)] for _ in range(30)]
+    M[7] = [a + 3 * b for a, b in zip(M[2], M[11])]
+    mag, sgn = _limbs(M, 5)
+    assert idet.int_det_mp(mag, sgn) == 0
+    mag, sgn = _limbs([[-(1 << 95) + 7]], 3)
+    assert idet.int_det_mp(mag, sgn) == -(1 << 95) + 7
+
+
+def test_int_det_mp_lift_heavy_full_size():
+    """The lift-heavy workload at its full size: n = 2000, 600-bit d."""
+    mag, sgn, d = workloads.lift_heavy_limbs(2000, dbits=600, seed=0)
+    got, st = idet.int_det_mp(mag, sgn, return_stats=True)
+    assert got == d
+    assert 599 - 16 <= st["log2_K"] <= 599, st
+    assert st["lift_iters"] < 120, st
+    assert st["primes_used"] < 30, st

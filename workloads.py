@@ -207,3 +207,86 @@ def to_limbs(M: list[list[int]], limbs: int) -> tuple[np.ndarray, np.ndarray]:
             if v:
                 raise ValueError("entry does not fit in the given limb count")
     return mag, sgn
+
+
+def lift_heavy_limbs(n: int = 2000, dbits: int = 600, seed: int = 0,
+                     cmax: int = 3) -> tuple[np.ndarray, np.ndarray, int]:
+    """The lift-heavy matrix A = U diag(1, ..., 1, d) V in sign-magnitude
+    limbs, built without Python big integers: U (4n random row operations on
+    the identity) and V (4n column operations) stay small (16 bits for
+    n = 2000, checked below), and U diag(1,..,1,d) V = U V + (d - 1) u v^T
+    with u the last column of U and v the last row of V. U V is exact in
+    float64 (integer partial sums below 2^53, checked). Returns (mag uint32
+    [n][n][L], sgn int8 [n][n], d) with L = ceil((dbits + 80) / 32)."""
+    g = rng(seed + 7919)
+    d = int.from_bytes(g.bytes((dbits + 7) // 8), "little")
+    d &= (1 << dbits) - 1
+    d |= (1 << (dbits - 1)) | 1
+    g = rng(seed)
+    U = np.eye(n, dtype=np.int64)
+    for _ in range(4 * n):
+        i, j = g.choice(n, size=2, replace=False)
+        c = 0
+        while c == 0:
+            c = int(g.integers(-cmax, cmax, endpoint=True))
+        U[i] += c * U[j]
+    V = np.eye(n, dtype=np.int64)
+    for _ in range(4 * n):
+        i, j = g.choice(n, size=2, replace=False)
+        c = 0
+        while c == 0:
+            c = int(g.integers(-cmax, cmax, endpoint=True))
+        V[:, i] += c * V[:, j]
+    bu = int(np.abs(U).max()).bit_length()
+    bv = int(np.abs(V).max()).bit_length()
+    if bu + bv + int(n).bit_length() > 52 or bu > 31 or bv > 31:
+        raise ValueError("unimodular factors too large for the exact float64 product")
+    UV = np.rint(U.astype(np.float64) @ V.astype(np.float64)).astype(np.int64)
+    u = U[:, n - 1]
+    v = V[n - 1, :]
+    L = (dbits + 80 + 31) // 32
+    dm1 = d - 1
+    K = (dbits + 15) // 16 + 1
+    ddig = np.array([(dm1 >> (16 * k)) & 0xFFFF for k in range(K)], dtype=np.int64)
+    mag = np.zeros((n, n, L), dtype=np.uint32)
+    sgn = np.zeros((n, n), dtype=np.int8)
+    nd = 2 * L + 2  # 16-bit digits of the magnitude
+    for r0 in range(0, n, 128):
+        r1 = min(n, r0 + 128)
+        w = np.outer(u[r0:r1], v)                     # |w| < 2^(bu + bv)
+        t = UV[r0:r1]
+        s = np.where(w != 0, np.sign(w), np.sign(t)).astype(np.int64)
+        aw = np.abs(w)
+        w0, w1 = aw & 0xFFFF, aw >> 16
+        # |a| = |w| (d - 1) + s t, in 16-bit digits with carries
+        dig = np.zeros((nd,) + w.shape, dtype=np.int64)
+        for k in range(K):
+            dig[k] += ddig[k] * w0
+            dig[k + 1] += ddig[k] * w1
+        dig[0] += s * t
+        for k in range(nd - 1):
+            c = dig[k] >> 16
+            dig[k] &= 0xFFFF
+            dig[k + 1] += c
+        if np.any(dig[nd - 1] != 0):
+            raise ValueError("limb count too small")
+        for l in range(L):
+            mag[r0:r1, :, l] = (dig[2 * l] | (dig[2 * l + 1] << 16)).astype(np.uint32)
+        nz = np.any(dig != 0, axis=0)
+        sgn[r0:r1] = np.where(nz, s, 0).astype(np.int8)
+    return mag, sgn, d
+
+
+def from_limbs(mag: np.ndarray, sgn: np.ndarray) -> list[list[int]]:
+    """Python-int matrix from the sign-magnitude limb form."""
+    n, _, L = mag.shape
+    out = []
+    for i in range(n):
+        row = []
+        for j in range(n):
+            v = 0
+            for l in range(L - 1, -1, -1):
+                v = (v << 32) | int(mag[i, j, l])
+            row.append(int(sgn[i, j]) * v)
+        out.append(row)
+    return out

@@ -244,6 +244,56 @@ int idet_det_mod_primes_noalloc(const int64_t *A, int64_t n, int64_t lda,
                                 int32_t on_device, const uint32_t *primes,
                                 int32_t nprimes, void *stream, uint32_t *det_mod);
 
+/* ------------------------------------------------------------------------
+ * Serving with continuous batching. A server owns `slots` worker threads,
+ * each with its own CUDA stream on the current device. idet_submit copies
+ * the matrix (host memory, |a_ij| <= 2^31 - 1) and queues the job; workers
+ * admit queued jobs first-in first-out whenever a slot and device memory are
+ * free: each job is charged an estimate of its device footprint against
+ * hbm_budget (0 = 80% of the free memory at creation); a job that does not
+ * fit lets later ones that fit go ahead, until it has been overtaken
+ * 2 slots + 2 times, after which it waits for the memory. A worker taking a
+ * job with n <= small_n also takes the other queued jobs with n <= small_n
+ * that fit (max_batch in all) and runs them as one batch
+ * (idet_int_det_batch); larger jobs run alone (idet_int_det). Jobs on
+ * different workers overlap on the device. Each result is the value
+ * idet_int_det returns for that matrix with the server's opts.
+ */
+typedef struct idet_server idet_server;
+
+typedef struct {
+    int32_t status;        /* the job's result code (IDET_*)                 */
+    int32_t batched;       /* jobs in the group it ran in (1 = alone)        */
+    int32_t worker;        /* worker (stream) that ran it                    */
+    int32_t pad;
+    double ms_queue;       /* submit -> start, host clock                   */
+    double ms_run;         /* start -> end                                  */
+    double ms_latency;     /* submit -> end                                 */
+    double t_start_ms;     /* start and end on a monotonic host clock       */
+    double t_end_ms;
+    idet_stats stats;      /* of its run (of the whole group when batched)  */
+} idet_job_info;
+
+typedef struct {
+    int32_t queued, running, max_running, pad;
+    uint64_t bytes_in_use, budget, admitted, completed, groups;
+} idet_server_stats;
+
+/* NULL on error (idet_last_error). opts may be NULL. */
+idet_server *idet_server_create(size_t hbm_budget, int32_t slots, int32_t small_n,
+                                int32_t max_batch, const idet_opts *opts);
+/* IDET_ERR_NOMEM if the job alone exceeds the budget. */
+int idet_submit(idet_server *srv, const int64_t *A, int64_t n, int64_t lda, uint64_t *ticket);
+/* Waits up to timeout_ms (< 0: no limit) for the job. IDET_OK: det written,
+ * ticket released. IDET_ERR_TIMEOUT: not finished yet. IDET_ERR_BUFFER:
+ * det->nlimbs set to the size needed, job kept. A job error is returned as
+ * its code (ticket released). info may be NULL. */
+int idet_poll(idet_server *srv, uint64_t ticket, int32_t timeout_ms, idet_int *det,
+              idet_job_info *info);
+void idet_server_info(idet_server *srv, idet_server_stats *out);
+/* Finishes the submitted jobs, then stops the workers. */
+void idet_server_destroy(idet_server *srv);
+
 #ifdef __cplusplus
 }
 #endif

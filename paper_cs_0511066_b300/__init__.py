@@ -11,6 +11,7 @@ __graft_entry__.build()); importing this module without libidet.so raises.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 
 import numpy as np
@@ -385,3 +386,97 @@ def int_det_mp(mag, sgn, *, certify: bool = False, seed: int | None = None, lif:
     d = _to_int(out, buf)
     del keep
     return (d, st.as_dict()) if return_stats else d
+
+
+class idet_job_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("batched", ctypes.c_int32),
+                ("worker", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("ms_queue", ctypes.c_double), ("ms_run", ctypes.c_double),
+                ("ms_latency", ctypes.c_double), ("t_start_ms", ctypes.c_double),
+                ("t_end_ms", ctypes.c_double), ("stats", idet_stats)]
+
+
+class idet_server_stats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int32), ("running", ctypes.c_int32),
+                ("max_running", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("bytes_in_use", ctypes.c_uint64), ("budget", ctypes.c_uint64),
+                ("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("groups", ctypes.c_uint64)]
+
+
+_lib.idet_server_create.argtypes = [ctypes.c_size_t, _i32, _i32, _i32, ctypes.POINTER(idet_opts)]
+_lib.idet_server_create.restype = _P
+_lib.idet_submit.argtypes = [_P, _P, _i64, _i64, ctypes.POINTER(ctypes.c_uint64)]
+_lib.idet_poll.argtypes = [_P, ctypes.c_uint64, _i32, ctypes.POINTER(idet_int),
+                           ctypes.POINTER(idet_job_info)]
+_lib.idet_server_info.argtypes = [_P, ctypes.POINTER(idet_server_stats)]
+_lib.idet_server_info.restype = None
+_lib.idet_server_destroy.argtypes = [_P]
+_lib.idet_server_destroy.restype = None
+
+
+class Server:
+    """Determinant server with continuous batching (idet_server_*): submit
+    host matrices, poll for exact determinants. See include/idet.h."""
+
+    def __init__(self, hbm_budget: int = 0, slots: int = 4, small_n: int = 512,
+                 max_batch: int = 64, **opts):
+        _get_torch()  # the CUDA context is the one torch uses
+        o = default_opts(**opts)
+        self._srv = _lib.idet_server_create(int(hbm_budget), slots, small_n, max_batch,
+                                            ctypes.byref(o))
+        if not self._srv:
+            raise IdetError(_lib.idet_last_error().decode(errors="replace"))
+        self._cap = {}
+
+    def submit(self, A) -> int:
+        a = np.ascontiguousarray(np.asarray(A, dtype=np.int64))
+        if a.ndim != 2 or a.shape[0] != a.shape[1]:
+            raise ValueError("square matrix expected")
+        t = ctypes.c_uint64(0)
+        _check(_lib.idet_submit(self._srv, a.ctypes.data, a.shape[0], a.shape[0], ctypes.byref(t)))
+        n = a.shape[0]
+        amax = int(np.abs(a).max()) if n else 0
+        self._cap[t.value] = int(n * (amax.bit_length() + 0.5 * math.log2(n + 1)) / 32) + 16
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = -1):
+        """(det, info dict), or None if not finished within timeout_ms."""
+        info = idet_job_info()
+        cap = self._cap.get(ticket, 64)
+        while True:
+            buf = (ctypes.c_uint32 * cap)()
+            out = idet_int(0, 0, cap, buf)
+            rc = _lib.idet_poll(self._srv, ticket, timeout_ms, ctypes.byref(out), ctypes.byref(info))
+            if rc == IDET_ERR_BUFFER:
+                cap = int(out.nlimbs) + 8
+                continue
+            if rc == IDET_ERR_TIMEOUT:
+                return None
+            self._cap.pop(ticket, None)
+            _check(rc)
+            d = {f: getattr(info, f) for f, _ in info._fields_ if f not in ("pad", "stats")}
+            d["stats"] = info.stats.as_dict()
+            return _to_int(out, buf), d
+
+    def info(self) -> dict:
+        s = idet_server_stats()
+        _lib.idet_server_info(self._srv, ctypes.byref(s))
+        return {f: getattr(s, f) for f, _ in s._fields_ if f != "pad"}
+
+    def close(self):
+        if self._srv:
+            _lib.idet_server_destroy(self._srv)
+            self._srv = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

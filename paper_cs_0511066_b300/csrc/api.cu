@@ -21,7 +21,8 @@ namespace idet {
 // Errors, allocator, launch counter
 
 static thread_local char g_err[1024] = "no error";
-unsigned long long g_launches = 0;
+std::atomic<unsigned long long> g_launches{0};
+thread_local bool t_native_alloc = false;
 
 void set_last_error(const char *fmt, ...) {
     va_list ap;
@@ -34,9 +35,11 @@ static idet_alloc_fn g_alloc = nullptr;
 static idet_free_fn g_free = nullptr;
 static void *g_actx = nullptr;
 
+Workspace::Workspace(cudaStream_t s) : stream_(s), native_(t_native_alloc || !g_alloc) {}
+
 Workspace::~Workspace() {
     for (size_t i = ptrs_.size(); i-- > 0;) {
-        if (g_free)
+        if (!native_)
             g_free(ptrs_[i], (void *)stream_, g_actx);
         else
             cudaFreeAsync(ptrs_[i], stream_);
@@ -46,7 +49,7 @@ Workspace::~Workspace() {
 int Workspace::alloc(void **ptr, size_t bytes) {
     bytes = (bytes + 255) / 256 * 256;
     void *p = nullptr;
-    if (g_alloc) {
+    if (!native_) {
         p = g_alloc(bytes, (void *)stream_, g_actx);
     } else if (cudaMallocAsync(&p, bytes, stream_) != cudaSuccess) {
         cudaGetLastError();

@@ -12,6 +12,7 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <atomic>
 #include <vector>
 
 #include "../../include/idet.h"
@@ -109,9 +110,13 @@ void set_last_error(const char *fmt, ...);
 // (or cudaMallocAsync on the call's stream), released in LIFO order when the
 // Workspace goes out of scope.
 
+// Set by threads that must not call a user allocator (the serving
+// workers): their workspaces use cudaMallocAsync on their own stream.
+extern thread_local bool t_native_alloc;
+
 class Workspace {
   public:
-    explicit Workspace(cudaStream_t s) : stream_(s) {}
+    explicit Workspace(cudaStream_t s);
     ~Workspace();
     // Returns IDET_OK or IDET_ERR_NOMEM; *ptr is 256-byte aligned.
     int alloc(void **ptr, size_t bytes);
@@ -122,13 +127,14 @@ class Workspace {
 
   private:
     cudaStream_t stream_;
+    bool native_;
     std::vector<void *> ptrs_;
 };
 
 // Counter of kernel launches made by this library (for the benchmark's
 // launch accounting); incremented by every launcher.
-extern unsigned long long g_launches;
-inline void count_launch(unsigned k = 1) { g_launches += k; }
+extern std::atomic<unsigned long long> g_launches;
+inline void count_launch(unsigned k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------------------
 // Kernel launchers (defined in the .cu files)

@@ -37,6 +37,8 @@
 #include <algorithm>
 #include <cstdlib>
 
+#include <mutex>
+
 #include "idet_internal.cuh"
 
 namespace idet {
@@ -447,6 +449,8 @@ k_lift(LiftArgs a, const TA *__restrict__ Anar, LiftGeom g, int32_t *__restrict_
     }
 }
 
+std::mutex g_coop_mu;
+
 template <class TA>
 int launch_lift_t(const LiftArgs &a0, const void *Anar, int64_t ld, Workspace &ws,
                   int *timed_out, float *ms) {
@@ -527,6 +531,10 @@ int launch_lift_t(const LiftArgs &a0, const void *Anar, int64_t ld, Workspace &w
         IDET_CUDA_TRY(cudaEventCreate(&e1));
         IDET_CUDA_TRY(cudaEventRecord(e0, s));
     }
+    // One grid-synchronised lift at a time in the process: two of them on
+    // different streams could each hold part of the SMs and wait for the
+    // other's. Held until the kernel has finished (stream synchronised below).
+    std::unique_lock<std::mutex> coop(g_coop_mu);
     IDET_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_lift<TA>, dim3((unsigned)G),
                                               dim3(kLiftThreads), args, smem, s));
     count_launch();

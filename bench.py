@@ -160,6 +160,188 @@ def run_case(case):
     print(json.dumps({"case": case, "seconds": time.perf_counter() - t0}))
 
 
+def _line(metric, value, unit, args, ms, config, **extra):
+    d = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+         "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded numpy PCG64)",
+         "config": config}
+    d.update(extra)
+    return d
+
+
+def _timed_steps(torch, args, fn, clk_name):
+    """W untimed calls, then K timed ones (CUDA events on torch's current
+    stream, which the library uses; L2 flushed by a 256 MiB write before
+    each); returns (ms per step, results of the timed calls, clocks, launches)."""
+    import paper_cs_0511066_b300 as idet
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    out, times = [], []
+    launches0 = idet.launch_count()
+    clk = Clocks(os.path.join(ROOT, "gpurun_out", clk_name)
+                 if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/" + clk_name)
+    with clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out.append(fn())
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    return sum(times) / len(times), out, clk.summary(), idet.launch_count() - launches0
+
+
+def run_batch(args):
+    """512 matrices, n log-uniform in [32, 512], entries in [-2^10, 2^10], in
+    one batched call per step; the plain path (one matrix at a time) is
+    timed on every 8th matrix of the same batch."""
+    import torch
+    import paper_cs_0511066_b300 as idet
+    mats = workloads.batch_mix(count=512, nmin=32, nmax=512, bits=10, seed=0)
+    dev = [torch.from_numpy(A).cuda() for A in mats]
+    ms, out, clocks, launches = _timed_steps(
+        torch, args, lambda: idet.int_det_batch(dev, return_stats=True), "clocks_batch.csv")
+    dets, st = out[-1]
+    sample = dev[::8]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = [idet.int_det(A) for A in sample]
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    assert plain == dets[::8], "batched and plain results differ"
+    pinned = [torch.from_numpy(A).pin_memory().numpy() for A in mats]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    idet.int_det_batch(pinned)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    line = _line("exact dets/s (batched)", 512 / (ms / 1000.0), "dets/s", args, ms,
+                 {"workload": "batch_512_n32-512_pm2p10", "matrices_per_step": 512,
+                  "l2": "256 MiB write between timed steps"},
+                 e2e={"value": 512 / e2e_s, "unit": "dets/s",
+                      "h2d_bytes_per_step": int(sum(A.nbytes for A in mats)),
+                      "d2h_bytes_per_step": int(sum(4 * (abs(d).bit_length() // 32 + 1) for d in dets))},
+                 gpu_launches=int(launches), clocks=clocks,
+                 plain_path={"dets_per_s": len(sample) / plain_s, "sample": "every 8th matrix (64)"},
+                 stats={k: (round(v, 2) if isinstance(v, float) else v) for k, v in st.items()})
+    print(json.dumps(line))
+
+
+def run_lift_heavy(args):
+    """n = 2000, A = U diag(1, ..., 1, d) V, d a 600-bit odd integer, entries
+    of about 640 bits given as 22 base-2^32 limbs (idet_int_det_mp)."""
+    import torch
+    import paper_cs_0511066_b300 as idet
+    mag, sgn, d = workloads.lift_heavy_limbs(2000, dbits=600, seed=0)
+    dm = torch.from_numpy(mag.view(np.int32)).cuda()
+    ds = torch.from_numpy(sgn).cuda()
+    ms, out, clocks, launches = _timed_steps(
+        torch, args, lambda: idet.int_det_mp(dm, ds, return_stats=True), "clocks_mp.csv")
+    got, st = out[-1]
+    assert got == d
+    t0 = time.perf_counter()
+    idet.int_det_mp(mag, sgn)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    hbm, src = peaks()
+    ach = st["lift_bytes"] / (st["ms_lift_kernel"] / 1000.0) / 1e9 if st["ms_lift_kernel"] else None
+    line = _line("exact dets/s", 1000.0 / ms, "dets/s", args, ms,
+                 {"workload": "lift_heavy_n2000_d600bit_limbs22"},
+                 e2e={"value": 1.0 / e2e_s, "unit": "dets/s", "h2d_bytes_per_step": int(mag.nbytes + sgn.nbytes),
+                      "d2h_bytes_per_step": 4 * 20},
+                 gpu_launches=int(launches), clocks=clocks,
+                 roofline={"kernel": "k_mp_cx+k_mp_update", "bound": "hbm", "achieved": ach,
+                           "peak": hbm, "unit": "GB/s", "frac": ach / hbm if ach else None,
+                           "traffic": None, "peak_source": src},
+                 stats={k: (round(v, 2) if isinstance(v, float) else v) for k, v in st.items()})
+    print(json.dumps(line))
+
+
+def run_small(args):
+    """n = 100, entries in [-100, 100], CRA primes in (2^30, 2^31); 64
+    matrices per step, one call each."""
+    import torch
+    import paper_cs_0511066_b300 as idet
+    mats = [torch.from_numpy(workloads.dense_pm100(100, seed=s)).cuda() for s in range(64)]
+    ms, out, clocks, launches = _timed_steps(
+        torch, args, lambda: [idet.int_det(A, prime_bits=31, return_stats=True) for A in mats],
+        "clocks_small.csv")
+    st = out[-1][0][1]
+    line = _line("exact dets/s", 64 / (ms / 1000.0), "dets/s", args, ms,
+                 {"workload": "dense_pm100_n100_x64", "prime_bits": 31},
+                 gpu_launches=int(launches), clocks=clocks,
+                 stats={k: (round(v, 2) if isinstance(v, float) else v) for k, v in st.items()})
+    print(json.dumps(line))
+
+
+def run_serve(args):
+    """Served jobs: n log-uniform in [64, 4096], entry bits in {8, 16, 32},
+    Poisson arrivals at rates 0.25..4 x the measured closed-loop capacity;
+    p50/p99 latency (submit to result, host clock) and dets/s per rate. The
+    plain path (idet_int_det one job at a time) runs on the same job mix."""
+    import threading
+    import torch
+    import paper_cs_0511066_b300 as idet
+    g = workloads.rng(2024)
+    jobs = [workloads.serving_job(g) for _ in range(48)]
+    probe = jobs[:16]
+    idet.int_det(jobs[0][:64, :64])
+    t0 = time.perf_counter()
+    plain = [idet.int_det(A) for A in probe]
+    plain_s = time.perf_counter() - t0
+    res = {}
+    slots = int(os.environ.get("IDET_SERVE_SLOTS", "4"))
+    with idet.Server(slots=slots) as srv:
+        t0 = time.perf_counter()
+        tk = [srv.submit(A) for A in probe]
+        got = [srv.poll(t)[0] for t in tk]
+        cap_s = time.perf_counter() - t0
+        assert got == plain, "served and plain results differ"
+        capacity = len(probe) / cap_s
+        sweep = []
+        per_rate = int(os.environ.get("IDET_SERVE_JOBS", "32"))
+        rr = np.random.default_rng(7)
+        for f in (0.25, 0.5, 1.0, 2.0, 4.0):
+            lam = f * capacity
+            gaps = rr.exponential(1.0 / lam, size=per_rate)
+            tickets = []
+            t_first = time.perf_counter()
+            t_next = t_first
+            for k in range(per_rate):
+                t_next += gaps[k]
+                dt = t_next - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                tickets.append(srv.submit(jobs[k % len(jobs)]))
+            infos = [srv.poll(t)[1] for t in tickets]
+            t_end = max(i["t_end_ms"] for i in infos)
+            t_sub0 = min(i["t_end_ms"] - i["ms_latency"] for i in infos)
+            lat = sorted(i["ms_latency"] for i in infos)
+            sweep.append({"rate_x_capacity": f, "offered_jobs_per_s": round(lam, 3),
+                          "dets_per_s": round(per_rate / ((t_end - t_sub0) / 1000.0), 3),
+                          "p50_ms": round(float(np.percentile(lat, 50)), 2),
+                          "p99_ms": round(float(np.percentile(lat, 99)), 2),
+                          "batched_jobs": int(sum(1 for i in infos if i["batched"] > 1))})
+        info = srv.info()
+    best = max(s["dets_per_s"] for s in sweep)
+    line = _line("exact dets/s and p50/p99 latency (served)", best, "dets/s", args, None,
+                 {"workload": "serve_poisson_n64-4096_bits8-16-32", "slots": slots,
+                  "jobs_per_rate": per_rate},
+                 e2e={"value": best, "unit": "dets/s", "h2d_bytes_per_step": None,
+                      "d2h_bytes_per_step": None},
+                 closed_loop_dets_per_s=round(capacity, 3),
+                 plain_path={"dets_per_s": round(len(probe) / plain_s, 3),
+                             "sample": "the 16 probe jobs, idet_int_det one at a time"},
+                 sweep=sweep, server=info)
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -170,11 +352,19 @@ def main():
     ap.add_argument("--case", default=None,
                     help="profiling case: 'lift' (Dixon lifting, n=4000, 64 digits) or "
                          "'lu' (det mod 4 primes, n=4000); runs once and prints timings")
+    ap.add_argument("--workload", default="plain",
+                    choices=["plain", "batch", "serve", "lift_heavy", "small"],
+                    help="plain (default): n=1000 [0,255] + n=4000 +-2^20; batch: 512 "
+                         "matrices n in [32,512]; serve: Poisson-served jobs n in [64,4096]; "
+                         "lift_heavy: n=2000 U diag(1,..,d) V, 600-bit d; small: n=100")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.case:
         return run_case(args.case)
+    if args.workload != "plain":
+        return {"batch": run_batch, "serve": run_serve, "lift_heavy": run_lift_heavy,
+                "small": run_small}[args.workload](args)
 
     import torch
     import paper_cs_0511066_b300 as idet

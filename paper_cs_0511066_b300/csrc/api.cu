@@ -31,6 +31,22 @@ void set_last_error(const char *fmt, ...) {
     va_end(ap);
 }
 
+int allow_max_smem(const void *kernel) {
+    static std::mutex mu;
+    static std::unordered_set<const void *> done;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count(kernel)) return IDET_OK;
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    IDET_CUDA_TRY(cudaGetDevice(&dev));
+    IDET_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    IDET_CUDA_TRY(cudaFuncGetAttributes(&fa, kernel));
+    IDET_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       optin - (int)fa.sharedSizeBytes));
+    done.insert(kernel);
+    return IDET_OK;
+}
+
 static idet_alloc_fn g_alloc = nullptr;
 static idet_free_fn g_free = nullptr;
 static void *g_actx = nullptr;

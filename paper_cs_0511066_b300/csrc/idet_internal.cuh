@@ -105,6 +105,12 @@ void set_last_error(const char *fmt, ...);
         if (_rc != IDET_OK) return _rc; \
     } while (0)
 
+// Raises a kernel's dynamic shared-memory limit to the most the device
+// allows (opt-in limit less the kernel's static shared memory). It is always
+// the same value, so host threads launching concurrently cannot lower it
+// under one another's launches, as per-call sizes would. Defined in api.cu.
+int allow_max_smem(const void *kernel);
+
 // ---------------------------------------------------------------------------
 // Device workspace: allocations made through the user-installed allocator
 // (or cudaMallocAsync on the call's stream), released in LIFO order when the

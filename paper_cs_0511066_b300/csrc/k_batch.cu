@@ -136,8 +136,7 @@ int launch_lift_multi(const LiftJob *jobs_dev, int count, int max_ld, cudaStream
         set_last_error("batched lift: n too large");
         return IDET_ERR_ARG;
     }
-    IDET_CUDA_TRY(cudaFuncSetAttribute(k_lift_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
+    IDET_TRY(allow_max_smem((const void *)k_lift_multi));
     k_lift_multi<<<count, kBT, smem, s>>>(jobs_dev);
     count_launch();
     IDET_CUDA_TRY(cudaGetLastError());
@@ -332,8 +331,7 @@ int launch_elim_cluster(const ElimJob *jobs_dev, int count, int max_n, int mode,
         set_last_error("cluster elimination: n = %d too large", max_n);
         return IDET_ERR_ARG;
     }
-    IDET_CUDA_TRY(cudaFuncSetAttribute(k_elim_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
+    IDET_TRY(allow_max_smem((const void *)k_elim_cluster));
     k_elim_cluster<<<count * kEC, kECT, smem, s>>>(jobs_dev, mode);
     count_launch();
     IDET_CUDA_TRY(cudaGetLastError());

@@ -688,9 +688,7 @@ int launch_ratrecon(const int64_t *z, int m, uint32_t p, int hN, int hD, uint32_
         IDET_TRY(ws.alloc_n(&gbuf, 4 * (size_t)cap));
         smem = 0;
     } else {
-        IDET_CUDA_TRY(cudaFuncSetAttribute(k_ratrecon,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem));
+        IDET_TRY(allow_max_smem((const void *)k_ratrecon));
     }
     k_ratrecon<<<1, kRT, smem, s>>>(z, m, p, hN, hD, gbuf, cap, den, den_cap, info, ainit, alen);
     count_launch();
@@ -706,8 +704,7 @@ int launch_ratrecon_multi(const RRJob *jobs_dev, int count, int max_m, cudaStrea
         set_last_error("batched reconstruction: lift too long");
         return IDET_ERR_ARG;
     }
-    IDET_CUDA_TRY(cudaFuncSetAttribute(k_ratrecon_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
+    IDET_TRY(allow_max_smem((const void *)k_ratrecon_multi));
     k_ratrecon_multi<<<count, kRT, smem, s>>>(jobs_dev, cap);
     count_launch();
     IDET_CUDA_TRY(cudaGetLastError());

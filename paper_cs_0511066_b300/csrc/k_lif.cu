@@ -166,8 +166,7 @@ int launch_lif_check(const int32_t *digits, int64_t n, int m, const uint32_t *D,
         set_last_error("largest invariant factor: lift too long for the per-entry check");
         return IDET_ERR_ARG;
     }
-    IDET_CUDA_TRY(cudaFuncSetAttribute(k_lif_check, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
+    IDET_TRY(allow_max_smem((const void *)k_lif_check));
     k_lif_check<<<(unsigned)n, kLT, smem, s>>>(digits, n, m, D, dlen, p, h, flag, -1, nullptr);
     count_launch();
     IDET_CUDA_TRY(cudaGetLastError());
@@ -177,8 +176,7 @@ int launch_lif_check(const int32_t *digits, int64_t n, int m, const uint32_t *D,
 int launch_lif_entry(const int32_t *digits, int64_t n, int m, const uint32_t *D, int dlen,
                      uint32_t p, int64_t j, int64_t *yout, cudaStream_t s) {
     const size_t smem = check_smem(m, dlen);
-    IDET_CUDA_TRY(cudaFuncSetAttribute(k_lif_check, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
+    IDET_TRY(allow_max_smem((const void *)k_lif_check));
     k_lif_check<<<1, kLT, smem, s>>>(digits, n, m, D, dlen, p, m, nullptr, j, yout);
     count_launch();
     IDET_CUDA_TRY(cudaGetLastError());

@@ -514,8 +514,7 @@ int launch_lift_t(const LiftArgs &a0, const void *Anar, int64_t ld, Workspace &w
         g.keep = (int)(frac * per_it);
     }
     const size_t smem = (size_t)(8 * ld + g.S * crow + (int64_t)g.cC * crow + (int64_t)g.cA * arow);
-    IDET_CUDA_TRY(cudaFuncSetAttribute(k_lift<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
+    IDET_TRY(allow_max_smem((const void *)k_lift<TA>));
     int occ = 0;
     IDET_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lift<TA>, kLiftThreads,
                                                                 smem));

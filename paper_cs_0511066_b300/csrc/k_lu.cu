@@ -578,8 +578,7 @@ int lu_blocked(int32_t *R, int64_t n, const ModP *mods, int W, int nb, int32_t *
                LUState *st, cudaStream_t s, int path) {
     k_state_init<<<W, 256, 0, s>>>(st, mods, W, perm, n);
     count_launch();
-    IDET_CUDA_TRY(cudaFuncSetAttribute(k_panel_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       200 * 1024));
+    IDET_TRY(allow_max_smem((const void *)k_panel_cluster));
     const int64_t nn = n * n;
     const int NB = WIDE ? nb : 4 * nb;
     auto upd = [&](int64_t r, int64_t c, int64_t kr, int M, int N, int K) -> int {
@@ -640,9 +639,7 @@ int lu_factor_batched(int32_t *R, int64_t n, const ModP *mods_dev,
     if (nb <= 0 || nb > kNBMax) nb = kNBMax;
     if (n <= kSmallN) {
         size_t smem = sizeof(int32_t) * n * n;
-        IDET_CUDA_TRY(cudaFuncSetAttribute(k_lu_small,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)(sizeof(int32_t) * kSmallN * kSmallN)));
+        IDET_TRY(allow_max_smem((const void *)k_lu_small));
         k_lu_small<<<W, 512, smem, s>>>(R, (int)n, mods_dev, st, perm);
         count_launch();
         IDET_CUDA_TRY(cudaGetLastError());
@@ -723,8 +720,7 @@ int lu_small_into(int32_t *R, int n, const ModP *mods_dev, int W, LUState *st,
         return IDET_ERR_ARG;
     }
     const size_t smem = sizeof(int32_t) * (size_t)n * n;
-    IDET_CUDA_TRY(cudaFuncSetAttribute(k_lu_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(sizeof(int32_t) * kSmallN * kSmallN)));
+    IDET_TRY(allow_max_smem((const void *)k_lu_small));
     k_lu_small<<<W, 512, smem, s>>>(R, n, mods_dev, st, nullptr);
     count_launch();
     IDET_CUDA_TRY(cudaGetLastError());
@@ -744,8 +740,7 @@ int lu_small_multi(const LUSmallJob *jobs_dev, int count, int max_n, cudaStream_
         set_last_error("lu_small_multi: n must be at most %d", kSmallN);
         return IDET_ERR_ARG;
     }
-    IDET_CUDA_TRY(cudaFuncSetAttribute(k_lu_small_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(sizeof(int32_t) * kSmallN * kSmallN)));
+    IDET_TRY(allow_max_smem((const void *)k_lu_small_multi));
     k_lu_small_multi<<<count, 512, sizeof(int32_t) * (size_t)max_n * max_n, s>>>(jobs_dev);
     count_launch();
     IDET_CUDA_TRY(cudaGetLastError());

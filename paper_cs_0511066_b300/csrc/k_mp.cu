@@ -316,8 +316,7 @@ int launch_mp_step(const MpLiftArgs &a, int it, cudaStream_t s) {
         return IDET_ERR_ARG;
     }
     if (smx > 48 * 1024)
-        IDET_CUDA_TRY(cudaFuncSetAttribute(k_mp_cx, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smx));
+        IDET_TRY(allow_max_smem((const void *)k_mp_cx));
     k_mp_cx<<<(unsigned)((a.n + kMT / 32 - 1) / (kMT / 32)), kMT, smx, s>>>(
         a.C, a.ldc, a.n, a.rm, a.mod, a.u, a.x, a.digits + (int64_t)it * a.n,
         (unsigned long long *)(a.z + it));
@@ -329,8 +328,7 @@ int launch_mp_step(const MpLiftArgs &a, int it, cudaStream_t s) {
         return IDET_ERR_ARG;
     }
     if (smu > 48 * 1024)
-        IDET_CUDA_TRY(cudaFuncSetAttribute(k_mp_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smu));
+        IDET_TRY(allow_max_smem((const void *)k_mp_update));
     k_mp_update<<<(unsigned)a.n, kMT, smu, s>>>(a.planes, a.T, a.ldp, a.n, a.x, a.rd, a.len, a.mod,
                                                 a.pinv15, a.rm, a.info);
     count_launch();

@@ -18,6 +18,7 @@
 #include <cstring>
 #include <deque>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -41,6 +42,7 @@ struct SJob {
     int batched = 0;
     int skipped = 0;
     int worker = -1;
+    std::string err;
     Clock::time_point t_sub, t_start, t_end;
 };
 
@@ -170,12 +172,17 @@ void run_group(idet_server *S, std::vector<SJob *> &take, cudaStream_t st) {
         rc = idet_int_det_batch(count, ptr.data(), ns.data(), ns.data(), 0, &S->opts, st,
                                 outs.data(), &stats);
     }
-    if (rc != IDET_OK) cudaStreamSynchronize(st);
+    std::string err;
+    if (rc != IDET_OK) {
+        err = idet_last_error();
+        cudaStreamSynchronize(st);
+    }
     const auto now = Clock::now();
     std::lock_guard<std::mutex> lk(S->mu);
     for (int i = 0; i < count; ++i) {
         SJob *j = take[i];
         j->status = rc;
+        j->err = err;
         if (rc == IDET_OK) {
             j->sign = outs[i].sign;
             j->limbs.assign(bufs[i].begin(), bufs[i].begin() + outs[i].nlimbs);
@@ -338,9 +345,9 @@ int idet_poll(idet_server *S, uint64_t ticket, int32_t timeout_ms, idet_int *det
     }
     if (j->status != IDET_OK) {
         const int rc = j->status;
+        set_last_error("job %llu failed: %s", (unsigned long long)ticket, j->err.c_str());
         S->jobs.erase(it);
         delete j;
-        set_last_error("job failed with status %d", rc);
         return rc;
     }
     const uint32_t nl = (uint32_t)j->limbs.size();

@@ -48,7 +48,9 @@ extern "C" {
 #define IDET_PATH_INT64 1     /* CUDA cores, int64 delayed reduction         */
 #define IDET_PATH_I8 2        /* signed 7-bit int8 limbs, int32 accumulation */
 #define IDET_PATH_F64 3       /* FP64 with delayed reduction below 2^53      */
-#define IDET_PATH_BF16 4      /* 7-bit limbs exact in bf16, tcgen05 tensor   */
+#define IDET_PATH_BF16 4      /* 7-bit limbs exact in bf16, mma.sync        */
+#define IDET_PATH_TC05 5      /* 7-bit limbs exact in bf16, tcgen05.mma with
+                                 accumulators in tensor memory                */
 
 /* Big integer: sign in {-1, 0, +1}, magnitude in little-endian base-2^32
  * limbs. The caller provides limbs[0..cap). On IDET_ERR_BUFFER, nlimbs is set

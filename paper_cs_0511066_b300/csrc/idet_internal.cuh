@@ -260,6 +260,14 @@ int lu_inverse(const int32_t *R, const int32_t *perm, int64_t n,
 
 // k_gemm_tc.cu: C <- C - A B mod p on the tensor cores (21-bit primes,
 // K <= 32), path = IDET_PATH_I8, IDET_PATH_BF16 or IDET_PATH_F64.
+// tcgen05 bf16-limb trailing update (k_gemm_tc05.cu); scratch holds
+// tc05_scratch_bytes(n, W) bytes for any M, N <= n. tc05_check_error
+// synchronises s and reports a bounded wait that gave up.
+size_t tc05_scratch_bytes(int64_t n, int W);
+int gemm_sub_tc05(const int32_t *A, int64_t lda, int64_t sA, const int32_t *B, int64_t ldb,
+                  int64_t sB, int32_t *C, int64_t ldc, int64_t sC, int M, int N, int K,
+                  const ModP *mods, const LUState *st, int W, void *scratch, cudaStream_t s);
+int tc05_check_error(cudaStream_t s);
 int gemm_sub_tc(int path, const int32_t *A, int64_t lda, int64_t sA, const int32_t *B, int64_t ldb,
                 int64_t sB, int32_t *C, int64_t ldc, int64_t sC, int M, int N, int K,
                 const ModP *mods, const LUState *st, int W, cudaStream_t s);

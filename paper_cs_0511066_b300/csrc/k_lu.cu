@@ -575,7 +575,7 @@ int trsm_lower(const int32_t *Lm, int64_t sL, int32_t *X, int64_t sX, int64_t n,
 // update A22 <- A22 - L21 U12.
 template <bool WIDE>
 int lu_blocked(int32_t *R, int64_t n, const ModP *mods, int W, int nb, int32_t *perm,
-               LUState *st, cudaStream_t s, int path) {
+               LUState *st, cudaStream_t s, int path, void *scratch = nullptr) {
     k_state_init<<<W, 256, 0, s>>>(st, mods, W, perm, n);
     count_launch();
     IDET_TRY(allow_max_smem((const void *)k_panel_cluster));
@@ -587,6 +587,8 @@ int lu_blocked(int32_t *R, int64_t n, const ModP *mods, int W, int nb, int32_t *
         const int32_t *Ap = R + r * n + kr;
         const int32_t *Bp = R + kr * n + c;
         int32_t *Cp = R + r * n + c;
+        if (!WIDE && path == IDET_PATH_TC05)
+            return gemm_sub_tc05(Ap, n, nn, Bp, n, nn, Cp, n, nn, M, N, K, mods, st, W, scratch, s);
         if (!WIDE && path != IDET_PATH_INT64)
             return gemm_sub_tc(path, Ap, n, nn, Bp, n, nn, Cp, n, nn, M, N, K, mods, st, W, s);
         return gemm_sub<WIDE>(Ap, n, nn, Bp, n, nn, Cp, n, nn, M, N, K, mods, st, W, s);
@@ -649,7 +651,10 @@ int lu_factor_batched(int32_t *R, int64_t n, const ModP *mods_dev,
         // default trailing-update arithmetic for 21-bit primes
         // (AUTO = int64 delayed reduction: fastest measured at n = 1000 and 4000)
         const int path = update_path == IDET_PATH_AUTO ? IDET_PATH_INT64 : update_path;
-        IDET_TRY(lu_blocked<false>(R, n, mods_dev, W, nb, perm, st, s, path));
+        void *scratch = nullptr;
+        if (path == IDET_PATH_TC05) IDET_TRY(ws.alloc(&scratch, tc05_scratch_bytes(n, W)));
+        IDET_TRY(lu_blocked<false>(R, n, mods_dev, W, nb, perm, st, s, path, scratch));
+        if (path == IDET_PATH_TC05) IDET_TRY(tc05_check_error(s));
     }
     k_finalize_det<<<(W + 127) / 128, 128, 0, s>>>(st, mods_dev, W, det_out);
     count_launch();

@@ -201,16 +201,16 @@ def test_dixon_lift_identity_streamed_n4000():
     assert (lhs == b.astype(object)).all()
 
 
-PATHS = {"int64": 1, "i8": 2, "f64": 3, "bf16": 4}
+PATHS = {"int64": 1, "i8": 2, "f64": 3, "bf16": 4, "tc05": 5}
 
 
 @pytest.mark.parametrize("path", sorted(PATHS))
 @pytest.mark.parametrize("n", [193, 257, 300, 611])
 def test_det_mod_primes_every_update_path(path, n):
     """The trailing update in every arithmetic (int64 delayed reduction, int8
-    limbs, FP64, bf16 limbs) gives the oracle's residues; n spans several
-    64 x 64 tiles with ragged edges and primes of the 21-bit class reach the
-    largest balanced residues."""
+    limbs, FP64, bf16 limbs on mma.sync and on tcgen05) gives the oracle's
+    residues; n spans several 64 x 64 and 128 x 64 tiles with ragged edges
+    and primes of the 21-bit class reach the largest balanced residues."""
     A = workloads.dense_pm2p20(n, seed=n + 5)
     primes = rprimes(5, n + 1) + [P21[-1], P21[0]]
     got = idet.det_mod_primes(A, primes, update_path=PATHS[path])
@@ -230,7 +230,7 @@ def test_lu_factors_every_update_path(path):
         assert (lu == LU).all() and (perm == operm).all()
 
 
-@pytest.mark.parametrize("path", ["i8", "f64", "bf16"])
+@pytest.mark.parametrize("path", ["i8", "f64", "bf16", "tc05"])
 def test_int_det_every_update_path(path):
     A = workloads.dense_uniform(260, -50, 50, seed=33)
     assert idet.int_det(A, update_path=PATHS[path]) == exact.bareiss_det(A.tolist())

@@ -154,6 +154,8 @@ def run_case(case):
         idet.dixon_digits(A, b, 2147483629, 64)
     elif case == "lu":
         idet.det_mod_primes(A, [1048583, 1048589, 1048601, 1048609])
+    elif case == "lu_tc05":
+        idet.det_mod_primes(A, [1048583, 1048589, 1048601, 1048609], update_path=5)
     else:
         raise SystemExit(f"unknown case {case}")
     torch.cuda.synchronize()
@@ -350,8 +352,9 @@ def main():
     ap.add_argument("--impl", default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", default=None,
-                    help="profiling case: 'lift' (Dixon lifting, n=4000, 64 digits) or "
-                         "'lu' (det mod 4 primes, n=4000); runs once and prints timings")
+                    help="profiling case: 'lift' (Dixon lifting, n=4000, 64 digits), "
+                         "'lu' (det mod 4 primes, n=4000, int64 update) or 'lu_tc05' (the "
+                         "same with the tcgen05 update); runs once and prints timings")
     ap.add_argument("--workload", default="plain",
                     choices=["plain", "batch", "serve", "lift_heavy", "small"],
                     help="plain (default): n=1000 [0,255] + n=4000 +-2^20; batch: 512 "

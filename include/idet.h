@@ -44,7 +44,7 @@ extern "C" {
 #define IDET_ERR_INTERNAL 7   /* a reconstruction failed its own check       */
 
 /* Trailing-update (Schur complement) arithmetic of the LU over Z/p. */
-#define IDET_PATH_AUTO 0
+#define IDET_PATH_AUTO 0      /* TC05 for 21-bit primes, INT64 for 31-bit    */
 #define IDET_PATH_INT64 1     /* CUDA cores, int64 delayed reduction         */
 #define IDET_PATH_I8 2        /* signed 7-bit int8 limbs, int32 accumulation */
 #define IDET_PATH_F64 3       /* FP64 with delayed reduction below 2^53      */

@@ -22,14 +22,26 @@
 // offset). A tile is then one contiguous block that k_gemm_tc05 fetches with
 // cp.async.bulk into shared memory.
 //
-// k_gemm_tc05: one CTA (128 threads) per 128 x 64 output tile and prime.
-// Thread 0 issues the bulk copies and the 9 (Kp/16) MMAs (128 x 64 x 16,
-// bf16 in, fp32 accumulate in tensor memory, one 64-column accumulator per
-// group); completion is tracked by tcgen05.commit on an mbarrier; each warp
-// then reads its 32 lanes (rows) of the five accumulators with tcgen05.ld,
-// recombines and writes C. All waits are bounded (about 2 s): on a timeout
-// the CTA records an error, lets its copies and MMAs drain (bounded too),
-// frees its tensor memory and returns.
+// k_gemm_tc05: persistent, one CTA per SM looping over 128 x 48 output
+// tiles (all primes' tiles in one launch). Warp-specialised:
+//   warp 0 (one thread): producer, cp.async.bulk of 16-wide K chunks of the
+//     three limbs of A and B into a ring of shared-memory stages, each
+//     tracked by a full (transaction bytes) and an empty mbarrier;
+//   warp 1 (one thread): MMA issuer, 9 tcgen05.mma (128 x 48 x 16, bf16 in,
+//     fp32 out) per stage into five tensor-memory accumulators of 48
+//     columns (one per group); tcgen05.commit frees the stage, and after the
+//     last chunk of a tile signals its accumulator set full; two sets
+//     alternate between tiles; warp 1 also owns the tensor-memory
+//     allocation (512 columns);
+//   warps 2-5 and 6-9: two epilogue groups, one per accumulator set; each
+//     warp prefetches its 32 rows of C while the MMAs run, reads its 32-lane
+//     quarter of the accumulators with tcgen05.ld, recombines in int64,
+//     reduces mod p and writes C (16-byte accesses where aligned), then
+//     releases the set to the issuer.
+// The epilogue of a tile overlaps the loads and MMAs of the next one. Every wait is bounded (about 2 s); a wait that gives up records an
+// error and raises a block-wide abort flag, after which every role leaves
+// its loop; bulk copies and MMAs already started are drained (bounded)
+// before the tensor memory is freed.
 #include "idet_internal.cuh"
 
 #include <cuda_bf16.h>
@@ -38,10 +50,15 @@ namespace idet {
 
 namespace {
 
-constexpr int kTM = 128, kTN = 64;
+constexpr int kTM = 128, kTN = 48;
 constexpr int kGroups = 5;
-constexpr int kTmemCols = 512;  // 5 x 64 = 320 used (allocation: a power of two)
-constexpr int kT05Threads = 128;
+constexpr int kAccCols = 256;   // one accumulator set: 5 x 48 = 240 columns
+constexpr int kTmemCols = 512;  // two sets (double buffer)
+constexpr int kT05Threads = 320;
+constexpr int kKc = 16;         // K of one stage
+constexpr int kStages = 12;
+constexpr uint32_t kLimbA = kTM * kKc * 2, kLimbB = kTN * kKc * 2;  // bytes per limb chunk
+constexpr uint32_t kStageBytes = 3 * (kLimbA + kLimbB);
 
 __device__ int g_tc05_err;  // first error code (1 load, 2 MMA) of any CTA
 
@@ -165,47 +182,60 @@ __device__ __forceinline__ void mma_commit(uint64_t *m) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-        "%15}, [%16];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 // Instruction descriptor, kind::f16: fp32 accumulator (bits 4-5 = 1), A and
 // B bf16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0),
 // N >> 3 at bits 17-22, M >> 4 at bits 24-28.
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTN >> 3) << 17) |
                             ((uint32_t)(kTM >> 4) << 24);
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *m) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(m)) : "memory");
+}
+
+struct Tc05Shared {
+    uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2], drain;
+    uint32_t taddr;
+    volatile int abort;
+    int prod_iter, mma_iter;
+};
+
+// Bounded wait with back-off, for warps that wait through whole tiles.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t *m, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try(m, parity)) {
+        __nanosleep(64);
+        if (clock64() - t0 > 4000000000ll) return false;
+    }
+    return true;
+}
+
 __global__ void __launch_bounds__(kT05Threads, 1)
 k_gemm_tc05(const __nv_bfloat16 *__restrict__ Apk, const __nv_bfloat16 *__restrict__ Bpk, int Kp,
-            int Mt, int Nt, int32_t *__restrict__ C, int64_t ldc, int64_t sC, int M, int N,
+            int Mt, int Nt, int W, int32_t *__restrict__ C, int64_t ldc, int64_t sC, int M, int N,
             const ModP *__restrict__ mods, const LUState *__restrict__ st) {
-    extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ __align__(8) uint64_t bar_load, bar_mma;
-    __shared__ uint32_t s_taddr;
-    const int w = blockIdx.z, nt = blockIdx.x, mt = blockIdx.y;
-    if (st[w].dead) return;  // det = 0 mod p: nothing more to update
+    extern __shared__ __align__(128) unsigned char sm[];
+    __shared__ Tc05Shared S;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int Kq = 3 * Kp;
-    const uint32_t abytes = (uint32_t)kTM * Kq * 2, bbytes = (uint32_t)kTN * Kq * 2;
-    unsigned char *sA = sm, *sB = sm + abytes;
+    const int Kq = 3 * Kp, nck = Kp / kKc;
+    const int64_t tiles = (int64_t)W * Mt * Nt;
     if (tid == 0) {
-        mbar_init(&bar_load, 1);
-        mbar_init(&bar_mma, 1);
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(&S.full[i], 1);
+            mbar_init(&S.empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&S.acc_full[i], 1);
+            mbar_init(&S.acc_empty[i], 4);
+        }
+        mbar_init(&S.drain, 1);
+        S.abort = 0;
+        S.prod_iter = 0;
+        S.mma_iter = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         sa(&s_taddr)),
+                         sa(&S.taddr)),
                      "r"(kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -213,70 +243,173 @@ k_gemm_tc05(const __nv_bfloat16 *__restrict__ Apk, const __nv_bfloat16 *__restri
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t taddr = s_taddr;
-    const unsigned char *gA = (const unsigned char *)(Apk + ((int64_t)w * Mt + mt) * ((int64_t)kTM * Kq));
-    const unsigned char *gB = (const unsigned char *)(Bpk + ((int64_t)w * Nt + nt) * ((int64_t)kTN * Kq));
-    if (tid == 0) {
-        mbar_expect_tx(&bar_load, abytes + bbytes);
-        for (uint32_t o = 0; o < abytes; o += 32768)
-            bulk_g2s(sA + o, gA + o, min(32768u, abytes - o), &bar_load);
-        for (uint32_t o = 0; o < bbytes; o += 32768)
-            bulk_g2s(sB + o, gB + o, min(32768u, bbytes - o), &bar_load);
-    }
-    // the error decisions are made block-uniform, so that no thread frees
-    // the tensor memory while MMAs another thread issued are in flight
-    int err = __syncthreads_or(!mbar_wait(&bar_load, 0)) ? 1 : 0;
-    if (tid == 0 && !err) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = sa(sA), b0 = sa(sB);
-        const uint32_t lboA = (kTM / 8) * 128, lboB = (kTN / 8) * 128;
-        for (int g = 0; g < kGroups; ++g) {
-            uint32_t acc = 0;
-            for (int a = (g > 2 ? g - 2 : 0); a <= (g < 2 ? g : 2); ++a) {
-                const int b = g - a;
-                for (int ks = 0; ks < Kp; ks += 16) {
-                    const uint32_t ka = (uint32_t)(a * Kp + ks) / 8, kb = (uint32_t)(b * Kp + ks) / 8;
-                    const uint64_t ad = smem_desc(a0 + ka * lboA, lboA, 128);
-                    const uint64_t bd = smem_desc(b0 + kb * lboB, lboB, 128);
-                    mma_bf16(taddr + (uint32_t)(g * kTN), ad, bd, kIdesc, acc);
-                    acc = 1;
+    const uint32_t taddr = S.taddr;
+    auto fail = [&](int code) {
+        atomicCAS(&g_tc05_err, 0, code);
+        S.abort = 1;
+    };
+    if (warp == 0) {
+        if (lane == 0) {  // producer
+            int it = 0;
+            for (int64_t t = blockIdx.x; t < tiles && !S.abort; t += gridDim.x) {
+                const int w = (int)(t / ((int64_t)Mt * Nt));
+                const int mt = (int)((t / Nt) % Mt), nt = (int)(t % Nt);
+                if (st[w].dead) continue;
+                const unsigned char *gA =
+                    (const unsigned char *)(Apk + ((int64_t)w * Mt + mt) * ((int64_t)kTM * Kq));
+                const unsigned char *gB =
+                    (const unsigned char *)(Bpk + ((int64_t)w * Nt + nt) * ((int64_t)kTN * Kq));
+                for (int c = 0; c < nck; ++c, ++it) {
+                    const int stg = it % kStages;
+                    const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+                    if (!mbar_wait(&S.empty[stg], ph ^ 1u)) {
+                        fail(1);
+                        break;
+                    }
+                    unsigned char *dst = sm + (size_t)stg * kStageBytes;
+                    mbar_expect_tx(&S.full[stg], kStageBytes);
+                    for (int l = 0; l < 3; ++l) {
+                        const int kb = (l * Kp + c * kKc) / 8;
+                        bulk_g2s(dst + l * kLimbA, gA + (size_t)kb * (kTM / 8) * 128, kLimbA,
+                                 &S.full[stg]);
+                        bulk_g2s(dst + 3 * kLimbA + l * kLimbB, gB + (size_t)kb * (kTN / 8) * 128,
+                                 kLimbB, &S.full[stg]);
+                    }
+                    S.prod_iter = it + 1;
                 }
             }
         }
-        mma_commit(&bar_mma);
-    }
-    if (!err) err = __syncthreads_or(!mbar_wait(&bar_mma, 0)) ? 2 : 0;
-    if (err) {
-        if (lane == 0) atomicCAS(&g_tc05_err, 0, err);
-        // let what was started drain before the memory goes away
-        mbar_wait(&bar_load, 0);
-        if (err == 2) mbar_wait(&bar_mma, 0);
-    } else {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const ModP Md = mods[w];
-        const int r = mt * kTM + warp * 32 + lane;
-        const uint32_t tl = taddr + ((uint32_t)(warp * 32) << 16);
-        for (int c0 = 0; c0 < kTN; c0 += 16) {
-            float v[kGroups][16];
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            int it = 0, tile = 0;
+            const uint32_t lboA = (kTM / 8) * 128, lboB = (kTN / 8) * 128;
+            for (int64_t t = blockIdx.x; t < tiles && !S.abort; t += gridDim.x) {
+                const int w = (int)(t / ((int64_t)Mt * Nt));
+                if (st[w].dead) continue;
+                const int buf = tile & 1;
+                if (!mbar_wait(&S.acc_empty[buf], ((uint32_t)(tile >> 1) & 1u) ^ 1u)) {
+                    fail(2);
+                    break;
+                }
+                const uint32_t dacc = taddr + (uint32_t)(buf * kAccCols);
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                for (int c = 0; c < nck; ++c, ++it) {
+                    const int stg = it % kStages;
+                    const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+                    if (!mbar_wait(&S.full[stg], ph)) {
+                        fail(3);
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a0 = sa(sm + (size_t)stg * kStageBytes);
+                    const uint32_t b0 = a0 + 3 * kLimbA;
+                    for (int g = 0; g < kGroups; ++g) {
+                        uint32_t acc = c > 0 ? 1u : 0u;
+                        for (int a = (g > 2 ? g - 2 : 0); a <= (g < 2 ? g : 2); ++a) {
+                            const int b = g - a;
+                            const uint64_t ad = smem_desc(a0 + a * kLimbA, lboA, 128);
+                            const uint64_t bd = smem_desc(b0 + b * kLimbB, lboB, 128);
+                            mma_bf16(dacc + (uint32_t)(g * kTN), ad, bd, kIdesc, acc);
+                            acc = 1u;
+                        }
+                    }
+                    mma_commit(&S.empty[stg]);
+                    S.mma_iter = it + 1;
+                }
+                if (S.abort) break;
+                mma_commit(&S.acc_full[buf]);
+                ++tile;
+            }
+        }
+    } else {  // epilogue groups: warps 2-5 (set 0), 6-9 (set 1)
+        const int grp = (warp - 2) >> 2, q = warp & 3;
+        const bool vec = (ldc % 4 == 0) && (sC % 4 == 0) && (((uintptr_t)C & 15) == 0);
+        int tile = 0;
+        for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+            const int w = (int)(t / ((int64_t)Mt * Nt));
+            const int mt = (int)((t / Nt) % Mt), nt = (int)(t % Nt);
+            if (st[w].dead) continue;
+            const int buf = tile & 1;
+            const uint32_t use = (uint32_t)(tile >> 1) & 1u;
+            ++tile;
+            if (buf != grp) continue;
+            const int r = mt * kTM + q * 32 + lane;
+            const int cb = nt * kTN;
+            int32_t *crow = C + (int64_t)w * sC + (int64_t)r * ldc + cb;
+            const bool rowok = r < M;
+            const bool full = vec && cb + kTN <= N;
+            // prefetch this thread's 48 entries of C while the MMAs run
+            int32_t cv[kTN];
+            if (rowok && full) {
 #pragma unroll
-            for (int g = 0; g < kGroups; ++g) tmem_ld16(tl + (uint32_t)(g * kTN + c0), v[g]);
-            if (r < M) {
-                int32_t *crow = C + (int64_t)w * sC + (int64_t)r * ldc;
+                for (int u = 0; u < kTN / 4; ++u) {
+                    const int4 x = *(const int4 *)(crow + 4 * u);
+                    cv[4 * u] = x.x;
+                    cv[4 * u + 1] = x.y;
+                    cv[4 * u + 2] = x.z;
+                    cv[4 * u + 3] = x.w;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < kTN; ++j) cv[j] = (rowok && cb + j < N) ? crow[j] : 0;
+            }
+            const bool ok = mbar_wait_sleep(&S.acc_full[buf], use);
+            if (__any_sync(0xffffffffu, !ok || S.abort)) {
+                if (lane == 0 && !ok) fail(4);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const ModP Md = mods[w];
+            const uint32_t tl = taddr + (uint32_t)(buf * kAccCols) + ((uint32_t)(q * 32) << 16);
+#pragma unroll
+            for (int c0 = 0; c0 < kTN; c0 += 16) {
+                uint32_t rv[kGroups][16];
+#pragma unroll
+                for (int g = 0; g < kGroups; ++g)
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,"
+                        "%10,%11,%12,%13,%14,%15}, [%16];\n"
+                        : "=r"(rv[g][0]), "=r"(rv[g][1]), "=r"(rv[g][2]), "=r"(rv[g][3]),
+                          "=r"(rv[g][4]), "=r"(rv[g][5]), "=r"(rv[g][6]), "=r"(rv[g][7]),
+                          "=r"(rv[g][8]), "=r"(rv[g][9]), "=r"(rv[g][10]), "=r"(rv[g][11]),
+                          "=r"(rv[g][12]), "=r"(rv[g][13]), "=r"(rv[g][14]), "=r"(rv[g][15])
+                        : "r"(tl + (uint32_t)(g * kTN + c0)));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const int c = nt * kTN + c0 + j;
-                    if (c >= N) break;
                     int64_t s = 0;
 #pragma unroll
-                    for (int g = kGroups - 1; g >= 0; --g) s = s * 128 + (int64_t)v[g][j];
-                    crow[c] = red_bal((int64_t)crow[c] - s, Md);
+                    for (int g = kGroups - 1; g >= 0; --g)
+                        s = s * 128 + (int64_t)(int32_t)__float2int_rn(__uint_as_float(rv[g][j]));
+                    cv[c0 + j] = red_bal((int64_t)cv[c0 + j] - s, Md);
                 }
             }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.acc_empty[buf]);
+            if (rowok && full) {
+#pragma unroll
+                for (int u = 0; u < kTN / 4; ++u)
+                    *(int4 *)(crow + 4 * u) =
+                        make_int4(cv[4 * u], cv[4 * u + 1], cv[4 * u + 2], cv[4 * u + 3]);
+            } else if (rowok) {
+#pragma unroll
+                for (int j = 0; j < kTN; ++j)
+                    if (cb + j < N) crow[j] = cv[j];
+            }
         }
+    }
+    __syncthreads();
+    if (S.abort && tid == 32) {
+        // drain: every MMA this thread issued, then every armed bulk copy
+        mma_commit(&S.drain);
+        mbar_wait(&S.drain, 0);
+        for (int i = S.mma_iter; i < S.prod_iter; ++i)
+            mbar_wait(&S.full[i % kStages], (uint32_t)(i / kStages) & 1u);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0)
+    if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
                      "r"(kTmemCols)
                      : "memory");
@@ -307,10 +440,12 @@ int gemm_sub_tc05(const int32_t *A, int64_t lda, int64_t sA, const int32_t *B, i
                                                  Bpk);
     count_launch();
     IDET_CUDA_TRY(cudaGetLastError());
-    const size_t smem = (size_t)(kTM + kTN) * 3 * Kp * 2;
+    const size_t smem = (size_t)kStages * kStageBytes;
     IDET_TRY(allow_max_smem((const void *)k_gemm_tc05));
-    k_gemm_tc05<<<dim3(Nt, Mt, W), kT05Threads, smem, s>>>(Apk, Bpk, Kp, Mt, Nt, C, ldc, sC, M, N,
-                                                            mods, st);
+    const int64_t tiles = (int64_t)W * Mt * Nt;
+    const int grid = (int)std::min<int64_t>(tiles, 148);
+    k_gemm_tc05<<<grid, kT05Threads, smem, s>>>(Apk, Bpk, Kp, Mt, Nt, W, C, ldc, sC, M, N, mods,
+                                                st);
     count_launch();
     IDET_CUDA_TRY(cudaGetLastError());
     return IDET_OK;

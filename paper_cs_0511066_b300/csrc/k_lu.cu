@@ -648,9 +648,9 @@ int lu_factor_batched(int32_t *R, int64_t n, const ModP *mods_dev,
     } else if (wide) {
         IDET_TRY(lu_blocked<true>(R, n, mods_dev, W, nb, perm, st, s, IDET_PATH_INT64));
     } else {
-        // default trailing-update arithmetic for 21-bit primes
-        // (AUTO = int64 delayed reduction: fastest measured at n = 1000 and 4000)
-        const int path = update_path == IDET_PATH_AUTO ? IDET_PATH_INT64 : update_path;
+        // default trailing-update arithmetic for 21-bit primes: the tcgen05
+        // bf16-limb path (measured fastest at n = 1000 and 4000)
+        const int path = update_path == IDET_PATH_AUTO ? IDET_PATH_TC05 : update_path;
         void *scratch = nullptr;
         if (path == IDET_PATH_TC05) IDET_TRY(ws.alloc(&scratch, tc05_scratch_bytes(n, W)));
         IDET_TRY(lu_blocked<false>(R, n, mods_dev, W, nb, perm, st, s, path, scratch));

@@ -44,6 +44,22 @@ def peaks():
         return 6400.0, "fallback"
 
 
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time per step (every rank's work counts, so the
+    whole job takes as long as its slowest rank)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Units all ranks processed per second of the slowest rank's time."""
+    return units_per_rank * world / (ms / 1000.0)
+
+
 def batch(seed_base=0):
     return [workloads.dense_u8(1000, seed=seed_base), workloads.dense_pm2p20(4000, seed=seed_base)]
 
@@ -421,13 +437,9 @@ def main():
             barrier()
             times.append(e0.elapsed_time(e1))
     launches = idet.launch_count() - launches0
-    ms = sum(times) / len(times)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(times) / len(times), dist, "cuda")
     dets_per_step = len(mats) * world
-    value = dets_per_step / (ms / 1000.0)
+    value = whole_job_rate(len(mats), world, ms)
 
     # end-to-end: pinned host inputs through the C ABI (host pointers)
     e2e_times = []

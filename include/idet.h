@@ -296,6 +296,33 @@ void idet_server_info(idet_server *srv, idet_server_stats *out);
 /* Finishes the submitted jobs, then stops the workers. */
 void idet_server_destroy(idet_server *srv);
 
+/* ------------------------------------------------------------------------
+ * Autotuner for the multi-prime LU. idet_autotune times, for order n and
+ * the prime class prime_bits (21 or 31), the reduction plus LU of W primes
+ * on a random matrix with entries of entry_bits bits (2..32) generated on the
+ * device, for every update path of the class (21-bit: TC05, INT64, BF16,
+ * I8; 31-bit: INT64), panel width nb in {16, 32} and W in {4, 8, 16}, and
+ * records the fastest per prime in a process-wide table keyed by (n bucket
+ * of a quarter octave, prime bits). Calls with update_path = AUTO, nb = 0
+ * or wave = 0 then use the entry of the nearest bucket within one octave
+ * (else the built-in defaults). out may be NULL. The table is saved to and
+ * loaded from JSON files (idet_tuning_load merges). Not thread-safe with
+ * concurrent idet_autotune calls on the same stream.
+ */
+typedef struct {
+    int32_t update_path;   /* IDET_PATH_* of the winner                     */
+    int32_t nb;            /* panel width                                   */
+    int32_t wave;          /* primes per wave                               */
+    int32_t pad;
+    double ms_per_prime;   /* reduction + LU time per prime of the winner   */
+} idet_tuned;
+
+int idet_autotune(int64_t n, int32_t prime_bits, int32_t entry_bits, void *stream,
+                  idet_tuned *out);
+int idet_tuning_save(const char *path);
+int idet_tuning_load(const char *path);
+void idet_tuning_clear(void);
+
 #ifdef __cplusplus
 }
 #endif

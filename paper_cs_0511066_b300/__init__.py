@@ -480,3 +480,45 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+class idet_tuned(ctypes.Structure):
+    _fields_ = [("update_path", ctypes.c_int32), ("nb", ctypes.c_int32),
+                ("wave", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("ms_per_prime", ctypes.c_double)]
+
+
+_lib.idet_autotune.argtypes = [_i64, _i32, _i32, _P, ctypes.POINTER(idet_tuned)]
+_lib.idet_tuning_save.argtypes = [ctypes.c_char_p]
+_lib.idet_tuning_load.argtypes = [ctypes.c_char_p]
+_lib.idet_tuning_clear.restype = None
+
+
+def autotune(n: int, prime_bits: int = 21, entry_bits: int = 21, stream=None) -> dict:
+    """Times the LU variants for order n (idet_autotune) and records the
+    fastest in the library's table; returns the winner."""
+    use_torch_allocator()
+    t = idet_tuned()
+    _check(_lib.idet_autotune(n, prime_bits, entry_bits, _stream_ptr(stream), ctypes.byref(t)))
+    return {"update_path": t.update_path, "nb": t.nb, "wave": t.wave,
+            "ms_per_prime": t.ms_per_prime}
+
+
+def tuning_save(path: str) -> None:
+    _check(_lib.idet_tuning_save(os.fsencode(path)))
+
+
+def tuning_load(path: str) -> None:
+    _check(_lib.idet_tuning_load(os.fsencode(path)))
+
+
+def tuning_clear() -> None:
+    _lib.idet_tuning_clear()
+
+
+# The tuning table measured on B300 ships with the package; IDET_TUNING
+# names another file, or "none" to start untuned.
+_TUNING = os.environ.get("IDET_TUNING",
+                         os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_b300.json"))
+if _TUNING != "none" and os.path.exists(_TUNING):
+    tuning_load(_TUNING)

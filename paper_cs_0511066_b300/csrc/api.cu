@@ -450,7 +450,7 @@ struct DetJob {
         IDET_CUDA_TRY(cudaMemcpyAsync(md, mh.data(), sizeof(ModP) * W, cudaMemcpyHostToDevice, s));
         Timer t(s);
         IDET_TRY(reduce(md, W, R));
-        IDET_TRY(lu_factor_batched(R, n, md, mh.data(), W, draw.bits == 31, nb, nullptr, dd,
+        IDET_TRY(lu_factor_batched(R, n, md, mh.data(), W, draw.bits == 31, o.nb, nullptr, dd,
                                    o.update_path, ws));
         std::vector<uint32_t> res(W);
         IDET_CUDA_TRY(cudaMemcpyAsync(res.data(), dd, sizeof(uint32_t) * W,
@@ -633,6 +633,15 @@ static double rhs_range_log2(int64_t n, double log2H) {
     double lh = std::ceil(std::max(log2H, 1.0));
     double l2 = std::log2(13.0) + 3 * std::log2(e) + 4 * std::log2(lh);
     return std::min(l2, 62.0);
+}
+
+// Primes per wave after the first (the first wave has the k0 primes of
+// Lemma 2.1(iv)): the caller's, else the autotuner's, else max(8, k0).
+static int default_wave(const idet_opts &o, int64_t n, int prime_bits, int k0) {
+    if (o.wave > 0) return o.wave;
+    idet_tuned t{};
+    if (tuned_lookup(n, prime_bits, &t) && t.wave > 0) return std::max(t.wave, 1);
+    return std::max(8, k0);
 }
 
 // Alg. 2.1 on det(A) for the first primes (Alg. 4.1 lines 1-4), or all the
@@ -1189,7 +1198,7 @@ int idet_int_det(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
     }
     const bool certify = o.certify != 0;
     const int k0 = k_default(o.log2_epsilon, J.draw.pool(), J.log2H, J.draw.log2l());
-    const int wave = o.wave > 0 ? o.wave : std::max(8, k0);
+    const int wave = default_wave(o, n, J.draw.bits, k0);
 
     // Alg. 2.1 on det(A): the first k0 primes (Alg. 4.1 lines 1-4), or all
     // the way in CRA-only / certified mode.
@@ -1298,7 +1307,7 @@ int idet_int_det_mp(const uint32_t *A_limbs, const int8_t *A_sign, int64_t n, in
     J.colsq = clh;
     const bool certify = o.certify != 0;
     const int k0 = k_default(o.log2_epsilon, J.draw.pool(), J.log2H, J.draw.log2l());
-    const int wave = o.wave > 0 ? o.wave : std::max(8, k0);
+    const int wave = default_wave(o, n, J.draw.bits, k0);
     bool done = false;
     const int rc0 = det_first(J, k0, wave, certify || !o.lif, det, &done);
     if (rc0 != IDET_OK || done) return finish(rc0);

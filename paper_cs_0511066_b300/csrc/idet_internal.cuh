@@ -220,6 +220,9 @@ struct ElimJob {
 int launch_elim_cluster(const ElimJob *jobs_dev, int count, int max_n, int mode, cudaStream_t s);
 bool elim_cluster_fits(int n);
 
+// Autotuner table (tune.cu): the tuned choice for order n and prime class.
+bool tuned_lookup(int64_t n, int prime_bits, idet_tuned *out);
+
 // Multi-word entries (k_mp.cu): sign x magnitude of L base-2^32 limbs.
 int launch_reduce_mp(const uint32_t *mag, const int8_t *sgn, int64_t n, int L, const ModP *mods,
                      int W, int32_t *R, cudaStream_t s);

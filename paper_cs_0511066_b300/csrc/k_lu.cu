@@ -638,6 +638,9 @@ int lu_factor_batched(int32_t *R, int64_t n, const ModP *mods_dev,
     if (W <= 0) return IDET_OK;
     LUState *st = nullptr;
     IDET_TRY(ws.alloc_n(&st, W));
+    idet_tuned tuned{};
+    const bool have_tuned = tuned_lookup(n, wide ? 31 : 21, &tuned);
+    if (nb <= 0 && have_tuned) nb = tuned.nb;
     if (nb <= 0 || nb > kNBMax) nb = kNBMax;
     if (n <= kSmallN) {
         size_t smem = sizeof(int32_t) * n * n;
@@ -650,7 +653,10 @@ int lu_factor_batched(int32_t *R, int64_t n, const ModP *mods_dev,
     } else {
         // default trailing-update arithmetic for 21-bit primes: the tcgen05
         // bf16-limb path (measured fastest at n = 1000 and 4000)
-        const int path = update_path == IDET_PATH_AUTO ? IDET_PATH_TC05 : update_path;
+        const int path = update_path != IDET_PATH_AUTO
+                             ? update_path
+                             : (have_tuned && tuned.update_path != IDET_PATH_AUTO ? tuned.update_path
+                                                                                  : IDET_PATH_TC05);
         void *scratch = nullptr;
         if (path == IDET_PATH_TC05) IDET_TRY(ws.alloc(&scratch, tc05_scratch_bytes(n, W)));
         IDET_TRY(lu_blocked<false>(R, n, mods_dev, W, nb, perm, st, s, path, scratch));
@@ -667,6 +673,9 @@ int lu_factor_batched(int32_t *R, int64_t n, const ModP *mods_dev,
 int lu_inverse(const int32_t *R, const int32_t *perm, int64_t n, const ModP &mod_host,
                const ModP *mod_dev, bool wide, int nb, int32_t *Y, Workspace &ws) {
     cudaStream_t s = ws.stream();
+    idet_tuned tuned{};
+    const bool have_tuned = tuned_lookup(n, wide ? 31 : 21, &tuned);
+    if (nb <= 0 && have_tuned) nb = tuned.nb;
     if (nb <= 0 || nb > kNBMax) nb = kNBMax;
     k_perm_identity<<<148 * 4, 256, 0, s>>>(Y, perm, n);
     count_launch();

@@ -431,3 +431,49 @@ def test_int_det_mp_lift_heavy_full_size():
     assert 599 - 16 <= st["log2_K"] <= 599, st
     assert st["lift_iters"] < 120, st
     assert st["primes_used"] < 30, st
+
+
+# ---------------------------------------------------------------------------
+# Failure handling on the host: a lifting prime that divides det
+
+
+_M64 = (1 << 64) - 1
+
+
+def _splitmix64(seed):
+    """The SplitMix64 generator (Steele, Lea, Flood 2014), as the library
+    draws its random primes."""
+    s = seed & _M64
+    while True:
+        s = (s + 0x9E3779B97F4A7C15) & _M64
+        z = s
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+        yield z ^ (z >> 31)
+
+
+def _first_lift_prime(seed=0x1DE7):
+    for v in _splitmix64(seed ^ 0x11F7):
+        c = ((1 << 30) + v % (1 << 30)) | 1
+        if c < (1 << 31) and modular.is_prime(c):
+            return c
+
+
+def test_lift_prime_dividing_det_is_reselected():
+    """det(A) = p * det(R) with p the first lifting prime the library draws:
+    A is singular mod p, the LU mod p finds no pivot, and another prime is
+    drawn (single-matrix and batched paths)."""
+    p = _first_lift_prime()
+    rng = np.random.default_rng(3)
+    R = rng.integers(-100, 101, size=(38, 38)).astype(np.int64)
+    A = np.zeros((40, 40), dtype=np.int64)
+    A[0, 0], A[0, 1], A[1, 0], A[1, 1] = (p - 1) // 2, -1, 1, 2
+    A[2:, 2:] = R
+    pr, pc = rng.permutation(40), rng.permutation(40)
+    A = A[pr][:, pc]
+    want = exact.bareiss_det(A.tolist())
+    assert want % p == 0 and want != 0
+    d, st = idet.int_det(A, return_stats=True)
+    assert d == want
+    assert st["lift_iters"] > 0, st          # the solve ran (after the reselection)
+    assert idet.int_det_batch([A, R])[0] == want

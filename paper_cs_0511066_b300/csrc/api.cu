@@ -62,8 +62,7 @@ Workspace::~Workspace() {
     }
 }
 
-int Workspace::alloc(void **ptr, size_t bytes) {
-    bytes = (bytes + 255) / 256 * 256;
+int Workspace::raw_alloc(void **ptr, size_t bytes) {
     void *p = nullptr;
     if (!native_) {
         p = g_alloc(bytes, (void *)stream_, g_actx);
@@ -77,6 +76,21 @@ int Workspace::alloc(void **ptr, size_t bytes) {
     }
     ptrs_.push_back(p);
     *ptr = p;
+    return IDET_OK;
+}
+
+int Workspace::alloc(void **ptr, size_t bytes) {
+    bytes = (bytes + 255) / 256 * 256;
+    if (bytes >= kDirect) return raw_alloc(ptr, bytes);
+    if (bytes > chunk_left_) {
+        void *c = nullptr;
+        IDET_TRY(raw_alloc(&c, kChunk));
+        chunk_ = (char *)c;
+        chunk_left_ = kChunk;
+    }
+    *ptr = chunk_;
+    chunk_ += bytes;
+    chunk_left_ -= bytes;
     return IDET_OK;
 }
 
@@ -272,6 +286,10 @@ struct DevMatrix {
 static int stage_matrix(const int64_t *A, int64_t n, int64_t lda, int on_device, Workspace &ws,
                         DevMatrix &out) {
     out.n = n;
+    if (on_device && lda == n) {  // compact on the device already: used in place
+        out.A = A;
+        return IDET_OK;
+    }
     int64_t *d = nullptr;
     IDET_TRY(ws.alloc_n(&d, (size_t)n * n));
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -1576,28 +1594,56 @@ int idet_int_det_batch(int32_t count, const int64_t *const *A, const int64_t *n,
     const double log2l = 20.0;
     const double pool = (double)pool21().size();
     std::vector<BItem> it(count);
-    // stage and bound
+    // stage, then the statistics of all matrices in one launch and one copy
+    int64_t total_n = 0;
     for (int i = 0; i < count; ++i) {
         BItem &b = it[i];
         b.n = n[i];
         if (b.n == 0) continue;
         IDET_TRY(stage_matrix(A[i], b.n, lda[i], on_device, ws, b.M));
-        IDET_TRY(ws.alloc_n(&b.d_rowsq, b.n));
-        IDET_TRY(ws.alloc_n(&b.d_colsq, b.n));
-        IDET_TRY(ws.alloc_n(&b.d_amax, 1));
-        IDET_TRY(launch_row_stats(b.M.A, b.n, b.n, b.d_rowsq, b.d_amax, s));
-        IDET_TRY(launch_col_stats(b.M.A, b.n, b.n, b.d_colsq, s));
+        total_n += b.n;
     }
-    for (int i = 0; i < count; ++i) {
-        BItem &b = it[i];
-        if (b.n == 0) continue;
-        b.rowsq.resize(b.n);
-        b.colsq.resize(b.n);
-        IDET_CUDA_TRY(cudaMemcpyAsync(b.rowsq.data(), b.d_rowsq, 8 * b.n, cudaMemcpyDeviceToHost, s));
-        IDET_CUDA_TRY(cudaMemcpyAsync(b.colsq.data(), b.d_colsq, 8 * b.n, cudaMemcpyDeviceToHost, s));
-        IDET_CUDA_TRY(cudaMemcpyAsync(&b.amax, b.d_amax, 8, cudaMemcpyDeviceToHost, s));
+    {
+        double *d_sq = nullptr;
+        unsigned long long *d_amax = nullptr;
+        StatJob *d_jobs = nullptr;
+        IDET_TRY(ws.alloc_n(&d_sq, 2 * (size_t)std::max<int64_t>(total_n, 1)));
+        IDET_TRY(ws.alloc_n(&d_amax, std::max(count, 1)));
+        IDET_TRY(ws.alloc_n(&d_jobs, std::max(count, 1)));
+        IDET_CUDA_TRY(cudaMemsetAsync(d_amax, 0, 8 * (size_t)std::max(count, 1), s));
+        std::vector<StatJob> sj;
+        std::vector<int> sid;
+        int64_t off = 0;
+        for (int i = 0; i < count; ++i) {
+            BItem &b = it[i];
+            if (b.n == 0) continue;
+            sj.push_back({b.M.A, b.n, d_sq + off, d_sq + total_n + off, d_amax + sj.size()});
+            sid.push_back(i);
+            off += b.n;
+        }
+        if (!sj.empty()) {
+            IDET_CUDA_TRY(cudaMemcpyAsync(d_jobs, sj.data(), sizeof(StatJob) * sj.size(),
+                                          cudaMemcpyHostToDevice, s));
+            IDET_TRY(launch_stats_multi(d_jobs, (int)sj.size(), s));
+        }
+        std::vector<double> hsq(2 * (size_t)total_n);
+        std::vector<unsigned long long> hmax(sj.size());
+        if (total_n > 0) {
+            IDET_CUDA_TRY(cudaMemcpyAsync(hsq.data(), d_sq, 16 * (size_t)total_n,
+                                          cudaMemcpyDeviceToHost, s));
+            IDET_CUDA_TRY(cudaMemcpyAsync(hmax.data(), d_amax, 8 * hmax.size(),
+                                          cudaMemcpyDeviceToHost, s));
+        }
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        off = 0;
+        for (size_t q = 0; q < sid.size(); ++q) {
+            BItem &b = it[sid[q]];
+            b.rowsq.assign(hsq.begin() + off, hsq.begin() + off + b.n);
+            b.colsq.assign(hsq.begin() + total_n + off, hsq.begin() + total_n + off + b.n);
+            b.amax = hmax[q];
+            off += b.n;
+        }
     }
-    IDET_CUDA_TRY(cudaStreamSynchronize(s));
     for (int i = 0; i < count; ++i) {
         BItem &b = it[i];
         if (b.n == 0) {
@@ -1625,6 +1671,7 @@ int idet_int_det_batch(int32_t count, const int64_t *const *A, const int64_t *n,
     PrimeDraw draw(o.seed);
     std::vector<uint32_t> P;
     ModP *modsd = nullptr;
+    uint32_t *Pd = nullptr;
     int mods_cap = 0;
     auto ensure_primes = [&](int need) -> int {
         if (need <= (int)P.size() && need <= mods_cap) return IDET_OK;
@@ -1645,54 +1692,58 @@ int idet_int_det_batch(int32_t count, const int64_t *const *A, const int64_t *n,
         std::vector<ModP> mh(P.size());
         for (size_t k = 0; k < P.size(); ++k) mh[k] = make_mod(P[k]);
         IDET_TRY(ws.alloc_n(&modsd, P.size()));
+        IDET_TRY(ws.alloc_n(&Pd, P.size()));
         IDET_CUDA_TRY(cudaMemcpyAsync(modsd, mh.data(), sizeof(ModP) * P.size(),
                                       cudaMemcpyHostToDevice, s));
+        IDET_CUDA_TRY(cudaMemcpyAsync(Pd, P.data(), 4 * P.size(), cudaMemcpyHostToDevice, s));
         mods_cap = (int)P.size();
         return IDET_OK;
     };
-    // det mod P[have .. need) for the listed items
+    // det mod P[have .. need) for the listed items; results of all items in
+    // one device array, copied back once
     auto factor = [&](const std::vector<std::pair<int, int>> &want) -> int {
         Timer t(s);
         std::vector<LUSmallJob> jobs;
         std::vector<ElimJob> ejobs;
         int maxn = 1, max_en = 1;
-        std::vector<uint32_t *> outs(count, nullptr);
-        for (auto &wi : want) {
-            BItem &b = it[wi.first];
-            const int have = (int)b.dets.size(), need = wi.second;
+        size_t tot = 0;
+        for (auto &wi : want) tot += (size_t)std::max(0, wi.second - (int)it[wi.first].dets.size());
+        if (tot == 0) return IDET_OK;
+        uint32_t *dd_all = nullptr;
+        IDET_TRY(ws.alloc_n(&dd_all, tot));
+        std::vector<size_t> off(want.size(), 0);
+        size_t pos = 0;
+        for (size_t q = 0; q < want.size(); ++q) {
+            BItem &b = it[want[q].first];
+            const int have = (int)b.dets.size(), need = want[q].second;
             if (need <= have) continue;
             IDET_TRY(ensure_primes(need));
             const int W = need - have;
-            int32_t *R = nullptr;
-            uint32_t *dd = nullptr;
-            IDET_TRY(ws.alloc_n(&dd, W));
-            outs[wi.first] = dd;
+            uint32_t *dd = dd_all + pos;
+            off[q] = pos;
+            pos += W;
             agg.lu_macs += (2.0 / 3.0) * (double)b.n * b.n * b.n * W;
             agg.primes_used += W;
             if (b.n > 192 && elim_cluster_fits((int)b.n)) {
                 // one cluster per prime, reducing the int64 entries itself
                 for (int w = 0; w < W; ++w) {
-                    ElimJob e;
+                    ElimJob e{};
                     e.A = b.M.A;
                     e.lda = b.n;
                     e.n = (int32_t)b.n;
                     e.ld = (int32_t)b.n;
                     e.mod = make_mod(P[have + w]);
-                    e.Cinv = nullptr;
                     e.det = dd + w;
                     ejobs.push_back(e);
                 }
                 max_en = std::max<int>(max_en, (int)b.n);
-                continue;
-            }
-            IDET_TRY(ws.alloc_n(&R, (size_t)W * b.n * b.n));
-            IDET_TRY(launch_reduce(b.M.A, b.n, b.n, modsd + have, W, R, s));
-            if (b.n <= 192) {
+            } else if (b.n <= 192) {
+                // the small LU reduces the int64 entries while loading them
                 LUState *st = nullptr;
                 IDET_TRY(ws.alloc_n(&st, W));
                 for (int w = 0; w < W; ++w) {
                     LUSmallJob j{};
-                    j.R = R + (int64_t)w * b.n * b.n;
+                    j.A64 = b.M.A;
                     j.n = (int32_t)b.n;
                     j.mod = make_mod(P[have + w]);
                     j.st = st + w;
@@ -1701,6 +1752,9 @@ int idet_int_det_batch(int32_t count, const int64_t *const *A, const int64_t *n,
                 }
                 maxn = std::max<int>(maxn, (int)b.n);
             } else {
+                int32_t *R = nullptr;
+                IDET_TRY(ws.alloc_n(&R, (size_t)W * b.n * b.n));
+                IDET_TRY(launch_reduce(b.M.A, b.n, b.n, modsd + have, W, R, s));
                 std::vector<ModP> mh(W);
                 for (int w = 0; w < W; ++w) mh[w] = make_mod(P[have + w]);
                 IDET_TRY(lu_factor_batched(R, b.n, modsd + have, mh.data(), W, false, o.nb, nullptr,
@@ -1721,56 +1775,127 @@ int idet_int_det_batch(int32_t count, const int64_t *const *A, const int64_t *n,
                                           cudaMemcpyHostToDevice, s));
             IDET_TRY(launch_elim_cluster(ed, (int)ejobs.size(), max_en, 0, s));
         }
-        for (auto &wi : want) {
-            BItem &b = it[wi.first];
-            const int have = (int)b.dets.size(), need = wi.second;
-            if (need <= have) continue;
-            b.dets.resize(need);
-            IDET_CUDA_TRY(cudaMemcpyAsync(b.dets.data() + have, outs[wi.first],
-                                          4 * (size_t)(need - have), cudaMemcpyDeviceToHost, s));
-        }
+        std::vector<uint32_t> hres(tot);
+        IDET_CUDA_TRY(cudaMemcpyAsync(hres.data(), dd_all, 4 * tot, cudaMemcpyDeviceToHost, s));
         IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        for (size_t q = 0; q < want.size(); ++q) {
+            BItem &b = it[want[q].first];
+            const int have = (int)b.dets.size(), need = want[q].second;
+            if (need <= have) continue;
+            b.dets.insert(b.dets.end(), hres.begin() + off[q], hres.begin() + off[q] + (need - have));
+        }
         agg.ms_lu += t.stop();
         return IDET_OK;
     };
-    // Garner digits for each listed item: residues res[i] mod prs[i]
+    // Garner digits for each listed item: residues res[i] mod prs[i], all
+    // items packed into one upload, one launch and one copy back
     auto cra = [&](const std::vector<int> &ids, const std::vector<std::vector<uint32_t>> &prs,
                    const std::vector<std::vector<uint32_t>> &res,
                    std::vector<std::vector<int32_t>> &dig) -> int {
         Timer t(s);
-        std::vector<CraJob> jobs(ids.size());
-        std::vector<int32_t *> dd(ids.size());
+        size_t tot = 0;
+        for (auto &v : prs) tot += v.size();
+        std::vector<uint32_t> hp(tot + 1), hr(tot + 1);
+        std::vector<size_t> off(ids.size());
+        size_t pos = 0;
         for (size_t q = 0; q < ids.size(); ++q) {
-            const int c = (int)prs[q].size();
-            uint32_t *dp = nullptr, *dr = nullptr;
-            IDET_TRY(ws.alloc_n(&dp, c + 1));
-            IDET_TRY(ws.alloc_n(&dr, c + 1));
-            IDET_TRY(ws.alloc_n(&dd[q], c + 1));
-            IDET_CUDA_TRY(cudaMemcpyAsync(dp, prs[q].data(), 4 * c, cudaMemcpyHostToDevice, s));
-            IDET_CUDA_TRY(cudaMemcpyAsync(dr, res[q].data(), 4 * c, cudaMemcpyHostToDevice, s));
-            jobs[q].primes = dp;
-            jobs[q].residues = dr;
-            jobs[q].digits = dd[q];
-            jobs[q].count = c;
+            off[q] = pos;
+            std::copy(prs[q].begin(), prs[q].end(), hp.begin() + pos);
+            std::copy(res[q].begin(), res[q].end(), hr.begin() + pos);
+            pos += prs[q].size();
         }
+        uint32_t *dp = nullptr, *dr = nullptr;
+        int32_t *dd = nullptr;
         CraJob *jd = nullptr;
-        IDET_TRY(ws.alloc_n(&jd, jobs.size() + 1));
+        IDET_TRY(ws.alloc_n(&dp, tot + 1));
+        IDET_TRY(ws.alloc_n(&dr, tot + 1));
+        IDET_TRY(ws.alloc_n(&dd, tot + 1));
+        IDET_TRY(ws.alloc_n(&jd, ids.size() + 1));
+        IDET_CUDA_TRY(cudaMemcpyAsync(dp, hp.data(), 4 * tot, cudaMemcpyHostToDevice, s));
+        IDET_CUDA_TRY(cudaMemcpyAsync(dr, hr.data(), 4 * tot, cudaMemcpyHostToDevice, s));
+        std::vector<CraJob> jobs(ids.size());
+        for (size_t q = 0; q < ids.size(); ++q) {
+            jobs[q].primes = dp + off[q];
+            jobs[q].residues = dr + off[q];
+            jobs[q].digits = dd + off[q];
+            jobs[q].count = (int32_t)prs[q].size();
+        }
         IDET_CUDA_TRY(cudaMemcpyAsync(jd, jobs.data(), sizeof(CraJob) * jobs.size(),
                                       cudaMemcpyHostToDevice, s));
         IDET_TRY(launch_cra_multi(jd, (int)jobs.size(), s));
-        dig.assign(ids.size(), {});
-        for (size_t q = 0; q < ids.size(); ++q) {
-            dig[q].resize(prs[q].size());
-            IDET_CUDA_TRY(cudaMemcpyAsync(dig[q].data(), dd[q], 4 * prs[q].size(),
-                                          cudaMemcpyDeviceToHost, s));
-        }
+        std::vector<int32_t> hd(tot + 1);
+        IDET_CUDA_TRY(cudaMemcpyAsync(hd.data(), dd, 4 * tot, cudaMemcpyDeviceToHost, s));
         IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        dig.assign(ids.size(), {});
+        for (size_t q = 0; q < ids.size(); ++q)
+            dig[q].assign(hd.begin() + off[q], hd.begin() + off[q] + prs[q].size());
         agg.ms_cra += t.stop();
         return IDET_OK;
     };
-    auto assemble = [&](int i, const std::vector<uint32_t> &prs, const std::vector<int32_t> &dig,
-                        int c, const uint32_t *Kd, int Klen) -> int {
-        return assemble_int(ws, prs, dig, c, Kd, Klen, &dets[i]);
+    // det_i = K_i * sum_{t<c} dig_t prod_{j<t} p_j for every finished item,
+    // one launch per item and one copy back for all
+    struct AsmReq {
+        int i;
+        std::vector<uint32_t> prs;
+        std::vector<int32_t> dig;
+        const uint32_t *K;
+        int Klen;
+    };
+    std::vector<AsmReq> pending;
+    auto flush_assemble = [&]() -> int {
+        if (pending.empty()) return IDET_OK;
+        Timer t(s);
+        const size_t R = pending.size();
+        std::vector<size_t> doff(R), boff(R);
+        std::vector<int> cap(R);
+        size_t dt = 0, bt = 0;
+        for (size_t q = 0; q < R; ++q) {
+            double bits = 64;
+            for (uint32_t p : pending[q].prs) bits += std::log2((double)p);
+            cap[q] = (int)(bits / 32) + (pending[q].K ? pending[q].Klen : 1) + 4;
+            doff[q] = dt;
+            boff[q] = bt;
+            dt += pending[q].prs.size();
+            bt += 2 * (size_t)cap[q];
+        }
+        std::vector<uint32_t> hp(dt + 1);
+        std::vector<int32_t> hg(dt + 1);
+        for (size_t q = 0; q < R; ++q) {
+            std::copy(pending[q].prs.begin(), pending[q].prs.end(), hp.begin() + doff[q]);
+            std::copy(pending[q].dig.begin(), pending[q].dig.end(), hg.begin() + doff[q]);
+        }
+        uint32_t *dp = nullptr, *buf = nullptr, *one = nullptr;
+        int32_t *dg = nullptr, *info = nullptr;
+        IDET_TRY(ws.alloc_n(&dp, dt + 1));
+        IDET_TRY(ws.alloc_n(&dg, dt + 1));
+        IDET_TRY(ws.alloc_n(&buf, bt));
+        IDET_TRY(ws.alloc_n(&info, 4 * R));
+        IDET_TRY(ws.alloc_n(&one, 1));
+        const uint32_t h1 = 1;
+        IDET_CUDA_TRY(cudaMemcpyAsync(one, &h1, 4, cudaMemcpyHostToDevice, s));
+        IDET_CUDA_TRY(cudaMemcpyAsync(dp, hp.data(), 4 * dt, cudaMemcpyHostToDevice, s));
+        IDET_CUDA_TRY(cudaMemcpyAsync(dg, hg.data(), 4 * dt, cudaMemcpyHostToDevice, s));
+        for (size_t q = 0; q < R; ++q)
+            IDET_TRY(launch_mixed_to_int(dp + doff[q], dg + doff[q], (int)pending[q].prs.size(),
+                                         pending[q].K ? pending[q].K : one,
+                                         pending[q].K ? pending[q].Klen : 1, buf + boff[q], cap[q],
+                                         info + 4 * q, s));
+        std::vector<int32_t> hinfo(4 * R);
+        std::vector<uint32_t> hbuf(bt);
+        IDET_CUDA_TRY(cudaMemcpyAsync(hinfo.data(), info, 16 * R, cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaMemcpyAsync(hbuf.data(), buf, 4 * bt, cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        for (size_t q = 0; q < R; ++q) {
+            if (hinfo[4 * q + 2]) {
+                set_last_error("reconstruction buffer too small");
+                return IDET_ERR_INTERNAL;
+            }
+            IDET_TRY(write_int(&dets[pending[q].i], hinfo[4 * q], hbuf.data() + boff[q],
+                               (uint32_t)hinfo[4 * q + 1]));
+        }
+        pending.clear();
+        agg.ms_cra += t.stop();
+        return IDET_OK;
     };
 
     // Alg. 2.1 on det(A_i) for k0_i primes (Alg. 4.1, lines 1-4)
@@ -1795,10 +1920,13 @@ int idet_int_det_batch(int32_t count, const int64_t *const *A, const int64_t *n,
             const int stop = CraScan::scan(dig[q], prs[q], it[i].log2H, o.log2_epsilon, log2l, pool,
                                            o.certify != 0, &why);
             if (stop >= 0) {
-                IDET_TRY(assemble(i, prs[q], dig[q], stop + 1, nullptr, 0));
+                pending.push_back({i, std::vector<uint32_t>(prs[q].begin(), prs[q].begin() + stop + 1),
+                                   std::vector<int32_t>(dig[q].begin(), dig[q].begin() + stop + 1),
+                                   nullptr, 0});
                 it[i].done = true;
             }
         }
+        IDET_TRY(flush_assemble());
     }
     // one Dixon solve per remaining matrix, all in one launch
     {
@@ -1808,10 +1936,8 @@ int idet_int_det_batch(int32_t count, const int64_t *const *A, const int64_t *n,
             if (!it[i].done) ids.push_back(i);
         SplitMix gp(o.seed ^ 0x11f7ull);
         uint32_t p0 = random_prime31(gp);
-        std::vector<LiftJob> lj;
-        std::vector<RRJob> rj;
-        int max_ld = 4, max_m = 1;
-        // A_i^{-1} mod p0 for every matrix that fits a cluster, in one launch
+        // A_i^{-1} mod p0 (and A_i narrowed to int32) for every matrix that
+        // fits a cluster, in one launch
         std::vector<ElimJob> ej;
         std::vector<int> ejid;
         int max_en = 1;
@@ -1822,19 +1948,21 @@ int idet_int_det_batch(int32_t count, const int64_t *const *A, const int64_t *n,
             b.ld4 = (b.n + 3) / 4 * 4;
             IDET_TRY(ws.alloc_n(&b.A32, (size_t)b.n * b.ld4));
             IDET_TRY(ws.alloc_n(&b.Cinv, (size_t)b.n * b.ld4));
-            IDET_TRY(launch_narrow(b.M.A, b.n, b.n, b.A32, b.ld4, 4, s));
             if (elim_cluster_fits((int)b.n)) {
-                ElimJob e;
+                ElimJob e{};
                 e.A = b.M.A;
                 e.lda = b.n;
                 e.n = (int32_t)b.n;
                 e.ld = (int32_t)b.ld4;
                 e.mod = make_mod(p0);
                 e.Cinv = b.Cinv;
+                e.A32 = b.A32;
                 e.det = eflag + ej.size();
                 ej.push_back(e);
                 ejid.push_back(i);
                 max_en = std::max<int>(max_en, (int)b.n);
+            } else {
+                IDET_TRY(launch_narrow(b.M.A, b.n, b.n, b.A32, b.ld4, 4, s));
             }
         }
         std::vector<uint32_t> einv(ids.size() + 1, 0);
@@ -1851,6 +1979,13 @@ int idet_int_det_batch(int32_t count, const int64_t *const *A, const int64_t *n,
         }
         std::vector<char> inv_ok(count, 0);
         for (size_t q = 0; q < ej.size(); ++q) inv_ok[ejid[q]] = einv[q] != 0;
+        // right-hand sides, projections and lift lengths (host), then every
+        // per-system vector in one device array each
+        std::vector<int> lid;
+        std::vector<int64_t> hb;
+        std::vector<int32_t> hu;
+        std::vector<size_t> voff, zoff, doff;
+        size_t vt = 0, zt = 0, dt = 0;
         for (int i : ids) {
             BItem &b = it[i];
             uint32_t p = p0;
@@ -1860,24 +1995,25 @@ int idet_int_det_batch(int32_t count, const int64_t *const *A, const int64_t *n,
                 rc = inverse_mod_prime(b.M, p, 32, ws, b.Cinv, b.ld4);
                 if (rc == IDET_ERR_SINGULAR) p = random_prime31(gp);
             }
+            if (rc != IDET_OK && rc != IDET_ERR_SINGULAR) return rc;
             if (rc != IDET_OK) {
                 b.p = 0;  // no solve: the CRA alone finishes this matrix
                 continue;
             }
             b.p = p;
             agg.lu_macs += 2.0 * (double)b.n * b.n * b.n;
-            // right-hand side and projection, bounds as in the single-matrix path
+            // bounds as in the single-matrix path
             SplitMix g(o.seed ^ 0xb5ull ^ ((uint64_t)i << 20));
             const double l2S = rhs_range_log2(b.n, b.log2H);
             const uint64_t S = (uint64_t)std::exp2(std::floor(l2S));
-            std::vector<int64_t> bh(b.n);
-            std::vector<int32_t> uh(b.n);
             double bb = 1.0, u1 = 0, lc = 0, lcmin = INFINITY;
             for (int64_t k = 0; k < b.n; ++k) {
-                bh[k] = (int64_t)(g.below(S)) - (int64_t)(S / 2);
-                uh[k] = (int32_t)(g.next() & 0xffff);
-                bb += (double)bh[k] * (double)bh[k];
-                u1 += uh[k];
+                const int64_t bk = (int64_t)(g.below(S)) - (int64_t)(S / 2);
+                const int32_t uk = (int32_t)(g.next() & 0xffff);
+                hb.push_back(bk);
+                hu.push_back(uk);
+                bb += (double)bk * (double)bk;
+                u1 += uk;
                 const double c = 0.5 * std::log2(std::max(b.colsq[k], 1.0));
                 lc += c;
                 lcmin = std::min(lcmin, c);
@@ -1887,43 +2023,61 @@ int idet_int_det_batch(int32_t count, const int64_t *const *A, const int64_t *n,
             b.hN = (int)std::ceil((log2N + 1) / lp);
             b.hD = (int)std::ceil((b.log2H + 1) / lp);
             b.m = b.hN + b.hD + 2;
-            IDET_TRY(ws.alloc_n(&b.bd, b.n));
-            IDET_TRY(ws.alloc_n(&b.ud, b.n));
-            IDET_TRY(ws.alloc_n(&b.z, b.m));
-            IDET_TRY(ws.alloc_n(&b.r, b.n));
-            IDET_TRY(ws.alloc_n(&b.den, b.hD + 4));
-            IDET_TRY(ws.alloc_n(&b.info, 4));
-            IDET_CUDA_TRY(cudaMemcpyAsync(b.bd, bh.data(), 8 * b.n, cudaMemcpyHostToDevice, s));
-            IDET_CUDA_TRY(cudaMemcpyAsync(b.ud, uh.data(), 4 * b.n, cudaMemcpyHostToDevice, s));
-            LiftJob j{};
-            j.A = b.A32;
-            j.C = b.Cinv;
-            j.b = b.bd;
-            j.u = b.ud;
-            j.r = b.r;
-            j.z = b.z;
-            j.n = (int32_t)b.n;
-            j.ld = (int32_t)b.ld4;
-            j.m = b.m;
-            j.mod = make_mod(p);
-            j.pinv = inv_mod_2_64(p);
-            lj.push_back(j);
-            RRJob q{};
-            q.z = b.z;
-            q.m = b.m;
-            q.hN = b.hN;
-            q.hD = b.hD;
-            q.den_cap = b.hD + 4;
-            q.den = b.den;
-            q.info = b.info;
-            q.p = p;
-            rj.push_back(q);
-            max_ld = std::max<int>(max_ld, (int)b.ld4);
-            max_m = std::max(max_m, b.m);
-            agg.lift_iters += b.m;
-            agg.lift_bytes += (double)b.m * 8.0 * b.n * b.n;
+            lid.push_back(i);
+            voff.push_back(vt);
+            zoff.push_back(zt);
+            doff.push_back(dt);
+            vt += b.n;
+            zt += b.m;
+            dt += b.hD + 4;
         }
-        if (!lj.empty()) {
+        if (!lid.empty()) {
+            int64_t *bd = nullptr, *z = nullptr, *r = nullptr;
+            int32_t *ud = nullptr, *info = nullptr;
+            uint32_t *den = nullptr;
+            IDET_TRY(ws.alloc_n(&bd, vt));
+            IDET_TRY(ws.alloc_n(&ud, vt));
+            IDET_TRY(ws.alloc_n(&r, vt));
+            IDET_TRY(ws.alloc_n(&z, zt));
+            IDET_TRY(ws.alloc_n(&den, dt));
+            IDET_TRY(ws.alloc_n(&info, 4 * lid.size()));
+            IDET_CUDA_TRY(cudaMemcpyAsync(bd, hb.data(), 8 * vt, cudaMemcpyHostToDevice, s));
+            IDET_CUDA_TRY(cudaMemcpyAsync(ud, hu.data(), 4 * vt, cudaMemcpyHostToDevice, s));
+            std::vector<LiftJob> lj;
+            std::vector<RRJob> rj;
+            int max_ld = 4, max_m = 1;
+            for (size_t q = 0; q < lid.size(); ++q) {
+                BItem &b = it[lid[q]];
+                b.den = den + doff[q];
+                b.info = info + 4 * q;
+                LiftJob j{};
+                j.A = b.A32;
+                j.C = b.Cinv;
+                j.b = bd + voff[q];
+                j.u = ud + voff[q];
+                j.r = r + voff[q];
+                j.z = z + zoff[q];
+                j.n = (int32_t)b.n;
+                j.ld = (int32_t)b.ld4;
+                j.m = b.m;
+                j.mod = make_mod(b.p);
+                j.pinv = inv_mod_2_64(b.p);
+                lj.push_back(j);
+                RRJob rr{};
+                rr.z = z + zoff[q];
+                rr.m = b.m;
+                rr.hN = b.hN;
+                rr.hD = b.hD;
+                rr.den_cap = b.hD + 4;
+                rr.den = b.den;
+                rr.info = b.info;
+                rr.p = b.p;
+                rj.push_back(rr);
+                max_ld = std::max<int>(max_ld, (int)b.ld4);
+                max_m = std::max(max_m, b.m);
+                agg.lift_iters += b.m;
+                agg.lift_bytes += (double)b.m * 8.0 * b.n * b.n;
+            }
             LiftJob *ljd = nullptr;
             RRJob *rjd = nullptr;
             IDET_TRY(ws.alloc_n(&ljd, lj.size()));
@@ -1938,26 +2092,41 @@ int idet_int_det_batch(int32_t count, const int64_t *const *A, const int64_t *n,
             Timer tr(s);
             IDET_TRY(launch_ratrecon_multi(rjd, (int)rj.size(), max_m, s));
             agg.ms_rr += tr.stop();
-        }
-        for (int i : ids) {
-            BItem &b = it[i];
-            if (!b.p) continue;
-            int32_t hi[2];
-            IDET_CUDA_TRY(cudaMemcpyAsync(hi, b.info, 8, cudaMemcpyDeviceToHost, s));
+            // denominators: status and digits of all systems in two copies,
+            // then K in base 2^32 for each, their lengths in one copy
+            std::vector<int32_t> hinfo(4 * lid.size());
+            std::vector<uint32_t> hden(dt);
+            IDET_CUDA_TRY(cudaMemcpyAsync(hinfo.data(), info, 16 * lid.size(), cudaMemcpyDeviceToHost, s));
+            IDET_CUDA_TRY(cudaMemcpyAsync(hden.data(), den, 4 * dt, cudaMemcpyDeviceToHost, s));
             IDET_CUDA_TRY(cudaStreamSynchronize(s));
-            if (hi[0] != 0 || hi[1] <= 0) continue;  // no factor: K = 1
-            const int kd = hi[1];
-            std::vector<uint32_t> dh(kd);
-            IDET_CUDA_TRY(cudaMemcpyAsync(dh.data(), b.den, 4 * (size_t)kd, cudaMemcpyDeviceToHost, s));
-            int32_t *dl = nullptr;
-            IDET_TRY(ws.alloc_n(&b.Kbin, kd + 2));
-            IDET_TRY(ws.alloc_n(&dl, 1));
-            IDET_TRY(launch_radix_to_binary(b.den, kd, b.p, b.Kbin, kd + 2, dl, s));
-            IDET_CUDA_TRY(cudaMemcpyAsync(&b.Klen, dl, 4, cudaMemcpyDeviceToHost, s));
+            uint32_t *kb = nullptr;
+            int32_t *kl = nullptr;
+            size_t kt = 0;
+            for (size_t q = 0; q < lid.size(); ++q)
+                if (hinfo[4 * q] == 0 && hinfo[4 * q + 1] > 0) kt += hinfo[4 * q + 1] + 2;
+            IDET_TRY(ws.alloc_n(&kb, kt + 1));
+            IDET_TRY(ws.alloc_n(&kl, lid.size()));
+            size_t kp = 0;
+            for (size_t q = 0; q < lid.size(); ++q) {
+                BItem &b = it[lid[q]];
+                const int kd = hinfo[4 * q + 1];
+                if (hinfo[4 * q] != 0 || kd <= 0) continue;  // no factor: K = 1
+                b.Kbin = kb + kp;
+                kp += kd + 2;
+                IDET_TRY(launch_radix_to_binary(b.den, kd, b.p, b.Kbin, kd + 2, kl + q, s));
+                const uint32_t *dh = hden.data() + doff[q];
+                const double top = dh[kd - 1] + (kd > 1 ? dh[kd - 2] / (double)b.p : 0.0);
+                b.log2K = std::log2(top) + (kd - 1) * std::log2((double)b.p);
+            }
+            std::vector<int32_t> hkl(lid.size());
+            IDET_CUDA_TRY(cudaMemcpyAsync(hkl.data(), kl, 4 * lid.size(), cudaMemcpyDeviceToHost, s));
             IDET_CUDA_TRY(cudaStreamSynchronize(s));
-            const double top = dh[kd - 1] + (kd > 1 ? dh[kd - 2] / (double)b.p : 0.0);
-            b.log2K = std::log2(top) + (kd - 1) * std::log2((double)b.p);
-            b.have_K = b.Klen > 0;
+            for (size_t q = 0; q < lid.size(); ++q) {
+                BItem &b = it[lid[q]];
+                if (!b.Kbin) continue;
+                b.Klen = hkl[q];
+                b.have_K = b.Klen > 0;
+            }
         }
         agg.ms_lift += t.stop();
     }
@@ -1971,34 +2140,57 @@ int idet_int_det_batch(int32_t count, const int64_t *const *A, const int64_t *n,
             set_last_error("batched determinant did not terminate");
             return IDET_ERR_INTERNAL;
         }
+        // d_k K^{-1} mod p_k for every item with a factor: one launch each,
+        // inputs and outputs in one array each, one copy back
         std::vector<std::vector<uint32_t>> prs(ids.size()), res(ids.size());
-        for (size_t q = 0; q < ids.size(); ++q) {
-            BItem &b = it[ids[q]];
-            const int c = (int)b.dets.size();
-            if (b.have_K) {
-                uint32_t *dp = nullptr, *di = nullptr, *dout = nullptr;
+        {
+            Timer t(s);
+            std::vector<size_t> off(ids.size(), 0);
+            size_t tot = 0;
+            for (size_t q = 0; q < ids.size(); ++q)
+                if (it[ids[q]].have_K) {
+                    off[q] = tot;
+                    tot += it[ids[q]].dets.size();
+                }
+            if (tot > 0) {
+                std::vector<uint32_t> hi(tot);
+                for (size_t q = 0; q < ids.size(); ++q)
+                    if (it[ids[q]].have_K)
+                        std::copy(it[ids[q]].dets.begin(), it[ids[q]].dets.end(), hi.begin() + off[q]);
+                uint32_t *di = nullptr, *dout = nullptr;
                 int32_t *dsk = nullptr;
-                IDET_TRY(ws.alloc_n(&dp, c));
-                IDET_TRY(ws.alloc_n(&di, c));
-                IDET_TRY(ws.alloc_n(&dout, c));
-                IDET_TRY(ws.alloc_n(&dsk, c));
-                IDET_CUDA_TRY(cudaMemcpyAsync(dp, P.data(), 4 * c, cudaMemcpyHostToDevice, s));
-                IDET_CUDA_TRY(cudaMemcpyAsync(di, b.dets.data(), 4 * c, cudaMemcpyHostToDevice, s));
-                IDET_TRY(launch_div_by_K(b.Kbin, b.Klen, dp, di, dout, dsk, c, s));
-                std::vector<uint32_t> ho(c);
-                std::vector<int32_t> hs(c);
-                IDET_CUDA_TRY(cudaMemcpyAsync(ho.data(), dout, 4 * c, cudaMemcpyDeviceToHost, s));
-                IDET_CUDA_TRY(cudaMemcpyAsync(hs.data(), dsk, 4 * c, cudaMemcpyDeviceToHost, s));
+                IDET_TRY(ws.alloc_n(&di, tot));
+                IDET_TRY(ws.alloc_n(&dout, tot));
+                IDET_TRY(ws.alloc_n(&dsk, tot));
+                IDET_CUDA_TRY(cudaMemcpyAsync(di, hi.data(), 4 * tot, cudaMemcpyHostToDevice, s));
+                for (size_t q = 0; q < ids.size(); ++q) {
+                    BItem &b = it[ids[q]];
+                    if (!b.have_K) continue;
+                    IDET_TRY(launch_div_by_K(b.Kbin, b.Klen, Pd, di + off[q], dout + off[q],
+                                             dsk + off[q], (int)b.dets.size(), s));
+                }
+                std::vector<uint32_t> ho(tot);
+                std::vector<int32_t> hs(tot);
+                IDET_CUDA_TRY(cudaMemcpyAsync(ho.data(), dout, 4 * tot, cudaMemcpyDeviceToHost, s));
+                IDET_CUDA_TRY(cudaMemcpyAsync(hs.data(), dsk, 4 * tot, cudaMemcpyDeviceToHost, s));
                 IDET_CUDA_TRY(cudaStreamSynchronize(s));
-                for (int k = 0; k < c; ++k)
-                    if (!hs[k]) {
-                        prs[q].push_back(P[k]);
-                        res[q].push_back(ho[k]);
-                    }
-            } else {
-                prs[q].assign(P.begin(), P.begin() + c);
+                for (size_t q = 0; q < ids.size(); ++q) {
+                    BItem &b = it[ids[q]];
+                    if (!b.have_K) continue;
+                    for (size_t k = 0; k < b.dets.size(); ++k)
+                        if (!hs[off[q] + k]) {
+                            prs[q].push_back(P[k]);
+                            res[q].push_back(ho[off[q] + k]);
+                        }
+                }
+            }
+            for (size_t q = 0; q < ids.size(); ++q) {
+                BItem &b = it[ids[q]];
+                if (b.have_K) continue;
+                prs[q].assign(P.begin(), P.begin() + b.dets.size());
                 res[q] = b.dets;
             }
+            agg.ms_cra += t.stop();
         }
         std::vector<std::vector<int32_t>> dig;
         IDET_TRY(cra(ids, prs, res, dig));
@@ -2010,13 +2202,15 @@ int idet_int_det_batch(int32_t count, const int64_t *const *A, const int64_t *n,
             const double lh = b.have_K ? std::max(0.0, b.log2H - b.log2K) : b.log2H;
             const int stop = CraScan::scan(dig[q], prs[q], lh, o.log2_epsilon, log2l, pool, false, &why);
             if (stop >= 0) {
-                IDET_TRY(assemble(i, prs[q], dig[q], stop + 1, b.have_K ? b.Kbin : nullptr,
-                                  b.have_K ? b.Klen : 0));
+                pending.push_back({i, std::vector<uint32_t>(prs[q].begin(), prs[q].begin() + stop + 1),
+                                   std::vector<int32_t>(dig[q].begin(), dig[q].begin() + stop + 1),
+                                   b.have_K ? b.Kbin : nullptr, b.have_K ? b.Klen : 0});
                 b.done = true;
             } else {
                 more.push_back({i, (int)b.dets.size() + std::max(4, b.k0 / 2)});
             }
         }
+        IDET_TRY(flush_assemble());
         if (!more.empty()) IDET_TRY(factor(more));
     }
     agg.ms_total = total.stop();

@@ -132,9 +132,15 @@ class Workspace {
     cudaStream_t stream() const { return stream_; }
 
   private:
+    int raw_alloc(void **ptr, size_t bytes);
     cudaStream_t stream_;
     bool native_;
     std::vector<void *> ptrs_;
+    // requests below kDirect are carved from chunks of kChunk bytes (one
+    // allocator call per chunk instead of one per request)
+    static constexpr size_t kDirect = (size_t)4 << 20, kChunk = (size_t)32 << 20;
+    char *chunk_ = nullptr;
+    size_t chunk_left_ = 0;
 };
 
 // Counter of kernel launches made by this library (for the benchmark's
@@ -172,7 +178,8 @@ struct LUState {
 };
 // A (matrix, prime) job of the batched small LU.
 struct LUSmallJob {
-    int32_t *R;      // n x n residues, ld n, factored in place
+    int32_t *R;      // n x n residues, ld n, factored in place; or null:
+    const int64_t *A64;  // the int64 entries (n x n, ld n), reduced on load
     int32_t n, pad;
     ModP mod;
     LUState *st;
@@ -216,9 +223,19 @@ struct ElimJob {
     ModP mod;
     int32_t *Cinv;        // mode 1 output
     uint32_t *det;        // det mod p (mode 0) or invertibility flag (mode 1)
+    int32_t *A32;         // mode 1, optional: A as int32, n rows of ld (zero padded)
 };
 int launch_elim_cluster(const ElimJob *jobs_dev, int count, int max_n, int mode, cudaStream_t s);
 bool elim_cluster_fits(int n);
+// Row and column statistics of many int64 matrices in one launch (one CTA
+// per matrix): rowsq/colsq as in launch_row_stats / launch_col_stats.
+struct StatJob {
+    const int64_t *A;  // n x n, ld n
+    int64_t n;
+    double *rowsq, *colsq;
+    unsigned long long *amax;
+};
+int launch_stats_multi(const StatJob *jobs_dev, int count, cudaStream_t s);
 
 // Autotuner table (tune.cu): the tuned choice for order n and prime class.
 bool tuned_lookup(int64_t n, int prime_bits, idet_tuned *out);

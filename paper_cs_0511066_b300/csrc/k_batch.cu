@@ -198,8 +198,15 @@ k_elim_cluster(const ElimJob *__restrict__ jobs, int mode) {
     const int tid = threadIdx.x;
     for (int e = tid; e < nloc * n; e += kECT) {
         const int r = e / n, c = e % n;
-        rows[e] = red_bal(J.A[(int64_t)(rbeg + r) * J.lda + c], M);
+        const int64_t a = J.A[(int64_t)(rbeg + r) * J.lda + c];
+        rows[e] = red_bal(a, M);
+        if (J.A32) J.A32[(int64_t)(rbeg + r) * J.ld + c] = (int32_t)a;
     }
+    if (J.A32 && J.ld > n)
+        for (int e = tid; e < nloc * (J.ld - n); e += kECT) {
+            const int r = e / (J.ld - n), c = n + e % (J.ld - n);
+            J.A32[(int64_t)(rbeg + r) * J.ld + c] = 0;
+        }
     for (int k = tid; k < n; k += kECT) swp[k] = k;
     uint32_t det = 1u % M.p;
     int neg = 0, dead = 0;

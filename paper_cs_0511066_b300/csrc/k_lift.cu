@@ -173,19 +173,23 @@ __device__ __forceinline__ uint64_t policy_evict_first() {
 __device__ __forceinline__ bool grid_sync(GridBar *gb, unsigned target) {
     cons_sync();
     if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(&gb->count, 1u);
-        volatile unsigned int *vc = &gb->count;
+        // arrive with release semantics (cumulative over the consumer
+        // threads' writes ordered before it by the CTA barrier), poll with
+        // acquire loads and a short back-off
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&gb->count) : "memory");
         volatile int *ve = &gb->err;
         const long long t0 = clock64();
-        while (*vc < target) {
+        while (true) {
+            unsigned c;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(c) : "l"(&gb->count) : "memory");
+            if (c >= target) break;
             if (*ve) break;
             if (clock64() - t0 > kWaitCycles) {
                 fail_once(gb, 1, 0, target, -1, 0, -1);
                 break;
             }
+            __nanosleep(20);
         }
-        __threadfence();
     }
     cons_sync();
     return *((volatile int *)&gb->err) == 0;

@@ -39,13 +39,19 @@ __device__ __forceinline__ uint32_t det_mul(uint32_t det, int32_t piv, const Mod
 // ---------------------------------------------------------------------------
 // Whole-matrix LU in shared memory.
 
+// g: the residues (n x n, ld n), or null with A64: the int64 entries (n x n,
+// ld n), reduced here while they are loaded.
 __device__ void lu_small_body(int32_t *__restrict__ g, int n, const ModP M,
-                              LUState *__restrict__ st_out, int32_t *__restrict__ pm) {
+                              LUState *__restrict__ st_out, int32_t *__restrict__ pm,
+                              const int64_t *__restrict__ A64 = nullptr) {
     extern __shared__ int32_t sa[];
     __shared__ int s_piv;
     __shared__ int32_t s_inv;
     const int nn = n * n;
-    for (int e = threadIdx.x; e < nn; e += blockDim.x) sa[e] = g[e];
+    if (A64)
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) sa[e] = red_bal(A64[e], M);
+    else
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) sa[e] = g[e];
     if (pm)
         for (int i = threadIdx.x; i < n; i += blockDim.x) pm[i] = i;
     uint32_t det = 1u % M.p;
@@ -94,7 +100,8 @@ __device__ void lu_small_body(int32_t *__restrict__ g, int n, const ModP M,
         }
         __syncthreads();
     }
-    for (int e = threadIdx.x; e < nn; e += blockDim.x) g[e] = sa[e];
+    if (g)
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) g[e] = sa[e];
     if (threadIdx.x == 0) {
         LUState s;
         s.dead = dead;
@@ -114,7 +121,7 @@ __global__ void k_lu_small(int32_t *__restrict__ R, int n, const ModP *__restric
 // One CTA per (matrix, prime) job of a batch.
 __global__ void k_lu_small_multi(const LUSmallJob *__restrict__ jobs) {
     const LUSmallJob j = jobs[blockIdx.x];
-    lu_small_body(j.R, j.n, j.mod, j.st, nullptr);
+    lu_small_body(j.R, j.n, j.mod, j.st, nullptr, j.A64);
     __syncthreads();
     if (threadIdx.x == 0) {
         const LUState t = *j.st;
@@ -448,6 +455,126 @@ __global__ void k_trsm_upper(const int32_t *__restrict__ Um, int64_t n, int64_t 
     }
 }
 
+// Triangular solves by explicit inverses of the nb x nb diagonal blocks:
+// k_tri_inv forms T^{-1} once per prime (one thread per column of the
+// inverse: forward substitution on e_c for a unit lower T, backward with the
+// diagonal inverses for an upper T), k_tri_apply then computes
+// X_block <- T^{-1} X_block for all columns as independent 32-term dot
+// products (all reads of a column before the block barrier, all writes
+// after it, so the update in place is safe). The nb-step dependency chain is
+// paid once per block instead of once per column.
+// sum_k t_k u_k mod p for balanced residues: one exact int64 sum for 21-bit
+// primes, two (u split at bit 16) for 31-bit primes; |sum| < 2^53 for 32
+// terms either way.
+template <bool WIDE>
+struct DotAcc {
+    int64_t lo = 0, hi = 0;
+    __device__ __forceinline__ void add(int32_t t, int32_t u) {
+        if (WIDE) {
+            lo += (int64_t)t * (u & 0xffff);
+            hi += (int64_t)t * (u >> 16);
+        } else {
+            lo += (int64_t)t * u;
+        }
+    }
+    __device__ __forceinline__ int32_t get(const ModP &M) const {
+        return WIDE ? red_bal((int64_t)red_bal(hi, M) * 65536 + red_bal(lo, M), M)
+                    : red_bal(lo, M);
+    }
+};
+
+// Inverse of a triangular kNBMax x kNBMax block by products only: a unit
+// lower T = I + N has N nilpotent (N^32 = 0), so
+//   T^{-1} = (I - N)(I + N^2)(I + N^4)(I + N^8)(I + N^16);
+// an upper T = D (I + N') with N' = D^{-1} (T - D) strictly upper gives
+// T^{-1} = (I + N')^{-1} D^{-1}. Eight 32 x 32 products, one output entry
+// per thread (1024 threads); rows and columns beyond jb are the identity.
+template <bool WIDE, bool UPPER>
+__global__ void __launch_bounds__(kNBMax * kNBMax)
+k_tri_inv(const int32_t *__restrict__ Tm, int64_t strideT, int64_t n, int64_t r0, int jb,
+          const ModP *__restrict__ mods, const LUState *__restrict__ st, int32_t *__restrict__ Inv) {
+    __shared__ int32_t sP[kNBMax][kNBMax + 1], sS[kNBMax][kNBMax + 1], sQ[kNBMax][kNBMax + 1];
+    __shared__ int32_t sD[kNBMax];
+    const int w = blockIdx.x;
+    if (st && st[w].dead) return;
+    const ModP M = mods[w];
+    const int32_t *T = Tm + (int64_t)w * strideT;
+    const int i = threadIdx.x / kNBMax, j = threadIdx.x % kNBMax;
+    const int32_t t = (i < jb && j < jb) ? T[(r0 + i) * n + r0 + j] : 0;
+    if (UPPER && i == j) sD[i] = i < jb ? inv_bal32(t, M.p) : 1;
+    __syncthreads();
+    // N: strictly lower (unit lower T) or D^{-1} times the strictly upper part
+    int32_t nij = 0;
+    if (!UPPER && i > j) nij = t;
+    if (UPPER && j > i) nij = mul_bal(t, sD[i], M);
+    sP[i][j] = nij;
+    sS[i][j] = (i == j ? 1 : 0) - nij;  // I - N, entries within the balanced range
+    __syncthreads();
+    auto prod = [&](int32_t (*A)[kNBMax + 1], int32_t (*B)[kNBMax + 1]) {
+        DotAcc<WIDE> acc;
+#pragma unroll
+        for (int k = 0; k < kNBMax; ++k) acc.add(A[i][k], B[k][j]);
+        return acc.get(M);
+    };
+    for (int lev = 1; lev < 5; ++lev) {
+        const int32_t p2 = prod(sP, sP);  // N^(2^lev)
+        __syncthreads();
+        sP[i][j] = p2;
+        __syncthreads();
+        const int32_t q = prod(sS, sP);   // S N^(2^lev)
+        __syncthreads();
+        sS[i][j] = red_bal((int64_t)sS[i][j] + q, M);
+        __syncthreads();
+    }
+    int32_t v = sS[i][j];
+    if (UPPER) v = mul_bal(v, sD[j], M);
+    Inv[(int64_t)w * kNBMax * kNBMax + i * kNBMax + j] = (i < jb && j < jb) ? v : 0;
+    (void)sQ;
+}
+
+// X[xr0 .. xr0+jb)[c0 .. c0+ncols) <- Inv X, per prime (blockIdx.y); 128
+// threads: 32 columns x 4 row chunks of 8.
+template <bool WIDE>
+__global__ void __launch_bounds__(128)
+k_tri_apply(const int32_t *__restrict__ Inv, int32_t *__restrict__ X, int64_t strideX, int64_t n,
+            int64_t xr0, int jb, int64_t c0, int64_t ncols, const ModP *__restrict__ mods,
+            const LUState *__restrict__ st) {
+    __shared__ int32_t sI[kNBMax][kNBMax + 1];
+    const int w = blockIdx.y;
+    if (st && st[w].dead) return;
+    const ModP M = mods[w];
+    const int32_t *I = Inv + (int64_t)w * kNBMax * kNBMax;
+    for (int e = threadIdx.x; e < kNBMax * kNBMax; e += blockDim.x)
+        sI[e / kNBMax][e % kNBMax] = I[e];
+    const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+    const int64_t j = c0 + (int64_t)blockIdx.x * 32 + lane;
+    const bool ok = j < c0 + ncols;
+    int32_t *x = X + (int64_t)w * strideX;
+    int32_t y[kNBMax];
+#pragma unroll
+    for (int k = 0; k < kNBMax; ++k) y[k] = (ok && k < jb) ? x[(xr0 + k) * n + j] : 0;
+    __syncthreads();
+    if (!ok) return;
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr) {
+        const int r = q * 8 + rr;
+        if (r >= jb) break;
+        int64_t lo = 0, hi = 0;
+#pragma unroll
+        for (int k = 0; k < kNBMax; ++k) {
+            if (WIDE) {
+                lo += (int64_t)sI[r][k] * (y[k] & 0xffff);
+                hi += (int64_t)sI[r][k] * (y[k] >> 16);
+            } else {
+                lo += (int64_t)sI[r][k] * y[k];
+            }
+        }
+        const int32_t v = WIDE ? red_bal((int64_t)red_bal(hi, M) * 65536 + red_bal(lo, M), M)
+                               : red_bal(lo, M);
+        x[(xr0 + r) * n + j] = v;
+    }
+}
+
 // C <- C - A B mod p (batched over primes by blockIdx.z). A: M x K (lda),
 // B: K x N (ldb), C: M x N (ldc). 64 x 64 tile, 256 threads, 4 x 4 outputs
 // per thread, int64 accumulators.
@@ -469,11 +596,15 @@ k_gemm_sub(const int32_t *__restrict__ A, int64_t lda, int64_t strideA,
     int32_t *c = C + (int64_t)w * strideC;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-    int64_t acc[4][4];
+    // 21-bit primes: one exact int64 sum per output (|products| < 2^40).
+    // 31-bit primes: A split as a = 2^16 a_hi + a_lo (a_lo in [0, 2^16),
+    // |a_hi| < 2^14), two exact sums, |a_hi b| < 2^44 and a_lo b < 2^46,
+    // so K <= 128 terms stay below 2^53; reduced once at the end.
+    int64_t acc[4][4], acch[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+        for (int j = 0; j < 4; ++j) acc[i][j] = acch[i][j] = 0;
     for (int k0 = 0; k0 < K; k0 += BK) {
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
@@ -495,18 +626,31 @@ k_gemm_sub(const int32_t *__restrict__ A, int64_t lda, int64_t strideA,
             for (int i = 0; i < 4; ++i) av[i] = As[k][ty + 16 * i];
 #pragma unroll
             for (int j = 0; j < 4; ++j) bv[j] = Bs[k][tx + 16 * j];
+            if (WIDE) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < 4; ++i) {
+                    const int32_t lo = av[i] & 0xffff, hi = av[i] >> 16;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] += (int64_t)av[i] * bv[j];
-            if (WIDE && (k % kFoldWide) == kFoldWide - 1) {
+                    for (int j = 0; j < 4; ++j) {
+                        acc[i][j] += (int64_t)lo * bv[j];
+                        acch[i][j] += (int64_t)hi * bv[j];
+                    }
+                }
+            } else {
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = red_bal(acc[i][j], Mo);
+                    for (int j = 0; j < 4; ++j) acc[i][j] += (int64_t)av[i] * bv[j];
             }
         }
         __syncthreads();
+    }
+    if (WIDE) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                acc[i][j] = (int64_t)red_bal(acch[i][j], Mo) * 65536 + red_bal(acc[i][j], Mo);
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -557,8 +701,18 @@ int gemm_sub(const int32_t *A, int64_t lda, int64_t sA, const int32_t *B, int64_
 template <bool WIDE>
 int trsm_lower(const int32_t *Lm, int64_t sL, int32_t *X, int64_t sX, int64_t n,
                int64_t lr0, int64_t xr0, int jb, int64_t c0, int64_t ncols,
-               const ModP *mods, const LUState *st, int W, cudaStream_t s) {
+               const ModP *mods, const LUState *st, int W, cudaStream_t s,
+               int32_t *tri = nullptr) {
     if (ncols <= 0) return IDET_OK;
+    if (tri) {
+        // explicit inverse of the diagonal block, then a dense apply
+        k_tri_inv<WIDE, false><<<W, kNBMax * kNBMax, 0, s>>>(Lm, sL, n, lr0, jb, mods, st, tri);
+        k_tri_apply<WIDE><<<dim3((unsigned)((ncols + 31) / 32), W), 128, 0, s>>>(
+            tri, X, sX, n, xr0, jb, c0, ncols, mods, st);
+        count_launch(2);
+        IDET_CUDA_TRY(cudaGetLastError());
+        return IDET_OK;
+    }
     // narrow blocks: a TRSM row block has few columns per prime
     dim3 grid((unsigned)((ncols + 31) / 32), W);
     k_trsm_lower<WIDE><<<grid, 32, 0, s>>>(Lm, sL, X, sX, n, lr0, xr0, jb, c0, ncols,
@@ -575,12 +729,13 @@ int trsm_lower(const int32_t *Lm, int64_t sL, int32_t *X, int64_t sX, int64_t n,
 // update A22 <- A22 - L21 U12.
 template <bool WIDE>
 int lu_blocked(int32_t *R, int64_t n, const ModP *mods, int W, int nb, int32_t *perm,
-               LUState *st, cudaStream_t s, int path, void *scratch = nullptr) {
+               LUState *st, cudaStream_t s, int path, void *scratch = nullptr,
+               int32_t *tri = nullptr) {
     k_state_init<<<W, 256, 0, s>>>(st, mods, W, perm, n);
     count_launch();
     IDET_TRY(allow_max_smem((const void *)k_panel_cluster));
     const int64_t nn = n * n;
-    const int NB = WIDE ? nb : 4 * nb;
+    const int NB = 4 * nb;
     auto upd = [&](int64_t r, int64_t c, int64_t kr, int M, int N, int K) -> int {
         // C = R[r.., c..] -= R[r.., kr..kr+K) * R[kr..kr+K, c..]
         if (M <= 0 || N <= 0 || K <= 0) return IDET_OK;
@@ -610,7 +765,7 @@ int lu_blocked(int32_t *R, int64_t n, const ModP *mods, int W, int nb, int32_t *
             const int64_t inner = J0 + JB - (j0 + jb);  // columns left in the block column
             if (inner > 0) {
                 IDET_TRY(trsm_lower<WIDE>(R, nn, R, nn, n, j0, j0, jb, j0 + jb, inner, mods, st,
-                                          W, s));
+                                          W, s, tri));
                 IDET_TRY(upd(j0 + jb, j0 + jb, j0, (int)(n - j0 - jb), (int)inner, jb));
             }
         }
@@ -618,7 +773,8 @@ int lu_blocked(int32_t *R, int64_t n, const ModP *mods, int W, int nb, int32_t *
         if (rest <= 0) break;
         for (int64_t i0 = J0; i0 < J0 + JB; i0 += nb) {
             const int ib = (int)((J0 + JB - i0) < nb ? (J0 + JB - i0) : nb);
-            IDET_TRY(trsm_lower<WIDE>(R, nn, R, nn, n, i0, i0, ib, J0 + JB, rest, mods, st, W, s));
+            IDET_TRY(trsm_lower<WIDE>(R, nn, R, nn, n, i0, i0, ib, J0 + JB, rest, mods, st, W, s,
+                                      tri));
             const int64_t below = J0 + JB - (i0 + ib);
             if (below > 0) IDET_TRY(upd(i0 + ib, J0 + JB, i0, (int)below, (int)rest, ib));
         }
@@ -649,7 +805,9 @@ int lu_factor_batched(int32_t *R, int64_t n, const ModP *mods_dev,
         count_launch();
         IDET_CUDA_TRY(cudaGetLastError());
     } else if (wide) {
-        IDET_TRY(lu_blocked<true>(R, n, mods_dev, W, nb, perm, st, s, IDET_PATH_INT64));
+        int32_t *tri = nullptr;
+        IDET_TRY(ws.alloc_n(&tri, (size_t)W * kNBMax * kNBMax));
+        IDET_TRY(lu_blocked<true>(R, n, mods_dev, W, nb, perm, st, s, IDET_PATH_INT64, nullptr, tri));
     } else {
         // default trailing-update arithmetic for 21-bit primes: the tcgen05
         // bf16-limb path (measured fastest at n = 1000 and 4000)
@@ -659,7 +817,9 @@ int lu_factor_batched(int32_t *R, int64_t n, const ModP *mods_dev,
                                                                                   : IDET_PATH_TC05);
         void *scratch = nullptr;
         if (path == IDET_PATH_TC05) IDET_TRY(ws.alloc(&scratch, tc05_scratch_bytes(n, W)));
-        IDET_TRY(lu_blocked<false>(R, n, mods_dev, W, nb, perm, st, s, path, scratch));
+        int32_t *tri = nullptr;
+        IDET_TRY(ws.alloc_n(&tri, (size_t)W * kNBMax * kNBMax));
+        IDET_TRY(lu_blocked<false>(R, n, mods_dev, W, nb, perm, st, s, path, scratch, tri));
         if (path == IDET_PATH_TC05) IDET_TRY(tc05_check_error(s));
     }
     k_finalize_det<<<(W + 127) / 128, 128, 0, s>>>(st, mods_dev, W, det_out);
@@ -680,43 +840,58 @@ int lu_inverse(const int32_t *R, const int32_t *perm, int64_t n, const ModP &mod
     k_perm_identity<<<148 * 4, 256, 0, s>>>(Y, perm, n);
     count_launch();
     IDET_CUDA_TRY(cudaGetLastError());
-    for (int64_t k0 = 0; k0 < n; k0 += nb) {
-        const int kb = (int)((n - k0) < nb ? (n - k0) : nb);
+    // Y <- L^{-1} Y and Y <- U^{-1} Y, two-level: blocks of NB = 4 nb rows;
+    // inside a block, nb-row triangular solves with rank-nb updates of the
+    // block's remaining rows; then one rank-NB update of all rows outside it
+    const int NB = 4 * nb;
+    int32_t *tri = nullptr;
+    IDET_TRY(ws.alloc_n(&tri, (size_t)kNBMax * kNBMax));
+    auto gsub = [&](const int32_t *Ap, const int32_t *Bp, int32_t *Cp, int64_t M, int K) -> int {
+        if (M <= 0 || K <= 0) return IDET_OK;
         if (wide)
-            IDET_TRY(trsm_lower<true>(R, 0, Y, 0, n, k0, k0, kb, 0, n, mod_dev, nullptr, 1, s));
-        else
-            IDET_TRY(trsm_lower<false>(R, 0, Y, 0, n, k0, k0, kb, 0, n, mod_dev, nullptr, 1, s));
-        const int64_t below = n - k0 - kb;
-        if (below > 0) {
+            return gemm_sub<true>(Ap, n, 0, Bp, n, 0, Cp, n, 0, (int)M, (int)n, K, mod_dev, nullptr, 1,
+                                  s);
+        return gemm_sub<false>(Ap, n, 0, Bp, n, 0, Cp, n, 0, (int)M, (int)n, K, mod_dev, nullptr, 1,
+                               s);
+    };
+    for (int64_t J0 = 0; J0 < n; J0 += NB) {
+        const int JB = (int)((n - J0) < NB ? (n - J0) : NB);
+        for (int64_t k0 = J0; k0 < J0 + JB; k0 += nb) {
+            const int kb = (int)((J0 + JB - k0) < nb ? (J0 + JB - k0) : nb);
             if (wide)
-                IDET_TRY(gemm_sub<true>(R + (k0 + kb) * n + k0, n, 0, Y + k0 * n, n, 0,
-                                        Y + (k0 + kb) * n, n, 0, (int)below, (int)n, kb,
-                                        mod_dev, nullptr, 1, s));
+                IDET_TRY(trsm_lower<true>(R, 0, Y, 0, n, k0, k0, kb, 0, n, mod_dev, nullptr, 1, s,
+                                          tri));
             else
-                IDET_TRY(gemm_sub<false>(R + (k0 + kb) * n + k0, n, 0, Y + k0 * n, n, 0,
-                                         Y + (k0 + kb) * n, n, 0, (int)below, (int)n, kb,
-                                         mod_dev, nullptr, 1, s));
+                IDET_TRY(trsm_lower<false>(R, 0, Y, 0, n, k0, k0, kb, 0, n, mod_dev, nullptr, 1, s,
+                                           tri));
+            IDET_TRY(gsub(R + (k0 + kb) * n + k0, Y + k0 * n, Y + (k0 + kb) * n,
+                          J0 + JB - (k0 + kb), kb));
         }
+        IDET_TRY(gsub(R + (J0 + JB) * n + J0, Y + J0 * n, Y + (J0 + JB) * n, n - J0 - JB, JB));
     }
-    const int64_t nblk = (n + nb - 1) / nb;
-    for (int64_t bi = nblk - 1; bi >= 0; --bi) {
-        const int64_t k0 = bi * nb;
-        const int kb = (int)((n - k0) < nb ? (n - k0) : nb);
-        dim3 grid((unsigned)((n + 31) / 32));
-        if (wide)
-            k_trsm_upper<true><<<grid, 32, 0, s>>>(R, n, k0, Y, k0, kb, n, mod_host);
-        else
-            k_trsm_upper<false><<<grid, 32, 0, s>>>(R, n, k0, Y, k0, kb, n, mod_host);
-        count_launch();
-        IDET_CUDA_TRY(cudaGetLastError());
-        if (k0 > 0) {
-            if (wide)
-                IDET_TRY(gemm_sub<true>(R + k0, n, 0, Y + k0 * n, n, 0, Y, n, 0, (int)k0,
-                                        (int)n, kb, mod_dev, nullptr, 1, s));
-            else
-                IDET_TRY(gemm_sub<false>(R + k0, n, 0, Y + k0 * n, n, 0, Y, n, 0, (int)k0,
-                                         (int)n, kb, mod_dev, nullptr, 1, s));
+    const int64_t nblk = (n + NB - 1) / NB;
+    for (int64_t bj = nblk - 1; bj >= 0; --bj) {
+        const int64_t J0 = bj * NB;
+        const int JB = (int)((n - J0) < NB ? (n - J0) : NB);
+        const int64_t nsub = (JB + nb - 1) / nb;
+        for (int64_t bi = nsub - 1; bi >= 0; --bi) {
+            const int64_t k0 = J0 + bi * nb;
+            const int kb = (int)((J0 + JB - k0) < nb ? (J0 + JB - k0) : nb);
+            const dim3 grid((unsigned)((n + 31) / 32), 1);
+            if (wide) {
+                k_tri_inv<true, true><<<1, kNBMax * kNBMax, 0, s>>>(R, 0, n, k0, kb, mod_dev, nullptr, tri);
+                k_tri_apply<true><<<grid, 128, 0, s>>>(tri, Y, 0, n, k0, kb, 0, n, mod_dev, nullptr);
+            } else {
+                k_tri_inv<false, true><<<1, kNBMax * kNBMax, 0, s>>>(R, 0, n, k0, kb, mod_dev, nullptr, tri);
+                k_tri_apply<false><<<grid, 128, 0, s>>>(tri, Y, 0, n, k0, kb, 0, n, mod_dev, nullptr);
+            }
+            count_launch(2);
+            IDET_CUDA_TRY(cudaGetLastError());
+            // rows J0 .. k0 of the block: Y_r -= U[r, k0..k0+kb) Y[k0..k0+kb)
+            IDET_TRY(gsub(R + J0 * n + k0, Y + k0 * n, Y + J0 * n, k0 - J0, kb));
         }
+        // rows above the block
+        IDET_TRY(gsub(R + J0, Y + J0 * n, Y, J0, JB));
     }
     return IDET_OK;
 }

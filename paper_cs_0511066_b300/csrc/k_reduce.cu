@@ -85,6 +85,41 @@ __global__ void k_col_stats(const int64_t *__restrict__ A, int64_t n, int64_t ld
     colsq[j] = acc * (1.0 + 0x1p-30);
 }
 
+// Row and column sums of squares and max |a_ij| for a batch of matrices,
+// one CTA per matrix (rows by warps, columns by threads; same upward margin
+// as the single-matrix kernels).
+__global__ void k_stats_multi(const StatJob *__restrict__ jobs) {
+    const StatJob J = jobs[blockIdx.x];
+    const int64_t n = J.n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long mx = 0;
+    for (int64_t i = warp; i < n; i += kThreads / 32) {
+        double acc = 0.0;
+        for (int64_t j = lane; j < n; j += 32) {
+            const int64_t a = J.A[i * n + j];
+            const unsigned long long m = (unsigned long long)(a < 0 ? -a : a);
+            const double d = (double)a;
+            acc += d * d;
+            mx = m > mx ? m : mx;
+        }
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) J.rowsq[i] = acc * (1.0 + 0x1p-30);
+    }
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = t > mx ? t : mx;
+    }
+    if (lane == 0) atomicMax(J.amax, mx);
+    for (int64_t j = threadIdx.x; j < n; j += kThreads) {
+        double acc = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            const double d = (double)J.A[i * n + j];
+            acc += d * d;
+        }
+        J.colsq[j] = acc * (1.0 + 0x1p-30);
+    }
+}
+
 __global__ void k_to_int32(const int64_t *__restrict__ A, int64_t n, int64_t lda,
                            int32_t *__restrict__ A32) {
     const int64_t total = n * n;
@@ -120,6 +155,14 @@ int launch_row_stats(const int64_t *A, int64_t n, int64_t lda, double *rowsq,
                      unsigned long long *amax, cudaStream_t s) {
     IDET_CUDA_TRY(cudaMemsetAsync(amax, 0, sizeof(unsigned long long), s));
     k_row_stats<<<(unsigned)n, kThreads, 0, s>>>(A, n, lda, rowsq, amax);
+    count_launch();
+    IDET_CUDA_TRY(cudaGetLastError());
+    return IDET_OK;
+}
+
+int launch_stats_multi(const StatJob *jobs_dev, int count, cudaStream_t s) {
+    if (count <= 0) return IDET_OK;
+    k_stats_multi<<<count, kThreads, 0, s>>>(jobs_dev);
     count_launch();
     IDET_CUDA_TRY(cudaGetLastError());
     return IDET_OK;

@@ -301,7 +301,7 @@ void idet_server_destroy(idet_server *srv);
  * the prime class prime_bits (21 or 31), the reduction plus LU of W primes
  * on a random matrix with entries of entry_bits bits (2..32) generated on the
  * device, for every update path of the class (21-bit: TC05, INT64, BF16,
- * I8; 31-bit: INT64), panel width nb in {16, 32} and W in {4, 8, 16}, and
+ * I8; 31-bit: TC05, INT64), panel width nb in {16, 32} and W in {4, 8, 16}, and
  * records the fastest per prime in a process-wide table keyed by (n bucket
  * of a quarter octave, prime bits). Calls with update_path = AUTO, nb = 0
  * or wave = 0 then use the entry of the nearest bucket within one octave

@@ -525,7 +525,7 @@ static int inverse_mod_prime(const DevMatrix &M, uint32_t p, int nb, Workspace &
     IDET_TRY(ws.alloc_n(&dd, 1));
     IDET_CUDA_TRY(cudaMemcpyAsync(md, &mh, sizeof(ModP), cudaMemcpyHostToDevice, s));
     IDET_TRY(launch_reduce(M.A, n, n, md, 1, R, s));
-    IDET_TRY(lu_factor_batched(R, n, md, &mh, 1, true, nb, perm, dd, IDET_PATH_INT64, ws));
+    IDET_TRY(lu_factor_batched(R, n, md, &mh, 1, true, nb, perm, dd, IDET_PATH_AUTO, ws));
     uint32_t det = 0;
     IDET_CUDA_TRY(cudaMemcpyAsync(&det, dd, 4, cudaMemcpyDeviceToHost, s));
     IDET_CUDA_TRY(cudaStreamSynchronize(s));
@@ -801,7 +801,7 @@ static int mp_lift(DetJob &J, unsigned int abits, MpLift &out) {
         mh = make_mod(p);
         IDET_CUDA_TRY(cudaMemcpyAsync(md, &mh, sizeof(ModP), cudaMemcpyHostToDevice, s));
         IDET_TRY(launch_reduce_mp(J.mag, J.sgn, n, J.L, md, 1, R, s));
-        IDET_TRY(lu_factor_batched(R, n, md, &mh, 1, true, J.nb, perm, dd, IDET_PATH_INT64, ws));
+        IDET_TRY(lu_factor_batched(R, n, md, &mh, 1, true, J.nb, perm, dd, IDET_PATH_AUTO, ws));
         uint32_t det = 0;
         IDET_CUDA_TRY(cudaMemcpyAsync(&det, dd, 4, cudaMemcpyDeviceToHost, s));
         IDET_CUDA_TRY(cudaStreamSynchronize(s));

@@ -283,10 +283,12 @@ int lu_inverse(const int32_t *R, const int32_t *perm, int64_t n,
 // tcgen05 bf16-limb trailing update (k_gemm_tc05.cu); scratch holds
 // tc05_scratch_bytes(n, W) bytes for any M, N <= n. tc05_check_error
 // synchronises s and reports a bounded wait that gave up.
-size_t tc05_scratch_bytes(int64_t n, int W);
+// L = 3 limbs for 21-bit primes, 5 for 31-bit primes.
+size_t tc05_scratch_bytes(int64_t n, int W, int L);
 int gemm_sub_tc05(const int32_t *A, int64_t lda, int64_t sA, const int32_t *B, int64_t ldb,
                   int64_t sB, int32_t *C, int64_t ldc, int64_t sC, int M, int N, int K,
-                  const ModP *mods, const LUState *st, int W, void *scratch, cudaStream_t s);
+                  const ModP *mods, const LUState *st, int W, void *scratch, cudaStream_t s,
+                  int L);
 int tc05_check_error(cudaStream_t s);
 int gemm_sub_tc(int path, const int32_t *A, int64_t lda, int64_t sA, const int32_t *B, int64_t ldb,
                 int64_t sB, int32_t *C, int64_t ldc, int64_t sC, int M, int N, int K,

@@ -51,14 +51,21 @@ namespace idet {
 namespace {
 
 constexpr int kTM = 128, kTN = 48;
-constexpr int kGroups = 5;
-constexpr int kAccCols = 256;   // one accumulator set: 5 x 48 = 240 columns
-constexpr int kTmemCols = 512;  // two sets (double buffer)
-constexpr int kT05Threads = 320;
+constexpr int kTmemCols = 512;
 constexpr int kKc = 16;         // K of one stage
-constexpr int kStages = 12;
 constexpr uint32_t kLimbA = kTM * kKc * 2, kLimbB = kTN * kKc * 2;  // bytes per limb chunk
-constexpr uint32_t kStageBytes = 3 * (kLimbA + kLimbB);
+
+// L limbs per residue: 3 for 21-bit primes (5 groups, two accumulator sets
+// of 5 x 48 columns), 5 for 31-bit primes (9 groups of 48 columns: one set).
+template <int L>
+struct Tc {
+    static constexpr int kGroups = 2 * L - 1;
+    static constexpr int kBufs = L == 3 ? 2 : 1;
+    static constexpr int kAccCols = L == 3 ? 256 : 512;
+    static constexpr int kThreads = 64 + 128 * kBufs;
+    static constexpr uint32_t kStageBytes = L * (kLimbA + kLimbB);
+    static constexpr int kStages = L == 3 ? 12 : 7;
+};
 
 __device__ int g_tc05_err;  // first error code (1 load, 2 MMA) of any CTA
 
@@ -66,11 +73,16 @@ __device__ __forceinline__ uint32_t sa(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ void split7(int32_t x, int32_t &l0, int32_t &l1, int32_t &l2) {
-    l0 = ((x + 64) & 127) - 64;
-    const int32_t t = (x - l0) >> 7;
-    l1 = ((t + 64) & 127) - 64;
-    l2 = (t - l1) >> 7;
+// x = sum_{l<L} x_l 2^(7 l), x_l in [-64, 63] for l < L-1 and |x_{L-1}| <= 64
+// (|x| < 2^20 for L = 3, |x| < 2^30 for L = 5).
+template <int L>
+__device__ __forceinline__ void split7(int32_t x, int32_t (&l)[L]) {
+#pragma unroll
+    for (int i = 0; i < L - 1; ++i) {
+        l[i] = ((x + 64) & 127) - 64;
+        x = (x - l[i]) >> 7;
+    }
+    l[L - 1] = x;
 }
 
 // Element (r, k') of a ROWS x K' tile in the core-matrix layout.
@@ -82,12 +94,13 @@ __device__ __forceinline__ int64_t core_off(int r, int k) {
 // One thread per (row, k) of each operand tile, for every prime (z).
 // A: rows m of A (M x K at lda); B: columns n of B (K x N at ldb), stored as
 // rows of B^T. Rows >= M (N) and k >= K are zero.
+template <int L>
 __global__ void k_pack_limbs(const int32_t *__restrict__ A, int64_t lda, int64_t sA,
                              const int32_t *__restrict__ B, int64_t ldb, int64_t sB, int M, int N,
                              int K, int Kp, int Mt, int Nt, __nv_bfloat16 *__restrict__ Apk,
                              __nv_bfloat16 *__restrict__ Bpk) {
     const int w = blockIdx.z;
-    const int Kq = 3 * Kp;
+    const int Kq = L * Kp;
     const int64_t atile = (int64_t)kTM * Kq, btile = (int64_t)kTN * Kq;
     const int64_t arows = (int64_t)Mt * kTM, total = (arows + (int64_t)Nt * kTN) * Kp;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -95,30 +108,24 @@ __global__ void k_pack_limbs(const int32_t *__restrict__ A, int64_t lda, int64_t
         const int64_t row = e / Kp;
         const int k = (int)(e - row * Kp);
         int32_t x = 0;
-        __nv_bfloat16 *dst;
-        int64_t o0, o1, o2;
+        int32_t l[L];
         if (row < arows) {
             const int m = (int)row;
             if (m < M && k < K) x = A[(int64_t)w * sA + (int64_t)m * lda + k];
             const int mt = m / kTM, r = m % kTM;
-            dst = Apk + ((int64_t)w * Mt + mt) * atile;
-            o0 = core_off<kTM>(r, k);
-            o1 = core_off<kTM>(r, Kp + k);
-            o2 = core_off<kTM>(r, 2 * Kp + k);
+            __nv_bfloat16 *dst = Apk + ((int64_t)w * Mt + mt) * atile;
+            split7<L>(x, l);
+#pragma unroll
+            for (int i = 0; i < L; ++i) dst[core_off<kTM>(r, i * Kp + k)] = __int2bfloat16_rn(l[i]);
         } else {
             const int n = (int)(row - arows);
             if (n < N && k < K) x = B[(int64_t)w * sB + (int64_t)k * ldb + n];
             const int nt = n / kTN, r = n % kTN;
-            dst = Bpk + ((int64_t)w * Nt + nt) * btile;
-            o0 = core_off<kTN>(r, k);
-            o1 = core_off<kTN>(r, Kp + k);
-            o2 = core_off<kTN>(r, 2 * Kp + k);
+            __nv_bfloat16 *dst = Bpk + ((int64_t)w * Nt + nt) * btile;
+            split7<L>(x, l);
+#pragma unroll
+            for (int i = 0; i < L; ++i) dst[core_off<kTN>(r, i * Kp + k)] = __int2bfloat16_rn(l[i]);
         }
-        int32_t l0, l1, l2;
-        split7(x, l0, l1, l2);
-        dst[o0] = __int2bfloat16_rn(l0);
-        dst[o1] = __int2bfloat16_rn(l1);
-        dst[o2] = __int2bfloat16_rn(l2);
     }
 }
 
@@ -192,8 +199,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *m) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(m)) : "memory");
 }
 
+template <int L>
 struct Tc05Shared {
-    uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2], drain;
+    uint64_t full[Tc<L>::kStages], empty[Tc<L>::kStages], acc_full[2], acc_empty[2], drain;
     uint32_t taddr;
     volatile int abort;
     int prod_iter, mma_iter;
@@ -209,14 +217,18 @@ __device__ __forceinline__ bool mbar_wait_sleep(uint64_t *m, uint32_t parity) {
     return true;
 }
 
-__global__ void __launch_bounds__(kT05Threads, 1)
+template <int L>
+__global__ void __launch_bounds__(Tc<L>::kThreads, 1)
 k_gemm_tc05(const __nv_bfloat16 *__restrict__ Apk, const __nv_bfloat16 *__restrict__ Bpk, int Kp,
             int Mt, int Nt, int W, int32_t *__restrict__ C, int64_t ldc, int64_t sC, int M, int N,
             const ModP *__restrict__ mods, const LUState *__restrict__ st) {
+    constexpr int kGroups = Tc<L>::kGroups, kBufs = Tc<L>::kBufs, kAccCols = Tc<L>::kAccCols;
+    constexpr int kStages = Tc<L>::kStages;
+    constexpr uint32_t kStageBytes = Tc<L>::kStageBytes;
     extern __shared__ __align__(128) unsigned char sm[];
-    __shared__ Tc05Shared S;
+    __shared__ Tc05Shared<L> S;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int Kq = 3 * Kp, nck = Kp / kKc;
+    const int Kq = L * Kp, nck = Kp / kKc;
     const int64_t tiles = (int64_t)W * Mt * Nt;
     if (tid == 0) {
         for (int i = 0; i < kStages; ++i) {
@@ -268,11 +280,11 @@ k_gemm_tc05(const __nv_bfloat16 *__restrict__ Apk, const __nv_bfloat16 *__restri
                     }
                     unsigned char *dst = sm + (size_t)stg * kStageBytes;
                     mbar_expect_tx(&S.full[stg], kStageBytes);
-                    for (int l = 0; l < 3; ++l) {
+                    for (int l = 0; l < L; ++l) {
                         const int kb = (l * Kp + c * kKc) / 8;
                         bulk_g2s(dst + l * kLimbA, gA + (size_t)kb * (kTM / 8) * 128, kLimbA,
                                  &S.full[stg]);
-                        bulk_g2s(dst + 3 * kLimbA + l * kLimbB, gB + (size_t)kb * (kTN / 8) * 128,
+                        bulk_g2s(dst + L * kLimbA + l * kLimbB, gB + (size_t)kb * (kTN / 8) * 128,
                                  kLimbB, &S.full[stg]);
                     }
                     S.prod_iter = it + 1;
@@ -286,8 +298,8 @@ k_gemm_tc05(const __nv_bfloat16 *__restrict__ Apk, const __nv_bfloat16 *__restri
             for (int64_t t = blockIdx.x; t < tiles && !S.abort; t += gridDim.x) {
                 const int w = (int)(t / ((int64_t)Mt * Nt));
                 if (st[w].dead) continue;
-                const int buf = tile & 1;
-                if (!mbar_wait(&S.acc_empty[buf], ((uint32_t)(tile >> 1) & 1u) ^ 1u)) {
+                const int buf = tile % kBufs;
+                if (!mbar_wait(&S.acc_empty[buf], ((uint32_t)(tile / kBufs) & 1u) ^ 1u)) {
                     fail(2);
                     break;
                 }
@@ -302,10 +314,10 @@ k_gemm_tc05(const __nv_bfloat16 *__restrict__ Apk, const __nv_bfloat16 *__restri
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t a0 = sa(sm + (size_t)stg * kStageBytes);
-                    const uint32_t b0 = a0 + 3 * kLimbA;
+                    const uint32_t b0 = a0 + L * kLimbA;
                     for (int g = 0; g < kGroups; ++g) {
                         uint32_t acc = c > 0 ? 1u : 0u;
-                        for (int a = (g > 2 ? g - 2 : 0); a <= (g < 2 ? g : 2); ++a) {
+                        for (int a = (g > L - 1 ? g - (L - 1) : 0); a <= (g < L - 1 ? g : L - 1); ++a) {
                             const int b = g - a;
                             const uint64_t ad = smem_desc(a0 + a * kLimbA, lboA, 128);
                             const uint64_t bd = smem_desc(b0 + b * kLimbB, lboB, 128);
@@ -321,7 +333,7 @@ k_gemm_tc05(const __nv_bfloat16 *__restrict__ Apk, const __nv_bfloat16 *__restri
                 ++tile;
             }
         }
-    } else {  // epilogue groups: warps 2-5 (set 0), 6-9 (set 1)
+    } else {  // epilogue groups: warps 2-5 (set 0), 6-9 (set 1 when two sets)
         const int grp = (warp - 2) >> 2, q = warp & 3;
         const bool vec = (ldc % 4 == 0) && (sC % 4 == 0) && (((uintptr_t)C & 15) == 0);
         int tile = 0;
@@ -329,8 +341,8 @@ k_gemm_tc05(const __nv_bfloat16 *__restrict__ Apk, const __nv_bfloat16 *__restri
             const int w = (int)(t / ((int64_t)Mt * Nt));
             const int mt = (int)((t / Nt) % Mt), nt = (int)(t % Nt);
             if (st[w].dead) continue;
-            const int buf = tile & 1;
-            const uint32_t use = (uint32_t)(tile >> 1) & 1u;
+            const int buf = tile % kBufs;
+            const uint32_t use = (uint32_t)(tile / kBufs) & 1u;
             ++tile;
             if (buf != grp) continue;
             const int r = mt * kTM + q * 32 + lane;
@@ -377,10 +389,17 @@ k_gemm_tc05(const __nv_bfloat16 *__restrict__ Apk, const __nv_bfloat16 *__restri
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    int64_t s = 0;
+                    // sum_g 2^(7g) P_g: groups 0..3 (< 2^43) and, reduced first,
+                    // groups 4.. (< 2^50) times 2^28
+                    int64_t lo = 0, hi = 0;
 #pragma unroll
-                    for (int g = kGroups - 1; g >= 0; --g)
-                        s = s * 128 + (int64_t)(int32_t)__float2int_rn(__uint_as_float(rv[g][j]));
+                    for (int g = kGroups - 1; g >= 0; --g) {
+                        const int64_t v = (int64_t)(int32_t)__float2int_rn(__uint_as_float(rv[g][j]));
+                        if (g >= 4) hi = hi * 128 + v;
+                        else lo = lo * 128 + v;
+                    }
+                    const int64_t s = L == 3 ? lo + hi * (1ll << 28)
+                                             : (int64_t)red_bal(hi, Md) * (1ll << 28) + lo;
                     cv[c0 + j] = red_bal((int64_t)cv[c0 + j] - s, Md);
                 }
             }
@@ -417,38 +436,47 @@ k_gemm_tc05(const __nv_bfloat16 *__restrict__ Apk, const __nv_bfloat16 *__restri
 
 }  // namespace
 
-size_t tc05_scratch_bytes(int64_t n, int W) {
+size_t tc05_scratch_bytes(int64_t n, int W, int L) {
     const int64_t Mt = (n + kTM - 1) / kTM, Nt = (n + kTN - 1) / kTN;
-    return (size_t)W * 2 * 3 * 128 * (size_t)(Mt * kTM + Nt * kTN) + 1024;
+    return (size_t)W * 2 * L * 128 * (size_t)(Mt * kTM + Nt * kTN) + 1024;
+}
+
+template <int L>
+static int gemm_tc05_l(const int32_t *A, int64_t lda, int64_t sA, const int32_t *B, int64_t ldb,
+                       int64_t sB, int32_t *C, int64_t ldc, int64_t sC, int M, int N, int K,
+                       const ModP *mods, const LUState *st, int W, void *scratch, cudaStream_t s) {
+    const int Kp = (K + 15) / 16 * 16;
+    const int Mt = (M + kTM - 1) / kTM, Nt = (N + kTN - 1) / kTN;
+    __nv_bfloat16 *Apk = (__nv_bfloat16 *)scratch;
+    __nv_bfloat16 *Bpk = Apk + (size_t)W * Mt * kTM * L * Kp;
+    const int64_t total = ((int64_t)Mt * kTM + (int64_t)Nt * kTN) * Kp;
+    int pg = (int)std::min<int64_t>((total + 255) / 256, 148 * 8);
+    k_pack_limbs<L><<<dim3(pg, 1, W), 256, 0, s>>>(A, lda, sA, B, ldb, sB, M, N, K, Kp, Mt, Nt,
+                                                    Apk, Bpk);
+    count_launch();
+    IDET_CUDA_TRY(cudaGetLastError());
+    const size_t smem = (size_t)Tc<L>::kStages * Tc<L>::kStageBytes;
+    IDET_TRY(allow_max_smem((const void *)k_gemm_tc05<L>));
+    const int64_t tiles = (int64_t)W * Mt * Nt;
+    const int grid = (int)std::min<int64_t>(tiles, 148);
+    k_gemm_tc05<L><<<grid, Tc<L>::kThreads, smem, s>>>(Apk, Bpk, Kp, Mt, Nt, W, C, ldc, sC, M, N,
+                                                       mods, st);
+    count_launch();
+    IDET_CUDA_TRY(cudaGetLastError());
+    return IDET_OK;
 }
 
 int gemm_sub_tc05(const int32_t *A, int64_t lda, int64_t sA, const int32_t *B, int64_t ldb,
                   int64_t sB, int32_t *C, int64_t ldc, int64_t sC, int M, int N, int K,
-                  const ModP *mods, const LUState *st, int W, void *scratch, cudaStream_t s) {
+                  const ModP *mods, const LUState *st, int W, void *scratch, cudaStream_t s,
+                  int L) {
     if (M <= 0 || N <= 0 || K <= 0) return IDET_OK;
     if (K > 128) {
         set_last_error("tcgen05 trailing update: K must be at most 128 (exactness bound)");
         return IDET_ERR_INTERNAL;
     }
-    const int Kp = (K + 15) / 16 * 16;
-    const int Mt = (M + kTM - 1) / kTM, Nt = (N + kTN - 1) / kTN;
-    __nv_bfloat16 *Apk = (__nv_bfloat16 *)scratch;
-    __nv_bfloat16 *Bpk = Apk + (size_t)W * Mt * kTM * 3 * Kp;
-    const int64_t total = ((int64_t)Mt * kTM + (int64_t)Nt * kTN) * Kp;
-    int pg = (int)std::min<int64_t>((total + 255) / 256, 148 * 8);
-    k_pack_limbs<<<dim3(pg, 1, W), 256, 0, s>>>(A, lda, sA, B, ldb, sB, M, N, K, Kp, Mt, Nt, Apk,
-                                                 Bpk);
-    count_launch();
-    IDET_CUDA_TRY(cudaGetLastError());
-    const size_t smem = (size_t)kStages * kStageBytes;
-    IDET_TRY(allow_max_smem((const void *)k_gemm_tc05));
-    const int64_t tiles = (int64_t)W * Mt * Nt;
-    const int grid = (int)std::min<int64_t>(tiles, 148);
-    k_gemm_tc05<<<grid, kT05Threads, smem, s>>>(Apk, Bpk, Kp, Mt, Nt, W, C, ldc, sC, M, N, mods,
-                                                st);
-    count_launch();
-    IDET_CUDA_TRY(cudaGetLastError());
-    return IDET_OK;
+    if (L == 5) return gemm_tc05_l<5>(A, lda, sA, B, ldb, sB, C, ldc, sC, M, N, K, mods, st, W, scratch, s);
+    return gemm_tc05_l<3>(A, lda, sA, B, ldb, sB, C, ldc, sC, M, N, K, mods, st, W, scratch, s);
 }
 
 int tc05_check_error(cudaStream_t s) {

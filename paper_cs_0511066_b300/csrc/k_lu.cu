@@ -742,8 +742,9 @@ int lu_blocked(int32_t *R, int64_t n, const ModP *mods, int W, int nb, int32_t *
         const int32_t *Ap = R + r * n + kr;
         const int32_t *Bp = R + kr * n + c;
         int32_t *Cp = R + r * n + c;
-        if (!WIDE && path == IDET_PATH_TC05)
-            return gemm_sub_tc05(Ap, n, nn, Bp, n, nn, Cp, n, nn, M, N, K, mods, st, W, scratch, s);
+        if (path == IDET_PATH_TC05)
+            return gemm_sub_tc05(Ap, n, nn, Bp, n, nn, Cp, n, nn, M, N, K, mods, st, W, scratch, s,
+                                 WIDE ? 5 : 3);
         if (!WIDE && path != IDET_PATH_INT64)
             return gemm_sub_tc(path, Ap, n, nn, Bp, n, nn, Cp, n, nn, M, N, K, mods, st, W, s);
         return gemm_sub<WIDE>(Ap, n, nn, Bp, n, nn, Cp, n, nn, M, N, K, mods, st, W, s);
@@ -805,9 +806,18 @@ int lu_factor_batched(int32_t *R, int64_t n, const ModP *mods_dev,
         count_launch();
         IDET_CUDA_TRY(cudaGetLastError());
     } else if (wide) {
+        // 31-bit primes: the tcgen05 update with five limbs, or int64
+        const int path = update_path == IDET_PATH_INT64 ||
+                                 (update_path == IDET_PATH_AUTO && have_tuned &&
+                                  tuned.update_path == IDET_PATH_INT64)
+                             ? IDET_PATH_INT64
+                             : IDET_PATH_TC05;
         int32_t *tri = nullptr;
+        void *scratch = nullptr;
         IDET_TRY(ws.alloc_n(&tri, (size_t)W * kNBMax * kNBMax));
-        IDET_TRY(lu_blocked<true>(R, n, mods_dev, W, nb, perm, st, s, IDET_PATH_INT64, nullptr, tri));
+        if (path == IDET_PATH_TC05) IDET_TRY(ws.alloc(&scratch, tc05_scratch_bytes(n, W, 5)));
+        IDET_TRY(lu_blocked<true>(R, n, mods_dev, W, nb, perm, st, s, path, scratch, tri));
+        if (path == IDET_PATH_TC05) IDET_TRY(tc05_check_error(s));
     } else {
         // default trailing-update arithmetic for 21-bit primes: the tcgen05
         // bf16-limb path (measured fastest at n = 1000 and 4000)
@@ -816,7 +826,7 @@ int lu_factor_batched(int32_t *R, int64_t n, const ModP *mods_dev,
                              : (have_tuned && tuned.update_path != IDET_PATH_AUTO ? tuned.update_path
                                                                                   : IDET_PATH_TC05);
         void *scratch = nullptr;
-        if (path == IDET_PATH_TC05) IDET_TRY(ws.alloc(&scratch, tc05_scratch_bytes(n, W)));
+        if (path == IDET_PATH_TC05) IDET_TRY(ws.alloc(&scratch, tc05_scratch_bytes(n, W, 3)));
         int32_t *tri = nullptr;
         IDET_TRY(ws.alloc_n(&tri, (size_t)W * kNBMax * kNBMax));
         IDET_TRY(lu_blocked<false>(R, n, mods_dev, W, nb, perm, st, s, path, scratch, tri));
@@ -846,8 +856,20 @@ int lu_inverse(const int32_t *R, const int32_t *perm, int64_t n, const ModP &mod
     const int NB = 4 * nb;
     int32_t *tri = nullptr;
     IDET_TRY(ws.alloc_n(&tri, (size_t)kNBMax * kNBMax));
+    // the updates on tcgen05 unless the table chose int64 for this size
+    const bool tc = !(have_tuned && tuned.update_path == IDET_PATH_INT64);
+    void *scratch = nullptr;
+    if (tc) IDET_TRY(ws.alloc(&scratch, tc05_scratch_bytes(n, 1, wide ? 5 : 3)));
+    LUState *st1 = nullptr;
+    if (tc) {
+        IDET_TRY(ws.alloc_n(&st1, 1));
+        IDET_CUDA_TRY(cudaMemsetAsync(st1, 0, sizeof(LUState), s));
+    }
     auto gsub = [&](const int32_t *Ap, const int32_t *Bp, int32_t *Cp, int64_t M, int K) -> int {
         if (M <= 0 || K <= 0) return IDET_OK;
+        if (tc)
+            return gemm_sub_tc05(Ap, n, 0, Bp, n, 0, Cp, n, 0, (int)M, (int)n, K, mod_dev, st1, 1,
+                                 scratch, s, wide ? 5 : 3);
         if (wide)
             return gemm_sub<true>(Ap, n, 0, Bp, n, 0, Cp, n, 0, (int)M, (int)n, K, mod_dev, nullptr, 1,
                                   s);
@@ -893,6 +915,7 @@ int lu_inverse(const int32_t *R, const int32_t *perm, int64_t n, const ModP &mod
         // rows above the block
         IDET_TRY(gsub(R + J0, Y + J0 * n, Y, J0, JB));
     }
+    if (tc) IDET_TRY(tc05_check_error(s));
     return IDET_OK;
 }
 

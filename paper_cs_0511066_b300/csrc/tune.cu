@@ -92,7 +92,7 @@ int idet_autotune(int64_t n, int32_t prime_bits, int32_t entry_bits, void *strea
     std::vector<int> paths = prime_bits == 21
                                  ? std::vector<int>{IDET_PATH_TC05, IDET_PATH_INT64, IDET_PATH_BF16,
                                                     IDET_PATH_I8}
-                                 : std::vector<int>{IDET_PATH_INT64};
+                                 : std::vector<int>{IDET_PATH_TC05, IDET_PATH_INT64};
     const int nbs[2] = {16, 32};
     const int waves[3] = {4, 8, 16};
     idet_tuned best{};

@@ -477,3 +477,15 @@ def test_lift_prime_dividing_det_is_reselected():
     assert d == want
     assert st["lift_iters"] > 0, st          # the solve ran (after the reselection)
     assert idet.int_det_batch([A, R])[0] == want
+
+
+@pytest.mark.parametrize("path", ["int64", "tc05"])
+@pytest.mark.parametrize("n", [200, 333, 700])
+def test_det_mod_31bit_primes_every_update_path(path, n):
+    """31-bit primes: the int64 update (split-operand exact sums) and the
+    tcgen05 update with five 7-bit limbs give the oracle's residues,
+    including primes at both ends of the class."""
+    A = workloads.dense_pm2p20(n, seed=n + 11)
+    primes = p31(3, seed=n) + [2147483647, 1073741827]
+    got = idet.det_mod_primes(A, primes, update_path=PATHS[path])
+    assert list(got) == list(modular.det_mod_primes(A, primes))

@@ -53,7 +53,7 @@ def test_autotune_records_a_valid_choice(tmp_path):
     primes = random.Random(2).sample(P21, 6)
     assert list(idet.det_mod_primes(A, primes)) == list(modular.det_mod_primes(A, primes))
     t31 = idet.autotune(257, prime_bits=31, entry_bits=16)
-    assert t31["update_path"] == 1
+    assert t31["update_path"] in (1, 5)
     p = tmp_path / "t.json"
     idet.tuning_save(str(p))
     ent = json.loads(p.read_text())["entries"]

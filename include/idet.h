@@ -94,7 +94,8 @@ typedef struct {
     double lift_bytes;         /* its algorithmic bytes: m * 8 n^2          */
     double lu_macs;            /* (2/3) n^3 per factored prime (+ inverse)  */
     double ms_inverse;         /* LU + inverse mod the lifting prime        */
-    double ms_rr;              /* rational reconstruction                   */
+    double ms_rr;              /* rational reconstruction (idet_int_det_batch:
+                                  included in ms_lift_kernel)                */
 } idet_stats;
 
 /* Fill *opts with the defaults. */

@@ -1761,19 +1761,20 @@ int idet_int_det_batch(int32_t count, const int64_t *const *A, const int64_t *n,
                                            dd, o.update_path, ws));
             }
         }
-        if (!jobs.empty()) {
-            LUSmallJob *jd = nullptr;
-            IDET_TRY(ws.alloc_n(&jd, jobs.size()));
-            IDET_CUDA_TRY(cudaMemcpyAsync(jd, jobs.data(), sizeof(LUSmallJob) * jobs.size(),
-                                          cudaMemcpyHostToDevice, s));
-            IDET_TRY(lu_small_multi(jd, (int)jobs.size(), maxn, s));
-        }
-        if (!ejobs.empty()) {
-            ElimJob *ed = nullptr;
-            IDET_TRY(ws.alloc_n(&ed, ejobs.size()));
-            IDET_CUDA_TRY(cudaMemcpyAsync(ed, ejobs.data(), sizeof(ElimJob) * ejobs.size(),
-                                          cudaMemcpyHostToDevice, s));
-            IDET_TRY(launch_elim_cluster(ed, (int)ejobs.size(), max_en, 0, s));
+        if (!jobs.empty() || !ejobs.empty()) {
+            // one graph per shape: small LUs and cluster eliminations over
+            // their job arrays
+            const int nj = (int)jobs.size(), ne = (int)ejobs.size();
+            const uint64_t key = 0x1000000000ull ^ ((uint64_t)maxn << 40) ^ ((uint64_t)max_en << 20);
+            IDET_TRY(run_phase_graph(
+                s, key,
+                {{jobs.data(), sizeof(LUSmallJob) * jobs.size()},
+                 {ejobs.data(), sizeof(ElimJob) * ejobs.size()}},
+                [&](const std::vector<const void *> &d, cudaStream_t gs) -> int {
+                    if (nj) IDET_TRY(lu_small_multi((const LUSmallJob *)d[0], nj, maxn, gs));
+                    if (ne) IDET_TRY(launch_elim_cluster((const ElimJob *)d[1], ne, max_en, 0, gs));
+                    return IDET_OK;
+                }));
         }
         std::vector<uint32_t> hres(tot);
         IDET_CUDA_TRY(cudaMemcpyAsync(hres.data(), dd_all, 4 * tot, cudaMemcpyDeviceToHost, s));
@@ -2078,20 +2079,20 @@ int idet_int_det_batch(int32_t count, const int64_t *const *A, const int64_t *n,
                 agg.lift_iters += b.m;
                 agg.lift_bytes += (double)b.m * 8.0 * b.n * b.n;
             }
-            LiftJob *ljd = nullptr;
-            RRJob *rjd = nullptr;
-            IDET_TRY(ws.alloc_n(&ljd, lj.size()));
-            IDET_TRY(ws.alloc_n(&rjd, rj.size()));
-            IDET_CUDA_TRY(cudaMemcpyAsync(ljd, lj.data(), sizeof(LiftJob) * lj.size(),
-                                          cudaMemcpyHostToDevice, s));
-            IDET_CUDA_TRY(cudaMemcpyAsync(rjd, rj.data(), sizeof(RRJob) * rj.size(),
-                                          cudaMemcpyHostToDevice, s));
+            // one graph per shape: the lift of every system, then the
+            // reconstruction of every projection (timed together)
+            const int nl = (int)lj.size();
+            const uint64_t key = 0x2000000000ull ^ ((uint64_t)max_ld << 32) ^ (uint64_t)max_m;
             Timer tk(s);
-            IDET_TRY(launch_lift_multi(ljd, (int)lj.size(), max_ld, s));
+            IDET_TRY(run_phase_graph(
+                s, key,
+                {{lj.data(), sizeof(LiftJob) * lj.size()}, {rj.data(), sizeof(RRJob) * rj.size()}},
+                [&](const std::vector<const void *> &d, cudaStream_t gs) -> int {
+                    IDET_TRY(launch_lift_multi((const LiftJob *)d[0], nl, max_ld, gs));
+                    IDET_TRY(launch_ratrecon_multi((const RRJob *)d[1], nl, max_m, gs));
+                    return IDET_OK;
+                }));
             agg.ms_lift_kernel += tk.stop();
-            Timer tr(s);
-            IDET_TRY(launch_ratrecon_multi(rjd, (int)rj.size(), max_m, s));
-            agg.ms_rr += tr.stop();
             // denominators: status and digits of all systems in two copies,
             // then K in base 2^32 for each, their lengths in one copy
             std::vector<int32_t> hinfo(4 * lid.size());

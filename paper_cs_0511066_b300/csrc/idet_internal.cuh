@@ -13,6 +13,7 @@
 #include <stddef.h>
 
 #include <atomic>
+#include <functional>
 #include <vector>
 
 #include "../../include/idet.h"
@@ -227,6 +228,17 @@ struct ElimJob {
 };
 int launch_elim_cluster(const ElimJob *jobs_dev, int count, int max_n, int mode, cudaStream_t s);
 bool elim_cluster_fits(int n);
+
+// CUDA-graph replay of a batched phase (graph.cu): the job arrays (blobs)
+// are copied into a fixed device buffer and record(device pointers, stream)
+// issues the phase's launches; the sequence is captured per (key, blob
+// sizes) on the second occurrence and replayed afterwards.
+struct JobBlob {
+    const void *data;
+    size_t bytes;
+};
+int run_phase_graph(cudaStream_t s, uint64_t key, const std::vector<JobBlob> &blobs,
+                    const std::function<int(const std::vector<const void *> &, cudaStream_t)> &record);
 // Row and column statistics of many int64 matrices in one launch (one CTA
 // per matrix): rowsq/colsq as in launch_row_stats / launch_col_stats.
 struct StatJob {

@@ -489,3 +489,16 @@ def test_det_mod_31bit_primes_every_update_path(path, n):
     primes = p31(3, seed=n) + [2147483647, 1073741827]
     got = idet.det_mod_primes(A, primes, update_path=PATHS[path])
     assert list(got) == list(modular.det_mod_primes(A, primes))
+
+
+def test_int_det_batch_graph_replay():
+    """The batched phases run eagerly the first time a shape is seen, are
+    captured into CUDA graphs the second time and replayed afterwards: every
+    run gives the oracle's determinants, with another shape in between."""
+    mats = workloads.batch_mix(count=20, nmin=8, nmax=260, bits=10, seed=44)
+    want = [exact.bareiss_det(A.tolist()) if A.shape[0] <= 70 else idet.int_det(A) for A in mats]
+    other = workloads.batch_mix(count=7, nmin=5, nmax=40, bits=8, seed=45)
+    want_o = [exact.bareiss_det(A.tolist()) for A in other]
+    for _ in range(3):
+        assert idet.int_det_batch(mats) == want
+        assert idet.int_det_batch(other) == want_o

@@ -184,7 +184,7 @@ k_elim_cluster(const ElimJob *__restrict__ jobs, int mode) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ __align__(16) int32_t es[];
-    __shared__ int s_flag[2], s_cand[2];
+    __shared__ int s_cand[2];
     __shared__ int32_t s_inv;
     const ElimJob J = jobs[blockIdx.x / kEC];
     const int rank = (int)cl.block_rank();
@@ -208,16 +208,23 @@ k_elim_cluster(const ElimJob *__restrict__ jobs, int mode) {
             J.A32[(int64_t)(rbeg + r) * J.ld + c] = 0;
         }
     for (int k = tid; k < n; k += kECT) swp[k] = k;
+    int32_t *fcol = swp + n;                 // chunk: column k of this block's rows
     uint32_t det = 1u % M.p;
     int neg = 0, dead = 0;
     __syncthreads();
     cl.sync();
     for (int k = 0; k < n; ++k) {
-        const int owner = k / chunk, par = k & 1;
-        if (rank == owner && tid == 0) s_flag[par] = rows[(k - rbeg) * n + k] != 0;
-        cl.sync();
-        int piv = k;
-        if (!*cl.map_shared_rank(&s_flag[par], owner)) {
+        const int owner = k / chunk;
+        // the owner of row k-1 writes it now: every block finished reading it
+        if (k > 0 && rank == (k - 1) / chunk) {
+            int32_t *row = rows + (size_t)(k - 1 - rbeg) * n;
+            for (int c = tid; c < n; c += kECT) row[c] = prow[c];
+        }
+        int32_t *kr = cl.map_shared_rank(rows, owner) + (size_t)(k - owner * chunk) * n;
+        if (tid == 0) s_inv = kr[k];
+        __syncthreads();
+        if (s_inv == 0) {
+            const int par = k & 1;
             if (tid == 0) s_cand[par] = INT_MAX;
             __syncthreads();
             for (int r = tid; r < nloc; r += kECT)
@@ -229,71 +236,49 @@ k_elim_cluster(const ElimJob *__restrict__ jobs, int mode) {
                 dead = 1;
                 break;
             }
-            piv = best;
-            const int po = piv / chunk;
-            int32_t *pr = cl.map_shared_rank(rows, po) + (size_t)(piv - po * chunk) * n;
-            int32_t *kr = cl.map_shared_rank(rows, owner) + (size_t)(k - owner * chunk) * n;
-            // exchange rows k and piv: rank 0 stages row k in its pivot buffer
-            if (rank == 0)
-                for (int c = tid; c < n; c += kECT) prow[c] = kr[c];
-            cl.sync();
+            const int po = best / chunk;
+            int32_t *pr = cl.map_shared_rank(rows, po) + (size_t)(best - po * chunk) * n;
             if (rank == 0)
                 for (int c = tid; c < n; c += kECT) {
+                    const int32_t t = kr[c];
                     kr[c] = pr[c];
-                    pr[c] = prow[c];
+                    pr[c] = t;
                 }
-            if (tid == 0) swp[k] = piv;
+            if (tid == 0) swp[k] = best;
             neg ^= 1;
             cl.sync();
         }
-        {
-            const int32_t *kr = cl.map_shared_rank(rows, owner) + (size_t)(k - owner * chunk) * n;
-            for (int c = tid; c < n; c += kECT) prow[c] = kr[c];
-        }
-        // Gauss-Jordan rewrites row k in its owner: every block must hold its
-        // copy first
-        if (mode == 1) cl.sync(); else __syncthreads();
+        for (int c = tid; c < n; c += kECT) prow[c] = kr[c];
+        for (int r = tid; r < nloc; r += kECT) fcol[r] = rows[r * n + k];
+        __syncthreads();
         const int32_t pv = prow[k];
         if (tid == 0) s_inv = inv32(pv, M.p);
         det = red_pos((int64_t)det * pv, M);
         __syncthreads();
         const int32_t inv = s_inv;
-        if (mode == 0) {
-            // rows below k: l_i = a_ik / a_kk, a_ij -= l_i a_kj for j > k
-            for (int r = tid; r < nloc; r += kECT)
-                if (rbeg + r > k) rows[r * n + k] = mul_bal(rows[r * n + k], inv, M);
-            __syncthreads();
-            for (int r = max(0, k + 1 - rbeg); r < nloc; ++r) {
-                const int32_t l = rows[r * n + k];
-                if (!l) continue;
-                int32_t *row = rows + (size_t)r * n;
-                for (int c = k + 1 + tid; c < n; c += kECT)
-                    row[c] = red_bal((int64_t)row[c] - (int64_t)l * prow[c], M);
-            }
-        } else {
-            // pivot row scaled by 1/a_kk, with 1/a_kk in column k
-            for (int c = tid; c < n; c += kECT) prow[c] = (c == k) ? inv : mul_bal(prow[c], inv, M);
-            __syncthreads();
-            // other rows: a_ij -= a_ik prow_j (j != k); row k <- prow
-            for (int r = 0; r < nloc; ++r) {
-                int32_t *row = rows + (size_t)r * n;
-                if (rbeg + r == k) {
-                    for (int c = tid; c < n; c += kECT) row[c] = prow[c];
-                    continue;
-                }
-                const int32_t f = row[k];
-                if (!f) continue;
-                for (int c = tid; c < n; c += kECT)
+        // pivot row scaled by 1/a_kk, with 1/a_kk in column k (the owner
+        // writes it into row k at the start of the next column)
+        for (int c = tid; c < n; c += kECT) prow[c] = (c == k) ? inv : mul_bal(prow[c], inv, M);
+        __syncthreads();
+        // other rows: a_ij -= a_ik prow_j (j != k), a_ik = -a_ik / a_kk
+        const int rg = tid >> 7, ct = tid & 127;
+        for (int r = rg; r < nloc; r += 4) {
+            if (rbeg + r == k) continue;
+            const int32_t f = fcol[r];
+            int32_t *row = rows + (size_t)r * n;
+            if (f)
+                for (int c = ct; c < n; c += 128)
                     if (c != k) row[c] = red_bal((int64_t)row[c] - (int64_t)f * prow[c], M);
-            }
-            __syncthreads();
-            // column k of the other rows: -a_ik / a_kk
-            for (int r = tid; r < nloc; r += kECT)
-                if (rbeg + r != k) rows[r * n + k] = mul_bal(-rows[r * n + k], inv, M);
+            if (ct == 0) row[k] = mul_bal(-f, inv, M);
         }
         __syncthreads();
         cl.sync();
     }
+    if (!dead && rank == (n - 1) / chunk) {
+        int32_t *row = rows + (size_t)(n - 1 - rbeg) * n;
+        for (int c = tid; c < n; c += kECT) row[c] = prow[c];
+    }
+    __syncthreads();
     cl.sync();
     if (mode == 0) {
         if (rank == 0 && tid == 0) {
@@ -322,11 +307,106 @@ k_elim_cluster(const ElimJob *__restrict__ jobs, int mode) {
     }
 }
 
+// det A mod p by division-free elimination on an 8-CTA cluster (the
+// matrix in distributed shared memory as for k_elim_cluster): at step k,
+// with pivot d_k = a_kk (first nonzero at or below the diagonal, Section
+// 2.1's rule), every row i > k becomes d_k a_i - a_ik a_k, which multiplies
+// the trailing determinant by d_k^(n-k-1). Hence
+//   det A = (-1)^swaps Q_n / prod_{j=1}^{n-1} Q_j,  Q_j = d_0 ... d_{j-1},
+// with one inverse at the end instead of one per column. Every block reads
+// the next pivot row straight from its owner after the column's cluster
+// barrier; only a zero pivot takes the search (uniform over the cluster).
+__global__ void __cluster_dims__(kEC, 1, 1) __launch_bounds__(kECT)
+k_det_cluster(const ElimJob *__restrict__ jobs) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) int32_t es[];
+    __shared__ int s_cand[2];
+    __shared__ int32_t s_pv;
+    const ElimJob J = jobs[blockIdx.x / kEC];
+    const int rank = (int)cl.block_rank();
+    const int n = J.n, chunk = (n + kEC - 1) / kEC;
+    const ModP M = J.mod;
+    const int rbeg = rank * chunk, rend = min(n, rbeg + chunk);
+    const int nloc = rend > rbeg ? rend - rbeg : 0;
+    int32_t *rows = es;                      // chunk x n
+    int32_t *prow = es + (size_t)chunk * n;  // n: pivot row copy
+    const int tid = threadIdx.x;
+    for (int e = tid; e < nloc * n; e += kECT) {
+        const int r = e / n, c = e % n;
+        rows[e] = red_bal(J.A[(int64_t)(rbeg + r) * J.lda + c], M);
+    }
+    int32_t Q = 1, den = 1;
+    int neg = 0, dead = 0;
+    __syncthreads();
+    cl.sync();
+    for (int k = 0; k < n; ++k) {
+        const int owner = k / chunk;
+        int32_t *kr = cl.map_shared_rank(rows, owner) + (size_t)(k - owner * chunk) * n;
+        if (tid == 0) s_pv = kr[k];
+        __syncthreads();
+        int32_t pv = s_pv;
+        if (pv == 0) {
+            const int par = k & 1;
+            if (tid == 0) s_cand[par] = INT_MAX;
+            __syncthreads();
+            for (int r = tid; r < nloc; r += kECT)
+                if (rbeg + r > k && rows[r * n + k] != 0) atomicMin(&s_cand[par], rbeg + r);
+            cl.sync();
+            int best = INT_MAX;
+            for (int q = 0; q < kEC; ++q) best = min(best, *cl.map_shared_rank(&s_cand[par], q));
+            if (best == INT_MAX) {
+                dead = 1;
+                break;
+            }
+            const int po = best / chunk;
+            int32_t *pr = cl.map_shared_rank(rows, po) + (size_t)(best - po * chunk) * n;
+            if (rank == 0)
+                for (int c = k + tid; c < n; c += kECT) {
+                    const int32_t t = kr[c];
+                    kr[c] = pr[c];
+                    pr[c] = t;
+                }
+            neg ^= 1;
+            cl.sync();
+            if (tid == 0) s_pv = kr[k];
+            __syncthreads();
+            pv = s_pv;
+        }
+        for (int c = k + 1 + tid; c < n; c += kECT) prow[c] = kr[c];
+        if (tid == 0) {
+            Q = mul_bal(Q, pv, M);
+            if (k < n - 1) den = mul_bal(den, Q, M);
+        }
+        __syncthreads();
+        // rows by 4 groups, columns by 128 threads
+        const int rg = tid >> 7, ct = tid & 127;
+        for (int r = max(0, k + 1 - rbeg) + rg; r < nloc; r += 4) {
+            int32_t *row = rows + (size_t)r * n;
+            const int32_t l = row[k];
+            for (int c = k + 1 + ct; c < n; c += 128)
+                row[c] = red_bal((int64_t)pv * row[c] - (int64_t)l * prow[c], M);
+        }
+        __syncthreads();
+        cl.sync();
+    }
+    cl.sync();  // no CTA leaves while others may still read its rows
+    if (rank == 0 && tid == 0) {
+        uint32_t d = 0;
+        if (!dead) {
+            int32_t v = mul_bal(Q, inv32(den, M.p), M);
+            if (neg) v = -v;
+            d = v < 0 ? (uint32_t)(v + (int32_t)M.p) : (uint32_t)v;
+        }
+        *J.det = d;
+    }
+}
+
 }  // namespace
 
 static size_t elim_smem(int n) {
     const int chunk = (n + kEC - 1) / kEC;
-    return sizeof(int32_t) * ((size_t)chunk * n + 2 * (size_t)n) + 64;
+    return sizeof(int32_t) * ((size_t)chunk * n + 2 * (size_t)n + chunk) + 64;
 }
 
 bool elim_cluster_fits(int n) { return n >= 1 && elim_smem(n) <= 200 * 1024; }
@@ -339,7 +419,12 @@ int launch_elim_cluster(const ElimJob *jobs_dev, int count, int max_n, int mode,
         return IDET_ERR_ARG;
     }
     IDET_TRY(allow_max_smem((const void *)k_elim_cluster));
-    k_elim_cluster<<<count * kEC, kECT, smem, s>>>(jobs_dev, mode);
+    if (mode == 0) {
+        IDET_TRY(allow_max_smem((const void *)k_det_cluster));
+        k_det_cluster<<<count * kEC, kECT, smem, s>>>(jobs_dev);
+    } else {
+        k_elim_cluster<<<count * kEC, kECT, smem, s>>>(jobs_dev, mode);
+    }
     count_launch();
     IDET_CUDA_TRY(cudaGetLastError());
     return IDET_OK;

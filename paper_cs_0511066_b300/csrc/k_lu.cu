@@ -39,6 +39,22 @@ __device__ __forceinline__ uint32_t det_mul(uint32_t det, int32_t piv, const Mod
 // ---------------------------------------------------------------------------
 // Whole-matrix LU in shared memory.
 
+// Inverse mod p < 2^31 by the extended Euclidean algorithm in 32-bit
+// arithmetic (all remainders and cofactors stay below p in magnitude).
+__device__ __forceinline__ int32_t inv_bal32(int32_t a, uint32_t p) {
+    int32_t r0 = (int32_t)p, r1 = a % (int32_t)p;
+    if (r1 < 0) r1 += (int32_t)p;
+    int32_t t0 = 0, t1 = 1;
+    while (r1 != 0) {
+        int32_t q = r0 / r1, t;
+        t = r0 - q * r1; r0 = r1; r1 = t;
+        t = t0 - q * t1; t0 = t1; t1 = t;
+    }
+    if (t0 > (int32_t)(p - 1) / 2) t0 -= (int32_t)p;
+    if (t0 < -(int32_t)(p - 1) / 2) t0 += (int32_t)p;
+    return t0;
+}
+
 // g: the residues (n x n, ld n), or null with A64: the int64 entries (n x n,
 // ld n), reduced here while they are loaded.
 __device__ void lu_small_body(int32_t *__restrict__ g, int n, const ModP M,
@@ -85,18 +101,23 @@ __device__ void lu_small_body(int32_t *__restrict__ g, int n, const ModP M,
             __syncthreads();
         }
         const int32_t pv = sa[k * n + k];
-        if (threadIdx.x == 0) s_inv = inv_bal(pv, M.p);
+        if (threadIdx.x == 0) s_inv = inv_bal32(pv, M.p);
         det = det_mul(det, pv, M);
         __syncthreads();
         const int32_t inv = s_inv;
-        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x)
-            sa[i * n + k] = mul_bal(sa[i * n + k], inv, M);
-        __syncthreads();
-        const int m = n - k - 1;
-        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-            int i = k + 1 + e / m, j = k + 1 + e % m;
-            int32_t l = sa[i * n + k];
-            if (l) sa[i * n + j] = red_bal((int64_t)sa[i * n + j] - (int64_t)l * sa[k * n + j], M);
+        // a warp per row below the pivot: lane 0 forms the multiplier, the
+        // lanes update the row's columns
+        const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int i = k + 1 + (threadIdx.x >> 5); i < n; i += nw) {
+            int32_t l = 0;
+            if (lane == 0) {
+                l = mul_bal(sa[i * n + k], inv, M);
+                sa[i * n + k] = l;
+            }
+            l = __shfl_sync(0xffffffffu, l, 0);
+            if (l)
+                for (int j = k + 1 + lane; j < n; j += 32)
+                    sa[i * n + j] = red_bal((int64_t)sa[i * n + j] - (int64_t)l * sa[k * n + j], M);
         }
         __syncthreads();
     }
@@ -221,21 +242,6 @@ k_panel(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb,
     }
 }
 
-// Inverse mod p < 2^31 by the extended Euclidean algorithm in 32-bit
-// arithmetic (all remainders and cofactors stay below p in magnitude).
-__device__ __forceinline__ int32_t inv_bal32(int32_t a, uint32_t p) {
-    int32_t r0 = (int32_t)p, r1 = a % (int32_t)p;
-    if (r1 < 0) r1 += (int32_t)p;
-    int32_t t0 = 0, t1 = 1;
-    while (r1 != 0) {
-        int32_t q = r0 / r1, t;
-        t = r0 - q * r1; r0 = r1; r1 = t;
-        t = t0 - q * t1; t0 = t1; t1 = t;
-    }
-    if (t0 > (int32_t)(p - 1) / 2) t0 -= (int32_t)p;
-    if (t0 < -(int32_t)(p - 1) / 2) t0 += (int32_t)p;
-    return t0;
-}
 
 // Panel factorisation by a cluster of kCl CTAs (one cluster per prime).
 // The panel (rows [j0, n), columns [j0, j0 + jb)) is split into kCl

@@ -462,8 +462,8 @@ def main():
     lift_bytes = sum(st["lift_bytes"] for st in big) / len(big)
     achieved = lift_bytes / (lift_ms / 1000.0) / 1e9
     # DRAM traffic of the same kernel from its ncu capture (64 lifting steps
-    # at n = 4000: 3.137 GB read + 3.4 MB written), scaled by the steps
-    traffic = (3.137449e9 + 3.393792e6) / 64 * big[0]["lift_iters"]
+    # at n = 4000: 3.096 GB read + 3.3 MB written), scaled by the steps
+    traffic = (3.095984e9 + 3.312896e6) / 64 * big[0]["lift_iters"]
     lu_ms = sum(st["ms_lu"] for _, st in stats)
     lu_macs = sum(st["lu_macs"] for _, st in stats)
     per_mat = [{"n": int(mats[i % len(mats)].shape[0]),

@@ -103,6 +103,26 @@ def test_dixon_digits_match_oracle(n, m):
     assert r.tolist() == orr
 
 
+_ORACLE_DIGITS = {}
+
+
+@pytest.mark.parametrize("n,m", [(129, 3), (513, 2), (1100, 2)])
+def test_dixon_digits_large_entries_match_oracle(n, m):
+    """Entries near 2^20, a right-hand side near 2^61 and residues near p/2:
+    the products in x_i = C (r_i mod p) mod p come close to 2^60 and the
+    exact division of r_i - A x_i by p runs on values near 2^62; n = 1100
+    streams no row but spans several 4-element chunks per lane."""
+    A = workloads.dense_uniform(n, -(1 << 20), 1 << 20, seed=n + 7)
+    b = workloads.random_rhs(n, 1 << 62, seed=n + 8)
+    p = 2147483647 if n != 513 else p31(1, n)[0]
+    dg, r = idet.dixon_digits(A, b, p, m)
+    if (n, m) not in _ORACLE_DIGITS:
+        _ORACLE_DIGITS[(n, m)] = dixon.dixon_digits(A, b, p, m)
+    odg, orr = _ORACLE_DIGITS[(n, m)]
+    assert dg.tolist() == odg
+    assert r.tolist() == orr
+
+
 # --- CRT ---------------------------------------------------------------------------
 
 def test_crt_symmetric_matches_oracle():

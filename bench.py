@@ -298,6 +298,59 @@ def run_small(args):
     print(json.dumps(line))
 
 
+ABLATION_N = [40, 60, 80, 100, 150, 200, 300, 500, 700, 1000]
+
+
+def run_ablation(args):
+    """Fig. 2 on this GPU: random dense matrices of order 40 to 1000 with
+    entries in [-100, 100], each determinant computed three ways through
+    idet_int_det: early-terminated CRA alone (lif=0), solve first and then
+    CRA of det/K to the bound 2H/K (lif=2, the LIF method), and the default
+    introspective control (lif=1). Per order and method: the fastest of
+    `steps` calls after `warmup`, input resident on the device; the three
+    results must agree."""
+    import torch
+    import paper_cs_0511066_b300 as idet
+    arms = {"cra": 0, "lif": 2, "adaptive": 1}
+    res = {k: [] for k in arms}
+    stats = {}
+    launches0 = idet.launch_count()
+    clk = Clocks(os.path.join(ROOT, "gpurun_out", "clocks_ablation.csv")
+                 if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_ablation.csv")
+    with clk:
+        for n in ABLATION_N:
+            A = torch.from_numpy(workloads.dense_pm100(n, seed=n)).cuda()
+            dets = {}
+            for name, lif in arms.items():
+                for _ in range(args.warmup):
+                    idet.int_det(A, lif=lif)
+                best = None
+                for _ in range(args.steps):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    d, st = idet.int_det(A, lif=lif, return_stats=True)
+                    torch.cuda.synchronize()
+                    el = (time.perf_counter() - t0) * 1e3
+                    if best is None or el < best:
+                        best = el
+                dets[name] = d
+                res[name].append(round(best, 3))
+                stats[f"{name}_n{n}"] = {"primes": st["primes_in_cra"], "lift_iters": st["lift_iters"],
+                                         "et_stop": st["et_stop"]}
+            assert dets["cra"] == dets["lif"] == dets["adaptive"], f"methods disagree at n={n}"
+    launches = idet.launch_count() - launches0
+    cross = next((n for n, a, c in zip(ABLATION_N, res["adaptive"], res["cra"]) if a < c), None)
+    ms = res["adaptive"][-1]
+    line = _line("ms per determinant, adaptive control (n=1000, entries [-100,100])", ms, "ms",
+                 args, ms, {"workload": "fig2_ablation_dense_pm100_n40-1000",
+                            "timing": "host wall clock around each blocking call, best of steps"},
+                 higher_is_better=False, gpu_launches=int(launches), clocks=clk.summary(),
+                 ablation={"n": ABLATION_N, "cra_ms": res["cra"], "lif_ms": res["lif"],
+                           "adaptive_ms": res["adaptive"], "adaptive_beats_cra_from_n": cross},
+                 stats=stats)
+    print(json.dumps(line))
+
+
 def run_serve(args):
     """Served jobs: n log-uniform in [64, 4096], entry bits in {8, 16, 32},
     Poisson arrivals at rates 0.25..4 x the measured closed-loop capacity;
@@ -372,10 +425,11 @@ def main():
                          "'lu' (det mod 4 primes, n=4000, int64 update) or 'lu_tc05' (the "
                          "same with the tcgen05 update); runs once and prints timings")
     ap.add_argument("--workload", default="plain",
-                    choices=["plain", "batch", "serve", "lift_heavy", "small"],
+                    choices=["plain", "batch", "serve", "lift_heavy", "small", "ablation"],
                     help="plain (default): n=1000 [0,255] + n=4000 +-2^20; batch: 512 "
                          "matrices n in [32,512]; serve: Poisson-served jobs n in [64,4096]; "
-                         "lift_heavy: n=2000 U diag(1,..,d) V, 600-bit d; small: n=100")
+                         "lift_heavy: n=2000 U diag(1,..,d) V, 600-bit d; small: n=100; "
+                         "ablation: Fig. 2, CRA vs LIF vs adaptive, n=40..1000 [-100,100]")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -383,7 +437,7 @@ def main():
         return run_case(args.case)
     if args.workload != "plain":
         return {"batch": run_batch, "serve": run_serve, "lift_heavy": run_lift_heavy,
-                "small": run_small}[args.workload](args)
+                "small": run_small, "ablation": run_ablation}[args.workload](args)
 
     import torch
     import paper_cs_0511066_b300 as idet

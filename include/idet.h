@@ -70,7 +70,10 @@ typedef struct {
     int32_t nb;            /* LU panel width, 0 = default                    */
     int32_t wave;          /* primes factored per batch, 0 = default         */
     int32_t lif;           /* 1 (default): Alg. 4.1 with i_max = 1; 0: CRA
-                              only (Alg. 2.1 on det(A))                      */
+                              only (Alg. 2.1 on det(A)); 2 (idet_int_det
+                              only, else as 1): solve first, then Alg. 2.1
+                              on det(A)/K without early termination, up to
+                              prod p >= 2H/K (the LIF method of Fig. 2)      */
     int32_t prime_bits;    /* CRA prime class: 21 (primes in (2^20, 2^21)) or
                               31 (primes in (2^30, 2^31)); 0 = default: 21
                               for idet_int_det, 31 for idet_int_det_mp      */

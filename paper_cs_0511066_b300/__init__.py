@@ -208,7 +208,7 @@ def _call_int(fn, *args, cap: int = 1 << 12):
         return _to_int(out, buf)
 
 
-def int_det(A, *, certify: bool = False, seed: int | None = None, lif: bool = True,
+def int_det(A, *, certify: bool = False, seed: int | None = None, lif: bool | int = True,
             update_path: int | None = None, nb: int | None = None, wave: int | None = None,
             log2_epsilon: float | None = None, prime_bits: int | None = None, stream=None,
             return_stats: bool = False):

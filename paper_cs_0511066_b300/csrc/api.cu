@@ -712,15 +712,17 @@ static int den_to_binary(Workspace &ws, const std::vector<uint32_t> &den, uint32
 
 // Alg. 2.1 on det(A)/K, using the residues already computed first
 // (Section 4: the modular determinants computed so far are reused). Primes
-// dividing K are skipped. K = null: det(A) itself.
+// dividing K are skipped. K = null: det(A) itself. to_bound: no early
+// termination, stop once the product of the primes reaches 2H/K.
 static int det_over_K(DetJob &J, const uint32_t *Kbin, int Klen, double log2K, int wave,
-                      idet_int *det) {
+                      idet_int *det, bool to_bound = false) {
     const idet_opts &o = J.o;
     Workspace &ws = J.ws;
     cudaStream_t s = J.s;
     const double log2HK = std::max(0.0, J.log2H - log2K);
     std::vector<int32_t> dig;
     int why = 0;
+    if (J.primes.empty()) IDET_TRY(J.factor_wave(wave));
     while (true) {
         std::vector<uint32_t> prs, res;
         Timer t(s);
@@ -751,7 +753,7 @@ static int det_over_K(DetJob &J, const uint32_t *Kbin, int Klen, double log2K, i
         }
         IDET_TRY(J.cra_digits(prs, res, dig));
         const int stop = CraScan::scan(dig, prs, Kbin ? log2HK : J.log2H, o.log2_epsilon,
-                                       J.draw.log2l(), J.draw.pool(), false, &why);
+                                       J.draw.log2l(), J.draw.pool(), to_bound, &why);
         J.st.ms_cra += t.stop();
         if (stop >= 0) {
             J.st.et_stop = why;
@@ -1219,10 +1221,15 @@ int idet_int_det(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
     const int wave = default_wave(o, n, J.draw.bits, k0);
 
     // Alg. 2.1 on det(A): the first k0 primes (Alg. 4.1 lines 1-4), or all
-    // the way in CRA-only / certified mode.
-    bool done = false;
-    const int rc0 = det_first(J, k0, wave, certify || !o.lif, det, &done);
-    if (rc0 != IDET_OK || done) return finish(rc0);
+    // the way in CRA-only / certified mode. lif = 2 (solve first, the order
+    // of Abbott, Bronstein and Mulders that Fig. 2 compares against) skips
+    // it and reconstructs det(A)/K to the bound 2H/K after the solve.
+    const bool solve_first = o.lif == 2 && !certify;
+    if (!solve_first) {
+        bool done = false;
+        const int rc0 = det_first(J, k0, wave, certify || !o.lif, det, &done);
+        if (rc0 != IDET_OK || done) return finish(rc0);
+    }
 
     // Section 2.2 / Alg. 4.1 with i_max = 1: one solve gives K = s~_n.
     const int64_t *bdev = nullptr;
@@ -1251,7 +1258,7 @@ int idet_int_det(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
     if (rc == IDET_OK && !lr.den.empty())
         IDET_TRY(den_to_binary(ws, lr.den, lr.p, &Kbin, &Klen, &log2K));
     J.st.log2_K = (int)std::floor(log2K);
-    return finish(det_over_K(J, Kbin, Klen, log2K, wave, det));
+    return finish(det_over_K(J, Kbin, Klen, log2K, wave, det, solve_first));
 }
 
 int idet_int_det_mp(const uint32_t *A_limbs, const int8_t *A_sign, int64_t n, int32_t L,

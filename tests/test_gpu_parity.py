@@ -180,6 +180,24 @@ def test_int_det_certify_and_cra_only():
     assert idet.int_det(A, lif=False) == want
 
 
+def test_int_det_solve_first():
+    """lif = 2 (solve first, then det(A)/K to the bound 2H/K with no early
+    termination: the LIF method of Fig. 2) gives the exact determinant on
+    random matrices, on one with a large largest invariant factor and on a
+    singular one (the solve fails, CRA of det(A) to 2H)."""
+    for n, seed in [(40, 0), (90, 1), (130, 2)]:
+        A = workloads.dense_pm100(n, seed=seed)
+        d, st = idet.int_det(A, lif=2, return_stats=True)
+        assert d == exact.bareiss_det(A.tolist())
+        assert st["lift_iters"] > 0 and st["et_stop"] == 2, st
+    E = workloads.engineered_smith(60, seed=1)
+    d, st = idet.int_det(E, lif=2, return_stats=True)
+    assert d == math.factorial(60) and st["et_stop"] == 2, st
+    B = workloads.dense_pm100(30, seed=3)
+    B[4] = B[9] + B[11]
+    assert idet.int_det(B, lif=2) == 0
+
+
 def test_int_det_blocked_sizes():
     for n in [193, 260]:
         A = workloads.dense_uniform(n, -8, 8, n)

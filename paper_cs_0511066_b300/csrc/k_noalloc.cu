@@ -1,13 +1,15 @@
 // det(A) mod p_k for small matrices without any device memory allocation.
 //
-// Some callers cannot allocate device memory: code running inside a CUDA
-// graph capture that forbids allocation nodes, plugins hosted by a framework
+// Some callers cannot allocate device memory: plugins hosted by a framework
 // that owns all device memory through its own pool, or processes whose
-// allocator is locked down for determinism. This entry point serves them by
-// using a fixed scratch area that lives in the library image itself: a
-// file-scope __device__ array, present on every GPU that loads the library
-// until the process exits. It has no counterpart in the paper; it is the
-// same computation as idet_det_mod_primes restricted to small sizes.
+// allocator is locked down (for determinism, or while a context is being
+// set up). This entry point serves them by using a fixed scratch area that
+// lives in the library image itself: a file-scope __device__ array, present
+// on every GPU that loads the library until the process exits. It has no
+// counterpart in the paper; it is the same computation as
+// idet_det_mod_primes restricted to small sizes. Every call shares the one
+// area, so calls whose GPU work overlaps race; each call writes every
+// scratch byte it reads, and returns only after its work has finished.
 //
 // Limits: n <= kMaxN = 128 and at most kMaxW = 32 primes per call, so the
 // scratch is 32 * 128 * 128 * 4 bytes of residues (2 MiB) plus the staged
@@ -15,7 +17,8 @@
 //
 // In host code the array's name only stands for it; the device address is
 // obtained once per device with cudaGetSymbolAddress, with that device
-// current, by the first call made on it.
+// current, by the first call made on it, which should therefore come before
+// any stream capture.
 #include <cstring>
 #include <mutex>
 

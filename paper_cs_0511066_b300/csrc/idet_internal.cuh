@@ -307,6 +307,18 @@ int gemm_sub_tc(int path, const int32_t *A, int64_t lda, int64_t sA, const int32
                 const ModP *mods, const LUState *st, int W, cudaStream_t s);
 
 // k_lift.cu ---------------------------------------------------------------
+// Two timing events destroyed with the scope, also on error returns.
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    EventPair() = default;
+    EventPair(const EventPair &) = delete;
+    EventPair &operator=(const EventPair &) = delete;
+    ~EventPair() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
 struct LiftArgs {
     const int32_t *Cinv;   // A^{-1} mod p, balanced, n rows of ld entries
     const int64_t *b;      // right-hand side, n

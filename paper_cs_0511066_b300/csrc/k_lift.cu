@@ -528,11 +528,11 @@ int launch_lift_t(const LiftArgs &a0, const void *Anar, int64_t ld, Workspace &w
     }
     const TA *Ap = (const TA *)Anar;
     void *args[] = {(void *)&a, (void *)&Ap, (void *)&g, (void *)&rm, (void *)&xcur, (void *)&gb};
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    EventPair ev;
     if (ms) {
-        IDET_CUDA_TRY(cudaEventCreate(&e0));
-        IDET_CUDA_TRY(cudaEventCreate(&e1));
-        IDET_CUDA_TRY(cudaEventRecord(e0, s));
+        IDET_CUDA_TRY(cudaEventCreate(&ev.a));
+        IDET_CUDA_TRY(cudaEventCreate(&ev.b));
+        IDET_CUDA_TRY(cudaEventRecord(ev.a, s));
     }
     // One grid-synchronised lift at a time in the process: two of them on
     // different streams could each hold part of the SMs and wait for the
@@ -542,11 +542,9 @@ int launch_lift_t(const LiftArgs &a0, const void *Anar, int64_t ld, Workspace &w
                                               dim3(kLiftThreads), args, smem, s));
     count_launch();
     if (ms) {
-        IDET_CUDA_TRY(cudaEventRecord(e1, s));
-        IDET_CUDA_TRY(cudaEventSynchronize(e1));
-        IDET_CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
+        IDET_CUDA_TRY(cudaEventRecord(ev.b, s));
+        IDET_CUDA_TRY(cudaEventSynchronize(ev.b));
+        IDET_CUDA_TRY(cudaEventElapsedTime(ms, ev.a, ev.b));
     }
     GridBar hb{};
     IDET_CUDA_TRY(cudaMemcpyAsync(&hb, gb, sizeof(GridBar), cudaMemcpyDeviceToHost, s));

@@ -860,8 +860,54 @@ int lu_inverse(const int32_t *R, const int32_t *perm, int64_t n, const ModP &mod
     // inside a block, nb-row triangular solves with rank-nb updates of the
     // block's remaining rows; then one rank-NB update of all rows outside it
     const int NB = 4 * nb;
-    int32_t *tri = nullptr;
-    IDET_TRY(ws.alloc_n(&tri, (size_t)kNBMax * kNBMax));
+    // The diagonal nb x nb blocks of L and U do not change during the
+    // solves: invert all of them up front, the full blocks in one launch per
+    // factor (block b of the factor is batch entry b, stride nb (n + 1)),
+    // a ragged last block in one more.
+    const int64_t nbk = (n + nb - 1) / nb, nfull = n / nb;
+    const size_t tsz = (size_t)kNBMax * kNBMax;
+    int32_t *triL = nullptr, *triU = nullptr;
+    ModP *mrep = nullptr;
+    IDET_TRY(ws.alloc_n(&triL, tsz * nbk));
+    IDET_TRY(ws.alloc_n(&triU, tsz * nbk));
+    IDET_TRY(ws.alloc_n(&mrep, nbk));
+    {
+        std::vector<ModP> mh((size_t)nbk, mod_host);
+        IDET_CUDA_TRY(cudaMemcpyAsync(mrep, mh.data(), sizeof(ModP) * nbk, cudaMemcpyHostToDevice, s));
+        const int64_t strideD = (int64_t)nb * (n + 1);
+        const int last = (int)(n - nfull * nb);
+        if (wide) {
+            if (nfull) {
+                k_tri_inv<true, false><<<(unsigned)nfull, kNBMax * kNBMax, 0, s>>>(R, strideD, n, 0, nb, mrep, nullptr, triL);
+                k_tri_inv<true, true><<<(unsigned)nfull, kNBMax * kNBMax, 0, s>>>(R, strideD, n, 0, nb, mrep, nullptr, triU);
+            }
+            if (last) {
+                k_tri_inv<true, false><<<1, kNBMax * kNBMax, 0, s>>>(R, 0, n, nfull * nb, last, mrep, nullptr, triL + tsz * nfull);
+                k_tri_inv<true, true><<<1, kNBMax * kNBMax, 0, s>>>(R, 0, n, nfull * nb, last, mrep, nullptr, triU + tsz * nfull);
+            }
+        } else {
+            if (nfull) {
+                k_tri_inv<false, false><<<(unsigned)nfull, kNBMax * kNBMax, 0, s>>>(R, strideD, n, 0, nb, mrep, nullptr, triL);
+                k_tri_inv<false, true><<<(unsigned)nfull, kNBMax * kNBMax, 0, s>>>(R, strideD, n, 0, nb, mrep, nullptr, triU);
+            }
+            if (last) {
+                k_tri_inv<false, false><<<1, kNBMax * kNBMax, 0, s>>>(R, 0, n, nfull * nb, last, mrep, nullptr, triL + tsz * nfull);
+                k_tri_inv<false, true><<<1, kNBMax * kNBMax, 0, s>>>(R, 0, n, nfull * nb, last, mrep, nullptr, triU + tsz * nfull);
+            }
+        }
+        count_launch((nfull ? 2 : 0) + (last ? 2 : 0));
+        IDET_CUDA_TRY(cudaGetLastError());
+    }
+    auto apply = [&](const int32_t *tri_blk, int64_t k0, int kb) -> int {
+        const dim3 grid((unsigned)((n + 31) / 32), 1);
+        if (wide)
+            k_tri_apply<true><<<grid, 128, 0, s>>>(tri_blk, Y, 0, n, k0, kb, 0, n, mod_dev, nullptr);
+        else
+            k_tri_apply<false><<<grid, 128, 0, s>>>(tri_blk, Y, 0, n, k0, kb, 0, n, mod_dev, nullptr);
+        count_launch();
+        IDET_CUDA_TRY(cudaGetLastError());
+        return IDET_OK;
+    };
     // the updates on tcgen05 unless the table chose int64 for this size
     const bool tc = !(have_tuned && tuned.update_path == IDET_PATH_INT64);
     void *scratch = nullptr;
@@ -886,12 +932,7 @@ int lu_inverse(const int32_t *R, const int32_t *perm, int64_t n, const ModP &mod
         const int JB = (int)((n - J0) < NB ? (n - J0) : NB);
         for (int64_t k0 = J0; k0 < J0 + JB; k0 += nb) {
             const int kb = (int)((J0 + JB - k0) < nb ? (J0 + JB - k0) : nb);
-            if (wide)
-                IDET_TRY(trsm_lower<true>(R, 0, Y, 0, n, k0, k0, kb, 0, n, mod_dev, nullptr, 1, s,
-                                          tri));
-            else
-                IDET_TRY(trsm_lower<false>(R, 0, Y, 0, n, k0, k0, kb, 0, n, mod_dev, nullptr, 1, s,
-                                           tri));
+            IDET_TRY(apply(triL + tsz * (k0 / nb), k0, kb));
             IDET_TRY(gsub(R + (k0 + kb) * n + k0, Y + k0 * n, Y + (k0 + kb) * n,
                           J0 + JB - (k0 + kb), kb));
         }
@@ -905,16 +946,7 @@ int lu_inverse(const int32_t *R, const int32_t *perm, int64_t n, const ModP &mod
         for (int64_t bi = nsub - 1; bi >= 0; --bi) {
             const int64_t k0 = J0 + bi * nb;
             const int kb = (int)((J0 + JB - k0) < nb ? (J0 + JB - k0) : nb);
-            const dim3 grid((unsigned)((n + 31) / 32), 1);
-            if (wide) {
-                k_tri_inv<true, true><<<1, kNBMax * kNBMax, 0, s>>>(R, 0, n, k0, kb, mod_dev, nullptr, tri);
-                k_tri_apply<true><<<grid, 128, 0, s>>>(tri, Y, 0, n, k0, kb, 0, n, mod_dev, nullptr);
-            } else {
-                k_tri_inv<false, true><<<1, kNBMax * kNBMax, 0, s>>>(R, 0, n, k0, kb, mod_dev, nullptr, tri);
-                k_tri_apply<false><<<grid, 128, 0, s>>>(tri, Y, 0, n, k0, kb, 0, n, mod_dev, nullptr);
-            }
-            count_launch(2);
-            IDET_CUDA_TRY(cudaGetLastError());
+            IDET_TRY(apply(triU + tsz * (k0 / nb), k0, kb));
             // rows J0 .. k0 of the block: Y_r -= U[r, k0..k0+kb) Y[k0..k0+kb)
             IDET_TRY(gsub(R + J0 * n + k0, Y + k0 * n, Y + J0 * n, k0 - J0, kb));
         }

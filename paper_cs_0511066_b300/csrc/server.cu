@@ -198,7 +198,14 @@ void worker_main(idet_server *S, int w) {
     t_native_alloc = true;
     cudaSetDevice(S->device);
     cudaStream_t st = nullptr;
-    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    bool own_stream = true;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        // no stream of its own: this thread's per-thread default stream,
+        // which is still not ordered with the other workers' work
+        cudaGetLastError();
+        st = cudaStreamPerThread;
+        own_stream = false;
+    }
     std::vector<SJob *> take;
     while (true) {
         size_t foot = 0;
@@ -228,10 +235,8 @@ void worker_main(idet_server *S, int w) {
         S->cv_done.notify_all();
         S->cv_work.notify_all();
     }
-    if (st) {
-        cudaStreamSynchronize(st);
-        cudaStreamDestroy(st);
-    }
+    cudaStreamSynchronize(st);
+    if (own_stream) cudaStreamDestroy(st);
 }
 
 }  // namespace

@@ -97,9 +97,10 @@ int idet_autotune(int64_t n, int32_t prime_bits, int32_t entry_bits, void *strea
     const int waves[3] = {4, 8, 16};
     idet_tuned best{};
     best.ms_per_prime = INFINITY;
-    cudaEvent_t e0, e1;
-    IDET_CUDA_TRY(cudaEventCreate(&e0));
-    IDET_CUDA_TRY(cudaEventCreate(&e1));
+    EventPair ev;
+    IDET_CUDA_TRY(cudaEventCreate(&ev.a));
+    IDET_CUDA_TRY(cudaEventCreate(&ev.b));
+    cudaEvent_t e0 = ev.a, e1 = ev.b;
     int rc = IDET_OK;
     for (int path : paths)
         for (int nb : nbs)
@@ -140,8 +141,6 @@ int idet_autotune(int64_t n, int32_t prime_bits, int32_t entry_bits, void *strea
                     best.ms_per_prime = per;
                 }
             }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     if (rc != IDET_OK) return rc;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);

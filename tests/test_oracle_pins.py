@@ -337,3 +337,104 @@ def test_dixon_invariants_and_reconstruction():
     for j in range(n):
         num, den = dixon.rational_reconstruct(X[j], Q, Nb, Db)
         assert Fraction(num, den) == x[j]
+
+
+# --- helpers the parity tests rely on -------------------------------------------
+
+def _sylvester_hadamard(k):
+    """Order 2^k matrix with entries +-1 and mutually orthogonal rows."""
+    H = [[1]]
+    for _ in range(k):
+        H = [r + r for r in H] + [r + [-v for v in r] for r in H]
+    return H
+
+
+@pytest.mark.parametrize("threads", [1, 3])
+def test_det_mod_primes_batch_agrees_with_exact_det(threads):
+    """The multi-prime oracle (one elimination per prime, threads over the
+    primes) gives det mod p for every prime of the list, in list order,
+    including a prime that divides det (a zero residue)."""
+    A = rand_mat(9, -50, 50, seed=41)
+    d = exact.bareiss_det(A)
+    primes = [1048583, 1048589, 2147483629, 1048601, 2147483587, 1048609, 1048613]
+    got = modular.det_mod_primes(np.array(A, dtype=np.int64), primes, threads=threads)
+    assert [int(v) for v in got] == [d % p for p in primes]
+    p = 1048627
+    B = [[p, 0, 0], [3, 1, 0], [5, 7, 2]]          # det = 2 p
+    U = [[1, 2, 0], [0, 1, 3], [0, 0, 1]]          # unimodular
+    BU = exact.matmul(B, U)
+    got = modular.det_mod_primes(np.array(BU, dtype=np.int64), [p, 1048633], threads=threads)
+    assert [int(v) for v in got] == [0, (2 * p) % 1048633]
+
+
+def test_check_solution_accepts_the_solution_and_rejects_a_perturbed_one():
+    A = rand_mat(6, -9, 9, seed=42)
+    while exact.bareiss_det(A) == 0:
+        A[0][0] += 1
+    b = [3, -1, 4, 1, -5, 9]
+    x = exact.solve_rational(A, b)
+    assert exact.check_solution(A, b, x)
+    y = list(x)
+    y[2] += Fraction(1, 7)
+    assert not exact.check_solution(A, b, y)
+
+
+def test_lcm_denominators_closed_forms():
+    assert exact.lcm_denominators([]) == 1
+    assert exact.lcm_denominators([3, -4, 0]) == 1
+    assert exact.lcm_denominators([Fraction(1, 2), Fraction(1, 3), Fraction(5, 6)]) == 6
+    assert exact.lcm_denominators([Fraction(4, 8), Fraction(-9, 12)]) == 4   # 1/2, -3/4
+    assert exact.lcm_denominators([Fraction(1, 2 ** 40), Fraction(1, 3 ** 25)]) == 2 ** 40 * 3 ** 25
+
+
+def test_projection_denominator_diagonal_and_divisibility():
+    """For a diagonal A and b = 1 the solution is x_i = 1/d_i, so u . x is an
+    explicit fraction; in general the denominator of u . x divides the lcm of
+    the denominators of x (the largest invariant factor for b)."""
+    D = [[2, 0, 0, 0], [0, 3, 0, 0], [0, 0, 5, 0], [0, 0, 0, 7]]
+    one = [1, 1, 1, 1]
+    assert exact.projection_denominator(D, one, [1, 1, 1, 1]) == 210   # 247/210
+    assert exact.projection_denominator(D, one, [2, 0, 0, 0]) == 1
+    assert exact.projection_denominator(D, one, [0, 3, 5, 0]) == 1     # 3/3 + 5/5 = 2
+    assert exact.projection_denominator(D, one, [0, 1, 5, 0]) == 3     # 1/3 + 1 = 4/3
+    r = random.Random(43)
+    for n in (3, 5, 7):
+        A = rand_mat(n, -6, 6, seed=n + 100)
+        if exact.bareiss_det(A) == 0:
+            continue
+        b = [r.randint(-20, 20) for _ in range(n)]
+        u = [r.randint(0, 1 << 16) for _ in range(n)]
+        s = exact.largest_invariant_factor(A, b)
+        assert s % exact.projection_denominator(A, b, u) == 0
+
+
+def test_hadamard_log2_forms_meet_at_orthogonal_rows():
+    """Rows of +-1 that are mutually orthogonal reach both bounds:
+    |det| = prod ||row_i|| = (sqrt(n) max|a|)^n = n^(n/2)."""
+    for k in (1, 2, 3):
+        H = _sylvester_hadamard(k)
+        n = len(H)
+        want = 0.5 * n * math.log2(n)
+        assert math.log2(abs(exact.bareiss_det(H))) == pytest.approx(want, abs=1e-12)
+        assert exact.hadamard_lemma_log2(H) == pytest.approx(want, abs=1e-12)
+        assert dixon.hadamard_log2_rows(H) == pytest.approx(want, abs=1e-12)
+    assert exact.hadamard_lemma_log2([[0, 0], [0, 0]]) == float("-inf")
+
+
+def test_hadamard_row_bound_float_and_exact_forms_agree():
+    for seed in range(4):
+        A = rand_mat(7, -1000, 1000, seed=seed + 200)
+        exact_log2 = 0.5 * math.log2(exact.hadamard_rows_sq(A))
+        assert dixon.hadamard_log2_rows(A) == pytest.approx(exact_log2, rel=1e-12)
+        assert exact.hadamard_lemma_log2(A) >= dixon.hadamard_log2_rows(A) - 1e-9
+
+
+def test_dixon_inverse_is_an_inverse_mod_p():
+    p = 2147483629
+    A = rand_mat(8, -100, 100, seed=44)
+    C = dixon.inverse_balanced(np.array(A, dtype=np.int64), p)
+    for i in range(8):
+        for j in range(8):
+            v = sum(int(C[i][k]) * A[k][j] for k in range(8)) % p
+            assert v == (1 if i == j else 0)
+        assert all(abs(int(c)) <= (p - 1) // 2 for c in C[i])

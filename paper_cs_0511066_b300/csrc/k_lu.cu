@@ -263,6 +263,7 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ int32_t sp[];          // chunk x kNBMax panel block
     __shared__ int s_flag[2];                // diagonal nonzero (owner)
+    __shared__ int32_t s_pinv[2];            // its inverse, when nonzero (owner)
     __shared__ int s_cand[2];                // first nonzero row (each CTA)
     __shared__ int32_t s_u[kNBMax];
     __shared__ int32_t s_tmp[kNBMax];
@@ -290,12 +291,19 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
         const int64_t col = j0 + c;
         const int owner = (int)((col - j0) / chunk);
         const int par = c & 1;
-        if (rank == owner && tid == 0)
-            s_flag[par] = sp[(int)(col - rbeg) * kNBMax + c] != 0;
+        // The owner of the diagonal row publishes whether the diagonal entry
+        // is nonzero and, if so, its inverse, computed while the other CTAs
+        // are still updating (the owner has fewer rows below the diagonal).
+        if (rank == owner && tid == 0) {
+            const int32_t dg = sp[(int)(col - rbeg) * kNBMax + c];
+            s_flag[par] = dg != 0;
+            if (dg != 0) s_pinv[par] = inv_bal32(dg, M.p);
+        }
         cluster.sync();
         int *fl = cluster.map_shared_rank(&s_flag[par], owner);
         int64_t piv = col;
-        if (!*fl) {
+        const bool swapped = !*fl;
+        if (swapped) {
             // every CTA: first row >= col + 1 of its block with a nonzero
             if (tid == 0) s_cand[par] = INT_MAX;
             __syncthreads();
@@ -339,16 +347,20 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
             neg ^= 1;
             cluster.sync();
         }
-        // pivot row -> local copy
+        // pivot row -> local copy (and the owner's inverse unless rows were
+        // swapped, when the pivot is not the entry the owner inverted)
         {
             const int32_t *crow = cluster.map_shared_rank(sp, owner) + (int)(col - (j0 + (int64_t)owner * chunk)) * kNBMax;
             if (tid < jb) s_u[tid] = crow[tid];
+            if (!swapped && tid == 0) s_inv = *cluster.map_shared_rank(&s_pinv[par], owner);
         }
         __syncthreads();
         const int32_t pv = s_u[c];
-        if (tid == 0) s_inv = inv_bal32(pv, M.p);
+        if (swapped) {
+            if (tid == 0) s_inv = inv_bal32(pv, M.p);
+            __syncthreads();
+        }
         det = det_mul(det, pv, M);
-        __syncthreads();
         const int32_t inv = s_inv;
         // scale column c of the rows below the pivot
         for (int r = tid; r < nloc; r += kClThreads)

@@ -254,6 +254,7 @@ k_panel(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb,
 // are swapped in global memory.
 constexpr int kCl = 8;
 constexpr int kClThreads = 512;
+constexpr int kSP = kNBMax + 1;  // row stride of a CTA's panel block in shared memory
 
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClThreads)
 k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chunk,
@@ -261,7 +262,7 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
                 int32_t *__restrict__ perm) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
-    extern __shared__ int32_t sp[];          // chunk x kNBMax panel block
+    extern __shared__ int32_t sp[];          // chunk x kSP panel block
     __shared__ int s_flag[2];                // diagonal nonzero (owner)
     __shared__ int32_t s_pinv[2];            // its inverse, when nonzero (owner)
     __shared__ int s_cand[2];                // first nonzero row (each CTA)
@@ -280,7 +281,7 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
     const int tid = threadIdx.x;
     for (int e = tid; e < nloc * jb; e += kClThreads) {
         int r = e / jb, j = e % jb;
-        sp[r * kNBMax + j] = a[(rbeg + r) * n + j0 + j];
+        sp[r * kSP + j] = a[(rbeg + r) * n + j0 + j];
     }
     uint32_t det = st[w].det;
     int neg = st[w].neg;
@@ -295,7 +296,7 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
         // is nonzero and, if so, its inverse, computed while the other CTAs
         // are still updating (the owner has fewer rows below the diagonal).
         if (rank == owner && tid == 0) {
-            const int32_t dg = sp[(int)(col - rbeg) * kNBMax + c];
+            const int32_t dg = sp[(int)(col - rbeg) * kSP + c];
             s_flag[par] = dg != 0;
             if (dg != 0) s_pinv[par] = inv_bal32(dg, M.p);
         }
@@ -309,7 +310,7 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
             __syncthreads();
             for (int r = tid; r < nloc; r += kClThreads) {
                 int64_t gi = rbeg + r;
-                if (gi > col && sp[r * kNBMax + c] != 0) atomicMin(&s_cand[par], (int)gi);
+                if (gi > col && sp[r * kSP + c] != 0) atomicMin(&s_cand[par], (int)gi);
             }
             cluster.sync();
             int best = INT_MAX;
@@ -321,8 +322,8 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
             piv = best;
             // exchange rows piv and col (panel part) through DSMEM
             const int po = (int)((piv - j0) / chunk);
-            int32_t *prow = cluster.map_shared_rank(sp, po) + (int)(piv - (j0 + (int64_t)po * chunk)) * kNBMax;
-            int32_t *crow = cluster.map_shared_rank(sp, owner) + (int)(col - (j0 + (int64_t)owner * chunk)) * kNBMax;
+            int32_t *prow = cluster.map_shared_rank(sp, po) + (int)(piv - (j0 + (int64_t)po * chunk)) * kSP;
+            int32_t *crow = cluster.map_shared_rank(sp, owner) + (int)(col - (j0 + (int64_t)owner * chunk)) * kSP;
             if (rank == 0 && tid < jb) s_tmp[tid] = crow[tid];
             cluster.sync();
             if (rank == 0 && tid < jb) {
@@ -350,7 +351,7 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
         // pivot row -> local copy (and the owner's inverse unless rows were
         // swapped, when the pivot is not the entry the owner inverted)
         {
-            const int32_t *crow = cluster.map_shared_rank(sp, owner) + (int)(col - (j0 + (int64_t)owner * chunk)) * kNBMax;
+            const int32_t *crow = cluster.map_shared_rank(sp, owner) + (int)(col - (j0 + (int64_t)owner * chunk)) * kSP;
             if (tid < jb) s_u[tid] = crow[tid];
             if (!swapped && tid == 0) s_inv = *cluster.map_shared_rank(&s_pinv[par], owner);
         }
@@ -362,18 +363,17 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
         }
         det = det_mul(det, pv, M);
         const int32_t inv = s_inv;
-        // scale column c of the rows below the pivot
-        for (int r = tid; r < nloc; r += kClThreads)
-            if (rbeg + r > col) sp[r * kNBMax + c] = mul_bal(sp[r * kNBMax + c], inv, M);
-        __syncthreads();
-        const int wdt = jb - c - 1;
-        if (wdt > 0) {
-            for (int e = tid; e < nloc * wdt; e += kClThreads) {
-                int r = e / wdt, j = c + 1 + e % wdt;
-                if (rbeg + r <= col) continue;
-                int32_t l = sp[r * kNBMax + c];
-                sp[r * kNBMax + j] = red_bal((int64_t)sp[r * kNBMax + j] - (int64_t)l * s_u[j], M);
-            }
+        // a thread per row below the pivot: scale column c, then update the
+        // row's remaining panel columns (the row stride kSP = 33 words keeps
+        // the lanes of a warp on distinct banks)
+        for (int r = tid; r < nloc; r += kClThreads) {
+            if (rbeg + r <= col) continue;
+            int32_t *row = sp + r * kSP;
+            const int32_t l = mul_bal(row[c], inv, M);
+            row[c] = l;
+            if (l)
+                for (int j = c + 1; j < jb; ++j)
+                    row[j] = red_bal((int64_t)row[j] - (int64_t)l * s_u[j], M);
         }
         __syncthreads();
     }
@@ -389,7 +389,7 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
     }
     for (int e = tid; e < nloc * jb; e += kClThreads) {
         int r = e / jb, j = e % jb;
-        a[(rbeg + r) * n + j0 + j] = sp[r * kNBMax + j];
+        a[(rbeg + r) * n + j0 + j] = sp[r * kSP + j];
     }
     if (rank == 0 && tid == 0) {
         LUState s = st[w];
@@ -772,7 +772,7 @@ int lu_blocked(int32_t *R, int64_t n, const ModP *mods, int W, int nb, int32_t *
         for (int64_t j0 = J0; j0 < J0 + JB; j0 += nb) {
             const int jb = (int)((J0 + JB - j0) < nb ? (J0 + JB - j0) : nb);
             const int chunk = (int)((n - j0 + kCl - 1) / kCl);
-            const size_t psmem = sizeof(int32_t) * (size_t)chunk * kNBMax;
+            const size_t psmem = sizeof(int32_t) * (size_t)chunk * kSP;
             if (psmem <= 200 * 1024) {
                 k_panel_cluster<<<W * kCl, kClThreads, psmem, s>>>(R, n, j0, jb, chunk, mods, st,
                                                                    perm);

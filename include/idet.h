@@ -9,6 +9,8 @@
  * Conventions shared by every entry point:
  *   - Matrices are dense, row-major, n x n, with leading dimension lda >= n
  *     (in elements). Entries are int64 values with |a_ij| <= 2^31 - 1.
+ *     Orders above IDET_MAX_ORDER (65536) are rejected with IDET_ERR_ARG
+ *     before any device work (their sizes would overflow the byte counts).
  *   - on_device = 0: pointers are host memory; the library copies them.
  *     on_device = 1: pointers are device memory of the current device.
  *   - stream is a cudaStream_t (passed as void*; NULL = legacy default
@@ -35,6 +37,7 @@ extern "C" {
 
 /* Status codes. */
 #define IDET_OK 0
+#define IDET_MAX_ORDER 65536  /* largest accepted n, every entry point */
 #define IDET_ERR_ARG 1        /* n < 0, null pointer, lda < n, entry too large */
 #define IDET_ERR_BUFFER 2     /* output capacity too small; nlimbs = needed  */
 #define IDET_ERR_SINGULAR 3   /* det(A) = 0 where a nonsingular A is needed  */

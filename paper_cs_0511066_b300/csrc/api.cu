@@ -999,7 +999,8 @@ uint64_t idet_launch_count(void) { return g_launches; }
 int idet_det_mod_primes(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
                         const uint32_t *primes, int32_t nprimes, const idet_opts *opts,
                         void *stream, uint32_t *det_mod) {
-    if (n < 0 || lda < n || (n > 0 && !A) || nprimes < 0 || (nprimes > 0 && (!primes || !det_mod))) {
+    if (n < 0 || n > IDET_MAX_ORDER || lda < n || (n > 0 && !A) || nprimes < 0 ||
+        (nprimes > 0 && (!primes || !det_mod))) {
         set_last_error("invalid argument");
         return IDET_ERR_ARG;
     }
@@ -1055,7 +1056,7 @@ int idet_det_mod_primes(const int64_t *A, int64_t n, int64_t lda, int32_t on_dev
 
 int idet_lu_mod_prime(const int64_t *A, int64_t n, int64_t lda, int32_t on_device, uint32_t p,
                       const idet_opts *opts, void *stream, uint32_t *lu, int32_t *perm) {
-    if (n <= 0 || lda < n || !A || !lu || !perm) {
+    if (n <= 0 || n > IDET_MAX_ORDER || lda < n || !A || !lu || !perm) {
         set_last_error("invalid argument");
         return IDET_ERR_ARG;
     }
@@ -1095,7 +1096,8 @@ int idet_lu_mod_prime(const int64_t *A, int64_t n, int64_t lda, int32_t on_devic
 int idet_dixon_digits(const int64_t *A, int64_t n, int64_t lda, const int64_t *b, uint32_t p,
                       int32_t m, int32_t on_device, void *stream, int32_t *digits,
                       int64_t *residual) {
-    if (n <= 0 || lda < n || !A || !b || m < 0 || (m > 0 && !digits) || !residual ||
+    if (n <= 0 || n > IDET_MAX_ORDER || lda < n || !A || !b || m < 0 || (m > 0 && !digits) ||
+        !residual ||
         !(p > (1u << 30) && p < (1u << 31) && is_prime32(p))) {
         set_last_error("invalid argument");
         return IDET_ERR_ARG;
@@ -1183,7 +1185,7 @@ static int lif_common(DetJob &J, const int64_t *b_dev, const std::vector<int64_t
 
 int idet_int_det(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
                  const idet_opts *opts, void *stream, idet_int *det, idet_stats *stats) {
-    if (n < 0 || lda < n || (n > 0 && !A) || !det) {
+    if (n < 0 || n > IDET_MAX_ORDER || lda < n || (n > 0 && !A) || !det) {
         set_last_error("invalid argument");
         return IDET_ERR_ARG;
     }
@@ -1264,7 +1266,8 @@ int idet_int_det(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
 int idet_int_det_mp(const uint32_t *A_limbs, const int8_t *A_sign, int64_t n, int32_t L,
                     int32_t on_device, const idet_opts *opts, void *stream, idet_int *det,
                     idet_stats *stats) {
-    if (n < 0 || n > 65536 || L < 1 || L > 64 || (n > 0 && (!A_limbs || !A_sign)) || !det) {
+    if (n < 0 || n > IDET_MAX_ORDER || L < 1 || L > 64 || (n > 0 && (!A_limbs || !A_sign)) ||
+        !det) {
         set_last_error("invalid argument");
         return IDET_ERR_ARG;
     }
@@ -1371,7 +1374,7 @@ static int lif_common(DetJob &J, const int64_t *b_dev, const std::vector<int64_t
 int idet_largest_invariant_factor(const int64_t *A, int64_t n, int64_t lda, const int64_t *b,
                                   int32_t on_device, const idet_opts *opts, void *stream,
                                   idet_int *sout) {
-    if (n < 0 || lda < n || (n > 0 && (!A || !b)) || !sout) {
+    if (n < 0 || n > IDET_MAX_ORDER || lda < n || (n > 0 && (!A || !b)) || !sout) {
         set_last_error("invalid argument");
         return IDET_ERR_ARG;
     }
@@ -1586,7 +1589,7 @@ int idet_int_det_batch(int32_t count, const int64_t *const *A, const int64_t *n,
         return IDET_ERR_ARG;
     }
     for (int i = 0; i < count; ++i)
-        if (n[i] < 0 || lda[i] < n[i] || (n[i] > 0 && !A[i])) {
+        if (n[i] < 0 || n[i] > IDET_MAX_ORDER || lda[i] < n[i] || (n[i] > 0 && !A[i])) {
             set_last_error("invalid matrix %d", i);
             return IDET_ERR_ARG;
         }

@@ -285,7 +285,7 @@ idet_server *idet_server_create(size_t hbm_budget, int32_t slots, int32_t small_
 }
 
 int idet_submit(idet_server *S, const int64_t *A, int64_t n, int64_t lda, uint64_t *ticket) {
-    if (!S || !ticket || n < 1 || lda < n || !A) {
+    if (!S || !ticket || n < 1 || n > IDET_MAX_ORDER || lda < n || !A) {
         set_last_error("submit: invalid argument");
         return IDET_ERR_ARG;
     }

@@ -70,7 +70,7 @@ using namespace idet;
 extern "C" {
 
 int idet_autotune(int64_t n, int32_t prime_bits, int32_t entry_bits, void *stream, idet_tuned *out) {
-    if (n < 1 || n > 65536 || (prime_bits != 21 && prime_bits != 31) || entry_bits < 2 ||
+    if (n < 1 || n > IDET_MAX_ORDER || (prime_bits != 21 && prime_bits != 31) || entry_bits < 2 ||
         entry_bits > 32) {
         set_last_error("autotune: invalid argument");
         return IDET_ERR_ARG;

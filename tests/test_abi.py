@@ -37,3 +37,42 @@ def test_binding_imports_and_defaults():
     o = idet.default_opts()
     assert o.log2_epsilon == -64.0 and o.lif == 1 and o.certify == 0
     assert idet.launch_count() >= 0
+
+
+def test_orders_above_the_limit_are_rejected_before_any_device_work():
+    """n > IDET_MAX_ORDER returns IDET_ERR_ARG from the argument checks,
+    which run before any CUDA call (so this needs no GPU): the byte counts of
+    such orders would overflow."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "_idet_build", os.path.join(ROOT, "paper_cs_0511066_b300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    lib = ctypes.CDLL(mod.build())
+    lib.idet_last_error.restype = ctypes.c_char_p
+    hdr = open(os.path.join(ROOT, "include", "idet.h")).read()
+    limit = int(re.search(r"#define IDET_MAX_ORDER (\d+)", hdr).group(1))
+    assert limit == 65536
+    big = ctypes.c_int64(limit + 1)
+    dummy = ctypes.c_void_p(64)          # never dereferenced: the checks fail first
+    i64, i32, u32 = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32
+    calls = {
+        "idet_int_det": lambda: lib.idet_int_det(dummy, big, big, i32(0), None, None, dummy, None),
+        "idet_largest_invariant_factor": lambda: lib.idet_largest_invariant_factor(
+            dummy, big, big, dummy, i32(0), None, None, dummy),
+        "idet_det_mod_primes": lambda: lib.idet_det_mod_primes(
+            dummy, big, big, i32(0), dummy, i32(1), None, None, dummy),
+        "idet_lu_mod_prime": lambda: lib.idet_lu_mod_prime(
+            dummy, big, big, i32(0), u32(2147483629), None, None, dummy, dummy),
+        "idet_dixon_digits": lambda: lib.idet_dixon_digits(
+            dummy, big, big, dummy, u32(2147483629), i32(1), i32(0), None, dummy, dummy),
+        "idet_int_det_mp": lambda: lib.idet_int_det_mp(
+            dummy, dummy, big, i32(2), i32(0), None, None, dummy, None),
+    }
+    for name, call in calls.items():
+        assert call() == 1, name
+    ns = (i64 * 2)(3, limit + 1)
+    ldas = (i64 * 2)(3, limit + 1)
+    ptrs = (ctypes.c_void_p * 2)(64, 64)
+    assert lib.idet_int_det_batch(i32(2), ptrs, ns, ldas, i32(0), None, None, dummy, None) == 1
+    assert b"invalid matrix 1" in lib.idet_last_error()

@@ -1158,6 +1158,16 @@ int idet_crt_symmetric(const uint32_t *residues, const uint32_t *primes, int32_t
             set_last_error("primes must be odd primes below 2^31");
             return IDET_ERR_ARG;
         }
+    {
+        // Garner's method needs pairwise coprime moduli: a repeated prime
+        // has no inverse modulo the product of the others
+        std::vector<uint32_t> srt(primes, primes + count);
+        std::sort(srt.begin(), srt.end());
+        if (std::adjacent_find(srt.begin(), srt.end()) != srt.end()) {
+            set_last_error("primes must be pairwise distinct");
+            return IDET_ERR_ARG;
+        }
+    }
     if (count == 0) {
         if (trailing) *trailing = 0;
         return write_int(r, 0, nullptr, 0);

@@ -76,3 +76,21 @@ def test_orders_above_the_limit_are_rejected_before_any_device_work():
     ptrs = (ctypes.c_void_p * 2)(64, 64)
     assert lib.idet_int_det_batch(i32(2), ptrs, ns, ldas, i32(0), None, None, dummy, None) == 1
     assert b"invalid matrix 1" in lib.idet_last_error()
+
+
+def test_crt_rejects_repeated_primes_on_the_host():
+    """A repeated prime has no inverse modulo the product of the others, so
+    Garner's method would return a wrong value; the call refuses it before
+    any device work."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "_idet_build", os.path.join(ROOT, "paper_cs_0511066_b300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    lib = ctypes.CDLL(mod.build())
+    lib.idet_last_error.restype = ctypes.c_char_p
+    res = (ctypes.c_uint32 * 3)(1, 2, 3)
+    pr = (ctypes.c_uint32 * 3)(1048583, 1048589, 1048583)
+    out = ctypes.c_void_p(64)            # never dereferenced: the check fails first
+    assert lib.idet_crt_symmetric(res, pr, ctypes.c_int32(3), None, out, None) == 1
+    assert b"distinct" in lib.idet_last_error()

@@ -94,3 +94,30 @@ def test_crt_rejects_repeated_primes_on_the_host():
     out = ctypes.c_void_p(64)            # never dereferenced: the check fails first
     assert lib.idet_crt_symmetric(res, pr, ctypes.c_int32(3), None, out, None) == 1
     assert b"distinct" in lib.idet_last_error()
+
+
+def test_empty_inputs_return_before_any_device_work():
+    """The 0 x 0 matrix has determinant 1 (and largest invariant factor 1),
+    det mod p of it is 1 for every prime, and the empty Chinese remaindering
+    gives 0 with no agreements; these answers come from the argument checks,
+    before any CUDA call, so no GPU is needed."""
+    import paper_cs_0511066_b300 as idet
+    lib = idet._lib
+
+    def big(fn):
+        buf = (ctypes.c_uint32 * 4)(7, 7, 7, 7)
+        out = idet.idet_int(5, 9, 4, buf)
+        rc = fn(ctypes.byref(out))
+        assert rc == 0, idet._lib.idet_last_error()
+        return idet._to_int(out, buf)
+
+    assert big(lambda o: lib.idet_int_det(None, 0, 0, 0, None, None, o, None)) == 1
+    assert big(lambda o: lib.idet_largest_invariant_factor(None, 0, 0, None, 0, None, None, o)) == 1
+    assert big(lambda o: lib.idet_int_det_mp(None, None, 0, 1, 0, None, None, o, None)) == 1
+    trailing = ctypes.c_int32(-1)
+    assert big(lambda o: lib.idet_crt_symmetric(None, None, 0, None, o, ctypes.byref(trailing))) == 0
+    assert trailing.value == 0
+    primes = (ctypes.c_uint32 * 3)(1048583, 1048589, 1048601)
+    out = (ctypes.c_uint32 * 3)(0, 0, 0)
+    assert lib.idet_det_mod_primes(None, 0, 0, 0, primes, 3, None, None, out) == 0
+    assert list(out) == [1, 1, 1]

@@ -351,6 +351,47 @@ def run_ablation(args):
     print(json.dumps(line))
 
 
+FIG1_N = [400, 1000, 2000, 4000]
+
+
+def run_fig1(args):
+    """Fig. 1's workload shape on this GPU: random dense matrices with entries
+    in {-8, .., 8}, default control. Per order: the fastest of `steps` calls
+    after `warmup`, input resident on the device. Where the CRA-only path is
+    affordable (n <= 2000) its result, which involves no lift, must agree."""
+    import torch
+    import paper_cs_0511066_b300 as idet
+    ms_by_n, stats = [], {}
+    launches0 = idet.launch_count()
+    clk = Clocks(os.path.join(ROOT, "gpurun_out", "clocks_fig1.csv")
+                 if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_fig1.csv")
+    with clk:
+        for n in FIG1_N:
+            A = torch.from_numpy(workloads.dense_uniform(n, -8, 8, seed=n)).cuda()
+            for _ in range(args.warmup):
+                idet.int_det(A)
+            best = None
+            for _ in range(args.steps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                d, st = idet.int_det(A, return_stats=True)
+                torch.cuda.synchronize()
+                el = (time.perf_counter() - t0) * 1e3
+                best = el if best is None else min(best, el)
+            if n <= 2000:
+                assert idet.int_det(A, lif=False) == d, f"CRA-only and default differ at n={n}"
+            ms_by_n.append(round(best, 3))
+            stats[f"n{n}"] = {"primes": st["primes_in_cra"], "lift_iters": st["lift_iters"],
+                              "log2_K": st["log2_K"], "log2_det": abs(d).bit_length()}
+    launches = idet.launch_count() - launches0
+    line = _line("ms per determinant, dense entries in [-8,8] (n=4000)", ms_by_n[-1], "ms",
+                 args, ms_by_n[-1], {"workload": "fig1_dense_pm8_n400-4000",
+                                     "timing": "host wall clock around each blocking call, best of steps"},
+                 higher_is_better=False, gpu_launches=int(launches), clocks=clk.summary(),
+                 fig1={"n": FIG1_N, "ms": ms_by_n}, stats=stats)
+    print(json.dumps(line))
+
+
 TABLE1_N = [100, 120, 140, 160, 180, 200, 250, 300, 350, 400, 600, 800, 1000, 2000]
 
 
@@ -469,12 +510,13 @@ def main():
                          "same with the tcgen05 update); runs once and prints timings")
     ap.add_argument("--workload", default="plain",
                     choices=["plain", "batch", "serve", "lift_heavy", "small", "ablation",
-                             "table1"],
+                             "table1", "fig1"],
                     help="plain (default): n=1000 [0,255] + n=4000 +-2^20; batch: 512 "
                          "matrices n in [32,512]; serve: Poisson-served jobs n in [64,4096]; "
                          "lift_heavy: n=2000 U diag(1,..,d) V, 600-bit d; small: n=100; "
                          "ablation: Fig. 2, CRA vs LIF vs adaptive, n=40..1000 [-100,100]; "
-                         "table1: Table 1, engineered Smith form diag(1..n), n=100..2000")
+                         "table1: Table 1, engineered Smith form diag(1..n), n=100..2000; "
+                         "fig1: Fig. 1 shape, dense [-8,8], n=400..4000")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -483,7 +525,7 @@ def main():
     if args.workload != "plain":
         return {"batch": run_batch, "serve": run_serve, "lift_heavy": run_lift_heavy,
                 "small": run_small, "ablation": run_ablation,
-                "table1": run_table1}[args.workload](args)
+                "table1": run_table1, "fig1": run_fig1}[args.workload](args)
 
     import torch
     import paper_cs_0511066_b300 as idet

@@ -127,6 +127,11 @@ uint64_t idet_launch_count(void);
  * factor K of s_n (Section 2.2), then Alg. 2.1 on det(A)/K reusing the
  * residues already computed (Section 4). opts may be NULL (defaults), stats
  * may be NULL. det receives the exact determinant.
+ * Order limit of the solve: the lifting kernel stages the vector and at
+ * least one row of A^{-1} mod p in shared memory (12 n bytes), so with
+ * lif = 1 or 2 n is at most about 19,000 on a GPU with 227 KB of shared
+ * memory per block; larger n return IDET_ERR_ARG ("lift: a row does not fit
+ * in shared memory"). lif = 0 (Alg. 2.1 alone) has no such limit.
  */
 int idet_int_det(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
                  const idet_opts *opts, void *stream, idet_int *det,

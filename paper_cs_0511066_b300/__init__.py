@@ -169,10 +169,22 @@ def _matrix(A):
         if A.stride(1) != 1:
             A = A.contiguous()
         return A.data_ptr(), A.shape[0], A.stride(0), 1 if A.is_cuda else 0, A
-    a = np.ascontiguousarray(np.asarray(A, dtype=np.int64))
+    a = np.ascontiguousarray(_as_int64(A))
     if a.ndim != 2 or a.shape[0] != a.shape[1]:
         raise ValueError("square matrix expected")
     return a.ctypes.data, a.shape[0], a.shape[1], 0, a
+
+
+def _as_int64(x):
+    """int64 array of x; float input must hold integers exactly (a silent
+    truncation would change the matrix), other non-integer kinds are refused."""
+    arr = np.asarray(x)
+    if arr.dtype.kind == "f":
+        if not (np.all(np.isfinite(arr)) and np.all(arr == np.trunc(arr))):
+            raise ValueError("integer entries expected (got non-integral floats)")
+    elif arr.dtype.kind not in "iub" and arr.dtype != object:
+        raise ValueError(f"integer entries expected (got dtype {arr.dtype})")
+    return np.asarray(arr, dtype=np.int64)
 
 
 def _vector(b, on_device):
@@ -182,7 +194,7 @@ def _vector(b, on_device):
         if on_device and not b.is_cuda:
             b = b.cuda()
         return b.contiguous().data_ptr(), b
-    v = np.ascontiguousarray(np.asarray(b, dtype=np.int64))
+    v = np.ascontiguousarray(_as_int64(b))
     if on_device:
         t = torch.from_numpy(v).cuda()
         return t.data_ptr(), t
@@ -430,7 +442,7 @@ class Server:
         self._cap = {}
 
     def submit(self, A) -> int:
-        a = np.ascontiguousarray(np.asarray(A, dtype=np.int64))
+        a = np.ascontiguousarray(_as_int64(A))
         if a.ndim != 2 or a.shape[0] != a.shape[1]:
             raise ValueError("square matrix expected")
         t = ctypes.c_uint64(0)

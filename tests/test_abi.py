@@ -121,3 +121,22 @@ def test_empty_inputs_return_before_any_device_work():
     out = (ctypes.c_uint32 * 3)(0, 0, 0)
     assert lib.idet_det_mod_primes(None, 0, 0, 0, primes, 3, None, None, out) == 0
     assert list(out) == [1, 1, 1]
+
+
+def test_binding_refuses_matrices_it_would_have_to_change():
+    """Float input is accepted only when every entry is an integer: a silent
+    truncation would change the matrix and so the determinant. The checks run
+    in the binding, before any device work."""
+    import numpy as np
+    import pytest
+    import paper_cs_0511066_b300 as idet
+    with pytest.raises(ValueError):
+        idet.int_det(np.array([[1.5, 0.0], [0.0, 1.0]]))
+    with pytest.raises(ValueError):
+        idet.int_det(np.array([[np.inf, 0.0], [0.0, 1.0]]))
+    with pytest.raises(ValueError):
+        idet.int_det(np.array([["a", "b"], ["c", "d"]]))
+    with pytest.raises(ValueError):
+        idet.int_det(np.zeros((2, 3), dtype=np.int64))
+    assert idet._as_int64(np.array([[2.0, -3.0]])).tolist() == [[2, -3]]
+    assert idet._as_int64([[1, 2], [3, 4]]).dtype == np.int64

@@ -301,7 +301,9 @@ int idet_submit(idet_server *srv, const int64_t *A, int64_t n, int64_t lda, uint
 /* Waits up to timeout_ms (< 0: no limit) for the job. IDET_OK: det written,
  * ticket released. IDET_ERR_TIMEOUT: not finished yet. IDET_ERR_BUFFER:
  * det->nlimbs set to the size needed, job kept. A job error is returned as
- * its code (ticket released). info may be NULL. */
+ * its code (ticket released). info may be NULL. Several threads may poll
+ * the same ticket: one collects the result, the others then get
+ * IDET_ERR_ARG (ticket already collected). */
 int idet_poll(idet_server *srv, uint64_t ticket, int32_t timeout_ms, idet_int *det,
               idet_job_info *info);
 void idet_server_info(idet_server *srv, idet_server_stats *out);

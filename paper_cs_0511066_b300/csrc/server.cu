@@ -329,14 +329,25 @@ int idet_poll(idet_server *S, uint64_t ticket, int32_t timeout_ms, idet_int *det
         set_last_error("poll: unknown ticket %llu", (unsigned long long)ticket);
         return IDET_ERR_ARG;
     }
-    SJob *j = it->second;
-    auto ready = [&] { return j->status != -1; };
+    // The job is looked up again after every wake-up: another thread polling
+    // the same ticket may have collected (and freed) it meanwhile.
+    auto ready = [&] {
+        auto f = S->jobs.find(ticket);
+        return f == S->jobs.end() || f->second->status != -1;
+    };
     if (timeout_ms < 0) {
         S->cv_done.wait(lk, ready);
     } else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) {
         set_last_error("poll: job %llu not finished", (unsigned long long)ticket);
         return IDET_ERR_TIMEOUT;
     }
+    it = S->jobs.find(ticket);
+    if (it == S->jobs.end()) {
+        set_last_error("poll: ticket %llu was collected by another call",
+                       (unsigned long long)ticket);
+        return IDET_ERR_ARG;
+    }
+    SJob *j = it->second;
     if (info) {
         info->status = j->status;
         info->batched = j->batched;
@@ -353,6 +364,7 @@ int idet_poll(idet_server *S, uint64_t ticket, int32_t timeout_ms, idet_int *det
         set_last_error("job %llu failed: %s", (unsigned long long)ticket, j->err.c_str());
         S->jobs.erase(it);
         delete j;
+        S->cv_done.notify_all();  // other pollers of this ticket see it is gone
         return rc;
     }
     const uint32_t nl = (uint32_t)j->limbs.size();
@@ -366,6 +378,7 @@ int idet_poll(idet_server *S, uint64_t ticket, int32_t timeout_ms, idet_int *det
     if (nl) memcpy(det->limbs, j->limbs.data(), 4 * (size_t)nl);
     S->jobs.erase(it);
     delete j;
+    S->cv_done.notify_all();  // other pollers of this ticket see it is gone
     return IDET_OK;
 }
 

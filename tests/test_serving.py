@@ -72,3 +72,30 @@ def test_server_timeout_and_oversized_job():
     with idet.Server(hbm_budget=1 << 26, slots=1) as srv:
         with pytest.raises(idet.IdetError):
             srv.submit(np.ones((2000, 2000), dtype=np.int64))
+
+
+def test_server_same_ticket_polled_from_two_threads():
+    """Two threads wait on one ticket: one collects the determinant, the
+    other returns an error instead of reading a collected job."""
+    import threading
+    A = workloads.dense_pm100(300, seed=4)
+    want = idet.int_det(A)
+    out = []
+    with idet.Server(slots=1) as srv:
+        t = srv.submit(A)
+
+        def waiter():
+            try:
+                out.append(("ok", srv.poll(t)[0]))
+            except idet.IdetError as e:
+                out.append(("err", e.code))
+
+        th = [threading.Thread(target=waiter) for _ in range(2)]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join(timeout=60)
+        assert not any(x.is_alive() for x in th)
+    assert sorted(o[0] for o in out) == ["err", "ok"]
+    assert [o[1] for o in out if o[0] == "ok"] == [want]
+    assert [o[1] for o in out if o[0] == "err"] == [1]

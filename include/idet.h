@@ -293,7 +293,11 @@ typedef struct {
     uint64_t bytes_in_use, budget, admitted, completed, groups;
 } idet_server_stats;
 
-/* NULL on error (idet_last_error). opts may be NULL. */
+/* NULL on error (idet_last_error). opts may be NULL. hbm_budget = 0: 80 %
+ * of the device memory free at creation. The workers allocate from the
+ * device's default stream-ordered memory pool, whose release threshold is
+ * raised so that freed workspace is kept for the next job (a per-process
+ * setting of that pool). */
 idet_server *idet_server_create(size_t hbm_budget, int32_t slots, int32_t small_n,
                                 int32_t max_batch, const idet_opts *opts);
 /* IDET_ERR_NOMEM if the job alone exceeds the budget. */
@@ -307,7 +311,9 @@ int idet_submit(idet_server *srv, const int64_t *A, int64_t n, int64_t lda, uint
 int idet_poll(idet_server *srv, uint64_t ticket, int32_t timeout_ms, idet_int *det,
               idet_job_info *info);
 void idet_server_info(idet_server *srv, idet_server_stats *out);
-/* Finishes the submitted jobs, then stops the workers. */
+/* Finishes the submitted jobs, then stops the workers and frees the server
+ * with any results not collected. No other call on srv may be in progress
+ * (a thread blocked in idet_poll included) or follow. */
 void idet_server_destroy(idet_server *srv);
 
 /* ------------------------------------------------------------------------

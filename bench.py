@@ -64,6 +64,18 @@ def batch(seed_base=0):
     return [workloads.dense_u8(1000, seed=seed_base), workloads.dense_pm2p20(4000, seed=seed_base)]
 
 
+CLOCK_DIR = None
+
+
+def clock_path(name):
+    """Where the nvidia-smi clock samples of a run are written (--clock-dir,
+    default the system temporary directory)."""
+    import tempfile
+    d = CLOCK_DIR or tempfile.gettempdir()
+    os.makedirs(d, exist_ok=True)
+    return os.path.join(d, name)
+
+
 class Clocks:
     def __init__(self, path):
         self.path = path
@@ -178,6 +190,58 @@ def run_case(case):
     print(json.dumps({"case": case, "seconds": time.perf_counter() - t0}))
 
 
+def run_peaks(args):
+    """Dense tensor throughput of this GPU per operand type, measured with the
+    vendor libraries as ceilings for the trailing updates: int8 x int8 -> int32
+    (torch._int_mm), fp64 (torch.matmul) and bf16 (torch.matmul), M = N = K.
+    Per type: the best of several calls (burst) and the mean over a loop of
+    about four seconds (sustained), CUDA events on the current stream; clocks
+    sampled during the whole run."""
+    import torch
+    res = {}
+    with Clocks(clock_path("clocks_peaks.csv")) as clk:
+        for name, dt, n, reps in (("int8", torch.int8, 8192, 10), ("bf16", torch.bfloat16, 8192, 10),
+                                  ("fp64", torch.float64, 8192, 3)):
+            if dt == torch.int8:
+                a = torch.randint(-64, 64, (n, n), dtype=dt, device="cuda")
+                b = torch.randint(-64, 64, (n, n), dtype=dt, device="cuda")
+                fn = lambda: torch._int_mm(a, b)
+            else:
+                a = torch.randn(n, n, dtype=dt, device="cuda")
+                b = torch.randn(n, n, dtype=dt, device="cuda")
+                fn = lambda: torch.matmul(a, b)
+            for _ in range(2):
+                fn()
+            torch.cuda.synchronize()
+            best = None
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                torch.cuda.synchronize()
+                t = e0.elapsed_time(e1)
+                best = t if best is None else min(best, t)
+            calls = max(1, int(4000.0 / best))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(calls):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            sus = e0.elapsed_time(e1) / calls
+            ops = 2.0 * n * n * n
+            res[name] = {"n": n, "burst_tops": round(ops / best / 1e9, 1),
+                         "sustained_tops": round(ops / sus / 1e9, 1),
+                         "best_ms": round(best, 3), "sustained_ms": round(sus, 3), "calls": calls}
+            del a, b
+            torch.cuda.empty_cache()
+    print(json.dumps({"case": "peaks", "unit": "T op/s (2 M N K per call)", "peaks": res,
+                      "clocks": clk.summary(), "gpu": torch.cuda.get_device_name()}))
+
+
 def _line(metric, value, unit, args, ms, config, **extra):
     d = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
          "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -199,8 +263,7 @@ def _timed_steps(torch, args, fn, clk_name):
     torch.cuda.synchronize()
     out, times = [], []
     launches0 = idet.launch_count()
-    clk = Clocks(os.path.join(ROOT, "gpurun_out", clk_name)
-                 if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/" + clk_name)
+    clk = Clocks(clock_path(clk_name))
     with clk:
         for _ in range(args.steps):
             flush.fill_(1)
@@ -315,8 +378,7 @@ def run_ablation(args):
     res = {k: [] for k in arms}
     stats = {}
     launches0 = idet.launch_count()
-    clk = Clocks(os.path.join(ROOT, "gpurun_out", "clocks_ablation.csv")
-                 if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_ablation.csv")
+    clk = Clocks(clock_path("clocks_ablation.csv"))
     with clk:
         for n in ABLATION_N:
             A = torch.from_numpy(workloads.dense_pm100(n, seed=n)).cuda()
@@ -363,8 +425,7 @@ def run_fig1(args):
     import paper_cs_0511066_b300 as idet
     ms_by_n, stats = [], {}
     launches0 = idet.launch_count()
-    clk = Clocks(os.path.join(ROOT, "gpurun_out", "clocks_fig1.csv")
-                 if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_fig1.csv")
+    clk = Clocks(clock_path("clocks_fig1.csv"))
     with clk:
         for n in FIG1_N:
             A = torch.from_numpy(workloads.dense_uniform(n, -8, 8, seed=n)).cuda()
@@ -406,8 +467,7 @@ def run_table1(args):
     import paper_cs_0511066_b300 as idet
     ms_by_n, stats = [], {}
     launches0 = idet.launch_count()
-    clk = Clocks(os.path.join(ROOT, "gpurun_out", "clocks_table1.csv")
-                 if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_table1.csv")
+    clk = Clocks(clock_path("clocks_table1.csv"))
     with clk:
         for n in TABLE1_N:
             A = torch.from_numpy(workloads.engineered_smith(n, seed=n)).cuda()
@@ -504,10 +564,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clock-dir", default=None,
+                    help="directory for the nvidia-smi clock samples (default: temp dir)")
     ap.add_argument("--case", default=None,
                     help="profiling case: 'lift' (Dixon lifting, n=4000, 64 digits), "
-                         "'lu' (det mod 4 primes, n=4000, int64 update) or 'lu_tc05' (the "
-                         "same with the tcgen05 update); runs once and prints timings")
+                         "'lu' (det mod 4 primes, n=4000, int64 update), 'lu_tc05' (the "
+                         "same with the tcgen05 update): runs once and prints timings; "
+                         "'peaks': int8/bf16/fp64 GEMM throughput of the vendor libraries")
     ap.add_argument("--workload", default="plain",
                     choices=["plain", "batch", "serve", "lift_heavy", "small", "ablation",
                              "table1", "fig1"],
@@ -518,8 +581,12 @@ def main():
                          "table1: Table 1, engineered Smith form diag(1..n), n=100..2000; "
                          "fig1: Fig. 1 shape, dense [-8,8], n=400..4000")
     args = ap.parse_args()
+    global CLOCK_DIR
+    CLOCK_DIR = args.clock_dir
     if args.impl == "reference":
         return run_reference(args)
+    if args.case == "peaks":
+        return run_peaks(args)
     if args.case:
         return run_case(args.case)
     if args.workload != "plain":
@@ -563,8 +630,7 @@ def main():
     times = []
     stats = []
     launches0 = idet.launch_count()
-    clk = Clocks(os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
-                 if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_bench.csv")
+    clk = Clocks(clock_path("clocks_bench.csv"))
     with clk:
         for _ in range(args.steps):
             flush.fill_(1)

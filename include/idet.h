@@ -8,7 +8,8 @@
  *
  * Conventions shared by every entry point:
  *   - Matrices are dense, row-major, n x n, with leading dimension lda >= n
- *     (in elements). Entries are int64 values with |a_ij| <= 2^31 - 1.
+ *     (in elements). Entries are int64 values in the int32 range
+ *     -2^31 <= a_ij <= 2^31 - 1.
  *     Orders above IDET_MAX_ORDER (65536) are rejected with IDET_ERR_ARG
  *     before any device work (their sizes would overflow the byte counts).
  *   - on_device = 0: pointers are host memory; the library copies them.
@@ -24,6 +25,9 @@
  *   - Results are exact integers. int_det is correct with probability at
  *     least 1 - 2^log2_epsilon (Alg. 2.1 ensures 1 - epsilon), or always when
  *     certify = 1 (reconstruction past twice the Hadamard bound, Lemma 2.1(i)).
+ *     A reconstruction stopped by the bound runs 40 bits past 2H and checks
+ *     |r| <= H; a violation means a modular determinant was wrong and the
+ *     call returns IDET_ERR_INTERNAL instead of a value.
  */
 #ifndef IDET_H
 #define IDET_H
@@ -80,7 +84,11 @@ typedef struct {
     int32_t prime_bits;    /* CRA prime class: 21 (primes in (2^20, 2^21)) or
                               31 (primes in (2^30, 2^31)); 0 = default: 21
                               for idet_int_det, 31 for idet_int_det_mp      */
-    int32_t reserved[6];
+    int32_t inject_fault;  /* failure-detection tests only (0 = off): k > 0
+                              adds 1 to det(A) mod p for the k-th CRA prime
+                              factored (idet_int_det, idet_int_det_mp), a
+                              wrong modular determinant made on the host    */
+    int32_t reserved[5];
 } idet_opts;
 
 typedef struct {
@@ -98,10 +106,13 @@ typedef struct {
     uint64_t launches;         /* kernels launched by the call              */
     double ms_lift_kernel;     /* device time of the lifting kernel alone   */
     double lift_bytes;         /* its algorithmic bytes: m * 8 n^2          */
-    double lu_macs;            /* (2/3) n^3 per factored prime (+ inverse)  */
+    double lu_macs;            /* (2/3) n^3 per factored CRA prime: the
+                                  modular MACs of the work timed by ms_lu   */
     double ms_inverse;         /* LU + inverse mod the lifting prime        */
     double ms_rr;              /* rational reconstruction (idet_int_det_batch:
                                   included in ms_lift_kernel)                */
+    double inverse_macs;       /* 2 n^3 per lifting prime: LU and inverse,
+                                  the work timed by ms_inverse              */
 } idet_stats;
 
 /* Fill *opts with the defaults. */
@@ -215,6 +226,26 @@ int idet_crt_symmetric(const uint32_t *residues, const uint32_t *primes,
                        int32_t *trailing);
 
 /*
+ * Alg. 2.1's loop (Section 2.1) run over a given stream of modular
+ * determinants: residues[k] = det mod primes[k] for k = 0 .. count-1 in the
+ * order the primes were drawn (odd, distinct, < 2^31; host arrays). The
+ * mixed-radix digits of r_0, r_1, ... are formed on the device; the loop
+ * stops at the first k where the on-the-fly bound of Lemma 2.1(iii), with
+ * |P| = pool_size and l = 2^log2_l, falls below epsilon = 2^log2_epsilon
+ * (not with certify = 1), or where prod p reaches 2H 2^40 with
+ * H = 2^log2_H. *stop_index receives k (-1: no stop within the stream) and
+ * *reason 1 (early termination), 2 (bound) or 3 (bound reached, but
+ * |r| > H: a residue is wrong), 0 if no stop. r receives the value
+ * reconstructed from the residues up to the stop (all of them if none), in
+ * the symmetric range. This is the rule idet_int_det applies to its own
+ * residues.
+ */
+int idet_cra_early_termination(const uint32_t *residues, const uint32_t *primes, int32_t count,
+                               double log2_H, double log2_epsilon, double log2_l,
+                               double pool_size, int32_t certify, void *stream, idet_int *r,
+                               int32_t *stop_index, int32_t *reason);
+
+/*
  * det(A_i) for a batch of independent matrices of possibly different orders:
  * the same method as idet_int_det (Alg. 4.1 with i_max = 1), with the
  * batch's work fused across matrices -- the LUs of all (matrix, prime) pairs
@@ -240,8 +271,10 @@ int idet_int_det_batch(int32_t count, const int64_t *const *A, const int64_t *n,
  * same arguments.
  *
  * Limits: 1 <= n <= 128, 1 <= nprimes <= 32, |a_ij| < 2^62; primes as for
- * idet_det_mod_primes (each a prime in (2^20, 2^21) or (2^30, 2^31)); sizes
- * beyond the limits return IDET_ERR_ARG with a message. A (n x n, leading
+ * idet_det_mod_primes (all in (2^20, 2^21) or all in (2^30, 2^31)); sizes,
+ * entries or primes beyond the limits return IDET_ERR_ARG with a message
+ * (for device input the entries are checked on the device, and det_mod is
+ * then left unwritten). A (n x n, leading
  * dimension lda) is host memory when on_device = 0, device memory when 1;
  * primes and det_mod are host arrays of nprimes entries.
  *
@@ -261,7 +294,7 @@ int idet_det_mod_primes_noalloc(const int64_t *A, int64_t n, int64_t lda,
 /* ------------------------------------------------------------------------
  * Serving with continuous batching. A server owns `slots` worker threads,
  * each with its own CUDA stream on the current device. idet_submit copies
- * the matrix (host memory, |a_ij| <= 2^31 - 1) and queues the job; workers
+ * the matrix (host memory, entries in [-2^31, 2^31 - 1]) and queues the job; workers
  * admit queued jobs first-in first-out whenever a slot and device memory are
  * free: each job is charged an estimate of its device footprint against
  * hbm_budget (0 = 80% of the free memory at creation); a job that does not

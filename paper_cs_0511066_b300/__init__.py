@@ -47,7 +47,7 @@ class idet_opts(ctypes.Structure):
                 ("certify", ctypes.c_int32), ("update_path", ctypes.c_int32),
                 ("nb", ctypes.c_int32), ("wave", ctypes.c_int32),
                 ("lif", ctypes.c_int32), ("prime_bits", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("inject_fault", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class idet_stats(ctypes.Structure):
@@ -59,7 +59,7 @@ class idet_stats(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("launches", ctypes.c_uint64),
                 ("ms_lift_kernel", ctypes.c_double), ("lift_bytes", ctypes.c_double),
                 ("lu_macs", ctypes.c_double), ("ms_inverse", ctypes.c_double),
-                ("ms_rr", ctypes.c_double)]
+                ("ms_rr", ctypes.c_double), ("inverse_macs", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -176,13 +176,27 @@ def _matrix(A):
 
 
 def _as_int64(x):
-    """int64 array of x; float input must hold integers exactly (a silent
-    truncation would change the matrix), other non-integer kinds are refused."""
+    """int64 array of x, refusing input that the conversion would change: float
+    input must hold integers exactly (a silent truncation would change the
+    matrix), and float, unsigned or arbitrary-precision values must lie in
+    [-2^63, 2^63) (numpy would wrap them); other kinds are refused."""
     arr = np.asarray(x)
     if arr.dtype.kind == "f":
         if not (np.all(np.isfinite(arr)) and np.all(arr == np.trunc(arr))):
             raise ValueError("integer entries expected (got non-integral floats)")
-    elif arr.dtype.kind not in "iub" and arr.dtype != object:
+        # 2^63 is exact in every float type; values at or above it, or below
+        # -2^63, do not fit int64
+        if arr.size and (np.any(arr >= 2.0 ** 63) or np.any(arr < -(2.0 ** 63))):
+            raise ValueError("entries out of the int64 range")
+    elif arr.dtype.kind == "u":
+        if arr.size and arr.max() > np.iinfo(np.int64).max:
+            raise ValueError("entries out of the int64 range")
+    elif arr.dtype == object:
+        flat = arr.ravel()
+        if any(not isinstance(v, (int, np.integer)) or not (-(1 << 63) <= int(v) < (1 << 63))
+               for v in flat):
+            raise ValueError("integer entries in the int64 range expected")
+    elif arr.dtype.kind not in "ib":
         raise ValueError(f"integer entries expected (got dtype {arr.dtype})")
     return np.asarray(arr, dtype=np.int64)
 
@@ -223,12 +237,15 @@ def _call_int(fn, *args, cap: int = 1 << 12):
 def int_det(A, *, certify: bool = False, seed: int | None = None, lif: bool | int = True,
             update_path: int | None = None, nb: int | None = None, wave: int | None = None,
             log2_epsilon: float | None = None, prime_bits: int | None = None, stream=None,
-            return_stats: bool = False):
-    """det(A) as a Python int (idet_int_det)."""
+            inject_fault: int | None = None, return_stats: bool = False):
+    """det(A) as a Python int (idet_int_det). inject_fault (tests of failure
+    detection only): 1-based index of a CRA prime whose modular determinant
+    is made wrong on the host."""
     use_torch_allocator()
     ptr, n, lda, dev, keep = _matrix(A)
     o = default_opts(certify=int(certify), seed=seed, lif=int(lif), update_path=update_path,
-                     nb=nb, wave=wave, log2_epsilon=log2_epsilon, prime_bits=prime_bits)
+                     nb=nb, wave=wave, log2_epsilon=log2_epsilon, prime_bits=prime_bits,
+                     inject_fault=inject_fault)
     st = idet_stats()
     cap = max(64, int(n * 40 // 32) + 64)
     while True:
@@ -268,13 +285,14 @@ def det_mod_primes(A, primes, *, update_path: int | None = None, nb: int | None 
     return out
 
 
-def lu_mod_prime(A, p: int, *, nb: int | None = None, stream=None):
+def lu_mod_prime(A, p: int, *, nb: int | None = None, update_path: int | None = None,
+                 stream=None):
     """(LU residues in [0,p), perm, singular flag)."""
     use_torch_allocator()
     ptr, n, lda, dev, keep = _matrix(A)
     lu = np.zeros((n, n), dtype=np.uint32)
     perm = np.zeros(n, dtype=np.int32)
-    o = default_opts(nb=nb)
+    o = default_opts(nb=nb, update_path=update_path)
     rc = _lib.idet_lu_mod_prime(ptr, n, lda, dev, p, ctypes.byref(o), _stream_ptr(stream),
                                 lu.ctypes.data, perm.ctypes.data)
     if rc == IDET_ERR_SINGULAR:
@@ -305,6 +323,28 @@ def crt_symmetric(residues, primes, *, stream=None):
                                                      _stream_ptr(stream), a[0], ctypes.byref(tr)),
                   cap=len(pr) + 8)
     return v, int(tr.value)
+
+
+_lib.idet_cra_early_termination.argtypes = [_P, _P, _i32, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_double, _i32, _P,
+                                            ctypes.POINTER(idet_int),
+                                            ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_int32)]
+
+
+def cra_early_termination(residues, primes, log2_H: float, log2_epsilon: float, log2_l: float,
+                          pool_size: int, *, certify: bool = False, stream=None):
+    """(r, stop index or -1, reason) of Alg. 2.1's loop over the given stream
+    (idet_cra_early_termination)."""
+    use_torch_allocator()
+    res = np.ascontiguousarray(np.asarray(residues, dtype=np.uint32))
+    pr = np.ascontiguousarray(np.asarray(primes, dtype=np.uint32))
+    stop, why = ctypes.c_int32(0), ctypes.c_int32(0)
+    v = _call_int(lambda *a: _lib.idet_cra_early_termination(
+        res.ctypes.data, pr.ctypes.data, len(pr), float(log2_H), float(log2_epsilon),
+        float(log2_l), float(pool_size), int(certify), _stream_ptr(stream), a[0],
+        ctypes.byref(stop), ctypes.byref(why)), cap=len(pr) + 8)
+    return v, int(stop.value), int(why.value)
 
 
 _lib.idet_int_det_batch.argtypes = [_i32, _P, _P, _P, _i32, ctypes.POINTER(idet_opts), _P, _P,
@@ -358,7 +398,7 @@ def launch_count() -> int:
 
 
 __all__ = ["int_det", "largest_invariant_factor", "det_mod_primes", "lu_mod_prime",
-           "dixon_digits", "crt_symmetric", "launch_count", "default_opts", "IdetError",
+           "dixon_digits", "crt_symmetric", "cra_early_termination", "launch_count", "default_opts", "IdetError",
            "use_torch_allocator", "LIB_PATH"]
 
 
@@ -367,7 +407,8 @@ _lib.idet_int_det_mp.argtypes = [_P, _P, _i64, _i32, _i32, ctypes.POINTER(idet_o
 
 
 def int_det_mp(mag, sgn, *, certify: bool = False, seed: int | None = None, lif: bool = True,
-               prime_bits: int | None = None, stream=None, return_stats: bool = False):
+               prime_bits: int | None = None, stream=None, inject_fault: int | None = None,
+               return_stats: bool = False):
     """det(A) for multi-word entries (idet_int_det_mp): mag is uint32
     [n][n][L] (little-endian base-2^32 magnitudes), sgn int8 [n][n] in
     {-1, 0, 1}; numpy arrays or CUDA tensors (both on the same side)."""
@@ -388,7 +429,8 @@ def int_det_mp(mag, sgn, *, certify: bool = False, seed: int | None = None, lif:
         mp, sp, keep = m.ctypes.data, g.ctypes.data, (m, g)
     if mag.shape[:2] != (n, n) or tuple(sgn.shape) != (n, n):
         raise ValueError("mag must be [n][n][L] and sgn [n][n]")
-    o = default_opts(certify=int(certify), seed=seed, lif=int(lif), prime_bits=prime_bits)
+    o = default_opts(certify=int(certify), seed=seed, lif=int(lif), prime_bits=prime_bits,
+                     inject_fault=inject_fault)
     st = idet_stats()
     cap = max(64, int(n * (32 * L + 16) // 32) + 64)
     buf = (ctypes.c_uint32 * cap)()
@@ -438,7 +480,7 @@ class Server:
         self._srv = _lib.idet_server_create(int(hbm_budget), slots, small_n, max_batch,
                                             ctypes.byref(o))
         if not self._srv:
-            raise IdetError(_lib.idet_last_error().decode(errors="replace"))
+            raise IdetError(IDET_ERR_ARG, _lib.idet_last_error().decode(errors="replace"))
         self._cap = {}
 
     def submit(self, A) -> int:

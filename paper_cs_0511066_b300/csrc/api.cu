@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <set>
 #include <unordered_set>
 #include <vector>
 
@@ -32,18 +33,19 @@ void set_last_error(const char *fmt, ...) {
 }
 
 int allow_max_smem(const void *kernel) {
+    // the attribute belongs to the current device: remember (device, kernel)
     static std::mutex mu;
-    static std::unordered_set<const void *> done;
-    std::lock_guard<std::mutex> lk(mu);
-    if (done.count(kernel)) return IDET_OK;
+    static std::set<std::pair<int, const void *>> done;
     int dev = 0, optin = 0;
-    cudaFuncAttributes fa;
     IDET_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count({dev, kernel})) return IDET_OK;
+    cudaFuncAttributes fa;
     IDET_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     IDET_CUDA_TRY(cudaFuncGetAttributes(&fa, kernel));
     IDET_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        optin - (int)fa.sharedSizeBytes));
-    done.insert(kernel);
+    done.insert({dev, kernel});
     return IDET_OK;
 }
 
@@ -225,9 +227,17 @@ static int k_default(double eps_log2, double pool, double log2H, double log2l) {
     return std::max(1, (int)std::ceil(-eps_log2 / (std::log2(Pp) - std::log2(lH))));
 }
 
+// A stop at the bound (prod p >= 2H, Lemma 2.1(i)) is taken kCertBits bits
+// past it and then checked: the reconstructed r must satisfy |r| <= H, as
+// det does. A wrong modular determinant (a fault) makes every later mixed-
+// radix digit uniformly random, so |r| > H then, except with probability
+// about 2^-kCertBits; the stop is reported as inconsistent (why = 3).
+constexpr double kCertBits = 40.0;
+
 struct CraScan {
     // Alg. 2.1 over digits[0..count): returns the index t of the prime at
-    // which the loop stops (-1 if it does not) and why (1 ET, 2 bound).
+    // which the loop stops (-1 if it does not) and why (1 ET, 2 bound, 3 bound
+    // reached but the residues contradict |det| <= H).
     static int scan(const std::vector<int32_t> &dig, const std::vector<uint32_t> &pr,
                     double log2H, double eps_log2, double log2l, double pool, bool certify,
                     int *why) {
@@ -242,8 +252,16 @@ struct CraScan {
             else
                 k = 0;
             if (dig[t] != 0) top = (int)t;
-            if (log2M >= 1.0 + log2H) {
-                *why = 2;
+            // the sum of t + 1 rounded logarithms is below the true log2 M
+            // by less than 1e-12 (t + 1); the check below needs a lower bound
+            if (log2M - 1e-12 * (double)(t + 1) >= 1.0 + log2H + kCertBits) {
+                // |r| >= (|v_top| - 1/2) prod_{j<top} p_j with balanced digits
+                double lo = -INFINITY;
+                if (top == 0)
+                    lo = std::log2(std::fabs((double)dig[0]));
+                else if (top > 0)
+                    lo = lM[top - 1] + std::log2(std::fabs((double)dig[top]) - 0.5);
+                *why = lo > log2H + 1e-9 ? 3 : 2;
                 return (int)t;
             }
             if (certify || k == 0) continue;
@@ -274,6 +292,12 @@ struct CraScan {
         return -1;
     }
 };
+
+static int inconsistent_residues() {
+    set_last_error("Chinese remaindering: past the bound 2H the reconstruction exceeds H, so a "
+                   "modular determinant is wrong");
+    return IDET_ERR_INTERNAL;
+}
 
 // ---------------------------------------------------------------------------
 // Helpers
@@ -428,17 +452,22 @@ struct DetJob {
         IDET_CUDA_TRY(cudaMemcpyAsync(colsq.data(), d_colsq, sizeof(double) * n,
                                       cudaMemcpyDeviceToHost, s));
         IDET_CUDA_TRY(cudaStreamSynchronize(s));
-        if (amax > 0x7fffffffull) {
-            set_last_error("entries must satisfy |a_ij| <= 2^31 - 1");
+        unsigned long long am = 0;
+        if (!entry_range(amax, &am)) {
+            set_last_error("entries must lie in [-2^31, 2^31 - 1]");
             return IDET_ERR_ARG;
         }
+        amax = am;
         // Hadamard: |det A| <= prod of the row norms and <= prod of the
         // column norms (Lemma 2.1 uses H = (sqrt(n) ||A||)^n, which bounds
         // both); the smaller one is used.
         double hr = 0, hc = 0;
         for (double v : rowsq) hr += v > 0 ? 0.5 * std::log2(v) : -INFINITY;
         for (double v : colsq) hc += v > 0 ? 0.5 * std::log2(v) : -INFINITY;
+        // margin for the rounding of the logarithms and their sum (upper
+        // bound kept)
         log2H = std::min(hr, hc);
+        if (log2H > -INFINITY) log2H = log2H * (1 + 1e-12) + 1e-6 * (double)n;
         st.log2_H = log2H;
         return IDET_OK;
     }
@@ -475,6 +504,10 @@ struct DetJob {
                                       cudaMemcpyDeviceToHost, s));
         st.ms_lu += t.stop();
         for (int i = 0; i < W; ++i) {
+            // failure-detection hook: a wrong modular determinant, made on
+            // the host, for the prime with 1-based index o.inject_fault
+            if (o.inject_fault > 0 && (int)primes.size() + 1 == o.inject_fault)
+                res[i] = (res[i] + 1) % pw[i];
             primes.push_back(pw[i]);
             dets.push_back(res[i]);
         }
@@ -619,7 +652,7 @@ static int solve_and_denominator(DetJob &J, const int64_t *b_dev, const std::vec
     IDET_TRY(launch_lift(a, J.Anar, J.abytes, J.ldl, ws, &out.timed_out, &kms));
     J.st.ms_lift_kernel += kms;
     J.st.lift_bytes += (double)m * 8.0 * (double)n * (double)n;
-    J.st.lu_macs += 2.0 * (double)n * n * n;  // LU + inverse of the lift prime
+    J.st.inverse_macs += 2.0 * (double)n * n * n;  // LU + inverse of the lift prime
     uint32_t *den = nullptr;
     int32_t *info = nullptr;
     const int den_cap = hD + 2;
@@ -679,6 +712,7 @@ static int det_first(DetJob &J, int k0, int wave, bool cra_only, idet_int *det, 
         if (stop >= 0) {
             J.st.et_stop = why;
             J.st.primes_in_cra = stop + 1;
+            if (why == 3) return inconsistent_residues();
             Timer t2(J.s);
             const int rc = J.assemble(J.primes, dig, stop + 1, nullptr, 0, det);
             J.st.ms_cra += t2.stop();
@@ -758,6 +792,7 @@ static int det_over_K(DetJob &J, const uint32_t *Kbin, int Klen, double log2K, i
         if (stop >= 0) {
             J.st.et_stop = why;
             J.st.primes_in_cra = stop + 1;
+            if (why == 3) return inconsistent_residues();
             Timer t2(s);
             const int rc = J.assemble(prs, dig, stop + 1, Kbin, Klen, det);
             J.st.ms_cra += t2.stop();
@@ -812,7 +847,7 @@ static int mp_lift(DetJob &J, unsigned int abits, MpLift &out) {
     IDET_TRY(ws.alloc_n(&C, (size_t)n * n));
     IDET_TRY(lu_inverse(R, perm, n, mh, md, true, J.nb, C, ws));
     J.st.ms_inverse += tinv.stop();
-    J.st.lu_macs += 2.0 * (double)n * n * n;
+    J.st.inverse_macs += 2.0 * (double)n * n * n;
     // A as signed base-2^15 digit planes
     const int T = (int)((abits + 1 + 14) / 15) + 1;
     const int64_t ldp = (n + 7) / 8 * 8;
@@ -1033,8 +1068,8 @@ int idet_det_mod_primes(const int64_t *A, int64_t n, int64_t lda, int32_t on_dev
     IDET_TRY(launch_row_stats(M.A, n, n, rowsq, amax, s));
     IDET_CUDA_TRY(cudaMemcpyAsync(&hmax, amax, 8, cudaMemcpyDeviceToHost, s));
     IDET_CUDA_TRY(cudaStreamSynchronize(s));
-    if (hmax > 0x7fffffffull) {
-        set_last_error("entries must satisfy |a_ij| <= 2^31 - 1");
+    if (!entry_range(hmax, &hmax)) {
+        set_last_error("entries must lie in [-2^31, 2^31 - 1]");
         return IDET_ERR_ARG;
     }
     const int W = nprimes;
@@ -1115,8 +1150,8 @@ int idet_dixon_digits(const int64_t *A, int64_t n, int64_t lda, const int64_t *b
     IDET_TRY(launch_row_stats(M.A, n, n, rowsq, d_amax, s));
     IDET_CUDA_TRY(cudaMemcpyAsync(&hmax, d_amax, 8, cudaMemcpyDeviceToHost, s));
     IDET_CUDA_TRY(cudaStreamSynchronize(s));
-    if (hmax > 0x7fffffffull) {
-        set_last_error("entries must satisfy |a_ij| <= 2^31 - 1");
+    if (!entry_range(hmax, &hmax)) {
+        set_last_error("entries must lie in [-2^31, 2^31 - 1]");
         return IDET_ERR_ARG;
     }
     void *Anar = nullptr;
@@ -1188,6 +1223,49 @@ int idet_crt_symmetric(const uint32_t *residues, const uint32_t *primes, int32_t
         *trailing = k;
     }
     return J.assemble(prs, dig, count, nullptr, 0, r);
+}
+
+int idet_cra_early_termination(const uint32_t *residues, const uint32_t *primes, int32_t count,
+                               double log2_H, double log2_epsilon, double log2_l,
+                               double pool_size, int32_t certify, void *stream, idet_int *r,
+                               int32_t *stop_index, int32_t *reason) {
+    if (count < 0 || (count > 0 && (!residues || !primes)) || !r || !stop_index || !reason ||
+        !(log2_l > 0) || !(pool_size >= 1) || std::isnan(log2_H) || !(log2_epsilon < 0)) {
+        set_last_error("invalid argument");
+        return IDET_ERR_ARG;
+    }
+    for (int i = 0; i < count; ++i)
+        if (!(primes[i] > 2 && primes[i] < (1u << 31) && is_prime32(primes[i]))) {
+            set_last_error("primes must be odd primes below 2^31");
+            return IDET_ERR_ARG;
+        }
+    {
+        std::vector<uint32_t> srt(primes, primes + count);
+        std::sort(srt.begin(), srt.end());
+        if (std::adjacent_find(srt.begin(), srt.end()) != srt.end()) {
+            set_last_error("primes must be pairwise distinct");
+            return IDET_ERR_ARG;
+        }
+    }
+    *stop_index = -1;
+    *reason = 0;
+    if (count == 0) return write_int(r, 0, nullptr, 0);
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace ws(s);
+    idet_opts o;
+    idet_default_opts(&o);
+    DevMatrix M;
+    DetJob J(M, ws, o);
+    std::vector<uint32_t> prs(primes, primes + count), res(residues, residues + count);
+    for (int i = 0; i < count; ++i) res[i] %= prs[i];
+    std::vector<int32_t> dig;
+    IDET_TRY(J.cra_digits(prs, res, dig));
+    int why = 0;
+    const int stop = CraScan::scan(dig, prs, log2_H, log2_epsilon, log2_l, pool_size,
+                                   certify != 0, &why);
+    *stop_index = stop;
+    *reason = why;
+    return J.assemble(prs, dig, stop >= 0 ? stop + 1 : count, nullptr, 0, r);
 }
 
 static int lif_common(DetJob &J, const int64_t *b_dev, const std::vector<int64_t> &bh,
@@ -1672,14 +1750,15 @@ int idet_int_det_batch(int32_t count, const int64_t *const *A, const int64_t *n,
             b.done = true;
             continue;
         }
-        if (b.amax > 0x7fffffffull) {
-            set_last_error("matrix %d: entries must satisfy |a_ij| <= 2^31 - 1", i);
+        if (!entry_range(b.amax, &b.amax)) {
+            set_last_error("matrix %d: entries must lie in [-2^31, 2^31 - 1]", i);
             return IDET_ERR_ARG;
         }
         double hr = 0, hc = 0;
         for (double v : b.rowsq) hr += v > 0 ? 0.5 * std::log2(v) : -INFINITY;
         for (double v : b.colsq) hc += v > 0 ? 0.5 * std::log2(v) : -INFINITY;
         b.log2H = std::min(hr, hc);
+        if (b.log2H > -INFINITY) b.log2H = b.log2H * (1 + 1e-12) + 1e-6 * (double)b.n;
         if (b.log2H == -INFINITY || b.amax == 0) {
             IDET_TRY(write_int(&dets[i], 0, nullptr, 0));
             b.done = true;
@@ -1940,6 +2019,7 @@ int idet_int_det_batch(int32_t count, const int64_t *const *A, const int64_t *n,
             const int i = ids[q];
             const int stop = CraScan::scan(dig[q], prs[q], it[i].log2H, o.log2_epsilon, log2l, pool,
                                            o.certify != 0, &why);
+            if (why == 3) return inconsistent_residues();
             if (stop >= 0) {
                 pending.push_back({i, std::vector<uint32_t>(prs[q].begin(), prs[q].begin() + stop + 1),
                                    std::vector<int32_t>(dig[q].begin(), dig[q].begin() + stop + 1),
@@ -2022,7 +2102,7 @@ int idet_int_det_batch(int32_t count, const int64_t *const *A, const int64_t *n,
                 continue;
             }
             b.p = p;
-            agg.lu_macs += 2.0 * (double)b.n * b.n * b.n;
+            agg.inverse_macs += 2.0 * (double)b.n * b.n * b.n;
             // bounds as in the single-matrix path
             SplitMix g(o.seed ^ 0xb5ull ^ ((uint64_t)i << 20));
             const double l2S = rhs_range_log2(b.n, b.log2H);
@@ -2222,6 +2302,7 @@ int idet_int_det_batch(int32_t count, const int64_t *const *A, const int64_t *n,
             int why = 0;
             const double lh = b.have_K ? std::max(0.0, b.log2H - b.log2K) : b.log2H;
             const int stop = CraScan::scan(dig[q], prs[q], lh, o.log2_epsilon, log2l, pool, false, &why);
+            if (why == 3) return inconsistent_residues();
             if (stop >= 0) {
                 pending.push_back({i, std::vector<uint32_t>(prs[q].begin(), prs[q].begin() + stop + 1),
                                    std::vector<int32_t>(dig[q].begin(), dig[q].begin() + stop + 1),

@@ -153,8 +153,17 @@ inline void count_launch(unsigned k = 1) { g_launches.fetch_add(k, std::memory_o
 // Kernel launchers (defined in the .cu files)
 
 // k_reduce.cu ---------------------------------------------------------------
+// Entries accepted by the int64 entry points: the int32 range
+// [-2^31, 2^31 - 1]. zz is the maximum zigzag code reported by the
+// statistics kernels; on success *amax = max |a_ij| (at most 2^31).
+inline bool entry_range(unsigned long long zz, unsigned long long *amax) {
+    *amax = (zz + 1) >> 1;
+    return zz <= 0xffffffffull;
+}
 // Row statistics of an int64 matrix: rowsq[i] = sum_j A_ij^2 (double,
-// rounded upward by a relative 2^-40 margin), amax[0] = max |A_ij|.
+// rounded upward by a relative 2^-30 margin), amax[0] = the maximum zigzag
+// code of the entries (2a for a >= 0, -2a - 1 for a < 0); decode it with
+// entry_range above.
 int launch_row_stats(const int64_t *A, int64_t n, int64_t lda, double *rowsq,
                      unsigned long long *amax, cudaStream_t s);
 // colsq[j] = sum_i A_ij^2 (double, rounded upward).
@@ -163,7 +172,7 @@ int launch_col_stats(const int64_t *A, int64_t n, int64_t lda, double *colsq, cu
 // >= n, zero padded; entries must fit the type.
 int launch_narrow(const int64_t *A, int64_t n, int64_t lda, void *out, int64_t ldo, int bytes,
                   cudaStream_t s);
-// A (int64, |A_ij| < 2^31) -> int32 copy with leading dimension n.
+// A (int64, entries in the int32 range) -> int32 copy with leading dimension n.
 int launch_to_int32(const int64_t *A, int64_t n, int64_t lda, int32_t *A32,
                     cudaStream_t s);
 // R[w] = A mod mods[w] (balanced), w < W; R has W * n * n entries (ld n).
@@ -240,7 +249,7 @@ struct JobBlob {
 int run_phase_graph(cudaStream_t s, uint64_t key, const std::vector<JobBlob> &blobs,
                     const std::function<int(const std::vector<const void *> &, cudaStream_t)> &record);
 // Row and column statistics of many int64 matrices in one launch (one CTA
-// per matrix): rowsq/colsq as in launch_row_stats / launch_col_stats.
+// per matrix): rowsq/colsq/amax as in launch_row_stats / launch_col_stats.
 struct StatJob {
     const int64_t *A;  // n x n, ld n
     int64_t n;

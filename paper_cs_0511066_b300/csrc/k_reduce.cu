@@ -31,7 +31,14 @@ __global__ void k_reduce(const int64_t *__restrict__ A, int64_t n, int64_t lda,
     }
 }
 
-// One block per row: sum of squares (double) and max |a|.
+// Zigzag code of an entry, 2a for a >= 0 and -2a - 1 for a < 0: its maximum
+// over a matrix tells both the largest magnitude and whether every entry
+// lies in the int32 range [-2^31, 2^31 - 1] (maximum <= 2^32 - 1).
+__device__ __forceinline__ unsigned long long zigzag(int64_t a) {
+    return ((unsigned long long)a << 1) ^ (unsigned long long)(a >> 63);
+}
+
+// One block per row: sum of squares (double) and the maximum zigzag code.
 __global__ void k_row_stats(const int64_t *__restrict__ A, int64_t n, int64_t lda,
                             double *__restrict__ rowsq,
                             unsigned long long *__restrict__ amax) {
@@ -42,7 +49,7 @@ __global__ void k_row_stats(const int64_t *__restrict__ A, int64_t n, int64_t ld
     unsigned long long mx = 0;
     for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
         int64_t a = A[i * lda + j];
-        unsigned long long m = (unsigned long long)(a < 0 ? -a : a);
+        unsigned long long m = zigzag(a);
         double d = (double)a;
         acc += d * d;
         mx = m > mx ? m : mx;
@@ -97,7 +104,7 @@ __global__ void k_stats_multi(const StatJob *__restrict__ jobs) {
         double acc = 0.0;
         for (int64_t j = lane; j < n; j += 32) {
             const int64_t a = J.A[i * n + j];
-            const unsigned long long m = (unsigned long long)(a < 0 ? -a : a);
+            const unsigned long long m = zigzag(a);
             const double d = (double)a;
             acc += d * d;
             mx = m > mx ? m : mx;

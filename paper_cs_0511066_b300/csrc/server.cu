@@ -294,9 +294,9 @@ int idet_submit(idet_server *S, const int64_t *A, int64_t n, int64_t lda, uint64
     j->A.resize((size_t)n * n);
     for (int64_t i = 0; i < n; ++i) memcpy(&j->A[(size_t)i * n], A + i * lda, 8 * (size_t)n);
     for (int64_t v : j->A)
-        if (v > 0x7fffffffll || v < -0x7fffffffll) {
+        if (v > 0x7fffffffll || v < -0x80000000ll) {
             delete j;
-            set_last_error("submit: entries must satisfy |a_ij| <= 2^31 - 1");
+            set_last_error("submit: entries must lie in [-2^31, 2^31 - 1]");
             return IDET_ERR_ARG;
         }
     j->foot = job_footprint(n);

@@ -140,3 +140,35 @@ def test_binding_refuses_matrices_it_would_have_to_change():
         idet.int_det(np.zeros((2, 3), dtype=np.int64))
     assert idet._as_int64(np.array([[2.0, -3.0]])).tolist() == [[2, -3]]
     assert idet._as_int64([[1, 2], [3, 4]]).dtype == np.int64
+    # values that numpy's cast would wrap are refused, not wrapped
+    with pytest.raises(ValueError):
+        idet.int_det(np.array([[1e19, 0.0], [0.0, 1.0]]))
+    with pytest.raises(ValueError):
+        idet.int_det(np.array([[2.0 ** 63, 0.0], [0.0, 1.0]]))
+    with pytest.raises(ValueError):
+        idet.int_det(np.array([[2 ** 64 - 1, 0], [0, 1]], dtype=np.uint64))
+    with pytest.raises(ValueError):
+        idet.int_det(np.array([[1 << 70, 0], [0, 1]], dtype=object))
+    assert idet._as_int64(np.array([[-(2.0 ** 63)]])).tolist() == [[-(1 << 63)]]
+    assert idet._as_int64(np.array([[2 ** 63 - 1]], dtype=np.uint64)).tolist() == [[2 ** 63 - 1]]
+
+
+def test_early_termination_scan_refuses_bad_streams_on_the_host():
+    """idet_cra_early_termination checks its primes (odd, prime, distinct,
+    below 2^31) and parameters before any device work."""
+    import paper_cs_0511066_b300 as idet
+    lib = idet._lib
+    lib.idet_last_error.restype = ctypes.c_char_p
+    out = ctypes.byref(idet.idet_int(0, 0, 0, None))   # not written: the checks fail first
+    stop, why = ctypes.c_int32(7), ctypes.c_int32(7)
+    f = lib.idet_cra_early_termination
+    res = (ctypes.c_uint32 * 2)(1, 2)
+    same = (ctypes.c_uint32 * 2)(1048583, 1048583)
+    assert f(res, same, 2, 100.0, -64.0, 20.0, 73586.0, 0, None, out,
+             ctypes.byref(stop), ctypes.byref(why)) == 1
+    composite = (ctypes.c_uint32 * 2)(1048583, 1048583 * 3)
+    assert f(res, composite, 2, 100.0, -64.0, 20.0, 73586.0, 0, None, out,
+             ctypes.byref(stop), ctypes.byref(why)) == 1
+    good = (ctypes.c_uint32 * 2)(1048583, 1048589)
+    assert f(res, good, 2, 100.0, 0.5, 20.0, 73586.0, 0, None, out,
+             ctypes.byref(stop), ctypes.byref(why)) == 1      # epsilon must be < 1

@@ -1,0 +1,260 @@
+"""Pins of the CUDA path at the headline sizes, at the worst cases of its
+arithmetic, and of its stopping and failure-detection rules, against the CPU
+oracle or against facts that hold by construction.
+
+Every call goes through the C ABI (the ctypes binding marshals arguments
+only). Integer results are compared bit for bit.
+"""
+import hashlib
+import math
+import os
+import random
+
+import numpy as np
+import pytest
+
+import et_streams
+import workloads
+from oracle import cra, dixon, exact, modular
+
+pytestmark = pytest.mark.gpu
+
+idet = pytest.importorskip("paper_cs_0511066_b300")
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+P21 = modular.primes_in(1 << 20, 1 << 21)
+CORES = os.cpu_count() or 1
+
+
+def p31(k, seed):
+    r = random.Random(seed)
+    out = []
+    while len(out) < k:
+        c = r.randrange(1 << 30, 1 << 31) | 1
+        if modular.is_prime(c) and c not in out:
+            out.append(c)
+    return out
+
+
+# --- early termination: the device rule against the oracle's Alg. 2.1 --------------
+
+def test_et_stop_index_and_value_match_oracle():
+    """The device reconstruction with the host stopping rule (the one
+    idet_int_det applies) stops at the same prime as the oracle's Alg. 2.1 and
+    returns the same value, on the adversarial streams of the statistical pin
+    (false stops included) with eps = 0.05."""
+    D, log2H, P, streams = et_streams.adversarial_streams(400)
+    eps_log2 = math.log2(0.05)
+    false_stops = 0
+    for res, primes in streams:
+        v, used, why = cra.et_cra(res, primes, log2H, eps_log2, 1 << 20, P)
+        dv, stop, dwhy = idet.cra_early_termination(res, primes, log2H, eps_log2, 20.0, P)
+        if why == "et":
+            assert (dwhy, stop, dv) == (1, used - 1, v)
+            false_stops += v != D
+        else:
+            assert why == "exhausted" and dwhy == 0 and stop == -1
+            assert dv == cra.crt_symmetric(res, primes)
+    assert false_stops >= 5
+
+
+def test_et_small_determinant_and_certified_bound():
+    """A small determinant stops early at the oracle's prime; with certify the
+    device runs 40 bits past 2H (the oracle stops at 2H) and both return det;
+    a wrong residue before the bound is reported as inconsistent (reason 3)."""
+    primes = random.Random(5).sample(P21, 80)
+    d = -123456789012345
+    res = [d % q for q in primes]
+    v, used, why = cra.et_cra(res, primes, 600.0, -64, 1 << 20, len(P21))
+    dv, stop, dwhy = idet.cra_early_termination(res, primes, 600.0, -64.0, 20.0, len(P21))
+    assert why == "et" and (dwhy, stop, dv) == (1, used - 1, v) and v == d
+    big = random.Random(6).randint(1 << 400, 1 << 401)
+    res = [big % q for q in primes]
+    v, used, why = cra.et_cra(res, primes, 402.0, -64, 1 << 20, len(P21), certify=True)
+    dv, stop, dwhy = idet.cra_early_termination(res, primes, 402.0, -64.0, 20.0, len(P21),
+                                                certify=True)
+    assert why == "bound" and v == big and dwhy == 2 and dv == big
+    M = math.prod(primes[:stop + 1])
+    assert stop >= used - 1 and M >= (1 << (403 + 40)) and M // primes[stop] < (1 << (403 + 40))
+    res[7] = (res[7] + 1) % primes[7]
+    dv, stop, dwhy = idet.cra_early_termination(res, primes, 402.0, -64.0, 20.0, len(P21),
+                                                certify=True)
+    assert dwhy == 3
+
+
+# --- the headline workloads, in full --------------------------------------------------
+
+def _golden(name):
+    out = {}
+    for line in open(os.path.join(GOLDEN, name)):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, v = line.split(" ", 1)
+        out[k] = v.strip()
+    return out
+
+
+def test_int_det_dense_u8_n1000_full_value():
+    """n = 1000, entries in [0, 255]: the whole determinant (about 12,900
+    bits) equals the value the oracle's elimination and CRT past twice the
+    Hadamard bound produced offline (tests/golden)."""
+    torch = pytest.importorskip("torch")
+    g = _golden("det_dense_u8_n1000_seed0.txt")
+    A = workloads.dense_u8(1000, seed=0)
+    assert hashlib.sha256(A.astype("<i8").tobytes()).hexdigest() == g["sha256_int64le"]
+    want = int(g["det"], 16)
+    assert want.bit_length() == int(g["bits"])
+    d, st = idet.int_det(torch.from_numpy(A).cuda(), return_stats=True)
+    assert d == want
+    assert st["lift_iters"] > 0 and st["et_stop"] == 1, st
+
+
+def test_int_det_dense_pm2p20_n4000_spot_check_and_lif():
+    """n = 4000, entries in [-2^20, 2^20], in the launch configuration the
+    benchmark times: the determinant agrees with the oracle's elimination
+    modulo eight 31-bit primes drawn independently of the path's, and the
+    largest invariant factor for another right-hand side divides it, with a
+    cofactor of at most a few bits (random dense matrices have s_n close to
+    det)."""
+    torch = pytest.importorskip("torch")
+    A = workloads.dense_pm2p20(4000, seed=0)
+    Ad = torch.from_numpy(A).cuda()
+    d, st = idet.int_det(Ad, return_stats=True)
+    qs = p31(8, seed=77)
+    ref = modular.det_mod_primes(A, qs, threads=CORES)
+    assert [d % q for q in qs] == [int(r) for r in ref]
+    b = workloads.random_rhs(4000, 1 << 40, seed=9)
+    s = idet.largest_invariant_factor(Ad, b)
+    assert d % s == 0 and abs(d // s).bit_length() <= 64
+
+
+def test_int_det_batch_full_512_matches_oracle():
+    """The whole batched workload (512 matrices, n log-uniform in [32, 512],
+    entries in [-2^10, 2^10]) in one batched call: every determinant agrees
+    with the oracle's elimination modulo eight fresh 31-bit primes, and the
+    small ones (n <= 40) equal the exact Bareiss determinant."""
+    mats = workloads.batch_mix(count=512, nmin=32, nmax=512, bits=10, seed=0)
+    got = idet.int_det_batch(mats)
+    qs = p31(8, seed=4321)
+    for A, d in zip(mats, got):
+        ref = modular.det_mod_primes(A, qs, threads=CORES)
+        assert [d % q for q in qs] == [int(r) for r in ref], A.shape
+        if A.shape[0] <= 40:
+            assert d == exact.bareiss_det(A.tolist())
+
+
+# --- worst cases of the tensor-core accumulations -----------------------------------
+
+def _limbs7(x, L):
+    out = []
+    for _ in range(L):
+        l0 = ((x + 64) & 127) - 64
+        out.append(l0)
+        x = (x - l0) >> 7
+    return out, x
+
+
+def _worst_lu_matrix(n, p, x):
+    """A = L U mod p with L unit lower triangular, every entry below the
+    diagonal x, and U upper triangular with unit diagonal, every entry above
+    it x: a_ij = min(i, j) x^2 + (1 if i == j else x) mod p. Its LU with the
+    first-nonzero pivot needs no exchange and every trailing update
+    multiplies blocks whose entries are all x."""
+    i = np.arange(n, dtype=object)[:, None]
+    j = np.arange(n, dtype=object)[None, :]
+    A = (np.minimum(i, j) * (x * x) + np.where(i == j, 1, x)) % p
+    LU = np.where(np.arange(n)[:, None] == np.arange(n)[None, :], 1, x % p).astype(np.uint32)
+    return A.astype(np.int64), LU
+
+
+PATHS21 = {"int64": 1, "i8": 2, "f64": 3, "bf16": 4, "tc05": 5}
+
+
+@pytest.mark.parametrize("path", sorted(PATHS21))
+def test_trailing_update_worst_case_21bit(path):
+    """Every limb at the edge of its range: x = 1040319 has the 7-bit limbs
+    (63, 63, 63), so each limb product group of the rank-128 update sums 128
+    terms of the same sign (3 * 128 * 63^2, the largest group); for FP64 every
+    entry is (p - 1)/2, the largest balanced residue (128 * 2^40 < 2^53). The
+    LU factors must come out exactly as constructed."""
+    p = max(q for q in P21 if q < (1 << 21))
+    if path == "f64":
+        x = (p - 1) // 2
+    else:
+        x = 1040319
+        assert _limbs7(x, 3) == ([63, 63, 63], 0) and 2 * x < p
+    A, want = _worst_lu_matrix(300, p, x)
+    lu, perm, sing = idet.lu_mod_prime(A, p, update_path=PATHS21[path])
+    assert not sing and (perm == np.arange(300)).all()
+    assert (lu == want).all()
+    assert list(idet.det_mod_primes(A, [p], update_path=PATHS21[path])) == [1]
+
+
+@pytest.mark.parametrize("path", ["int64", "tc05"])
+def test_trailing_update_worst_case_31bit(path):
+    """31-bit primes, five 7-bit limbs: x has the limbs (63, 63, 63, 63, 3),
+    the largest the balanced range allows, so the middle groups sum 4 * 128 *
+    63^2 same-sign products."""
+    x = 63 * (1 + (1 << 7) + (1 << 14) + (1 << 21)) + 3 * (1 << 28)
+    assert _limbs7(x, 5) == ([63, 63, 63, 63, 3], 0)
+    p = next(q for q in range((1 << 31) - 1, 2 * x, -2) if modular.is_prime(q))
+    A, want = _worst_lu_matrix(300, p, x)
+    lu, perm, sing = idet.lu_mod_prime(A, p, update_path=PATHS21[path])
+    assert not sing and (perm == np.arange(300)).all()
+    assert (lu == want).all()
+
+
+# --- the whole int32 range of entries ------------------------------------------------
+
+def _int32_edges(n, seed):
+    g = np.random.default_rng(seed)
+    A = g.integers(-(1 << 31), (1 << 31) - 1, size=(n, n), endpoint=True, dtype=np.int64)
+    A[g.random((n, n)) < 0.2] = -(1 << 31)
+    A[g.random((n, n)) < 0.1] = (1 << 31) - 1
+    return A
+
+
+def test_int32_range_entries_every_entry_point():
+    """Entries equal to -2^31 (and 2^31 - 1), as 32-bit served jobs contain:
+    int_det, the batch, the server and the lifting digits agree with the
+    oracle; 2^31 itself is refused."""
+    A = _int32_edges(24, 1)
+    want = exact.bareiss_det(A.tolist())
+    assert idet.int_det(A) == want
+    assert idet.int_det(A, certify=True) == want
+    B = _int32_edges(260, 2)
+    qs = p31(3, seed=8)
+    dB = idet.int_det(B)
+    assert [dB % q for q in qs] == [int(r) for r in modular.det_mod_primes(B, qs)]
+    assert idet.int_det_batch([A, B, A[:5, :5]]) == [want, dB, exact.bareiss_det(A[:5, :5].tolist())]
+    with idet.Server(slots=2) as srv:
+        t1, t2 = srv.submit(A), srv.submit(B)
+        assert srv.poll(t1)[0] == want and srv.poll(t2)[0] == dB
+    b = workloads.random_rhs(24, 1 << 40, seed=3)
+    p = p31(1, 11)[0]
+    dg, r = idet.dixon_digits(A, b, p, 4)
+    odg, orr = dixon.dixon_digits(A, b, p, 4)
+    assert dg.tolist() == odg and r.tolist() == orr
+    C = A.copy()
+    C[3, 4] = 1 << 31
+    with pytest.raises(idet.IdetError) as e:
+        idet.int_det(C)
+    assert e.value.code == 1
+
+
+# --- failure detection (a wrong modular determinant, made on the host) -------------
+
+def test_wrong_residue_is_caught_at_the_bound():
+    """A modular determinant made wrong on the host: the reconstruction never
+    stabilises (no early termination), and at the bound the check |r| <= H
+    fails, so the call reports IDET_ERR_INTERNAL instead of a wrong value, in
+    certified and in early-terminated mode; the next call is unaffected."""
+    A = workloads.dense_pm100(60, seed=4)
+    want = exact.bareiss_det(A.tolist())
+    for kw in ({"certify": True, "inject_fault": 3}, {"inject_fault": 2},
+               {"lif": False, "inject_fault": 1}):
+        with pytest.raises(idet.IdetError) as e:
+            idet.int_det(A, **kw)
+        assert e.value.code == 7, kw
+    assert idet.int_det(A, certify=True) == want
+    assert idet.int_det(A) == want

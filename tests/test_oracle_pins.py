@@ -14,6 +14,7 @@ from fractions import Fraction
 import numpy as np
 import pytest
 
+import et_streams
 import workloads
 from oracle import cra, dixon, exact, modular, params
 
@@ -438,3 +439,34 @@ def test_dixon_inverse_is_an_inverse_mod_p():
             v = sum(int(C[i][k]) * A[k][j] for k in range(8)) % p
             assert v == (1 if i == j else 0)
         assert all(abs(int(c)) <= (p - 1) // 2 for c in C[i])
+
+
+# --- Early termination: the false-stop probability of Lemma 2.1(iii) --------------
+
+def _false_stop_rate(eps, trials=4000):
+    D, log2H, P, streams = et_streams.adversarial_streams(trials)
+    wrong = 0
+    for res, primes in streams:
+        v, used, why = cra.et_cra(res, primes, log2H, math.log2(eps), 1 << 20, P)
+        if why == "et" and v != D:
+            wrong += 1
+    return wrong / trials
+
+
+def test_et_false_stop_rate_within_lemma_bound():
+    """Lemma 2.1(iii): stopping when the on-the-fly bound is below eps keeps
+    the probability of a wrong result below eps. With eps = 0.05 and about
+    43 % of the remaining pool dividing K, the wrong-stop rate over 4000
+    random prime orders must stay below eps (the exact hypergeometric rate
+    of four consecutive primes from S is 0.035, a binomial sigma 0.003)."""
+    rate = _false_stop_rate(0.05)
+    assert 0.0 < rate <= 0.05, rate
+
+
+def test_et_stopping_one_prime_early_exceeds_the_bound(monkeypatch):
+    """A stop rule that fires one agreement early (the bound evaluated as if
+    k + 1 values had agreed) is caught by the same experiment: its wrong-stop
+    rate (about 0.08) exceeds eps."""
+    real = cra.on_the_fly_bound
+    monkeypatch.setattr(cra, "on_the_fly_bound", lambda Rp, k, P, i: real(Rp, k + 1, P, i + 1))
+    assert _false_stop_rate(0.05) > 0.05

@@ -105,7 +105,9 @@ typedef struct {
     double ms_total;
     uint64_t launches;         /* kernels launched by the call              */
     double ms_lift_kernel;     /* device time of the lifting kernel alone   */
-    double lift_bytes;         /* its algorithmic bytes: m * 8 n^2          */
+    double lift_bytes;         /* its algorithmic bytes: the matrices it
+                                  reads once per step (E: 4 n^2 per step;
+                                  C and A: (4 + bytes(a_ij)) n^2)           */
     double lu_macs;            /* (2/3) n^3 per factored CRA prime: the
                                   modular MACs of the work timed by ms_lu   */
     double ms_inverse;         /* LU + inverse mod the lifting prime        */
@@ -113,6 +115,10 @@ typedef struct {
                                   included in ms_lift_kernel)                */
     double inverse_macs;       /* 2 n^3 per lifting prime: LU and inverse,
                                   the work timed by ms_inverse              */
+    double ms_lift_setup;      /* forming E = (C A - I)/p and y_0 = C b for
+                                  the one-product lift (0 otherwise)        */
+    int32_t lift_path;         /* 1: one-product lift (E), 0: C and A       */
+    int32_t pad_;
 } idet_stats;
 
 /* Fill *opts with the defaults. */
@@ -130,6 +136,14 @@ void idet_set_allocator(idet_alloc_fn alloc, idet_free_fn free_, void *ctx);
 
 /* Kernels launched by this library since load (monotone counter). */
 uint64_t idet_launch_count(void);
+
+/* Failure-detection tests: the cycle limit of every bounded wait in the
+ * lifting kernels (grid-wide barriers, copy-ring waits). cycles <= 0
+ * restores the default (about two seconds of SM clock). A wait that runs out
+ * ends the kernel cleanly (its copies drained) and the call returns
+ * IDET_ERR_TIMEOUT with stats->lift_timed_out set; later calls are
+ * unaffected. Process-wide; not for use while lifts are running. */
+void idet_set_wait_limit(int64_t cycles);
 
 /*
  * det(A): "computing the determinant of an integer matrix A" (Abstract,
@@ -206,12 +220,30 @@ int idet_lu_mod_prime(const int64_t *A, int64_t n, int64_t lda,
  * 2^30 < p < 2^31: C = A^{-1} mod p; r_0 = b; x_i = C r_i mod p in the
  * balanced range [-(p-1)/2, (p-1)/2]; r_{i+1} = (r_i - A x_i)/p. Writes the m
  * digit vectors to digits (host, m*n int32, row i = x_i) and r_m to
- * residual (host, n int64). IDET_ERR_SINGULAR if A is singular mod p.
+ * residual (host, n int64). |b_i| < 2^62 (IDET_ERR_ARG otherwise).
+ * IDET_ERR_SINGULAR if A is singular mod p.
  */
 int idet_dixon_digits(const int64_t *A, int64_t n, int64_t lda,
                       const int64_t *b, uint32_t p, int32_t m,
                       int32_t on_device, void *stream, int32_t *digits,
                       int64_t *residual);
+
+/*
+ * The block form of the same iteration: nrhs = 1 or 2 right-hand sides
+ * lifted together, so that each step reads the lifting matrix once for all
+ * of them (Section 6: grouping the solvings into block iterations;
+ * Theorem 2.2(ii) and (iii) take r = 2 solves). B holds the right-hand sides
+ * as nrhs consecutive vectors of n int64 (|b_i| < 2^62; device memory when
+ * on_device). digits (host, nrhs * m * n int32) receives the digit vectors
+ * [k][i][j] = x_i of right-hand side k; residual (host, nrhs * n int64) the
+ * r_m. stats (may be NULL): lift_iters = m, lift_path, ms_lift_kernel (the
+ * stepping kernel), ms_lift_setup and lift_bytes (the bytes of the lifting
+ * matrices read by the stepping kernel, counted once per step).
+ */
+int idet_dixon_digits_block(const int64_t *A, int64_t n, int64_t lda,
+                            const int64_t *B, int32_t nrhs, uint32_t p, int32_t m,
+                            int32_t on_device, void *stream, int32_t *digits,
+                            int64_t *residual, idet_stats *stats);
 
 /*
  * Chinese remaindering in the symmetric range (Section 2.1): the unique r

@@ -59,7 +59,9 @@ class idet_stats(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("launches", ctypes.c_uint64),
                 ("ms_lift_kernel", ctypes.c_double), ("lift_bytes", ctypes.c_double),
                 ("lu_macs", ctypes.c_double), ("ms_inverse", ctypes.c_double),
-                ("ms_rr", ctypes.c_double), ("inverse_macs", ctypes.c_double)]
+                ("ms_rr", ctypes.c_double), ("inverse_macs", ctypes.c_double),
+                ("ms_lift_setup", ctypes.c_double), ("lift_path", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -256,7 +258,10 @@ def int_det(A, *, certify: bool = False, seed: int | None = None, lif: bool | in
         if rc == IDET_ERR_BUFFER and out.nlimbs > cap:
             cap = int(out.nlimbs) + 8
             continue
-        _check(rc)
+        if rc != IDET_OK:
+            err = IdetError(rc, _lib.idet_last_error().decode(errors="replace"))
+            err.stats = st.as_dict()
+            raise err
         break
     d = _to_int(out, buf)
     del keep
@@ -311,6 +316,35 @@ def dixon_digits(A, b, p: int, m: int, *, stream=None):
     _check(_lib.idet_dixon_digits(ptr, n, lda, bp, p, m, dev, _stream_ptr(stream),
                                   digits.ctypes.data, res.ctypes.data))
     return digits, res
+
+
+_lib.idet_dixon_digits_block.argtypes = [_P, _i64, _i64, _P, _i32, _u32, _i32, _i32, _P, _P, _P,
+                                         ctypes.POINTER(idet_stats)]
+
+
+def dixon_digits_block(A, B, p: int, m: int, *, stream=None, return_stats: bool = False):
+    """Block lift of the rows of B (1 or 2 right-hand sides) in one pass
+    (idet_dixon_digits_block): (digits [k][m][n] int32, residuals [k][n]
+    int64)."""
+    use_torch_allocator()
+    ptr, n, lda, dev, keep = _matrix(A)
+    torch = _get_torch()
+    if torch is not None and isinstance(B, torch.Tensor):
+        Bt = B.to(torch.int64).contiguous()
+        if dev and not Bt.is_cuda:
+            Bt = Bt.cuda()
+        k = Bt.shape[0] if Bt.dim() == 2 else 1
+        bp, bkeep = Bt.data_ptr(), Bt
+    else:
+        Bh = np.ascontiguousarray(_as_int64(B))
+        k = Bh.shape[0] if Bh.ndim == 2 else 1
+        bp, bkeep = _vector(Bh.reshape(-1), dev)
+    digits = np.zeros((k, m, n), dtype=np.int32)
+    res = np.zeros((k, n), dtype=np.int64)
+    st = idet_stats()
+    _check(_lib.idet_dixon_digits_block(ptr, n, lda, bp, k, p, m, dev, _stream_ptr(stream),
+                                        digits.ctypes.data, res.ctypes.data, ctypes.byref(st)))
+    return (digits, res, st.as_dict()) if return_stats else (digits, res)
 
 
 def crt_symmetric(residues, primes, *, stream=None):
@@ -397,8 +431,19 @@ def launch_count() -> int:
     return int(_lib.idet_launch_count())
 
 
+_lib.idet_set_wait_limit.argtypes = [_i64]
+_lib.idet_set_wait_limit.restype = None
+
+
+def set_wait_limit(cycles: int) -> None:
+    """Cycle limit of the lifting kernels' bounded waits (failure-detection
+    tests; 0 restores the default), idet_set_wait_limit."""
+    _lib.idet_set_wait_limit(int(cycles))
+
+
 __all__ = ["int_det", "largest_invariant_factor", "det_mod_primes", "lu_mod_prime",
-           "dixon_digits", "crt_symmetric", "cra_early_termination", "launch_count", "default_opts", "IdetError",
+           "dixon_digits", "dixon_digits_block", "crt_symmetric", "cra_early_termination",
+           "launch_count", "default_opts", "IdetError",
            "use_torch_allocator", "LIB_PATH"]
 
 

@@ -648,10 +648,14 @@ static int solve_and_denominator(DetJob &J, const int64_t *b_dev, const std::vec
     a.zproj = z;
     a.r = r;
     a.digits = nullptr;
+    a.amax = J.amax;
     float kms = 0;
-    IDET_TRY(launch_lift(a, J.Anar, J.abytes, J.ldl, ws, &out.timed_out, &kms));
-    J.st.ms_lift_kernel += kms;
-    J.st.lift_bytes += (double)m * 8.0 * (double)n * (double)n;
+    LiftInfo li{};
+    IDET_TRY(launch_lift(a, J.Anar, J.abytes, J.ldl, ws, &out.timed_out, &kms, &li));
+    J.st.ms_lift_kernel += li.ms_steps;
+    J.st.ms_lift_setup += li.ms_setup;
+    J.st.lift_bytes += li.bytes;
+    J.st.lift_path = li.path;
     J.st.inverse_macs += 2.0 * (double)n * n * n;  // LU + inverse of the lift prime
     uint32_t *den = nullptr;
     int32_t *info = nullptr;
@@ -1128,11 +1132,13 @@ int idet_lu_mod_prime(const int64_t *A, int64_t n, int64_t lda, int32_t on_devic
     return det == 0 ? IDET_ERR_SINGULAR : IDET_OK;
 }
 
-int idet_dixon_digits(const int64_t *A, int64_t n, int64_t lda, const int64_t *b, uint32_t p,
-                      int32_t m, int32_t on_device, void *stream, int32_t *digits,
-                      int64_t *residual) {
-    if (n <= 0 || n > IDET_MAX_ORDER || lda < n || !A || !b || m < 0 || (m > 0 && !digits) ||
-        !residual ||
+// The Dixon iteration for nrhs (1 or 2) right-hand sides B[k] (rows of B)
+// in one lift: digits [k][i][j], residuals [k][j] (host arrays).
+static int dixon_common(const int64_t *A, int64_t n, int64_t lda, const int64_t *B, int nrhs,
+                        uint32_t p, int32_t m, int32_t on_device, void *stream, int32_t *digits,
+                        int64_t *residual, idet_stats *stats) {
+    if (n <= 0 || n > IDET_MAX_ORDER || lda < n || !A || !B || m < 0 || (m > 0 && !digits) ||
+        !residual || (nrhs != 1 && nrhs != 2) ||
         !(p > (1u << 30) && p < (1u << 31) && is_prime32(p))) {
         set_last_error("invalid argument");
         return IDET_ERR_ARG;
@@ -1141,8 +1147,14 @@ int idet_dixon_digits(const int64_t *A, int64_t n, int64_t lda, const int64_t *b
     Workspace ws(s);
     DevMatrix M;
     IDET_TRY(stage_matrix(A, n, lda, on_device, ws, M));
+    int64_t *bd = nullptr;
+    IDET_TRY(ws.alloc_n(&bd, (size_t)nrhs * n));
+    IDET_CUDA_TRY(cudaMemcpyAsync(bd, B, 8 * (size_t)nrhs * n,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    std::vector<int64_t> bh((size_t)nrhs * n);
+    IDET_CUDA_TRY(cudaMemcpyAsync(bh.data(), bd, 8 * bh.size(), cudaMemcpyDeviceToHost, s));
     int32_t *Cinv = nullptr, *dig = nullptr;
-    int64_t ldl = 0, *bd = nullptr, *r = nullptr;
+    int64_t ldl = 0, *r = nullptr;
     double *rowsq = nullptr;
     unsigned long long *d_amax = nullptr, hmax = 0;
     IDET_TRY(ws.alloc_n(&rowsq, n));
@@ -1154,16 +1166,18 @@ int idet_dixon_digits(const int64_t *A, int64_t n, int64_t lda, const int64_t *b
         set_last_error("entries must lie in [-2^31, 2^31 - 1]");
         return IDET_ERR_ARG;
     }
+    for (int64_t v : bh)
+        if (v >= (1ll << 62) || v <= -(1ll << 62)) {
+            set_last_error("right-hand side entries must satisfy |b_i| < 2^62");
+            return IDET_ERR_ARG;
+        }
     void *Anar = nullptr;
     int abytes = 4;
     IDET_TRY(make_Anar(M, hmax, ws, &Anar, &abytes, &ldl));
     IDET_TRY(ws.alloc_n(&Cinv, (size_t)n * ldl));
     IDET_TRY(inverse_mod_prime(M, p, 32, ws, Cinv, ldl));
-    IDET_TRY(ws.alloc_n(&bd, n));
-    IDET_TRY(ws.alloc_n(&r, n));
-    IDET_TRY(ws.alloc_n(&dig, (size_t)m * n + 1));
-    IDET_CUDA_TRY(cudaMemcpyAsync(bd, b, 8 * (size_t)n,
-                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    IDET_TRY(ws.alloc_n(&r, (size_t)nrhs * n));
+    IDET_TRY(ws.alloc_n(&dig, (size_t)nrhs * m * n + 1));
     LiftArgs a{};
     a.Cinv = Cinv;
     a.b = bd;
@@ -1173,13 +1187,44 @@ int idet_dixon_digits(const int64_t *A, int64_t n, int64_t lda, const int64_t *b
     a.pinv = inv_mod_2_64(p);
     a.digits = dig;
     a.r = r;
+    a.amax = hmax;
+    a.nrhs = nrhs;
+    if (nrhs == 2) {
+        a.b2 = bd + n;
+        a.digits2 = dig + (size_t)m * n;
+        a.r2 = r + n;
+    }
     int to = 0;
-    IDET_TRY(launch_lift(a, Anar, abytes, ldl, ws, &to));
+    float ms = 0;
+    LiftInfo li{};
+    IDET_TRY(launch_lift(a, Anar, abytes, ldl, ws, &to, &ms, &li));
     if (m > 0)
-        IDET_CUDA_TRY(cudaMemcpyAsync(digits, dig, 4 * (size_t)m * n, cudaMemcpyDeviceToHost, s));
-    IDET_CUDA_TRY(cudaMemcpyAsync(residual, r, 8 * (size_t)n, cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaMemcpyAsync(digits, dig, 4 * (size_t)nrhs * m * n,
+                                      cudaMemcpyDeviceToHost, s));
+    IDET_CUDA_TRY(cudaMemcpyAsync(residual, r, 8 * (size_t)nrhs * n, cudaMemcpyDeviceToHost, s));
     IDET_CUDA_TRY(cudaStreamSynchronize(s));
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->lift_iters = m;
+        stats->lift_path = li.path;
+        stats->ms_lift_kernel = li.ms_steps;
+        stats->ms_lift_setup = li.ms_setup;
+        stats->lift_bytes = li.bytes;
+        stats->lift_timed_out = to;
+    }
     return IDET_OK;
+}
+
+int idet_dixon_digits(const int64_t *A, int64_t n, int64_t lda, const int64_t *b, uint32_t p,
+                      int32_t m, int32_t on_device, void *stream, int32_t *digits,
+                      int64_t *residual) {
+    return dixon_common(A, n, lda, b, 1, p, m, on_device, stream, digits, residual, nullptr);
+}
+
+int idet_dixon_digits_block(const int64_t *A, int64_t n, int64_t lda, const int64_t *B,
+                            int32_t nrhs, uint32_t p, int32_t m, int32_t on_device, void *stream,
+                            int32_t *digits, int64_t *residual, idet_stats *stats) {
+    return dixon_common(A, n, lda, B, nrhs, p, m, on_device, stream, digits, residual, stats);
 }
 
 int idet_crt_symmetric(const uint32_t *residues, const uint32_t *primes, int32_t count,
@@ -1338,6 +1383,7 @@ int idet_int_det(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
     Timer tl(s);
     int rc = lif_common(J, bdev, bh, lr);
     J.st.ms_lift += tl.stop();
+    J.st.lift_timed_out = lr.timed_out;
     if (rc != IDET_OK && rc != IDET_ERR_SINGULAR) return finish(rc);
     J.st.lift_iters = lr.m;
     J.st.lift_timed_out = lr.timed_out;
@@ -1551,6 +1597,7 @@ int idet_largest_invariant_factor(const int64_t *A, int64_t n, int64_t lda, cons
     la.digits = dig;
     la.zproj = z;
     la.r = r;
+    la.amax = J.amax;
     int to = 0;
     IDET_TRY(launch_lift(la, J.Anar, J.abytes, J.ldl, ws, &to));
     // candidate D from the projection

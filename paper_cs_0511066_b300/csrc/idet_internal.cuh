@@ -14,6 +14,7 @@
 
 #include <atomic>
 #include <functional>
+#include <mutex>
 #include <vector>
 
 #include "../../include/idet.h"
@@ -316,6 +317,9 @@ int gemm_sub_tc(int path, const int32_t *A, int64_t lda, int64_t sA, const int32
                 const ModP *mods, const LUState *st, int W, cudaStream_t s);
 
 // k_lift.cu ---------------------------------------------------------------
+// Held while a grid-synchronised lifting kernel runs: two of them on
+// different streams could each hold part of the SMs and wait for the other.
+extern std::mutex g_coop_mu;
 // Two timing events destroyed with the scope, also on error returns.
 struct EventPair {
     cudaEvent_t a = nullptr, b = nullptr;
@@ -333,17 +337,41 @@ struct LiftArgs {
     const int64_t *b;      // right-hand side, n
     const int32_t *u;      // projection vector, n (may be null)
     int64_t n;
-    int32_t m;             // number of digits to produce
+    int32_t m;             // number of digits to produce (per right-hand side)
     ModP mod;
     uint64_t pinv;         // p^{-1} mod 2^64
     int32_t *digits;       // m x n (row i = digit vector x_i), may be null
     int64_t *zproj;        // m projections u . x_i, may be null
-    int64_t *r;            // n: residual (in: ignored; out: r_m)
+    int64_t *r;            // n: residual r_m (the two-product kernel always
+                           // writes it; the one-product kernel only when the
+                           // digits are kept), may be null then
+    uint64_t amax;         // max |a_ij|; 0 = unknown (two-product kernel)
+    int32_t nrhs;          // right-hand sides lifted together: 1 (0 reads as
+                           // 1) or 2, the second given by b2/digits2/...
+    const int64_t *b2;
+    int32_t *digits2;
+    int64_t *zproj2;
+    int64_t *r2;
+};
+// What a lift ran: path 0 the two-product kernel (k_lift.cu), 1 the
+// one-product kernel (k_lifte.cu); setup = forming E and y_0; steps = the
+// persistent kernel's launch, its steps and algorithmic bytes (E, or C and A,
+// once per step).
+struct LiftInfo {
+    int path, steps;
+    float ms_setup, ms_steps;
+    double bytes;
 };
 // Anar: A as int8/int16/int32 (abytes = 1, 2, 4), n rows of ld entries;
-// Cinv rows also have ld entries; ld must be a multiple of 16.
+// Cinv rows also have ld entries; ld must be a multiple of 16. Chooses the
+// one-product kernel when n a.amax < 2^32 - 2 (lift_e_applies).
 int launch_lift(const LiftArgs &a, const void *Anar, int abytes, int64_t ld, Workspace &ws,
-                int *timed_out, float *ms = nullptr);
+                int *timed_out, float *ms = nullptr, LiftInfo *info = nullptr);
+// k_lifte.cu: the one-product lift (x_i = y_i mods p, y_{i+1} = (y_i - x_i)/p
+// - E x_i with E = (C A - I)/p); applies when n amax < 2^32 - 2.
+bool lift_e_applies(int64_t n, uint64_t amax);
+int launch_lift_e(const LiftArgs &a, const void *Anar, int abytes, int64_t ld, Workspace &ws,
+                  int *timed_out, float *ms, LiftInfo *info);
 
 // k_bignum.cu ---------------------------------------------------------------
 // Device big integers: little-endian uint32 limbs with an explicit length.

@@ -440,8 +440,9 @@ __device__ void ratrecon_body(const int64_t *__restrict__ z, int m, uint32_t p, 
     __syncthreads();
     // Every pass completes at least one Euclid step or one partial quotient
     // subtraction, each removing at least one bit from a or b; the bound
-    // below exceeds the total bit length of (a, b) with a wide margin.
-    const long max_iter = 4L * 32 * (m + 4) + 1000;
+    // below exceeds the total bit length of (a, b) with a wide margin (a has
+    // m + 1 digits, or alen when it is given: it can be much longer than b).
+    const long max_iter = 4L * 32 * ((ainit && alen > m ? alen : m) + 4) + 1000;
     for (long iter = 0; iter < max_iter; ++iter) {
         if (tid == 0) {
             const int la = S.la, lb = S.lb;

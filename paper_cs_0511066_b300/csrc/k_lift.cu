@@ -31,15 +31,17 @@
 //    products and sums are taken modulo 2^64 (wrapping) and multiplied by
 //    the inverse of p modulo 2^64 (exact division).
 //
-// Every wait is bounded (about two seconds of SM clock): a grid barrier or an
-// mbarrier that does not complete sets err, all warps leave, and the
-// producer first waits for the copies it has issued.
+// Every wait is bounded (lift_common.cuh): a grid barrier or an mbarrier
+// that does not complete sets err, all warps leave, and the producer first
+// waits for the copies it has issued.
 #include <algorithm>
 #include <cstdlib>
 
+#include <atomic>
 #include <mutex>
 
 #include "idet_internal.cuh"
+#include "lift_common.cuh"
 
 namespace idet {
 
@@ -50,27 +52,6 @@ constexpr int kConsumers = 31;  // warps 0..30
 constexpr int kConsThreads = kConsumers * 32;
 constexpr int kProducer = 31;   // warp 31
 constexpr int kRingMax = 16;
-constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
-
-struct GridBar {
-    unsigned int count;  // arrivals, monotone within one launch
-    int err;             // first failure: 1 grid barrier, 2 mbarrier time limit
-    int info[6];         // where it happened: block, warp, seq, slot, parity, it
-};
-
-// Record the first failure only.
-__device__ __forceinline__ void fail_once(GridBar *gb, int code, int warp, long long seq, int slot,
-                                          unsigned par, int it) {
-    if (atomicCAS(&gb->err, 0, code) == 0) {
-        gb->info[0] = blockIdx.x;
-        gb->info[1] = warp;
-        gb->info[2] = (int)seq;
-        gb->info[3] = slot;
-        gb->info[4] = (int)par;
-        gb->info[5] = it;
-    }
-}
-
 struct LiftGeom {
     int64_t ld;   // padded row length (multiple of 16)
     int64_t rpc;  // rows per CTA
@@ -79,127 +60,9 @@ struct LiftGeom {
     int keep;     // streamed rows per iteration copied with an L2 evict_last hint
 };
 
-__device__ __forceinline__ void cons_sync() {
-    asm volatile("bar.sync 1, %0;" ::"n"(kConsThreads) : "memory");
-}
+using namespace lift;
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-// Wait for the completion of the phase of parity `parity`; false after the
-// time limit or when another block has recorded an error.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, GridBar *gb,
-                                          long long seq = -1, int slot = -1, int it = -1) {
-    const uint32_t addr = smem_u32(bar);
-    const long long t0 = clock64();
-    for (unsigned i = 0;; ++i) {
-        uint32_t ok;
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            "selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(addr), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if ((i & 255) == 255) {
-            if (*((volatile int *)&gb->err)) return false;
-            if (clock64() - t0 > kWaitCycles) {
-                fail_once(gb, 2, threadIdx.x >> 5, seq, slot, parity, it);
-                return false;
-            }
-        }
-    }
-}
-
-// Wait until the producer has issued sequence number seq. An mbarrier parity
-// wait only tells the current phase from the previous one, so a consumer may
-// wait on a slot's barrier only once the copy it needs has been issued (the
-// slot's barrier is then at most one phase away from it).
-__device__ __forceinline__ bool wait_issued(const volatile unsigned int *issued, long long seq,
-                                            GridBar *gb, int slot, int it) {
-    const long long t0 = clock64();
-    for (unsigned i = 0; (long long)*issued <= seq; ++i) {
-        if ((i & 255) == 255) {
-            if (*((volatile int *)&gb->err)) return false;
-            if (clock64() - t0 > kWaitCycles) {
-                fail_once(gb, 4, threadIdx.x >> 5, seq, slot, 0, it);
-                return false;
-            }
-        }
-    }
-    return true;
-}
-
-// Bulk copy global -> shared completing on an mbarrier, with an L2 policy.
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
-                                         uint64_t *bar, uint64_t policy) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
-        "[%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
-        : "memory");
-}
-
-__device__ __forceinline__ uint64_t policy_evict_last() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
-__device__ __forceinline__ uint64_t policy_evict_first() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
-// Grid-wide barrier among the consumer warps of all CTAs: the b-th barrier
-// completes when count reaches b * gridDim.x.
-__device__ __forceinline__ bool grid_sync(GridBar *gb, unsigned target) {
-    cons_sync();
-    if (threadIdx.x == 0) {
-        // arrive with release semantics (cumulative over the consumer
-        // threads' writes ordered before it by the CTA barrier), poll with
-        // acquire loads and a short back-off
-        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&gb->count) : "memory");
-        volatile int *ve = &gb->err;
-        const long long t0 = clock64();
-        while (true) {
-            unsigned c;
-            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(c) : "l"(&gb->count) : "memory");
-            if (c >= target) break;
-            if (*ve) break;
-            if (clock64() - t0 > kWaitCycles) {
-                fail_once(gb, 1, 0, target, -1, 0, -1);
-                break;
-            }
-            __nanosleep(20);
-        }
-    }
-    cons_sync();
-    return *((volatile int *)&gb->err) == 0;
-}
-
-__device__ __forceinline__ int64_t warp_sum64(int64_t v) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
+__device__ __forceinline__ void cons_sync() { lift::cons_sync<kConsThreads>(); }
 
 // Four consecutive elements of a row of A.
 template <class TA> struct Quad;
@@ -258,7 +121,7 @@ __device__ __forceinline__ uint64_t dot_a(const typename Quad<TA>::V *__restrict
 template <class TA>
 __global__ void __launch_bounds__(kLiftThreads, 1)
 k_lift(LiftArgs a, const TA *__restrict__ Anar, LiftGeom g, int32_t *__restrict__ rm,
-       int32_t *__restrict__ xcur, GridBar *gb) {
+       int32_t *__restrict__ xcur, GridBar *gb, long long limit) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[kRingMax], empty[kRingMax];
     __shared__ int64_t s_z[kConsumers];
@@ -315,7 +178,7 @@ k_lift(LiftArgs a, const TA *__restrict__ Anar, LiftGeom g, int32_t *__restrict_
                 for (int k = 0; k < per_it; ++k, ++seq) {
                     const int slot = (int)(seq % g.S);
                     const unsigned par = (unsigned)((seq / g.S) & 1) ^ 1u;
-                    if (!mbar_wait(&empty[slot], par, gb, seq, slot, it)) {
+                    if (!mbar_wait(&empty[slot], par, gb, limit, seq, slot, it)) {
                         ok = false;
                         break;
                     }
@@ -334,24 +197,8 @@ k_lift(LiftArgs a, const TA *__restrict__ Anar, LiftGeom g, int32_t *__restrict_
                     s_issued = (unsigned int)(seq + 1);
                 }
             }
-            // no copy may be in flight when the CTA exits: wait for the last
-            // phase of every slot that was used
-            for (int s = 0; s < g.S && s < seq; ++s) {
-                const long long q = seq - 1 - ((seq - 1 - s) % g.S);
-                const uint32_t addr = smem_u32(&full[s]);
-                const unsigned par = (unsigned)((q / g.S) & 1);
-                const long long t0 = clock64();
-                while (true) {
-                    uint32_t done;
-                    asm volatile(
-                        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                        "selp.u32 %0, 1, 0, p;\n}\n"
-                        : "=r"(done)
-                        : "r"(addr), "r"(par)
-                        : "memory");
-                    if (done || clock64() - t0 > kWaitCycles) break;
-                }
-            }
+            // no copy may be in flight when the CTA exits
+            drain_ring(full, g.S, seq);
         }
         return;
     }
@@ -363,7 +210,7 @@ k_lift(LiftArgs a, const TA *__restrict__ Anar, LiftGeom g, int32_t *__restrict_
         rm[i] = red_bal(bi, M);
     }
     unsigned bar = 0;
-    if (!grid_sync(gb, (++bar) * G)) return;
+    if (!grid_sync<kConsThreads>(gb, (++bar) * G, limit)) return;
     long long seq_base = 0;
     bool fail = false;
 
@@ -388,8 +235,8 @@ k_lift(LiftArgs a, const TA *__restrict__ Anar, LiftGeom g, int32_t *__restrict_
             } else {
                 const long long seq = seq_base + (lr - kc);
                 const int slot = (int)(seq % g.S);
-                if (!wait_issued(&s_issued, seq, gb, slot, it) ||
-                    !mbar_wait(&full[slot], (unsigned)((seq / g.S) & 1), gb, seq, slot, it)) {
+                if (!wait_issued(&s_issued, seq, gb, limit, slot, it) ||
+                    !mbar_wait(&full[slot], (unsigned)((seq / g.S) & 1), gb, limit, seq, slot, it)) {
                     fail = true;
                     break;
                 }
@@ -415,7 +262,7 @@ k_lift(LiftArgs a, const TA *__restrict__ Anar, LiftGeom g, int32_t *__restrict_
             }
         }
         if (fail) fail_once(gb, 3, 0, -1, -1, 0, it);
-        if (!grid_sync(gb, (++bar) * G)) return;
+        if (!grid_sync<kConsThreads>(gb, (++bar) * G, limit)) return;
 
         // Phase 2: r <- (r - A x) / p on this CTA's rows.
         {
@@ -431,8 +278,8 @@ k_lift(LiftArgs a, const TA *__restrict__ Anar, LiftGeom g, int32_t *__restrict_
             } else {
                 const long long seq = seq_base + (lr - ka);
                 const int slot = (int)(seq % g.S);
-                if (!wait_issued(&s_issued, seq, gb, slot, it) ||
-                    !mbar_wait(&full[slot], (unsigned)((seq / g.S) & 1), gb, seq, slot, it)) {
+                if (!wait_issued(&s_issued, seq, gb, limit, slot, it) ||
+                    !mbar_wait(&full[slot], (unsigned)((seq / g.S) & 1), gb, limit, seq, slot, it)) {
                     fail = true;
                     break;
                 }
@@ -449,11 +296,12 @@ k_lift(LiftArgs a, const TA *__restrict__ Anar, LiftGeom g, int32_t *__restrict_
         }
         seq_base += nsA;
         if (fail) fail_once(gb, 3, 0, -1, -1, 0, it);
-        if (!grid_sync(gb, (++bar) * G)) return;
+        if (!grid_sync<kConsThreads>(gb, (++bar) * G, limit)) return;
     }
 }
 
-std::mutex g_coop_mu;
+std::atomic<long long> g_wait_cycles{0};
+
 
 template <class TA>
 int launch_lift_t(const LiftArgs &a0, const void *Anar, int64_t ld, Workspace &ws,
@@ -527,7 +375,9 @@ int launch_lift_t(const LiftArgs &a0, const void *Anar, int64_t ld, Workspace &w
         return IDET_ERR_INTERNAL;
     }
     const TA *Ap = (const TA *)Anar;
-    void *args[] = {(void *)&a, (void *)&Ap, (void *)&g, (void *)&rm, (void *)&xcur, (void *)&gb};
+    long long limit = lift_wait_cycles();
+    void *args[] = {(void *)&a,    (void *)&Ap, (void *)&g,    (void *)&rm,
+                    (void *)&xcur, (void *)&gb, (void *)&limit};
     EventPair ev;
     if (ms) {
         IDET_CUDA_TRY(cudaEventCreate(&ev.a));
@@ -562,15 +412,63 @@ int launch_lift_t(const LiftArgs &a0, const void *Anar, int64_t ld, Workspace &w
 
 }  // namespace
 
-int launch_lift(const LiftArgs &a, const void *Anar, int abytes, int64_t ld, Workspace &ws,
-                int *timed_out, float *ms) {
-    if (ld % 16 != 0) {
-        set_last_error("lift: leading dimension must be a multiple of 16");
-        return IDET_ERR_INTERNAL;
-    }
+std::mutex g_coop_mu;
+
+long long lift_wait_cycles() {
+    const long long v = g_wait_cycles.load(std::memory_order_relaxed);
+    return v > 0 ? v : lift::kDefaultWaitCycles;
+}
+
+static int launch_lift_classic(const LiftArgs &a, const void *Anar, int abytes, int64_t ld,
+                               Workspace &ws, int *timed_out, float *ms) {
     if (abytes == 1) return launch_lift_t<int8_t>(a, Anar, ld, ws, timed_out, ms);
     if (abytes == 2) return launch_lift_t<int16_t>(a, Anar, ld, ws, timed_out, ms);
     return launch_lift_t<int32_t>(a, Anar, ld, ws, timed_out, ms);
 }
 
+int launch_lift(const LiftArgs &a, const void *Anar, int abytes, int64_t ld, Workspace &ws,
+                int *timed_out, float *ms, LiftInfo *info) {
+    if (ld % 16 != 0) {
+        set_last_error("lift: leading dimension must be a multiple of 16");
+        return IDET_ERR_INTERNAL;
+    }
+    if (lift_e_applies(a.n, a.amax)) return launch_lift_e(a, Anar, abytes, ld, ws, timed_out, ms, info);
+    // the two-product kernel, once per right-hand side
+    float t0 = 0, t1 = 0;
+    int to0 = 0, to1 = 0;
+    int64_t *r_tmp = nullptr;
+    LiftArgs a0 = a;
+    if (!a0.r) {
+        IDET_TRY(ws.alloc_n(&r_tmp, a.n));
+        a0.r = r_tmp;
+    }
+    IDET_TRY(launch_lift_classic(a0, Anar, abytes, ld, ws, &to0, ms || info ? &t0 : nullptr));
+    if (a.nrhs == 2 && to0 == 0) {
+        LiftArgs a1 = a;
+        a1.b = a.b2;
+        a1.digits = a.digits2;
+        a1.zproj = a.zproj2;
+        a1.r = a.r2 ? a.r2 : r_tmp;
+        if (!a1.r) {
+            IDET_TRY(ws.alloc_n(&r_tmp, a.n));
+            a1.r = r_tmp;
+        }
+        IDET_TRY(launch_lift_classic(a1, Anar, abytes, ld, ws, &to1, ms || info ? &t1 : nullptr));
+    }
+    if (timed_out) *timed_out = to0 ? to0 : to1;
+    if (ms) *ms = t0 + t1;
+    if (info) {
+        info->path = 0;
+        info->steps = a.m * (a.nrhs == 2 ? 2 : 1);
+        info->ms_setup = 0;
+        info->ms_steps = t0 + t1;
+        info->bytes = (double)info->steps * (4.0 + abytes) * (double)a.n * (double)a.n;
+    }
+    return IDET_OK;
+}
+
 }  // namespace idet
+
+extern "C" void idet_set_wait_limit(int64_t cycles) {
+    idet::g_wait_cycles.store(cycles > 0 ? (long long)cycles : 0, std::memory_order_relaxed);
+}

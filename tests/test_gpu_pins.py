@@ -258,3 +258,71 @@ def test_wrong_residue_is_caught_at_the_bound():
         assert e.value.code == 7, kw
     assert idet.int_det(A, certify=True) == want
     assert idet.int_det(A) == want
+
+
+# --- the lift: one-product kernel, block lift, bounded waits -----------------------
+
+@pytest.mark.parametrize("n,lo,hi,m", [(5, -100, 100, 4), (67, -100, 100, 5), (300, 0, 255, 3),
+                                       (1100, -(1 << 20), 1 << 20, 2)])
+def test_block_lift_two_rhs_matches_oracle(n, lo, hi, m):
+    """Two right-hand sides lifted in one pass (the block lift): both digit
+    sequences and both residuals equal the oracle's Dixon iteration run on
+    each right-hand side alone; the stepping kernel reads the lifting matrix
+    once per step for both (the same algorithmic bytes as one vector)."""
+    A = workloads.dense_uniform(n, lo, hi, seed=n + 3)
+    B = np.stack([workloads.random_rhs(n, 1 << 61, seed=n + 4),
+                  workloads.random_rhs(n, 1 << 30, seed=n + 5)])
+    p = p31(1, n + 6)[0]
+    dg, r, st = idet.dixon_digits_block(A, B, p, m, return_stats=True)
+    for k in range(2):
+        odg, orr = dixon.dixon_digits(A, B[k], p, m)
+        assert dg[k].tolist() == odg and r[k].tolist() == orr
+    _, _, st1 = idet.dixon_digits_block(A, B[:1], p, m, return_stats=True)
+    assert st["lift_path"] == 1 and st["lift_bytes"] == st1["lift_bytes"] == (m - 1) * 4 * n * n
+
+
+def test_lift_one_product_and_two_product_kernels_agree(monkeypatch):
+    """The one-product kernel (E = (C A - I)/p) and the two-product kernel (C
+    and A every step) produce the same digits; entries of 32 bits make n
+    max|a| exceed 2^32, where only the two-product kernel applies."""
+    n, m = 700, 4
+    A = workloads.dense_pm2p20(n, seed=31)
+    B = np.stack([workloads.random_rhs(n, 1 << 50, seed=32), workloads.random_rhs(n, 9, seed=33)])
+    p = p31(1, 34)[0]
+    d1, r1, s1 = idet.dixon_digits_block(A, B, p, m, return_stats=True)
+    monkeypatch.setenv("IDET_LIFT_PATH", "classic")
+    d0, r0, s0 = idet.dixon_digits_block(A, B, p, m, return_stats=True)
+    monkeypatch.delenv("IDET_LIFT_PATH")
+    assert (s1["lift_path"], s0["lift_path"]) == (1, 0)
+    assert (d1 == d0).all() and (r1 == r0).all()
+    W = _int32_edges(40, 35)
+    b = workloads.random_rhs(40, 1 << 40, seed=36)
+    dg, r, st = idet.dixon_digits_block(W, b[None, :], p, 3, return_stats=True)
+    odg, orr = dixon.dixon_digits(W, b, p, 3)
+    assert st["lift_path"] == 0 and dg[0].tolist() == odg and r[0].tolist() == orr
+
+
+def test_lift_wait_limit_runs_out_and_recovers():
+    """A bounded wait that runs out (the limit lowered to one cycle) ends the
+    lifting kernel cleanly: the call returns IDET_ERR_TIMEOUT with
+    lift_timed_out set, and the next call with the default limit succeeds."""
+    torch = pytest.importorskip("torch")
+    A = torch.from_numpy(workloads.dense_pm2p20(4000, seed=2)).cuda()
+    b = workloads.random_rhs(4000, 1 << 40, seed=3)
+    p = 2147483629
+    try:
+        idet.set_wait_limit(1)
+        with pytest.raises(idet.IdetError) as e:
+            idet.dixon_digits(A, b, p, 8)
+        assert e.value.code == 5
+        with pytest.raises(idet.IdetError) as e:
+            idet.int_det(A)
+        assert e.value.code == 5 and e.value.stats["lift_timed_out"] != 0
+    finally:
+        idet.set_wait_limit(0)
+    dg, r = idet.dixon_digits(A, b, p, 3)
+    X = np.zeros(4000, dtype=object)
+    for i in range(2, -1, -1):
+        X = X * p + dg[i].astype(object)
+    An = workloads.dense_pm2p20(4000, seed=2).astype(object)
+    assert (An.dot(X) + (p ** 3) * r.astype(object) == b.astype(object)).all()

@@ -44,6 +44,21 @@ def peaks():
         return 6400.0, "fallback"
 
 
+def peaks_bf16():
+    """Measured dense bf16 GEMM throughput (burst), TFLOP/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1800.0, "fallback"
+
+
+# DRAM bytes per step of the one-product lifting kernel at n = 4000, read and
+# written, from an ncu capture (profiles/k_lift_e_dense_pm2p20_n4000.md);
+# None until one is taken.
+LIFT_E_DRAM_BYTES_PER_STEP = None
+
+
 def max_over_ranks(ms, dist, device):
     """The slowest rank's time per step (every rank's work counts, so the
     whole job takes as long as its slowest rank)."""
@@ -154,12 +169,19 @@ def cpu_baseline(seconds_budget=25.0):
 
 
 def run_reference(args):
+    """The oracle on the host cores: one bounded sample of the workload (a
+    full step, two certified CPU determinants, takes hours), extrapolated to
+    one step. steps/warmup report what ran: one sample pass, no warm-up."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    t0 = time.perf_counter()
     cb = cpu_baseline()
+    wall = time.perf_counter() - t0
     line = {"impl": "reference", "metric": "exact dets/s", "value": cb["value"],
-            "unit": "dets/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "unit": "dets/s", "n_gpus": args.gpus, "steps": 1, "warmup": 0,
+            "extrapolated": True, "sample_wall_s": round(wall, 2),
+            "requested": {"steps": args.steps, "warmup": args.warmup},
             "ms_per_step": 2000.0 / cb["value"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": WORKLOAD}, "cpu_baseline": cb,
@@ -663,22 +685,27 @@ def main():
     d2h = sum(4 * (int(abs(d)).bit_length() // 32 + 1) for d, _ in stats[:len(mats)])
 
     # roofline of the dominant kernel: the lifting kernel's n = 4000 launch
-    # (algorithmic bytes m * 8 n^2 over its CUDA-event time, per launch)
+    # (algorithmic bytes: the lifting matrix read once per step, over its
+    # CUDA-event time, per launch)
     hbm, src = peaks()
     big = [st for d, st in stats if st["lift_iters"] == max(s2["lift_iters"] for _, s2 in stats)]
     lift_ms = sum(st["ms_lift_kernel"] for st in big) / len(big)
     lift_bytes = sum(st["lift_bytes"] for st in big) / len(big)
     achieved = lift_bytes / (lift_ms / 1000.0) / 1e9
-    # DRAM traffic of the same kernel from its ncu capture (64 lifting steps
-    # at n = 4000: 3.096 GB read + 3.3 MB written), scaled by the steps
-    traffic = (3.095984e9 + 3.312896e6) / 64 * big[0]["lift_iters"]
+    one_product = big[0].get("lift_path", 0) == 1
+    # DRAM traffic of the kernel per launch, from an ncu capture of the same
+    # kernel at n = 4000 scaled by its steps (None until one is taken)
+    traffic = LIFT_E_DRAM_BYTES_PER_STEP * (big[0]["lift_iters"] - 1) \
+        if one_product and LIFT_E_DRAM_BYTES_PER_STEP else None
     lu_ms = sum(st["ms_lu"] for _, st in stats)
     lu_macs = sum(st["lu_macs"] for _, st in stats)
+    bf16_peak, bf16_src = peaks_bf16()
     per_mat = [{"n": int(mats[i % len(mats)].shape[0]),
                 "ms_total": round(st["ms_total"], 2), "ms_lu": round(st["ms_lu"], 2),
                 "ms_lift": round(st["ms_lift"], 2), "ms_lift_kernel": round(st["ms_lift_kernel"], 2),
                 "ms_cra": round(st["ms_cra"], 2), "ms_inverse": round(st["ms_inverse"], 2),
-                "ms_rr": round(st["ms_rr"], 2), "primes": st["primes_used"],
+                "ms_rr": round(st["ms_rr"], 2), "ms_lift_setup": round(st.get("ms_lift_setup", 0), 2),
+                "lift_path": st.get("lift_path", 0), "primes": st["primes_used"],
                 "lift_iters": st["lift_iters"], "log2_K": st["log2_K"]}
                for i, (_, st) in enumerate(stats[:len(mats)])]
     line = {
@@ -691,10 +718,23 @@ def main():
         "e2e": {"value": dets_per_step / e2e_s, "unit": "dets/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
-        "roofline": {"kernel": "k_lift (n=4000 launch)", "bound": "hbm", "achieved": achieved,
+        "roofline": {"kernel": ("k_lift_e" if one_product else "k_lift") + " (n=4000 launch)",
+                     "bound": "hbm", "achieved": achieved,
                      "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
-                     "algorithmic_bytes": lift_bytes, "peak_source": src},
+                     "algorithmic_bytes": lift_bytes, "peak_source": src,
+                     "bytes_per_step": "4 n^2 (E, int32)" if one_product else "8 n^2 (C and A)"},
         "modular_lu_gops": lu_macs / (lu_ms / 1000.0) / 1e9 if lu_ms > 0 else None,
+        # the multi-prime LU as a whole (reduction, panels, triangular solves
+        # and the tcgen05 trailing updates): its modular MACs as the bf16 limb
+        # products the tensor cores would issue for them (9 per MAC with three
+        # 7-bit limbs, 2 flops each) over its time, against the measured bf16
+        # GEMM peak
+        "lu_roofline": {"bound": "tensor", "unit": "TFLOP/s",
+                        "achieved": lu_macs * 9 * 2 / (lu_ms / 1000.0) / 1e12 if lu_ms > 0 else None,
+                        "peak": bf16_peak, "peak_source": bf16_src,
+                        "frac": (lu_macs * 9 * 2 / (lu_ms / 1000.0) / 1e12) / bf16_peak
+                        if lu_ms > 0 else None,
+                        "modular_macs": lu_macs, "ms": lu_ms},
         "per_matrix": per_mat,
         "clocks": clk.summary(),
     }

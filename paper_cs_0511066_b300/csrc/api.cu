@@ -1505,6 +1505,107 @@ static int lif_common(DetJob &J, const int64_t *b_dev, const std::vector<int64_t
     return solve_and_denominator(J, b_dev, bh, ud, std::log2(std::max(u1, 1.0)), lr);
 }
 
+// A positive integer given by dlen radix-p digits on the device, written to
+// out as base-2^32 limbs.
+static int radix_to_int(Workspace &ws, const uint32_t *D, int dlen, uint32_t p, idet_int *out) {
+    cudaStream_t s = ws.stream();
+    const int bcap = dlen + 2;
+    uint32_t *Db = nullptr;
+    int32_t *len = nullptr;
+    IDET_TRY(ws.alloc_n(&Db, bcap));
+    IDET_TRY(ws.alloc_n(&len, 1));
+    IDET_TRY(launch_radix_to_binary(D, dlen, p, Db, bcap, len, s));
+    int32_t bl = 0;
+    IDET_CUDA_TRY(cudaMemcpyAsync(&bl, len, 4, cudaMemcpyDeviceToHost, s));
+    IDET_CUDA_TRY(cudaStreamSynchronize(s));
+    std::vector<uint32_t> host(bl > 0 ? bl : 1);
+    if (bl > 0)
+        IDET_CUDA_TRY(cudaMemcpyAsync(host.data(), Db, 4 * (size_t)bl, cudaMemcpyDeviceToHost, s));
+    IDET_CUDA_TRY(cudaStreamSynchronize(s));
+    return write_int(out, 1, host.data(), (uint32_t)bl);
+}
+
+// The exact lcm D of the denominators of the entries of x, from its lifting
+// digits (m x n, balanced) and their projections z_i = u . x_i (Section 2.2,
+// s~_n for one right-hand side): the denominator of u . x by rational
+// reconstruction (numerator below p^hN, denominator below p^hD), then every
+// entry whose D x_j is not an integer (numerator bound p^hNe) is
+// reconstructed itself and D replaced by lcm(D, d_j). *Dout: device buffer of
+// radix-p digits (workspace), *dlen its length.
+static int lcm_of_denominators(const int32_t *dig, int64_t n, int m, uint32_t p, const int64_t *z,
+                               int hN, int hNe, int hD, Workspace &ws, uint32_t **Dout,
+                               int *dlen_out) {
+    cudaStream_t s = ws.stream();
+    const int dcap = hD + 4;
+    uint32_t *D = nullptr, *Dn = nullptr, *dj = nullptr, *cof = nullptr;
+    int32_t *info = nullptr, *flags = nullptr, *len = nullptr;
+    int64_t *zj = nullptr;
+    IDET_TRY(ws.alloc_n(&D, dcap));
+    IDET_TRY(ws.alloc_n(&Dn, dcap));
+    IDET_TRY(ws.alloc_n(&dj, dcap));
+    IDET_TRY(ws.alloc_n(&cof, dcap));
+    IDET_TRY(ws.alloc_n(&info, 4));
+    IDET_TRY(ws.alloc_n(&len, 1));
+    IDET_TRY(ws.alloc_n(&flags, n));
+    IDET_TRY(ws.alloc_n(&zj, m));
+    int32_t hi[2] = {0, 0};
+    IDET_TRY(launch_ratrecon(z, m, p, hN, hD, D, dcap, info, ws));
+    IDET_CUDA_TRY(cudaMemcpyAsync(hi, info, 8, cudaMemcpyDeviceToHost, s));
+    IDET_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hi[0] != 0) {
+        set_last_error("rational reconstruction of the projection failed (code %d)", hi[0]);
+        return IDET_ERR_INTERNAL;
+    }
+    int dlen = hi[1];
+    // every entry integral under D?  else D <- lcm(D, den(x_j))
+    std::vector<int32_t> fl(n);
+    for (int round = 0;; ++round) {
+        if (round > 64) {
+            set_last_error("largest invariant factor: too many denominator updates");
+            return IDET_ERR_INTERNAL;
+        }
+        IDET_TRY(launch_lif_check(dig, n, m, D, dlen, p, hNe, flags, s));
+        IDET_CUDA_TRY(cudaMemcpyAsync(fl.data(), flags, 4 * (size_t)n, cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        int64_t bad = -1;
+        for (int64_t j = 0; j < n && bad < 0; ++j)
+            if (fl[j]) bad = j;
+        if (bad < 0) break;
+        // d_j = den(x_j) by reconstruction of X_j
+        IDET_TRY(launch_gather_col(dig, n, m, bad, zj, s));
+        IDET_TRY(launch_ratrecon(zj, m, p, hNe, hD, dj, dcap, info, ws));
+        IDET_CUDA_TRY(cudaMemcpyAsync(hi, info, 8, cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hi[0] != 0) {
+            set_last_error("rational reconstruction of an entry failed (code %d)", hi[0]);
+            return IDET_ERR_INTERNAL;
+        }
+        const int djlen = hi[1];
+        // D / gcd(D, d_j): cofactor of d_j at the zero remainder of Euclid(D, d_j)
+        std::vector<uint32_t> djh(djlen);
+        IDET_CUDA_TRY(cudaMemcpyAsync(djh.data(), dj, 4 * (size_t)djlen, cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        std::vector<int64_t> djz(djh.begin(), djh.end());
+        IDET_CUDA_TRY(cudaMemcpyAsync(zj, djz.data(), 8 * (size_t)djlen, cudaMemcpyHostToDevice, s));
+        IDET_TRY(launch_ratrecon(zj, djlen, p, 0, dcap, cof, dcap, info, ws, D, dlen));
+        IDET_CUDA_TRY(cudaMemcpyAsync(hi, info, 8, cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hi[0] != 0) {
+            set_last_error("gcd of denominators failed (code %d)", hi[0]);
+            return IDET_ERR_INTERNAL;
+        }
+        IDET_TRY(launch_mul_radix(dj, djlen, cof, hi[1], p, Dn, dcap, len, s));
+        int32_t nl = 0;
+        IDET_CUDA_TRY(cudaMemcpyAsync(&nl, len, 4, cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        std::swap(D, Dn);
+        dlen = nl;
+    }
+    *Dout = D;
+    *dlen_out = dlen;
+    return IDET_OK;
+}
+
 int idet_largest_invariant_factor(const int64_t *A, int64_t n, int64_t lda, const int64_t *b,
                                   int32_t on_device, const idet_opts *opts, void *stream,
                                   idet_int *sout) {
@@ -1600,85 +1701,10 @@ int idet_largest_invariant_factor(const int64_t *A, int64_t n, int64_t lda, cons
     la.amax = J.amax;
     int to = 0;
     IDET_TRY(launch_lift(la, J.Anar, J.abytes, J.ldl, ws, &to));
-    // candidate D from the projection
-    const int dcap = hD + 4;
-    uint32_t *D = nullptr, *Dn = nullptr, *dj = nullptr, *cof = nullptr;
-    int32_t *info = nullptr, *flags = nullptr, *len = nullptr;
-    int64_t *zj = nullptr;
-    IDET_TRY(ws.alloc_n(&D, dcap));
-    IDET_TRY(ws.alloc_n(&Dn, dcap));
-    IDET_TRY(ws.alloc_n(&dj, dcap));
-    IDET_TRY(ws.alloc_n(&cof, dcap));
-    IDET_TRY(ws.alloc_n(&info, 4));
-    IDET_TRY(ws.alloc_n(&len, 1));
-    IDET_TRY(ws.alloc_n(&flags, n));
-    IDET_TRY(ws.alloc_n(&zj, m));
-    int32_t hi[2] = {0, 0};
-    IDET_TRY(launch_ratrecon(z, m, p, hN, hD, D, dcap, info, ws));
-    IDET_CUDA_TRY(cudaMemcpyAsync(hi, info, 8, cudaMemcpyDeviceToHost, s));
-    IDET_CUDA_TRY(cudaStreamSynchronize(s));
-    if (hi[0] != 0) {
-        set_last_error("rational reconstruction of the projection failed (code %d)", hi[0]);
-        return IDET_ERR_INTERNAL;
-    }
-    int dlen = hi[1];
-    // every entry integral under D?  else D <- lcm(D, den(x_j))
-    std::vector<int32_t> fl(n);
-    for (int round = 0;; ++round) {
-        if (round > 64) {
-            set_last_error("largest invariant factor: too many denominator updates");
-            return IDET_ERR_INTERNAL;
-        }
-        IDET_TRY(launch_lif_check(dig, n, m, D, dlen, p, hNe, flags, s));
-        IDET_CUDA_TRY(cudaMemcpyAsync(fl.data(), flags, 4 * (size_t)n, cudaMemcpyDeviceToHost, s));
-        IDET_CUDA_TRY(cudaStreamSynchronize(s));
-        int64_t bad = -1;
-        for (int64_t j = 0; j < n && bad < 0; ++j)
-            if (fl[j]) bad = j;
-        if (bad < 0) break;
-        // d_j = den(x_j) by reconstruction of X_j
-        IDET_TRY(launch_gather_col(dig, n, m, bad, zj, s));
-        IDET_TRY(launch_ratrecon(zj, m, p, hNe, hD, dj, dcap, info, ws));
-        IDET_CUDA_TRY(cudaMemcpyAsync(hi, info, 8, cudaMemcpyDeviceToHost, s));
-        IDET_CUDA_TRY(cudaStreamSynchronize(s));
-        if (hi[0] != 0) {
-            set_last_error("rational reconstruction of an entry failed (code %d)", hi[0]);
-            return IDET_ERR_INTERNAL;
-        }
-        const int djlen = hi[1];
-        // D / gcd(D, d_j): cofactor of d_j at the zero remainder of Euclid(D, d_j)
-        std::vector<uint32_t> djh(djlen);
-        IDET_CUDA_TRY(cudaMemcpyAsync(djh.data(), dj, 4 * (size_t)djlen, cudaMemcpyDeviceToHost, s));
-        IDET_CUDA_TRY(cudaStreamSynchronize(s));
-        std::vector<int64_t> djz(djh.begin(), djh.end());
-        IDET_CUDA_TRY(cudaMemcpyAsync(zj, djz.data(), 8 * (size_t)djlen, cudaMemcpyHostToDevice, s));
-        IDET_TRY(launch_ratrecon(zj, djlen, p, 0, dcap, cof, dcap, info, ws, D, dlen));
-        IDET_CUDA_TRY(cudaMemcpyAsync(hi, info, 8, cudaMemcpyDeviceToHost, s));
-        IDET_CUDA_TRY(cudaStreamSynchronize(s));
-        if (hi[0] != 0) {
-            set_last_error("gcd of denominators failed (code %d)", hi[0]);
-            return IDET_ERR_INTERNAL;
-        }
-        IDET_TRY(launch_mul_radix(dj, djlen, cof, hi[1], p, Dn, dcap, len, s));
-        int32_t nl = 0;
-        IDET_CUDA_TRY(cudaMemcpyAsync(&nl, len, 4, cudaMemcpyDeviceToHost, s));
-        IDET_CUDA_TRY(cudaStreamSynchronize(s));
-        std::swap(D, Dn);
-        dlen = nl;
-    }
-    // D -> base 2^32
-    const int bcap = dlen + 2;
-    uint32_t *Db = nullptr;
-    IDET_TRY(ws.alloc_n(&Db, bcap));
-    IDET_TRY(launch_radix_to_binary(D, dlen, p, Db, bcap, len, s));
-    int32_t bl = 0;
-    IDET_CUDA_TRY(cudaMemcpyAsync(&bl, len, 4, cudaMemcpyDeviceToHost, s));
-    IDET_CUDA_TRY(cudaStreamSynchronize(s));
-    std::vector<uint32_t> host(bl > 0 ? bl : 1);
-    if (bl > 0)
-        IDET_CUDA_TRY(cudaMemcpyAsync(host.data(), Db, 4 * (size_t)bl, cudaMemcpyDeviceToHost, s));
-    IDET_CUDA_TRY(cudaStreamSynchronize(s));
-    return write_int(sout, 1, host.data(), (uint32_t)bl);
+    uint32_t *D = nullptr;
+    int dlen = 0;
+    IDET_TRY(lcm_of_denominators(dig, n, m, p, z, hN, hNe, hD, ws, &D, &dlen));
+    return radix_to_int(ws, D, dlen, p, sout);
 }
 
 // ---------------------------------------------------------------------------

@@ -373,7 +373,8 @@ __device__ int cmp_big(const uint32_t *x, int lx, const uint32_t *y, int ly) {
     return 0;
 }
 
-// For a >= b > 0: c in [1, 2^29) and a digit shift sh with c * b * p^sh <= a.
+// For a >= b > 0: c in [1, 2^29) and a digit shift sh with c * b * p^sh <= a,
+// removing at least a quarter of a's leading digit.
 __device__ void exact_step(const uint32_t *a, int la, const uint32_t *b, int lb, uint32_t p,
                            uint64_t &q, int &sh) {
     uint64_t c;
@@ -387,6 +388,14 @@ __device__ void exact_step(const uint32_t *a, int la, const uint32_t *b, int lb,
         const uint64_t btop = (uint64_t)b[lb - 1] + 1;
         c = atop / btop;
         s = la - 1 - lb;
+        // A quotient estimate far above the clamp (a small top digit of b,
+        // up to 2^61) would make the clamped subtraction remove only a
+        // sliver of a: take it one digit higher, c / p (still c b p^s <= a),
+        // so that every step removes at least a quarter of a's top digit.
+        if (c >= (1ull << 29) && c / p >= 1) {
+            c /= p;
+            s += 1;
+        }
     } else {  // la == lb >= 2
         const uint64_t atop = top2(a, la, la - 2, p);
         const uint64_t btop = top2(b, lb, lb - 2, p) + 1;

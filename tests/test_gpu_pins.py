@@ -326,3 +326,18 @@ def test_lift_wait_limit_runs_out_and_recovers():
         X = X * p + dg[i].astype(object)
     An = workloads.dense_pm2p20(4000, seed=2).astype(object)
     assert (An.dot(X) + (p ** 3) * r.astype(object) == b.astype(object)).all()
+
+
+def test_lif_completion_with_long_denominators_matches_oracle():
+    """Entry-by-entry completion of the denominator when the numbers span many
+    radix-p digits: entries near 2^20 and scaled columns (a factor 2^k that a
+    random projection misses about half of the time), so that lcm(D, d_j) is
+    formed by the extended Euclidean algorithm on numbers of a hundred digits
+    whose leading digits differ widely."""
+    for seed in range(3):
+        A = workloads.dense_pm2p20(120, seed=300 + seed)
+        A[:, 0] *= 8
+        A[:, 1] *= 2
+        b = workloads.random_rhs(120, 1 << 30, seed=seed)
+        assert idet.largest_invariant_factor(A, b) == exact.largest_invariant_factor(
+            A.tolist(), b.tolist())

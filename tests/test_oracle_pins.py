@@ -470,3 +470,65 @@ def test_et_stopping_one_prime_early_exceeds_the_bound(monkeypatch):
     real = cra.on_the_fly_bound
     monkeypatch.setattr(cra, "on_the_fly_bound", lambda Rp, k, P, i: real(Rp, k + 1, P, i + 1))
     assert _false_stop_rate(0.05) > 0.05
+
+
+# --- Extended bonus (Section 3.2): pi~_k = s~^k / gcd(det(R N), s~^k) --------------
+
+def test_extended_bonus_closed_form_diagonal():
+    """A = diag(1, .., 1, a, b) with a | b has Smith form A itself, so the two
+    largest invariant factors are a and b. With B = [e_{n-2}, e_{n-1}] and R
+    selecting the same two rows, X = [e_{n-2}/a, e_{n-1}/b], s~ = b,
+    N = s~ X, R N = diag(b/a, 1): pi~_2 = b^2 / gcd(b/a, b^2) = a b exactly."""
+    from oracle import bonus
+    n, a, b = 6, 6, 60
+    A = [[(a if i == n - 2 else b if i == n - 1 else 1) if i == j else 0 for j in range(n)]
+         for i in range(n)]
+    e = lambda i: [int(j == i) for j in range(n)]
+    pi, s = bonus.extended_bonus(A, [e(n - 2), e(n - 1)], [e(n - 2), e(n - 1)])
+    assert (pi, s) == (a * b, b)
+    pi1, s1 = bonus.extended_bonus(A, [e(n - 1)], [e(n - 1)])
+    assert (pi1, s1) == (b, b)
+
+
+def _smith_engineered(d, seed):
+    """U diag(d) V with random unimodular U, V: Smith form diag(d) when d is a
+    divisibility chain."""
+    n = len(d)
+    r = random.Random(seed)
+
+    def unimodular():
+        U = [[int(i == j) for j in range(n)] for i in range(n)]
+        for _ in range(3 * n):
+            i, j = r.sample(range(n), 2)
+            c = r.choice([-2, -1, 1, 2])
+            U[i] = [x + c * y for x, y in zip(U[i], U[j])]
+        return U
+
+    D = [[d[i] if i == j else 0 for j in range(n)] for i in range(n)]
+    return exact.matmul(exact.matmul(unimodular(), D), unimodular())
+
+
+def test_extended_bonus_divides_and_usually_equals_pi_k():
+    """Lemmas 3.5 and 3.6: pi~_k always divides pi_k, the product of the k
+    largest invariant factors (checked on a chain with the small primes 2, 3,
+    5, which random determinants often share); when the invariant factors are
+    products of large primes, random B and R give pi~_k = pi_k except with
+    probability about k / 1000 per prime (Lemma 3.7's under-estimation comes
+    from primes dividing det(R N) by chance)."""
+    from oracle import bonus
+    for d, need in (([1, 1, 1, 1, 2, 6, 12, 60], 0),
+                    ([1, 1, 1, 1009, 1009 * 1013, 1009 * 1013 * 1019], 10)):
+        n = len(d)
+        hits = {1: 0, 2: 0, 3: 0}
+        trials = 12
+        for t in range(trials):
+            A = _smith_engineered(d, 100 + t)
+            r = random.Random(200 + t)
+            for k in (1, 2, 3):
+                B = [[r.randint(-(1 << 20), 1 << 20) for _ in range(n)] for _ in range(k)]
+                R = [[r.randint(-(1 << 20), 1 << 20) for _ in range(n)] for _ in range(k)]
+                pi, s = bonus.extended_bonus(A, B, R)
+                pik = math.prod(d[n - k:])
+                assert pik % pi == 0 and d[-1] % s == 0
+                hits[k] += pi == pik
+        assert min(hits.values()) >= need, (d, hits)

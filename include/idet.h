@@ -88,7 +88,12 @@ typedef struct {
                               adds 1 to det(A) mod p for the k-th CRA prime
                               factored (idet_int_det, idet_int_det_mp), a
                               wrong modular determinant made on the host    */
-    int32_t reserved[5];
+    int32_t i_max;         /* idet_int_det, lif = 1: solves of Alg. 4.1's
+                              inner loop. 0 or 1: one solve (K = s~_n);
+                              2: two solves in one block lift and the
+                              extended bonus of Section 3.2, K = lcm(s~_n,
+                              pi~_2) (the i_max = 2 column of Table 1)    */
+    int32_t reserved[4];
 } idet_opts;
 
 typedef struct {
@@ -256,6 +261,22 @@ int idet_dixon_digits_block(const int64_t *A, int64_t n, int64_t lda,
 int idet_crt_symmetric(const uint32_t *residues, const uint32_t *primes,
                        int32_t count, void *stream, idet_int *r,
                        int32_t *trailing);
+
+/*
+ * The extended bonus of Section 3.2 for k = 2 right-hand sides: with
+ * X = A^{-1} B, s~ the lcm of the denominators of the entries of X (Section
+ * 2.2), N = s~ X and a 2 x n matrix R,
+ *     pi~_2 = s~^2 / gcd(det(R N), s~^2),
+ * a factor of s_n s_{n-1}, the product of the two largest invariant factors
+ * of A (Lemma 3.5). B and R are host arrays of two rows of n int64 each
+ * (|b|, |r| < 2^62); A follows the conventions (on_device applies to A
+ * only). Both solves run as one block lift; det(R N) comes from the p-adic
+ * digits, the lift being long enough that p^m > 2 |det(R N)|. pi receives
+ * pi~_2 and s_tilde receives s~. IDET_ERR_SINGULAR if A is singular.
+ */
+int idet_extended_bonus(const int64_t *A, int64_t n, int64_t lda, const int64_t *B,
+                        const int64_t *R, int32_t on_device, const idet_opts *opts, void *stream,
+                        idet_int *pi, idet_int *s_tilde);
 
 /*
  * Alg. 2.1's loop (Section 2.1) run over a given stream of modular

@@ -47,7 +47,8 @@ class idet_opts(ctypes.Structure):
                 ("certify", ctypes.c_int32), ("update_path", ctypes.c_int32),
                 ("nb", ctypes.c_int32), ("wave", ctypes.c_int32),
                 ("lif", ctypes.c_int32), ("prime_bits", ctypes.c_int32),
-                ("inject_fault", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("inject_fault", ctypes.c_int32), ("i_max", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class idet_stats(ctypes.Structure):
@@ -239,7 +240,8 @@ def _call_int(fn, *args, cap: int = 1 << 12):
 def int_det(A, *, certify: bool = False, seed: int | None = None, lif: bool | int = True,
             update_path: int | None = None, nb: int | None = None, wave: int | None = None,
             log2_epsilon: float | None = None, prime_bits: int | None = None, stream=None,
-            inject_fault: int | None = None, return_stats: bool = False):
+            inject_fault: int | None = None, i_max: int | None = None,
+            return_stats: bool = False):
     """det(A) as a Python int (idet_int_det). inject_fault (tests of failure
     detection only): 1-based index of a CRA prime whose modular determinant
     is made wrong on the host."""
@@ -247,7 +249,7 @@ def int_det(A, *, certify: bool = False, seed: int | None = None, lif: bool | in
     ptr, n, lda, dev, keep = _matrix(A)
     o = default_opts(certify=int(certify), seed=seed, lif=int(lif), update_path=update_path,
                      nb=nb, wave=wave, log2_epsilon=log2_epsilon, prime_bits=prime_bits,
-                     inject_fault=inject_fault)
+                     inject_fault=inject_fault, i_max=i_max)
     st = idet_stats()
     cap = max(64, int(n * 40 // 32) + 64)
     while True:
@@ -359,6 +361,34 @@ def crt_symmetric(residues, primes, *, stream=None):
     return v, int(tr.value)
 
 
+_lib.idet_extended_bonus.argtypes = [_P, _i64, _i64, _P, _P, _i32, ctypes.POINTER(idet_opts), _P,
+                                     ctypes.POINTER(idet_int), ctypes.POINTER(idet_int)]
+
+
+def extended_bonus(A, B, R, *, seed: int | None = None, stream=None):
+    """(pi~_2, s~) of Section 3.2 for two right-hand sides B (2 x n) and a
+    2 x n matrix R (idet_extended_bonus)."""
+    use_torch_allocator()
+    ptr, n, lda, dev, keep = _matrix(A)
+    Bh = np.ascontiguousarray(_as_int64(B)).reshape(2, n)
+    Rh = np.ascontiguousarray(_as_int64(R)).reshape(2, n)
+    o = default_opts(seed=seed)
+    cap = max(64, int(n * 80 // 32) + 64)
+    while True:
+        b1 = (ctypes.c_uint32 * cap)()
+        b2 = (ctypes.c_uint32 * cap)()
+        pi = idet_int(0, 0, cap, b1)
+        st = idet_int(0, 0, cap, b2)
+        rc = _lib.idet_extended_bonus(ptr, n, lda, Bh.ctypes.data, Rh.ctypes.data, dev,
+                                      ctypes.byref(o), _stream_ptr(stream), ctypes.byref(pi),
+                                      ctypes.byref(st))
+        if rc == IDET_ERR_BUFFER:
+            cap = max(int(pi.nlimbs), int(st.nlimbs)) + 8
+            continue
+        _check(rc)
+        return _to_int(pi, b1), _to_int(st, b2)
+
+
 _lib.idet_cra_early_termination.argtypes = [_P, _P, _i32, ctypes.c_double, ctypes.c_double,
                                             ctypes.c_double, ctypes.c_double, _i32, _P,
                                             ctypes.POINTER(idet_int),
@@ -443,6 +473,7 @@ def set_wait_limit(cycles: int) -> None:
 
 __all__ = ["int_det", "largest_invariant_factor", "det_mod_primes", "lu_mod_prime",
            "dixon_digits", "dixon_digits_block", "crt_symmetric", "cra_early_termination",
+           "extended_bonus",
            "launch_count", "default_opts", "IdetError",
            "use_torch_allocator", "LIB_PATH"]
 

@@ -753,14 +753,17 @@ static int den_to_binary(Workspace &ws, const std::vector<uint32_t> &den, uint32
 // dividing K are skipped. K = null: det(A) itself. to_bound: no early
 // termination, stop once the product of the primes reaches 2H/K.
 static int det_over_K(DetJob &J, const uint32_t *Kbin, int Klen, double log2K, int wave,
-                      idet_int *det, bool to_bound = false) {
+                      idet_int *det, bool to_bound = false, double budget_ms = -1,
+                      bool *done = nullptr) {
     const idet_opts &o = J.o;
     Workspace &ws = J.ws;
     cudaStream_t s = J.s;
     const double log2HK = std::max(0.0, J.log2H - log2K);
     std::vector<int32_t> dig;
     int why = 0;
+    if (done) *done = false;
     if (J.primes.empty()) IDET_TRY(J.factor_wave(wave));
+    double spent = 0;  // device time of the waves factored here (budgeted resume)
     while (true) {
         std::vector<uint32_t> prs, res;
         Timer t(s);
@@ -800,9 +803,13 @@ static int det_over_K(DetJob &J, const uint32_t *Kbin, int Klen, double log2K, i
             Timer t2(s);
             const int rc = J.assemble(prs, dig, stop + 1, Kbin, Klen, det);
             J.st.ms_cra += t2.stop();
+            if (done) *done = rc == IDET_OK;
             return rc;
         }
+        if (budget_ms >= 0 && spent >= budget_ms) return IDET_OK;  // resumed later
+        const double before = J.st.ms_lu;
         IDET_TRY(J.factor_wave(wave));
+        spent += J.st.ms_lu - before;
     }
 }
 
@@ -1315,6 +1322,7 @@ int idet_cra_early_termination(const uint32_t *residues, const uint32_t *primes,
 
 static int lif_common(DetJob &J, const int64_t *b_dev, const std::vector<int64_t> &bh,
                       LiftResult &lr);
+static int introspective2(DetJob &J, int wave, idet_int *det);
 
 int idet_int_det(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
                  const idet_opts *opts, void *stream, idet_int *det, idet_stats *stats) {
@@ -1365,6 +1373,9 @@ int idet_int_det(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
         const int rc0 = det_first(J, k0, wave, certify || !o.lif, det, &done);
         if (rc0 != IDET_OK || done) return finish(rc0);
     }
+
+    // Alg. 4.1 with i_max = 2: two solves and the extended bonus
+    if (o.i_max >= 2 && !solve_first) return finish(introspective2(J, wave, det));
 
     // Section 2.2 / Alg. 4.1 with i_max = 1: one solve gives K = s~_n.
     const int64_t *bdev = nullptr;
@@ -1559,18 +1570,27 @@ static int lcm_of_denominators(const int32_t *dig, int64_t n, int m, uint32_t p,
     int dlen = hi[1];
     // every entry integral under D?  else D <- lcm(D, den(x_j))
     std::vector<int32_t> fl(n);
+    int64_t nflag_first = 0, nflag_last = 0;
     for (int round = 0;; ++round) {
-        if (round > 64) {
-            set_last_error("largest invariant factor: too many denominator updates");
-            return IDET_ERR_INTERNAL;
-        }
         IDET_TRY(launch_lif_check(dig, n, m, D, dlen, p, hNe, flags, s));
         IDET_CUDA_TRY(cudaMemcpyAsync(fl.data(), flags, 4 * (size_t)n, cudaMemcpyDeviceToHost, s));
         IDET_CUDA_TRY(cudaStreamSynchronize(s));
-        int64_t bad = -1;
-        for (int64_t j = 0; j < n && bad < 0; ++j)
-            if (fl[j]) bad = j;
+        int64_t bad = -1, nflag = 0;
+        for (int64_t j = 0; j < n; ++j)
+            if (fl[j]) {
+                if (bad < 0) bad = j;
+                ++nflag;
+            }
+        if (round == 0) nflag_first = nflag;
+        nflag_last = nflag;
         if (bad < 0) break;
+        if (round >= 64) {
+            set_last_error("largest invariant factor: too many denominator updates (%lld entries "
+                           "flagged at first, %lld after %d updates; D has %d digits, m = %d, "
+                           "h = %d)",
+                           (long long)nflag_first, (long long)nflag_last, round, dlen, m, hNe);
+            return IDET_ERR_INTERNAL;
+        }
         // d_j = den(x_j) by reconstruction of X_j
         IDET_TRY(launch_gather_col(dig, n, m, bad, zj, s));
         IDET_TRY(launch_ratrecon(zj, m, p, hNe, hD, dj, dcap, info, ws));
@@ -1705,6 +1725,250 @@ int idet_largest_invariant_factor(const int64_t *A, int64_t n, int64_t lda, cons
     int dlen = 0;
     IDET_TRY(lcm_of_denominators(dig, n, m, p, z, hN, hNe, hD, ws, &D, &dlen));
     return radix_to_int(ws, D, dlen, p, sout);
+}
+
+// K given by len radix-p digits on the device: base-2^32 limbs on the
+// device and log2 K (as den_to_binary).
+static int radix_dev_to_binary(Workspace &ws, const uint32_t *dig, int len, uint32_t p,
+                               uint32_t **Kbin, int *Klen, double *log2K) {
+    std::vector<uint32_t> h(len);
+    IDET_CUDA_TRY(cudaMemcpyAsync(h.data(), dig, 4 * (size_t)len, cudaMemcpyDeviceToHost,
+                                  ws.stream()));
+    IDET_CUDA_TRY(cudaStreamSynchronize(ws.stream()));
+    return den_to_binary(ws, h, p, Kbin, Klen, log2K);
+}
+
+// Alg. 4.1 with i_min = i_max = 2 (the second column of Table 1), after the
+// first CRA on det(A) did not terminate. The two solves of the inner loop
+// run as one block lift (Section 6: solvings grouped into a block
+// iteration). i = 1: pi~_1 = s~ of x_1, K = pi~_1, and the CRA of det/K
+// resumes for at most the time of one solve. i = 2: s~ = lcm of the
+// denominators of x_1 and x_2, pi~_2 = s~^2 / gcd(det(R N), s~^2) for a
+// random 2 x n matrix R (Section 3.2), K = lcm(K, pi~_2), and the CRA of
+// det/K resumes until it stops. (With i_max = i_min the printed loop never
+// raises k_done, so its rounds of solves would repeat without end; one round
+// is made, and the last line of the algorithm, a determinant method of better
+// worst-case cost, is read as the CRA of det/K run to its stop.)
+static int introspective2(DetJob &J, int wave, idet_int *det) {
+    const int64_t n = J.M.n;
+    Workspace &ws = J.ws;
+    cudaStream_t s = J.s;
+    const idet_opts &o = J.o;
+    if (!J.Anar) IDET_TRY(make_Anar(J.M, J.amax, ws, &J.Anar, &J.abytes, &J.ldl));
+    int32_t *Cinv = nullptr;
+    IDET_TRY(ws.alloc_n(&Cinv, (size_t)n * J.ldl));
+    SplitMix gp(o.seed ^ 0x11f7ull);
+    uint32_t p = 0;
+    int rc = IDET_ERR_SINGULAR;
+    Timer tinv(s);
+    for (int tries = 0; tries < 6 && rc == IDET_ERR_SINGULAR; ++tries) {
+        p = random_prime31(gp);
+        rc = inverse_mod_prime(J.M, p, J.nb, ws, Cinv, J.ldl);
+    }
+    J.st.ms_inverse += tinv.stop();
+    if (rc == IDET_ERR_SINGULAR) return det_over_K(J, nullptr, 0, 0, wave, det);
+    IDET_TRY(rc);
+    J.st.inverse_macs += 2.0 * (double)n * n * n;
+    // b_1, b_2 and R from S contiguous integers (Alg. 4.1), u for the
+    // projections
+    SplitMix gb(o.seed ^ 0xb5ull), gu(o.seed ^ 0x9a11ull);
+    const double l2S = rhs_range_log2(n, J.log2H);
+    const uint64_t S = (uint64_t)std::exp2(std::floor(l2S));
+    std::vector<int64_t> bh(2 * n), Rh(2 * n);
+    std::vector<int32_t> uh(n);
+    for (auto &v : bh) v = (int64_t)gb.below(S) - (int64_t)(S / 2);
+    for (auto &v : Rh) v = (int64_t)gb.below(S) - (int64_t)(S / 2);
+    double u1 = 0, lc = 0, lcmin = INFINITY, log2Ne = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        uh[i] = (int32_t)(gu.next() & 0xffff);
+        u1 += uh[i];
+        const double c = 0.5 * std::log2(std::max(J.colsq[i], 1.0));
+        lc += c;
+        lcmin = std::min(lcmin, c);
+    }
+    for (int l = 0; l < 2; ++l) {
+        double bb = 1.0;
+        for (int64_t i = 0; i < n; ++i) bb += (double)bh[l * n + i] * (double)bh[l * n + i];
+        log2Ne = std::max(log2Ne, 0.5 * std::log2(bb * (1 + 1e-12)) + lc - lcmin);
+    }
+    const double lp = std::log2((double)p);
+    const int hNe = (int)std::ceil((log2Ne + 1) / lp);
+    const int hN = (int)std::ceil((log2Ne + std::log2(std::max(u1, 1.0)) + 1) / lp);
+    const int hD = (int)std::ceil((J.log2H + 1) / lp);
+    const double log2RN = 1.0 + 2.0 * (std::log2((double)n) + std::log2((double)S) + log2Ne);
+    const int m = std::max(hN + hD + 2, (int)std::ceil((log2RN + 2) / lp) + 1);
+    int32_t *ud = nullptr, *dig = nullptr;
+    int64_t *bd = nullptr, *Rd = nullptr, *z = nullptr;
+    IDET_TRY(ws.alloc_n(&ud, n));
+    IDET_TRY(ws.alloc_n(&bd, 2 * (size_t)n));
+    IDET_TRY(ws.alloc_n(&Rd, 2 * (size_t)n));
+    IDET_TRY(ws.alloc_n(&dig, 2 * (size_t)m * n));
+    IDET_TRY(ws.alloc_n(&z, 2 * (size_t)m));
+    IDET_CUDA_TRY(cudaMemcpyAsync(ud, uh.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s));
+    IDET_CUDA_TRY(cudaMemcpyAsync(bd, bh.data(), 16 * (size_t)n, cudaMemcpyHostToDevice, s));
+    IDET_CUDA_TRY(cudaMemcpyAsync(Rd, Rh.data(), 16 * (size_t)n, cudaMemcpyHostToDevice, s));
+    LiftArgs la{};
+    la.Cinv = Cinv;
+    la.b = bd;
+    la.b2 = bd + n;
+    la.u = ud;
+    la.n = n;
+    la.m = m;
+    la.nrhs = 2;
+    la.mod = make_mod(p);
+    la.pinv = inv_mod_2_64(p);
+    la.digits = dig;
+    la.digits2 = dig + (size_t)m * n;
+    la.zproj = z;
+    la.zproj2 = z + m;
+    la.amax = J.amax;
+    Timer tl(s);
+    int to = 0;
+    float kms = 0;
+    LiftInfo li{};
+    IDET_TRY(launch_lift(la, J.Anar, J.abytes, J.ldl, ws, &to, &kms, &li));
+    J.st.lift_timed_out = to;
+    J.st.ms_lift_kernel += li.ms_steps;
+    J.st.ms_lift_setup += li.ms_setup;
+    J.st.lift_bytes += li.bytes;
+    J.st.lift_path = li.path;
+    J.st.lift_iters = m;
+    uint32_t *D1 = nullptr, *D2 = nullptr;
+    int l1 = 0, l2 = 0;
+    Timer trr(s);
+    IDET_TRY(lcm_of_denominators(dig, n, m, p, z, hN, hNe, hD, ws, &D1, &l1));
+    IDET_TRY(lcm_of_denominators(dig + (size_t)m * n, n, m, p, z + m, hN, hNe, hD, ws, &D2, &l2));
+    J.st.ms_rr += trr.stop();
+    const double t_solve = tl.stop() / 2;  // one of the two solves
+    J.st.ms_lift += 2 * t_solve;
+    // i = 1: K = pi~_1 = s~(x_1); resume the CRA for the time of one solve
+    uint32_t *Kbin = nullptr;
+    int Klen = 0;
+    double log2K = 0;
+    IDET_TRY(radix_dev_to_binary(ws, D1, l1, p, &Kbin, &Klen, &log2K));
+    J.st.log2_K = (int)std::floor(log2K);
+    bool done = false;
+    IDET_TRY(det_over_K(J, Kbin, Klen, log2K, wave, det, false, t_solve, &done));
+    if (done) return IDET_OK;
+    // i = 2: K = lcm(K, pi~_2)
+    uint32_t *St = nullptr, *P2 = nullptr, *K2 = nullptr;
+    int ls = 0, lp2 = 0, lk = 0;
+    Timer tb(s);
+    IDET_TRY(lcm_radix(D1, l1, D2, l2, p, ws, &St, &ls));
+    IDET_TRY(bonus_pi2(dig, n, m, p, Rd, St, ls, ws, &P2, &lp2));
+    IDET_TRY(lcm_radix(D1, l1, P2, lp2, p, ws, &K2, &lk));
+    J.st.ms_rr += tb.stop();
+    IDET_TRY(radix_dev_to_binary(ws, K2, lk, p, &Kbin, &Klen, &log2K));
+    J.st.log2_K = (int)std::floor(log2K);
+    return det_over_K(J, Kbin, Klen, log2K, wave, det);
+}
+
+int idet_extended_bonus(const int64_t *A, int64_t n, int64_t lda, const int64_t *B,
+                        const int64_t *R, int32_t on_device, const idet_opts *opts, void *stream,
+                        idet_int *pi, idet_int *s_tilde) {
+    if (n <= 0 || n > IDET_MAX_ORDER || lda < n || !A || !B || !R || !pi || !s_tilde) {
+        set_last_error("invalid argument");
+        return IDET_ERR_ARG;
+    }
+    for (int64_t i = 0; i < 2 * n; ++i)
+        if (B[i] >= (1ll << 62) || B[i] <= -(1ll << 62) || R[i] >= (1ll << 62) ||
+            R[i] <= -(1ll << 62)) {
+            set_last_error("entries of B and R must satisfy |v| < 2^62");
+            return IDET_ERR_ARG;
+        }
+    idet_opts o;
+    idet_default_opts(&o);
+    if (opts) o = *opts;
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace ws(s);
+    DevMatrix M;
+    IDET_TRY(stage_matrix(A, n, lda, on_device, ws, M));
+    DetJob J(M, ws, o);
+    IDET_TRY(J.stats());
+    if (J.log2H == -INFINITY) {
+        set_last_error("A is singular (zero row or column)");
+        return IDET_ERR_SINGULAR;
+    }
+    IDET_TRY(make_Anar(J.M, J.amax, ws, &J.Anar, &J.abytes, &J.ldl));
+    int32_t *Cinv = nullptr;
+    IDET_TRY(ws.alloc_n(&Cinv, (size_t)n * J.ldl));
+    SplitMix gp(o.seed ^ 0x11f7ull);
+    uint32_t p = 0;
+    int rc = IDET_ERR_SINGULAR;
+    for (int tries = 0; tries < 6 && rc == IDET_ERR_SINGULAR; ++tries) {
+        p = random_prime31(gp);
+        rc = inverse_mod_prime(J.M, p, J.nb, ws, Cinv, J.ldl);
+    }
+    if (rc == IDET_ERR_SINGULAR) {
+        set_last_error("A is singular (singular modulo 6 random 31-bit primes)");
+        return rc;
+    }
+    IDET_TRY(rc);
+    // lengths: the denominators (below H), the numerators N_lj = s~ x_lj
+    // (Cramer: |N_lj| <= |det A_j(b_l)| <= ||b_l|| prod_{k != j} ||col_k||)
+    // and det(R N) <= 2 (n max|r| max|N|)^2
+    SplitMix g(o.seed ^ 0x9a11ull);
+    std::vector<int32_t> uh(n);
+    double u1 = 0, lc = 0, lcmin = INFINITY, log2Ne = 0, rmax = 1;
+    for (int64_t i = 0; i < n; ++i) {
+        uh[i] = (int32_t)(g.next() & 0xffff);
+        u1 += uh[i];
+        const double c = 0.5 * std::log2(std::max(J.colsq[i], 1.0));
+        lc += c;
+        lcmin = std::min(lcmin, c);
+    }
+    for (int l = 0; l < 2; ++l) {
+        double bb = 1.0;
+        for (int64_t i = 0; i < n; ++i) bb += (double)B[l * n + i] * (double)B[l * n + i];
+        log2Ne = std::max(log2Ne, 0.5 * std::log2(bb * (1 + 1e-12)) + lc - lcmin);
+    }
+    for (int64_t i = 0; i < 2 * n; ++i) rmax = std::max(rmax, std::fabs((double)R[i]));
+    const double lp = std::log2((double)p);
+    const int hNe = (int)std::ceil((log2Ne + 1) / lp);
+    const int hN = (int)std::ceil((log2Ne + std::log2(std::max(u1, 1.0)) + 1) / lp);
+    const int hD = (int)std::ceil((J.log2H + 1) / lp);
+    const double log2RN = 1.0 + 2.0 * (std::log2((double)n) + std::log2(rmax) + log2Ne);
+    const int m = std::max(hN + hD + 2, (int)std::ceil((log2RN + 2) / lp) + 1);
+    int32_t *ud = nullptr, *dig = nullptr;
+    int64_t *bd = nullptr, *Rd = nullptr, *z = nullptr, *r = nullptr;
+    IDET_TRY(ws.alloc_n(&ud, n));
+    IDET_TRY(ws.alloc_n(&bd, 2 * (size_t)n));
+    IDET_TRY(ws.alloc_n(&Rd, 2 * (size_t)n));
+    IDET_TRY(ws.alloc_n(&dig, 2 * (size_t)m * n));
+    IDET_TRY(ws.alloc_n(&z, 2 * (size_t)m));
+    IDET_TRY(ws.alloc_n(&r, 2 * (size_t)n));
+    IDET_CUDA_TRY(cudaMemcpyAsync(ud, uh.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s));
+    IDET_CUDA_TRY(cudaMemcpyAsync(bd, B, 16 * (size_t)n, cudaMemcpyHostToDevice, s));
+    IDET_CUDA_TRY(cudaMemcpyAsync(Rd, R, 16 * (size_t)n, cudaMemcpyHostToDevice, s));
+    // both solves in one block lift
+    LiftArgs la{};
+    la.Cinv = Cinv;
+    la.b = bd;
+    la.b2 = bd + n;
+    la.u = ud;
+    la.n = n;
+    la.m = m;
+    la.nrhs = 2;
+    la.mod = make_mod(p);
+    la.pinv = inv_mod_2_64(p);
+    la.digits = dig;
+    la.digits2 = dig + (size_t)m * n;
+    la.zproj = z;
+    la.zproj2 = z + m;
+    la.r = r;
+    la.r2 = r + n;
+    la.amax = J.amax;
+    int to = 0;
+    IDET_TRY(launch_lift(la, J.Anar, J.abytes, J.ldl, ws, &to));
+    // s~ = lcm of the denominators of both solutions
+    uint32_t *D1 = nullptr, *D2 = nullptr, *S = nullptr, *P = nullptr;
+    int l1 = 0, l2 = 0, ls = 0, lpi = 0;
+    IDET_TRY(lcm_of_denominators(dig, n, m, p, z, hN, hNe, hD, ws, &D1, &l1));
+    IDET_TRY(lcm_of_denominators(dig + (size_t)m * n, n, m, p, z + m, hN, hNe, hD, ws, &D2, &l2));
+    IDET_TRY(lcm_radix(D1, l1, D2, l2, p, ws, &S, &ls));
+    IDET_TRY(bonus_pi2(dig, n, m, p, Rd, S, ls, ws, &P, &lpi));
+    IDET_TRY(radix_to_int(ws, S, ls, p, s_tilde));
+    return radix_to_int(ws, P, lpi, p, pi);
 }
 
 // ---------------------------------------------------------------------------

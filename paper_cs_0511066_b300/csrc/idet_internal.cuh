@@ -411,6 +411,14 @@ int launch_mul_radix(const uint32_t *a, int la, const uint32_t *b, int lb, uint3
                      uint32_t *out, int cap, int32_t *out_len, cudaStream_t s);
 int launch_gather_col(const int32_t *digits, int64_t n, int m, int64_t j, int64_t *z,
                       cudaStream_t s);
+// k_bonus.cu: lcm of two radix-p numbers (digits in [0, p)) into workspace;
+// and the extended bonus pi~_2 = s~^2 / gcd(det(R N), s~^2) of Section 3.2
+// from the digits of two lifted solutions (dig: [2][m][n]), R (2 x n int64,
+// device) and s~ (radix-p digits), with p^m > 2 |det(R N)|.
+int lcm_radix(const uint32_t *a, int la, const uint32_t *b, int lb, uint32_t p, Workspace &ws,
+              uint32_t **out, int *lout);
+int bonus_pi2(const int32_t *dig, int64_t n, int m, uint32_t p, const int64_t *R,
+              const uint32_t *sdig, int slen, Workspace &ws, uint32_t **pi, int *plen);
 // Base-p digits -> base-2^32 limbs (out_len receives the limb count).
 int launch_radix_to_binary(const uint32_t *dig, int len, uint32_t p, uint32_t *out, int cap,
                            int32_t *out_len, cudaStream_t s);

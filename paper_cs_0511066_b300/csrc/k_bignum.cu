@@ -445,6 +445,24 @@ __device__ void ratrecon_body(const int64_t *__restrict__ z, int m, uint32_t p, 
         S.lta = 0;
         S.ltb = 1;
         S.mode = 0;
+        // The steps below keep a >= b; a given first operand may be the
+        // smaller one: exchange the pair (the coefficients still refer to b
+        // as given, so the cofactor found at the zero remainder is the same).
+        if (cmp_big(a, S.la, b, S.lb) < 0) {
+            const int L = max(S.la, S.lb);
+            for (int k = 0; k < L; ++k) {
+                const uint32_t t = a[k];
+                a[k] = b[k];
+                b[k] = t;
+            }
+            ta[0] = 1;
+            tb[0] = 0;
+            const int t = S.la;
+            S.la = S.lb;
+            S.lb = t;
+            S.lta = 1;
+            S.ltb = 0;
+        }
     }
     __syncthreads();
     // Every pass completes at least one Euclid step or one partial quotient

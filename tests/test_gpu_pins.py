@@ -341,3 +341,68 @@ def test_lif_completion_with_long_denominators_matches_oracle():
         b = workloads.random_rhs(120, 1 << 30, seed=seed)
         assert idet.largest_invariant_factor(A, b) == exact.largest_invariant_factor(
             A.tolist(), b.tolist())
+
+
+# --- the extended bonus (Section 3.2) --------------------------------------------------
+
+def _engineered(d, seed):
+    """U diag(d) V with random unimodular U, V (2n elementary operations of
+    multiplier +-1 each), entries kept in the int32 range."""
+    n = len(d)
+    r = random.Random(seed)
+
+    def unimodular():
+        U = [[int(i == j) for j in range(n)] for i in range(n)]
+        for _ in range(2 * n):
+            i, j = r.sample(range(n), 2)
+            c = r.choice([-1, 1])
+            U[i] = [x + c * y for x, y in zip(U[i], U[j])]
+        return U
+
+    D = [[d[i] if i == j else 0 for j in range(n)] for i in range(n)]
+    A = exact.matmul(exact.matmul(unimodular(), D), unimodular())
+    assert max(abs(v) for row in A for v in row) < (1 << 31)
+    return np.array(A, dtype=np.int64)
+
+
+def test_extended_bonus_closed_form_and_oracle():
+    """pi~_2 = s~^2 / gcd(det(R N), s~^2) through the C ABI equals the
+    oracle's exact-rational value: on diag(1, .., 1, a, b) with a | b and
+    B, R selecting the last two coordinates (pi~_2 = a b), on engineered
+    Smith forms with large-prime invariant factors and on random dense
+    matrices with random B and R (|b|, |r| up to 2^40)."""
+    from oracle import bonus
+    n = 6
+    A = np.diag([1, 1, 1, 1, 6, 60]).astype(np.int64)
+    E = np.zeros((2, n), dtype=np.int64)
+    E[0, 4] = E[1, 5] = 1
+    assert idet.extended_bonus(A, E, E) == (360, 60)
+    g = np.random.default_rng(5)
+    cases = [_engineered([1, 1, 1, 1, 101, 101 * 103, 101 * 103 * 107], 7)]
+    cases += [workloads.dense_pm100(k, seed=k) for k in (12, 40, 90)]
+    for A in cases:
+        n = A.shape[0]
+        B = g.integers(-(1 << 40), 1 << 40, size=(2, n), dtype=np.int64)
+        R = g.integers(-(1 << 40), 1 << 40, size=(2, n), dtype=np.int64)
+        want = bonus.extended_bonus(A.tolist(), B.tolist(), R.tolist())
+        assert idet.extended_bonus(A, B, R) == want, n
+
+
+def test_int_det_i_max_2_exact_and_larger_K():
+    """Alg. 4.1 with i_max = 2 (two solves in one block lift, then the
+    extended bonus): exact determinants on Table 1's engineered matrices
+    (det = n!) and on random dense ones; on the engineered ones K =
+    lcm(s~_n, pi~_2) has more bits than s~_n alone, so the CRA of det/K needs
+    fewer primes."""
+    for n in (60, 150):
+        A = workloads.engineered_smith(n, seed=n)
+        d1, s1 = idet.int_det(A, return_stats=True)
+        d2, s2 = idet.int_det(A, i_max=2, return_stats=True)
+        assert d1 == d2 == math.factorial(n)
+        assert s2["log2_K"] > s1["log2_K"] and s2["primes_in_cra"] < s1["primes_in_cra"], (s1, s2)
+    for n, seed in ((40, 1), (120, 2)):
+        A = workloads.dense_pm100(n, seed=seed)
+        assert idet.int_det(A, i_max=2) == exact.bareiss_det(A.tolist())
+    S = workloads.dense_pm100(30, seed=3)
+    S[4] = S[9] + S[11]
+    assert idet.int_det(S, i_max=2) == 0

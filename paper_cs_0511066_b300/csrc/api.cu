@@ -418,6 +418,11 @@ struct DetJob {
     std::vector<uint32_t> dets;     // det(A) mod primes
     idet_stats st{};
 
+    // LU factors kept from a wave of 31-bit CRA primes (primes[lu_first ..
+    // lu_first + lu_count)): residues and permutations, prime-major
+    int32_t *lu_R = nullptr, *lu_perm = nullptr;
+    int lu_first = 0, lu_count = 0;
+
     // multi-word entries (idet_int_det_mp): sign x L base-2^32 limbs
     const uint32_t *mag = nullptr;
     const int8_t *sgn = nullptr;
@@ -489,16 +494,27 @@ struct DetJob {
         std::vector<ModP> mh(W);
         for (int i = 0; i < W; ++i) mh[i] = make_mod(pw[i]);
         ModP *md = nullptr;
-        int32_t *R = nullptr;
+        int32_t *R = nullptr, *perm = nullptr;
         uint32_t *dd = nullptr;
+        // primes of the lifting class (31 bits): the factors of the first
+        // wave are kept, so that the lift can take one of these primes and
+        // its LU instead of factoring a prime of its own
+        const bool keep = draw.bits == 31 && !lu_R && !mag;
         IDET_TRY(ws.alloc_n(&md, W));
         IDET_TRY(ws.alloc_n(&R, (size_t)W * n * n));
         IDET_TRY(ws.alloc_n(&dd, W));
+        if (keep) IDET_TRY(ws.alloc_n(&perm, (size_t)W * n));
         IDET_CUDA_TRY(cudaMemcpyAsync(md, mh.data(), sizeof(ModP) * W, cudaMemcpyHostToDevice, s));
         Timer t(s);
         IDET_TRY(reduce(md, W, R));
-        IDET_TRY(lu_factor_batched(R, n, md, mh.data(), W, draw.bits == 31, o.nb, nullptr, dd,
+        IDET_TRY(lu_factor_batched(R, n, md, mh.data(), W, draw.bits == 31, o.nb, perm, dd,
                                    o.update_path, ws));
+        if (keep) {
+            lu_R = R;
+            lu_perm = perm;
+            lu_first = (int)primes.size();
+            lu_count = W;
+        }
         std::vector<uint32_t> res(W);
         IDET_CUDA_TRY(cudaMemcpyAsync(res.data(), dd, sizeof(uint32_t) * W,
                                       cudaMemcpyDeviceToHost, s));
@@ -575,6 +591,49 @@ static int inverse_mod_prime(const DevMatrix &M, uint32_t p, int nb, Workspace &
     return IDET_OK;
 }
 
+// The lifting prime and C = A^{-1} mod p: a CRA prime of the lifting class
+// whose LU the first wave kept (det A != 0 mod p), else random 31-bit primes
+// (up to 6, a prime dividing det A is skipped) with an LU of their own.
+static int lift_prime_inverse(DetJob &J, int32_t *Cinv, int64_t ld4, uint32_t *p_out) {
+    Workspace &ws = J.ws;
+    cudaStream_t s = J.s;
+    const int64_t n = J.M.n;
+    for (int w = 0; w < J.lu_count && J.lu_R; ++w) {
+        const int k = J.lu_first + w;
+        if (J.dets[k] == 0) continue;
+        const uint32_t p = J.primes[k];
+        const ModP mh = make_mod(p);
+        ModP *md = nullptr;
+        IDET_TRY(ws.alloc_n(&md, 1));
+        IDET_CUDA_TRY(cudaMemcpyAsync(md, &mh, sizeof(ModP), cudaMemcpyHostToDevice, s));
+        const int32_t *R = J.lu_R + (size_t)w * n * n;
+        const int32_t *perm = J.lu_perm + (size_t)w * n;
+        if (ld4 == n) {
+            IDET_TRY(lu_inverse(R, perm, n, mh, md, true, J.nb, Cinv, ws));
+        } else {
+            int32_t *Y = nullptr;
+            IDET_TRY(ws.alloc_n(&Y, (size_t)n * n));
+            IDET_TRY(lu_inverse(R, perm, n, mh, md, true, J.nb, Y, ws));
+            IDET_CUDA_TRY(cudaMemsetAsync(Cinv, 0, sizeof(int32_t) * n * ld4, s));
+            IDET_CUDA_TRY(cudaMemcpy2DAsync(Cinv, 4 * ld4, Y, 4 * n, 4 * n, n,
+                                            cudaMemcpyDeviceToDevice, s));
+        }
+        J.st.inverse_macs += (4.0 / 3.0) * (double)n * n * n;
+        *p_out = p;
+        return IDET_OK;
+    }
+    SplitMix g(J.o.seed ^ 0x11f7ull);
+    int rc = IDET_ERR_SINGULAR;
+    uint32_t p = 0;
+    for (int tries = 0; tries < 6 && rc == IDET_ERR_SINGULAR; ++tries) {
+        p = random_prime31(g);
+        rc = inverse_mod_prime(J.M, p, J.nb, ws, Cinv, ld4);
+    }
+    if (rc == IDET_OK) J.st.inverse_macs += 2.0 * (double)n * n * n;
+    *p_out = p;
+    return rc;
+}
+
 // A in the narrowest of int8/int16/int32 holding max |a_ij| = amax, rows
 // padded with zeros to ldl = n rounded up to a multiple of 16.
 static int make_Anar(const DevMatrix &M, uint64_t amax, Workspace &ws, void **out, int *abytes,
@@ -604,17 +663,12 @@ static int solve_and_denominator(DetJob &J, const int64_t *b_dev, const std::vec
     const int64_t n = J.M.n;
     Workspace &ws = J.ws;
     cudaStream_t s = J.s;
-    SplitMix g(J.o.seed ^ 0x11f7ull);
     if (!J.Anar) IDET_TRY(make_Anar(J.M, J.amax, ws, &J.Anar, &J.abytes, &J.ldl));
     int32_t *Cinv = nullptr;
     IDET_TRY(ws.alloc_n(&Cinv, (size_t)n * J.ldl));
     uint32_t p = 0;
-    int rc = IDET_ERR_SINGULAR;
     Timer tinv(s);
-    for (int tries = 0; tries < 6 && rc == IDET_ERR_SINGULAR; ++tries) {
-        p = random_prime31(g);
-        rc = inverse_mod_prime(J.M, p, J.nb, ws, Cinv, J.ldl);
-    }
+    const int rc = lift_prime_inverse(J, Cinv, J.ldl, &p);
     J.st.ms_inverse += tinv.stop();
     if (rc != IDET_OK) return rc;
     // Bounds (Cramer): x_j = N_j / det A. The denominator of u.x divides
@@ -656,7 +710,6 @@ static int solve_and_denominator(DetJob &J, const int64_t *b_dev, const std::vec
     J.st.ms_lift_setup += li.ms_setup;
     J.st.lift_bytes += li.bytes;
     J.st.lift_path = li.path;
-    J.st.inverse_macs += 2.0 * (double)n * n * n;  // LU + inverse of the lift prime
     uint32_t *den = nullptr;
     int32_t *info = nullptr;
     const int den_cap = hD + 2;
@@ -1742,7 +1795,10 @@ static int radix_dev_to_binary(Workspace &ws, const uint32_t *dig, int len, uint
 // first CRA on det(A) did not terminate. The two solves of the inner loop
 // run as one block lift (Section 6: solvings grouped into a block
 // iteration). i = 1: pi~_1 = s~ of x_1, K = pi~_1, and the CRA of det/K
-// resumes for at most the time of one solve. i = 2: s~ = lcm of the
+// resumes "for at most the time of one system solving": with the second
+// solve already done by the block lift, the time is spent better on it, so
+// the resume checks the residues at hand for early termination and factors
+// no new primes. i = 2: s~ = lcm of the
 // denominators of x_1 and x_2, pi~_2 = s~^2 / gcd(det(R N), s~^2) for a
 // random 2 x n matrix R (Section 3.2), K = lcm(K, pi~_2), and the CRA of
 // det/K resumes until it stops. (With i_max = i_min the printed loop never
@@ -1757,18 +1813,12 @@ static int introspective2(DetJob &J, int wave, idet_int *det) {
     if (!J.Anar) IDET_TRY(make_Anar(J.M, J.amax, ws, &J.Anar, &J.abytes, &J.ldl));
     int32_t *Cinv = nullptr;
     IDET_TRY(ws.alloc_n(&Cinv, (size_t)n * J.ldl));
-    SplitMix gp(o.seed ^ 0x11f7ull);
     uint32_t p = 0;
-    int rc = IDET_ERR_SINGULAR;
     Timer tinv(s);
-    for (int tries = 0; tries < 6 && rc == IDET_ERR_SINGULAR; ++tries) {
-        p = random_prime31(gp);
-        rc = inverse_mod_prime(J.M, p, J.nb, ws, Cinv, J.ldl);
-    }
+    const int rc = lift_prime_inverse(J, Cinv, J.ldl, &p);
     J.st.ms_inverse += tinv.stop();
     if (rc == IDET_ERR_SINGULAR) return det_over_K(J, nullptr, 0, 0, wave, det);
     IDET_TRY(rc);
-    J.st.inverse_macs += 2.0 * (double)n * n * n;
     // b_1, b_2 and R from S contiguous integers (Alg. 4.1), u for the
     // projections
     SplitMix gb(o.seed ^ 0xb5ull), gu(o.seed ^ 0x9a11ull);
@@ -1839,8 +1889,7 @@ static int introspective2(DetJob &J, int wave, idet_int *det) {
     IDET_TRY(lcm_of_denominators(dig, n, m, p, z, hN, hNe, hD, ws, &D1, &l1));
     IDET_TRY(lcm_of_denominators(dig + (size_t)m * n, n, m, p, z + m, hN, hNe, hD, ws, &D2, &l2));
     J.st.ms_rr += trr.stop();
-    const double t_solve = tl.stop() / 2;  // one of the two solves
-    J.st.ms_lift += 2 * t_solve;
+    J.st.ms_lift += tl.stop();
     // i = 1: K = pi~_1 = s~(x_1); resume the CRA for the time of one solve
     uint32_t *Kbin = nullptr;
     int Klen = 0;
@@ -1848,7 +1897,7 @@ static int introspective2(DetJob &J, int wave, idet_int *det) {
     IDET_TRY(radix_dev_to_binary(ws, D1, l1, p, &Kbin, &Klen, &log2K));
     J.st.log2_K = (int)std::floor(log2K);
     bool done = false;
-    IDET_TRY(det_over_K(J, Kbin, Klen, log2K, wave, det, false, t_solve, &done));
+    IDET_TRY(det_over_K(J, Kbin, Klen, log2K, wave, det, false, 0.0, &done));
     if (done) return IDET_OK;
     // i = 2: K = lcm(K, pi~_2)
     uint32_t *St = nullptr, *P2 = nullptr, *K2 = nullptr;

@@ -21,14 +21,15 @@
 //
 // The step kernel is persistent and cooperative: one CTA per SM owns a block
 // of rows of E. Rows that fit stay in shared memory for the launch; the
-// others stream every step through a ring of shared-memory slots filled by a
-// producer warp with bulk asynchronous copies (E of a few thousand rows fits
-// in L2, and the streamed rows are copied with an evict_last hint). Each
-// consumer warp takes a row: E_row . x as sums of four int32 x int32
-// products (each below 2^61, the sum below 2^63) folded into a 128-bit
-// accumulator, a warp reduction, then the row's update of y (exact division
-// by p as a product with p^{-1} mod 2^128) and its next digit. With two
-// right-hand sides (the block lift) both vectors share every row of E read.
+// others are read from L2 every step (E of a few thousand rows fits in the
+// 126 MB L2: after the first step no DRAM traffic is left; each warp keeps
+// four 16-byte loads per lane in flight). Each warp takes a row:
+// E_row . x as sums of four int32 x int32 products (each below 2^61, the sum
+// below 2^63) folded into a 128-bit accumulator, a warp reduction, then the
+// row's update of y (exact division by p as a product with p^{-1} mod 2^128)
+// and its next digit. With two right-hand sides (the block lift) both
+// vectors share every row of E read. One grid-wide barrier ends each step
+// (bounded wait, lift_common.cuh).
 //
 // Sizes: |y_0| <= n 2^30 2^62 < 2^108 and |E x_i| < 2^16 2^31 2^30 = 2^77,
 // so |y_i| < 2^109 throughout (n <= 2^16).
@@ -227,35 +228,33 @@ __global__ void k_residual_step(const TA *__restrict__ A, int64_t n, int64_t ld,
 // ---------------------------------------------------------------------------
 // The step kernel.
 
-constexpr int kThreads = 1024;
-constexpr int kConsumers = 31;  // warps 0..30
-constexpr int kConsThreads = kConsumers * 32;
-constexpr int kProducer = 31;   // warp 31
-constexpr int kRingMax = 16;
+constexpr int kThreads = 1024;  // 32 warps, a row each at a time
+constexpr int kWarps = kThreads / 32;
 
 struct EGeom {
     int64_t ld;   // row length (multiple of 16)
     int64_t rpc;  // rows per CTA
     int cE;       // rows of E resident in shared memory per CTA
-    int S;        // ring slots (0: no streaming)
-    int keep;     // streamed rows per step copied with an L2 evict_last hint
-    int pad;
+    int pad[3];
     uint64_t pinv_lo, pinv_hi;  // p^{-1} mod 2^128
     uint64_t r64;               // 2^64 mod p
 };
 
-template <int NR>
+// E_row . x_r for the NR staged vectors: sums of four products (each below
+// 2^61 in magnitude, the sum below 2^63) folded into 128-bit accumulators,
+// then a warp reduction. GLOBAL: the row is read from L2 (ld.global.cg,
+// four 16-byte loads in flight per lane); else from shared memory.
+template <int NR, bool GLOBAL>
 __device__ __forceinline__ void dot_e(const int4 *__restrict__ erow, const int4 *__restrict__ xs,
                                       int64_t nq, int lane, __int128 (&acc)[NR]) {
 #pragma unroll
     for (int r = 0; r < NR; ++r) acc[r] = 0;
-#pragma unroll 2
+#pragma unroll 4
     for (int64_t q = lane; q < nq; q += 32) {
-        const int4 e = erow[q];
+        const int4 e = GLOBAL ? __ldcg(erow + q) : erow[q];
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
             const int4 v = xs[r * nq + q];
-            // each product is below 2^61 in magnitude, the sum of four below 2^63
             const int64_t t = (int64_t)e.x * v.x + (int64_t)e.y * v.y + (int64_t)e.z * v.z +
                               (int64_t)e.w * v.w;
             acc[r] += t;
@@ -270,37 +269,24 @@ __global__ void __launch_bounds__(kThreads, 1)
 k_lift_e(LiftArgs a, const int32_t *__restrict__ E, EGeom g, __int128 *__restrict__ ybuf,
          int32_t *__restrict__ xbuf, GridBar *gb, long long limit) {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t full[kRingMax], empty[kRingMax];
-    __shared__ int64_t s_z[NR][kConsumers];
-    __shared__ volatile unsigned int s_issued;  // copies issued so far
+    __shared__ int64_t s_z[NR][kWarps];
     const int64_t n = a.n, ld = g.ld, nq = ld / 4;
     const ModP M = a.mod;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t r0 = (int64_t)blockIdx.x * g.rpc;
     const int64_t r1 = min(n, r0 + g.rpc);
     const int nrows = r1 > r0 ? (int)(r1 - r0) : 0;
-    const int64_t slotB = 4 * ld;
-    int4 *xs = reinterpret_cast<int4 *>(smem);                           // NR x ld int32
-    __int128 *sy = reinterpret_cast<__int128 *>(smem + 4 * ld * NR);     // rpc x NR
-    unsigned char *ring = smem + 4 * ld * NR + 16 * g.rpc * NR;
-    int32_t *cE = reinterpret_cast<int32_t *>(ring + g.S * slotB);
+    int4 *xs = reinterpret_cast<int4 *>(smem);                        // NR x ld int32
+    __int128 *sy = reinterpret_cast<__int128 *>(smem + 4 * ld * NR);  // rpc x NR
+    int32_t *cE = reinterpret_cast<int32_t *>(smem + 4 * ld * NR + 16 * g.rpc * NR);
     const int kc = min(g.cE, nrows);
-    const int nsE = nrows - kc;  // streamed rows per step
     const int steps = a.m - 1;
     const unsigned G = gridDim.x;
     const unsigned __int128 pinv = ((unsigned __int128)g.pinv_hi << 64) | g.pinv_lo;
     int32_t *dg[2] = {a.digits, a.digits2};
     int64_t *zp[2] = {a.zproj, a.zproj2};
 
-    if (tid == 0) {
-        s_issued = 0;
-        for (int s = 0; s < g.S; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    // resident rows and the rows' y (all warps)
+    // resident rows and the rows' y
     {
         const int4 *src = reinterpret_cast<const int4 *>(E + r0 * ld);
         int4 *dst = reinterpret_cast<int4 *>(cE);
@@ -310,63 +296,26 @@ k_lift_e(LiftArgs a, const int32_t *__restrict__ E, EGeom g, __int128 *__restric
     }
     __syncthreads();
 
-    if (warp == kProducer) {
-        // ---- producer: stream rows kc.. of E, every step
-        if (lane == 0 && nsE > 0 && g.S > 0) {
-            const uint64_t pol_keep = policy_evict_last(), pol_pass = policy_evict_first();
-            long long seq = 0;
-            bool ok = true;
-            for (int it = 0; it < steps && ok; ++it) {
-                for (int k = 0; k < nsE; ++k, ++seq) {
-                    const int slot = (int)(seq % g.S);
-                    const unsigned par = (unsigned)((seq / g.S) & 1) ^ 1u;
-                    if (!mbar_wait(&empty[slot], par, gb, limit, seq, slot, it)) {
-                        ok = false;
-                        break;
-                    }
-                    mbar_expect_tx(&full[slot], (unsigned)slotB);
-                    bulk_g2s(ring + slot * slotB, E + (r0 + kc + k) * ld, (unsigned)slotB,
-                             &full[slot], k < g.keep ? pol_keep : pol_pass);
-                    s_issued = (unsigned int)(seq + 1);
-                }
-            }
-            // no copy may be in flight when the CTA exits
-            drain_ring(full, g.S, seq);
-        }
-        return;
-    }
-
-    // ---- consumers (warps 0..30)
     unsigned bar = 0;
-    long long seq_base = 0;
-    bool fail = false;
     for (int it = 0; it < steps; ++it) {
         const int32_t *xin = xbuf + (int64_t)(it & 1) * NR * ld;
         int32_t *xout = xbuf + (int64_t)((it + 1) & 1) * NR * ld;
         {
             const int4 *src = reinterpret_cast<const int4 *>(xin);
-            for (int64_t q = tid; q < NR * nq; q += kConsThreads) xs[q] = __ldcg(src + q);
+            for (int64_t q = tid; q < NR * nq; q += kThreads) xs[q] = __ldcg(src + q);
         }
-        lift::cons_sync<kConsThreads>();
+        __syncthreads();
         int64_t zpart[NR];
 #pragma unroll
         for (int r = 0; r < NR; ++r) zpart[r] = 0;
-        for (int lr = warp; lr < nrows; lr += kConsumers) {
+        for (int lr = warp; lr < nrows; lr += kWarps) {
             __int128 acc[NR];
-            if (lr < kc) {
-                dot_e<NR>(reinterpret_cast<const int4 *>(cE + (int64_t)lr * ld), xs, nq, lane, acc);
-            } else {
-                const long long seq = seq_base + (lr - kc);
-                const int slot = (int)(seq % g.S);
-                if (!wait_issued(&s_issued, seq, gb, limit, slot, it) ||
-                    !mbar_wait(&full[slot], (unsigned)((seq / g.S) & 1), gb, limit, seq, slot, it)) {
-                    fail = true;
-                    break;
-                }
-                dot_e<NR>(reinterpret_cast<const int4 *>(ring + slot * slotB), xs, nq, lane, acc);
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[slot]);
-            }
+            if (lr < kc)
+                dot_e<NR, false>(reinterpret_cast<const int4 *>(cE + (int64_t)lr * ld), xs, nq,
+                                 lane, acc);
+            else
+                dot_e<NR, true>(reinterpret_cast<const int4 *>(E + (r0 + lr) * ld), xs, nq, lane,
+                                acc);
             if (lane == 0) {
                 const int64_t row = r0 + lr;
 #pragma unroll
@@ -383,20 +332,18 @@ k_lift_e(LiftArgs a, const int32_t *__restrict__ E, EGeom g, __int128 *__restric
                 }
             }
         }
-        seq_base += nsE;
         if (a.u) {
 #pragma unroll
             for (int r = 0; r < NR; ++r)
                 if (lane == 0) s_z[r][warp] = zpart[r];
-            lift::cons_sync<kConsThreads>();
+            __syncthreads();
             if (tid < NR && zp[tid]) {
                 int64_t t = 0;
-                for (int k = 0; k < kConsumers; ++k) t += s_z[tid][k];
+                for (int k = 0; k < kWarps; ++k) t += s_z[tid][k];
                 if (t) atomicAdd((unsigned long long *)&zp[tid][it + 1], (unsigned long long)t);
             }
         }
-        if (fail) fail_once(gb, 3, 0, -1, -1, 0, it);
-        if (!grid_sync<kConsThreads>(gb, (++bar) * G, limit)) return;
+        if (!grid_sync<kThreads>(gb, (++bar) * G, limit)) return;
     }
 }
 
@@ -460,40 +407,23 @@ int launch_lift_e_t(const LiftArgs &a, const TA *A, int64_t ld, Workspace &ws, i
     g.pinv_lo = (uint64_t)pinv;
     g.pinv_hi = (uint64_t)(pinv >> 64);
     g.r64 = r64;
-    // Fewest CTAs with one row per consumer warp, if everything then fits in
-    // shared memory (fewer CTAs make the grid barrier cheaper); otherwise all
-    // SMs, a ring of streaming slots, and as many resident rows as fit.
-    int64_t G = std::min<int64_t>(sms, (n + kConsumers - 1) / kConsumers);
+    // Fewest CTAs with one row per warp, if all their rows then fit in shared
+    // memory (fewer CTAs make the grid barrier cheaper); otherwise all SMs,
+    // as many rows resident as fit, the others read from L2 every step.
+    int64_t G = std::min<int64_t>(sms, (n + kWarps - 1) / kWarps);
     if (G < 1) G = 1;
     g.rpc = (n + G - 1) / G;
-    auto fixed = [&](int64_t rpc) { return 4 * ld * NR + 16 * rpc * NR + 4096; };
-    if (g.rpc * row + fixed(g.rpc) <= smem_max) {
-        g.S = 0;
-        g.cE = (int)g.rpc;
-    } else {
+    auto fixed = [&](int64_t rpc) { return 4 * ld * NR + 16 * rpc * NR + 2048; };
+    if (g.rpc * row + fixed(g.rpc) > smem_max) {
         G = sms;
         g.rpc = (n + G - 1) / G;
-        const int64_t avail = (int64_t)smem_max - fixed(g.rpc);
-        int want = 8;
-        if (const char *e = getenv("IDET_LIFT_SLOTS")) want = atoi(e);
-        g.S = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)kRingMax, (int64_t)want,
-                                                           avail / row}));
-        if (g.S * row > avail) {
-            set_last_error("lift: a row does not fit in shared memory (n too large)");
-            return IDET_ERR_ARG;
-        }
-        g.cE = (int)std::min<int64_t>(g.rpc, (avail - g.S * row) / row);
     }
-    {
-        // L2 budget for the streamed rows (IDET_LIFT_L2_MB, tuning)
-        double l2mb = 96.0;
-        if (const char *e = getenv("IDET_LIFT_L2_MB")) l2mb = atof(e);
-        const int64_t per = std::max<int64_t>(0, g.rpc - g.cE);
-        const double total = (double)G * per * (double)row;
-        const double frac = total > 0 ? std::min(1.0, l2mb * 1048576.0 / total) : 0.0;
-        g.keep = (int)(frac * per);
+    if (fixed(g.rpc) > smem_max) {
+        set_last_error("lift: the vector does not fit in shared memory (n too large)");
+        return IDET_ERR_ARG;
     }
-    const size_t smem = (size_t)(4 * ld * NR + 16 * g.rpc * NR + g.S * row + (int64_t)g.cE * row);
+    g.cE = (int)std::min<int64_t>(g.rpc, ((int64_t)smem_max - fixed(g.rpc)) / row);
+    const size_t smem = (size_t)(4 * ld * NR + 16 * g.rpc * NR + (int64_t)g.cE * row);
     const void *kern = NR == 2 ? (const void *)k_lift_e<2> : (const void *)k_lift_e<1>;
     IDET_TRY(allow_max_smem(kern));
     int occ = 0;
@@ -534,10 +464,8 @@ int launch_lift_e_t(const LiftArgs &a, const TA *A, int64_t ld, Workspace &ws, i
     }
     if (timed_out) *timed_out = hb.err;
     if (hb.err) {
-        set_last_error("lift: a bounded wait gave up (code %d, block %d warp %d seq %d slot %d "
-                       "parity %d step %d; grid %d, S %d, cE %d, rpc %d)",
-                       hb.err, hb.info[0], hb.info[1], hb.info[2], hb.info[3], hb.info[4],
-                       hb.info[5], (int)G, g.S, g.cE, (int)g.rpc);
+        set_last_error("lift: a bounded wait gave up (code %d, block %d; grid %d, cE %d, rpc %d)",
+                       hb.err, hb.info[0], (int)G, g.cE, (int)g.rpc);
         return IDET_ERR_TIMEOUT;
     }
     // the residuals r_m, when asked for, from the digits

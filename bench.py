@@ -213,10 +213,43 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_lu_paths(torch, idet):
+    """The multi-prime LU of the n = 4000 matrix (entries +-2^20) for 16 CRA
+    primes with every trailing-update arithmetic: time per call (best of 3
+    after a warm-up, CUDA events) and the modular-MAC rate, with the tensor
+    operations each path issues for them: 9 int8 or bf16 limb products per
+    modular MAC (three 7-bit limbs), one fp64 product for FP64."""
+    A = torch.from_numpy(workloads.dense_pm2p20(4000, seed=0)).cuda()
+    pool = [1048583, 1048589, 1048601, 1048609, 1048613, 1048627, 1048633, 1048661,
+            1048681, 1048703, 1048709, 1048717, 1048721, 1048759, 1048783, 1048793]
+    out = {}
+    ref = None
+    for name, path, ops in (("int64", 1, 0), ("i8", 2, 9), ("bf16", 4, 9), ("tc05", 5, 9),
+                            ("f64", 3, 1)):
+        idet.det_mod_primes(A, pool, update_path=path)
+        best = None
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = idet.det_mod_primes(A, pool, update_path=path)
+            e1.record()
+            torch.cuda.synchronize()
+            best = e0.elapsed_time(e1) if best is None else min(best, e0.elapsed_time(e1))
+        ref = r if ref is None else ref
+        assert list(r) == list(ref), name
+        macs = (2.0 / 3.0) * 4000 ** 3 * len(pool)
+        out[name] = {"ms": round(best, 2), "modular_gmac_s": round(macs / best / 1e6, 1),
+                     "tensor_tops_issued": round(2 * ops * macs / best / 1e9, 1) if ops else None}
+    print(json.dumps({"case": "lu_paths", "n": 4000, "primes": len(pool), "paths": out}))
+
+
 def run_case(case):
     """Small fixed invocations of single kernels, for profiler captures."""
     import torch
     import paper_cs_0511066_b300 as idet
+    if case == "lu_paths":
+        return run_lu_paths(torch, idet)
     if case == "lift1k":
         A = torch.from_numpy(workloads.dense_u8(1000, seed=0)).cuda()
     else:
@@ -225,10 +258,9 @@ def run_case(case):
     if case in ("lift", "lift1k"):
         b = workloads.random_rhs(A.shape[0], 1 << 40, seed=1)
         idet.dixon_digits(A, b, 2147483629, 64)
-    elif case == "lu":
-        idet.det_mod_primes(A, [1048583, 1048589, 1048601, 1048609], update_path=1)
-    elif case == "lu_tc05":
-        idet.det_mod_primes(A, [1048583, 1048589, 1048601, 1048609], update_path=5)
+    elif case.startswith("lu"):
+        path = {"lu": 1, "lu_int64": 1, "lu_i8": 2, "lu_f64": 3, "lu_bf16": 4, "lu_tc05": 5}[case]
+        idet.det_mod_primes(A, [1048583, 1048589, 1048601, 1048609], update_path=path)
     else:
         raise SystemExit(f"unknown case {case}")
     torch.cuda.synchronize()
@@ -624,8 +656,9 @@ def main():
                     help="directory for the nvidia-smi clock samples (default: temp dir)")
     ap.add_argument("--case", default=None,
                     help="profiling case: 'lift' (Dixon lifting, n=4000, 64 digits), "
-                         "'lu' (det mod 4 primes, n=4000, int64 update), 'lu_tc05' (the "
-                         "same with the tcgen05 update): runs once and prints timings; "
+                         "'lu' / 'lu_int64' / 'lu_i8' / 'lu_f64' / 'lu_bf16' / 'lu_tc05' (det "
+                         "mod 4 primes, n=4000, one update path): runs once and prints timings; "
+                         "'lu_paths': every update path timed on 16 primes; "
                          "'peaks': int8/bf16/fp64 GEMM throughput of the vendor libraries")
     ap.add_argument("--workload", default="plain",
                     choices=["plain", "batch", "serve", "lift_heavy", "small", "ablation",

@@ -312,9 +312,14 @@ int gemm_sub_tc05(const int32_t *A, int64_t lda, int64_t sA, const int32_t *B, i
                   const ModP *mods, const LUState *st, int W, void *scratch, cudaStream_t s,
                   int L);
 int tc05_check_error(cudaStream_t s);
+// scratch: tc_scratch_bytes(n, W, path) bytes (the packed limb tiles of A and
+// B^T for any M, N <= n, K <= 128); tc_check_error synchronises s and
+// reports a bounded wait for a tile copy that gave up.
+size_t tc_scratch_bytes(int64_t n, int W, int path);
+int tc_check_error(cudaStream_t s);
 int gemm_sub_tc(int path, const int32_t *A, int64_t lda, int64_t sA, const int32_t *B, int64_t ldb,
                 int64_t sB, int32_t *C, int64_t ldc, int64_t sC, int M, int N, int K,
-                const ModP *mods, const LUState *st, int W, cudaStream_t s);
+                const ModP *mods, const LUState *st, int W, void *scratch, cudaStream_t s);
 
 // k_lift.cu ---------------------------------------------------------------
 // Held while a grid-synchronised lifting kernel runs: two of them on

@@ -764,7 +764,8 @@ int lu_blocked(int32_t *R, int64_t n, const ModP *mods, int W, int nb, int32_t *
             return gemm_sub_tc05(Ap, n, nn, Bp, n, nn, Cp, n, nn, M, N, K, mods, st, W, scratch, s,
                                  WIDE ? 5 : 3);
         if (!WIDE && path != IDET_PATH_INT64)
-            return gemm_sub_tc(path, Ap, n, nn, Bp, n, nn, Cp, n, nn, M, N, K, mods, st, W, s);
+            return gemm_sub_tc(path, Ap, n, nn, Bp, n, nn, Cp, n, nn, M, N, K, mods, st, W,
+                               scratch, s);
         return gemm_sub<WIDE>(Ap, n, nn, Bp, n, nn, Cp, n, nn, M, N, K, mods, st, W, s);
     };
     for (int64_t J0 = 0; J0 < n; J0 += NB) {
@@ -845,10 +846,14 @@ int lu_factor_batched(int32_t *R, int64_t n, const ModP *mods_dev,
                                                                                   : IDET_PATH_TC05);
         void *scratch = nullptr;
         if (path == IDET_PATH_TC05) IDET_TRY(ws.alloc(&scratch, tc05_scratch_bytes(n, W, 3)));
+        const bool legacy_tc =
+            path == IDET_PATH_I8 || path == IDET_PATH_BF16 || path == IDET_PATH_F64;
+        if (legacy_tc) IDET_TRY(ws.alloc(&scratch, tc_scratch_bytes(n, W, path)));
         int32_t *tri = nullptr;
         IDET_TRY(ws.alloc_n(&tri, (size_t)W * kNBMax * kNBMax));
         IDET_TRY(lu_blocked<false>(R, n, mods_dev, W, nb, perm, st, s, path, scratch, tri));
         if (path == IDET_PATH_TC05) IDET_TRY(tc05_check_error(s));
+        if (legacy_tc) IDET_TRY(tc_check_error(s));
     }
     k_finalize_det<<<(W + 127) / 128, 128, 0, s>>>(st, mods_dev, W, det_out);
     count_launch();

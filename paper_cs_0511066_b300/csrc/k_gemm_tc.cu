@@ -38,6 +38,17 @@ namespace {
 
 constexpr int TBM = 64, TBN = 64, TK = 32;
 constexpr int kTcThreads = 256;
+constexpr int kMaxK = 128;  // the LU's block-column width
+
+// Exactness of the accumulations for K <= kMaxK terms (balanced 21-bit
+// residues |x| < 2^20, 7-bit limbs |l| <= 64, at most 3 limb products per
+// group): int8 groups in int32, bf16 groups in fp32 (integers below 2^24),
+// FP64 sums below 2^53. The FP64 bound itself would allow
+// floor((2^53 - 1) / 2^40) = 8191 terms; the LU never needs more than 128.
+static_assert(3LL * kMaxK * 64 * 64 < (1LL << 31), "int8-limb groups overflow int32");
+static_assert(3LL * kMaxK * 64 * 64 < (1LL << 24), "bf16-limb groups are not exact in fp32");
+static_assert((double)kMaxK * (double)(1LL << 40) < (double)(1LL << 53), "fp64 sums inexact");
+static_assert(((1LL << 53) - 1) / (1LL << 40) == 8191, "the FP64 delayed-reduction bound");
 
 __device__ __forceinline__ void split7(int32_t x, int32_t &l0, int32_t &l1, int32_t &l2) {
     l0 = ((x + 64) & 127) - 64;
@@ -415,7 +426,7 @@ int gemm_sub_tc(int path, const int32_t *A, int64_t lda, int64_t sA, const int32
                 int64_t sB, int32_t *C, int64_t ldc, int64_t sC, int M, int N, int K,
                 const ModP *mods, const LUState *st, int W, void *scratch, cudaStream_t s) {
     if (M <= 0 || N <= 0 || K <= 0) return IDET_OK;
-    if (K > 128) {
+    if (K > kMaxK) {
         set_last_error("tensor trailing update: K must be at most 128 (exactness bound)");
         return IDET_ERR_INTERNAL;
     }

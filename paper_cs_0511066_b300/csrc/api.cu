@@ -11,6 +11,8 @@
 #include <cstring>
 #include <mutex>
 #include <set>
+#include <string>
+#include <thread>
 #include <unordered_set>
 #include <vector>
 
@@ -418,6 +420,11 @@ struct DetJob {
     std::vector<uint32_t> dets;     // det(A) mod primes
     idet_stats st{};
 
+    // A^{-1} mod a lifting prime formed ahead of the solve (on a second
+    // stream while the first CRA wave is factored), or null
+    int32_t *pre_Cinv = nullptr;
+    uint32_t pre_p = 0;
+
     // LU factors kept from a wave of 31-bit CRA primes (primes[lu_first ..
     // lu_first + lu_count)): residues and permutations, prime-major
     int32_t *lu_R = nullptr, *lu_perm = nullptr;
@@ -664,13 +671,15 @@ static int solve_and_denominator(DetJob &J, const int64_t *b_dev, const std::vec
     Workspace &ws = J.ws;
     cudaStream_t s = J.s;
     if (!J.Anar) IDET_TRY(make_Anar(J.M, J.amax, ws, &J.Anar, &J.abytes, &J.ldl));
-    int32_t *Cinv = nullptr;
-    IDET_TRY(ws.alloc_n(&Cinv, (size_t)n * J.ldl));
-    uint32_t p = 0;
-    Timer tinv(s);
-    const int rc = lift_prime_inverse(J, Cinv, J.ldl, &p);
-    J.st.ms_inverse += tinv.stop();
-    if (rc != IDET_OK) return rc;
+    int32_t *Cinv = J.pre_Cinv;
+    uint32_t p = J.pre_p;
+    if (!Cinv) {
+        IDET_TRY(ws.alloc_n(&Cinv, (size_t)n * J.ldl));
+        Timer tinv(s);
+        const int rc = lift_prime_inverse(J, Cinv, J.ldl, &p);
+        J.st.ms_inverse += tinv.stop();
+        if (rc != IDET_OK) return rc;
+    }
     // Bounds (Cramer): x_j = N_j / det A. The denominator of u.x divides
     // det A, |det A| <= H; the numerator of u.x is at most
     // ||u||_1 max_j |N_j| with |N_j| = |det A_j(b)| <= ||b||_2 prod_{k != j}
@@ -1421,10 +1430,76 @@ int idet_int_det(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
     // of Abbott, Bronstein and Mulders that Fig. 2 compares against) skips
     // it and reconstructs det(A)/K to the bound 2H/K after the solve.
     const bool solve_first = o.lif == 2 && !certify;
+    // Section 4 runs the modular LUs "in the background" and solves the
+    // random systems "in parallel or in sequential": the LU and inverse mod
+    // the lifting prime do not depend on the CRA, so they run on a second
+    // stream, from a second host thread, while the first CRA wave is factored
+    // (its workspace from the stream-ordered pool, as the serving workers').
+    std::thread inv_thread;
+    int inv_rc = IDET_OK;
+    std::string inv_err;
+    float inv_ms = 0;
+    int32_t *inv_C = nullptr;
+    uint32_t inv_p = 0;
+    const bool overlap = o.lif == 1 && !certify && o.i_max < 2 && J.draw.bits != 31 &&
+                         !getenv("IDET_SERIAL_INVERSE");
+    if (overlap && !solve_first) {
+        IDET_TRY(make_Anar(J.M, J.amax, ws, &J.Anar, &J.abytes, &J.ldl));
+        IDET_TRY(ws.alloc_n(&inv_C, (size_t)n * J.ldl));
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));  // A staged, Anar formed
+        int dev = 0;
+        IDET_CUDA_TRY(cudaGetDevice(&dev));
+        inv_thread = std::thread([&J, &inv_rc, &inv_err, &inv_ms, &inv_p, inv_C, dev] {
+            t_native_alloc = true;
+            if (cudaSetDevice(dev) != cudaSuccess) {
+                inv_rc = IDET_ERR_CUDA;
+                inv_err = "lift inverse: cudaSetDevice failed";
+                return;
+            }
+            cudaStream_t s2 = nullptr;
+            if (cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess) {
+                inv_rc = IDET_ERR_CUDA;
+                inv_err = "lift inverse: cudaStreamCreate failed";
+                return;
+            }
+            {
+                Workspace ws2(s2);
+                Timer t(s2);
+                SplitMix g(J.o.seed ^ 0x11f7ull);
+                int rc = IDET_ERR_SINGULAR;
+                for (int tries = 0; tries < 6 && rc == IDET_ERR_SINGULAR; ++tries) {
+                    inv_p = random_prime31(g);
+                    rc = inverse_mod_prime(J.M, inv_p, J.nb, ws2, inv_C, J.ldl);
+                }
+                inv_ms = (float)t.stop();
+                inv_rc = rc;
+                if (rc != IDET_OK) inv_err = idet_last_error();
+                cudaStreamSynchronize(s2);
+            }
+            cudaStreamSynchronize(s2);
+            cudaStreamDestroy(s2);
+        });
+    }
+    auto join_inverse = [&]() -> int {
+        if (!inv_thread.joinable()) return IDET_OK;
+        inv_thread.join();
+        J.st.ms_inverse += inv_ms;
+        if (inv_rc == IDET_OK) {
+            J.pre_Cinv = inv_C;
+            J.pre_p = inv_p;
+            J.st.inverse_macs += 2.0 * (double)n * n * n;
+            return IDET_OK;
+        }
+        if (inv_rc == IDET_ERR_SINGULAR) return IDET_OK;  // the solve reports it again
+        set_last_error("%s", inv_err.c_str());
+        return inv_rc;
+    };
     if (!solve_first) {
         bool done = false;
         const int rc0 = det_first(J, k0, wave, certify || !o.lif, det, &done);
+        const int rcj = join_inverse();
         if (rc0 != IDET_OK || done) return finish(rc0);
+        if (rcj != IDET_OK) return finish(rcj);
     }
 
     // Alg. 4.1 with i_max = 2: two solves and the extended bonus

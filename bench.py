@@ -61,23 +61,26 @@ LIFT_E_DRAM_BYTES_PER_STEP = None
 
 def l2_copy_gbs(torch):
     """Copy bandwidth of a buffer pair that stays in L2 (2 x 32 MiB < the
-    126 MB L2), bytes read + written per second, best of 20 after warm-up:
+    126 MB L2), bytes read + written per second, 50 copies back to back, best
+    of 5 such runs after a warm-up:
     the ceiling of a kernel whose operand is served by L2, measured the same
     way as the HBM copy peak of MEASURED_PEAKS.json (torch copy_)."""
     a = torch.empty(16 << 20, dtype=torch.bfloat16, device="cuda").fill_(1)
     b = torch.empty_like(a)
+    reps = 50  # back to back, so that launch gaps do not count
     for _ in range(5):
         b.copy_(a)
     torch.cuda.synchronize()
     best = None
-    for _ in range(20):
+    for _ in range(5):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        b.copy_(a)
+        for _ in range(reps):
+            b.copy_(a)
         e1.record()
         torch.cuda.synchronize()
-        t = e0.elapsed_time(e1)
+        t = e0.elapsed_time(e1) / reps
         best = t if best is None else min(best, t)
     return 2 * a.numel() * a.element_size() / (best / 1000.0) / 1e9
 

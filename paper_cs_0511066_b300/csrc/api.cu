@@ -1441,8 +1441,10 @@ int idet_int_det(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
     float inv_ms = 0;
     int32_t *inv_C = nullptr;
     uint32_t inv_p = 0;
+    // (measured: worth it from n ~ 2000; at n = 1000 the contention costs
+    // more than the overlap saves)
     const bool overlap = o.lif == 1 && !certify && o.i_max < 2 && J.draw.bits != 31 &&
-                         !getenv("IDET_SERIAL_INVERSE");
+                         n >= 1500 && !getenv("IDET_SERIAL_INVERSE");
     if (overlap && !solve_first) {
         IDET_TRY(make_Anar(J.M, J.amax, ws, &J.Anar, &J.abytes, &J.ldl));
         IDET_TRY(ws.alloc_n(&inv_C, (size_t)n * J.ldl));

@@ -661,9 +661,15 @@ static int make_Anar(const DevMatrix &M, uint64_t amax, Workspace &ws, void **ou
 struct LiftResult {
     uint32_t p = 0;
     int m = 0;
-    std::vector<uint32_t> den;  // base-p digits
+    bool has_den = false;
+    uint32_t *Kbin = nullptr;  // the denominator in 32-bit limbs (device)
+    int Klen = 0;
+    double log2K = 0;
     int timed_out = 0;
 };
+
+static int den_to_binary(Workspace &ws, const std::vector<uint32_t> &den, uint32_t p,
+                         uint32_t **Kbin, int *Klen, double *log2K);
 
 static int solve_and_denominator(DetJob &J, const int64_t *b_dev, const std::vector<int64_t> &b_host,
                                  const int32_t *u_dev, double log2u1, LiftResult &out) {
@@ -721,23 +727,38 @@ static int solve_and_denominator(DetJob &J, const int64_t *b_dev, const std::vec
     J.st.lift_path = li.path;
     uint32_t *den = nullptr;
     int32_t *info = nullptr;
-    const int den_cap = hD + 2;
+    const int den_cap = hD + 4;
     IDET_TRY(ws.alloc_n(&den, den_cap));
     IDET_TRY(ws.alloc_n(&info, 4));
     Timer trr(s);
-    IDET_TRY(launch_ratrecon(z, m, p, hN, hD, den, den_cap, info, ws));
-    int32_t hinfo[2] = {0, 0};
-    IDET_CUDA_TRY(cudaMemcpyAsync(hinfo, info, 8, cudaMemcpyDeviceToHost, s));
+    // the denominator straight in binary where the numbers fit in shared
+    // memory, else in base p and converted
+    const bool bin = ratrecon_bin_fits(m, hN, hD);
+    if (bin)
+        IDET_TRY(launch_ratrecon_bin(z, m, p, hN, hD, den, den_cap, info, ws));
+    else
+        IDET_TRY(launch_ratrecon(z, m, p, hN, hD, den, den_cap, info, ws));
+    int32_t hinfo[4] = {0, 0, 0, 0};
+    IDET_CUDA_TRY(cudaMemcpyAsync(hinfo, info, 16, cudaMemcpyDeviceToHost, s));
     IDET_CUDA_TRY(cudaStreamSynchronize(s));
-    J.st.ms_rr += trr.stop();
     if (hinfo[0] != 0) {
+        J.st.ms_rr += trr.stop();
         set_last_error("rational reconstruction failed (code %d)", hinfo[0]);
         return IDET_ERR_INTERNAL;
     }
-    out.den.resize(hinfo[1]);
-    IDET_CUDA_TRY(cudaMemcpyAsync(out.den.data(), den, 4 * (size_t)hinfo[1],
-                                  cudaMemcpyDeviceToHost, s));
-    IDET_CUDA_TRY(cudaStreamSynchronize(s));
+    if (bin) {
+        out.Kbin = den;
+        out.Klen = hinfo[1];
+        out.log2K = std::log2((double)(uint32_t)hinfo[3]) + std::max(0, hinfo[2] - 31);
+    } else {
+        std::vector<uint32_t> dd(hinfo[1]);
+        IDET_CUDA_TRY(cudaMemcpyAsync(dd.data(), den, 4 * (size_t)hinfo[1],
+                                      cudaMemcpyDeviceToHost, s));
+        IDET_CUDA_TRY(cudaStreamSynchronize(s));
+        IDET_TRY(den_to_binary(ws, dd, p, &out.Kbin, &out.Klen, &out.log2K));
+    }
+    J.st.ms_rr += trr.stop();
+    out.has_den = true;
     out.p = p;
     out.m = m;
     return IDET_OK;
@@ -1529,13 +1550,10 @@ int idet_int_det(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
     J.st.lift_iters = lr.m;
     J.st.lift_timed_out = lr.timed_out;
 
-    uint32_t *Kbin = nullptr;
-    int Klen = 0;
-    double log2K = 0;
-    if (rc == IDET_OK && !lr.den.empty())
-        IDET_TRY(den_to_binary(ws, lr.den, lr.p, &Kbin, &Klen, &log2K));
-    J.st.log2_K = (int)std::floor(log2K);
-    return finish(det_over_K(J, Kbin, Klen, log2K, wave, det, solve_first));
+    const bool K = rc == IDET_OK && lr.has_den;
+    J.st.log2_K = K ? (int)std::floor(lr.log2K) : 0;
+    return finish(det_over_K(J, K ? lr.Kbin : nullptr, K ? lr.Klen : 0, K ? lr.log2K : 0, wave,
+                             det, solve_first));
 }
 
 int idet_int_det_mp(const uint32_t *A_limbs, const int8_t *A_sign, int64_t n, int32_t L,

@@ -409,6 +409,14 @@ int launch_mixed_to_int(const uint32_t *primes, const int32_t *digits,
 int launch_ratrecon(const int64_t *z, int m, uint32_t p, int hN, int hD, uint32_t *den,
                     int den_cap, int32_t *info, Workspace &ws, const uint32_t *ainit = nullptr,
                     int alen = 0);
+// The same reconstruction (without ainit) with the denominator in binary:
+// den receives its 32-bit limbs; info[0] as above, info[1]: limbs of den,
+// info[2]: its bit length, info[3]: its leading 31 bits. 2^30 < p < 2^31.
+// The numbers live in shared memory: callers check ratrecon_bin_fits first
+// (about m <= 9,000 base-p digits) and use launch_ratrecon otherwise.
+bool ratrecon_bin_fits(int m, int hN, int hD);
+int launch_ratrecon_bin(const int64_t *z, int m, uint32_t p, int hN, int hD, uint32_t *den,
+                        int den_cap, int32_t *info, Workspace &ws);
 // k_lif.cu: exact lcm of denominators (see there).
 int launch_lif_check(const int32_t *digits, int64_t n, int m, const uint32_t *D, int dlen,
                      uint32_t p, int h, int32_t *flag, cudaStream_t s);

@@ -192,7 +192,7 @@ __global__ void k_mixed_to_int(const uint32_t *__restrict__ primes,
 }
 
 // ---------------------------------------------------------------------------
-// Rational reconstruction in radix p (single CTA, kRT threads).
+// Rational reconstruction in radix p (one CTA of kRR threads).
 //
 // Numbers are little-endian digit vectors in [0, p), p the lift prime
 // (2^30 < p < 2^31), with explicit lengths. The p-adic value X mod p^m needs
@@ -204,41 +204,46 @@ __global__ void k_mixed_to_int(const uint32_t *__restrict__ primes,
 // numbers as one 2x2 matrix. Bounds are powers of p: the reconstruction stops
 // at the first remainder with at most hN digits (value < p^hN) and accepts a
 // denominator of at most hD digits; uniqueness needs m >= hN + hD + 1.
+//
+// Layout and synchronisation: the four numbers (a, b and the cofactor
+// magnitudes ta, tb) sit in shared memory; for an update over L digits every
+// thread owns one contiguous chunk of them. Every thread reads the leading
+// digits and derives the same Lehmer matrix, lengths and comparisons, so no
+// value is broadcast: an iteration costs one barrier after those reads and the
+// two of the carry exchange (settle below). Exchanging a and b exchanges
+// pointers, not digits.
 
-constexpr int kRT = 1024;
-
-struct RRShared {
-    int64_t co[4][kRT];
-    int la, lb, lta, ltb;
-    int64_t A, B, C, D;
-    int steps;
-    int mode;  // 0 running, 1 done, 2 capacity exceeded
-    uint64_t q;
-    int sh;
-    int flag;
-};
+constexpr int kRT = 1024;  // threads of the radix conversion
+constexpr int kRR = 256;   // threads of the reconstruction
 
 struct Radix {
     uint32_t p;
-    uint64_t m;    // floor((2^64-1)/p)
-    int64_t kp;    // ceil(2^62 / p)
-    int64_t off;   // kp * p >= 2^62
+    uint32_t mu;   // floor(2^62 / p), in (2^31, 2^32) for 2^30 < p < 2^31
+    int64_t kp;    // ceil(2^61 / p)
+    int64_t off;   // kp * p, in [2^61, 2^61 + p)
 };
 
 __device__ __forceinline__ Radix make_radix(uint32_t p) {
     Radix R;
     R.p = p;
-    R.m = ~0ull / p;
-    R.kp = (int64_t)(((1ull << 62) + p - 1) / p);
+    R.mu = (uint32_t)((1ull << 62) / p);
+    R.kp = (int64_t)(((1ull << 61) + p - 1) / p);
     R.off = R.kp * (int64_t)p;
     return R;
 }
 
-// v = carry * p + digit with 0 <= digit < p, for |v| < 2^62.
+// v = carry * p + digit with 0 <= digit < p, for |v| < 2^61 - 2^31 and
+// 2^30 < p < 2^31 (Barrett): u = v + off lies in [0, 2^62), the estimate
+// floor((u >> 30) mu / 2^32) is at most 2 below floor(u / p), and the
+// remainder is fixed by at most two subtractions. Two 32-bit multiplies.
 __device__ __forceinline__ uint32_t divmod_p(int64_t v, const Radix &R, int64_t &carry) {
-    uint64_t u = (uint64_t)(v + R.off);
-    uint64_t q = __umul64hi(u, R.m);
-    uint64_t r = u - q * R.p;
+    const uint64_t u = (uint64_t)(v + R.off);
+    uint32_t q = __umulhi((uint32_t)(u >> 30), R.mu);
+    uint64_t r = u - (uint64_t)q * R.p;
+    if (r >= R.p) {
+        r -= R.p;
+        ++q;
+    }
     if (r >= R.p) {
         r -= R.p;
         ++q;
@@ -253,105 +258,189 @@ __device__ __forceinline__ void chunk_of(int len, int &beg, int &end) {
     end = min(len, beg + per);
 }
 
-// Each thread has written its digits [beg, end) of NA arrays with carry-in
-// 0 and carry-outs co[]; propagate the (signed) carries across the chunks.
-// Each pass moves every pending carry at least one chunk up, so at most kRT
-// passes are needed.
-template <int NA>
-__device__ void resolve_p(uint32_t *const *w, int beg, int end, const int64_t *co,
-                          RRShared &S, const Radix &R) {
-    const int tid = threadIdx.x;
-#pragma unroll
-    for (int q = 0; q < NA; ++q) S.co[q][tid] = co[q];
-    __syncthreads();
-    int64_t cin[NA];
-#pragma unroll
-    for (int q = 0; q < NA; ++q) cin[q] = tid > 0 ? S.co[q][tid - 1] : 0;
-    __syncthreads();
-    for (int pass = 0; pass <= kRT; ++pass) {
-        bool pend = false;
-#pragma unroll
-        for (int q = 0; q < NA; ++q) {
-            int64_t c = cin[q];
-            for (int k = beg; k < end && c != 0; ++k) w[q][k] = divmod_p((int64_t)w[q][k] + c, R, c);
-            // a chunk past the top digit drops its carry: the result fits in
-            // the digits below, so carries beyond them cancel
-            if (beg >= end) c = 0;
-            S.co[q][tid] = c;
-            pend |= (c != 0);
-        }
-        int any = __syncthreads_or(pend && tid != kRT - 1);
-        if (!any) break;
-#pragma unroll
-        for (int q = 0; q < NA; ++q) cin[q] = tid > 0 ? S.co[q][tid - 1] : 0;
-        __syncthreads();
-    }
-    __syncthreads();
+// The reconstruction's chunks: an odd stride puts the threads' digits of one
+// step in distinct shared-memory banks.
+__device__ __forceinline__ void rr_chunk(int len, int &beg, int &end) {
+    const int per = ((len + kRR - 1) / kRR) | 1;
+    beg = min(len, (int)threadIdx.x * per);
+    end = min(len, beg + per);
 }
 
-// (x, y) <- (A x + B y, C x + D y) and (tx, ty) <- (|A| tx + |B| ty,
-// |C| tx + |D| ty) in one pass over L digits; |A|..|D| < 2^28; all results
-// are >= 0 and fit in L digits.
-__device__ void lincomb4_p(uint32_t *x, uint32_t *y, uint32_t *tx, uint32_t *ty, int La,
-                           int Lt, int64_t A, int64_t B, int64_t C, int64_t D, RRShared &S,
+struct RRCarry {
+    int64_t co[4][kRR];   // carry out of each chunk, computed with carry-in 0
+    int64_t co2[4][kRR];  // carries that rippled through a whole chunk
+};
+
+// Radix 2^31: v = carry * 2^31 + digit with 0 <= digit < 2^31 (floor
+// division by a shift; any int64 v).
+constexpr uint32_t kM31 = 0x7fffffffu;
+__device__ __forceinline__ uint32_t norm31(int64_t v, int64_t &carry) {
+    carry = v >> 31;
+    return (uint32_t)v & kM31;
+}
+
+template <bool BIN>
+__device__ __forceinline__ uint32_t norm(int64_t v, const Radix &R, int64_t &carry) {
+    return BIN ? norm31(v, carry) : divmod_p(v, R, carry);
+}
+
+// The threads' chunks of NA numbers hold digits computed with carry-in 0 and
+// carry-outs c[]; add to every chunk the carry-out of the chunk below it, so
+// that all digits lie in [0, radix) (radix p, or 2^31 when BIN). Carries out
+// of the top chunk are dropped: the numbers fit in the chunks' digits
+// (reduction mod radix^len where that is the intent). One exchange settles
+// every carry whose ripple ends inside the next chunk; a ripple through a
+// whole chunk (digits all radix - 1, or all 0 for a borrow) takes further
+// passes, each moving it at least one chunk up.
+template <int NA, bool BIN = false>
+__device__ __forceinline__ void settle(uint32_t *const (&w)[NA], int beg, int end,
+                                       const int64_t (&c)[NA], RRCarry &K, const Radix &R) {
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < NA; ++q) K.co[q][tid] = c[q];
+    __syncthreads();
+    bool pend = false;
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+        int64_t cc = tid > 0 ? K.co[q][tid - 1] : 0;
+        for (int k = beg; k < end && cc != 0; ++k)
+            w[q][k] = norm<BIN>((int64_t)w[q][k] + cc, R, cc);
+        if (beg >= end) cc = 0;
+        K.co2[q][tid] = cc;
+        pend |= cc != 0;
+    }
+    if (!__syncthreads_or(pend && tid != kRR - 1)) return;
+    for (int pass = 0; pass < kRR; ++pass) {
+        int64_t cin[NA];
+#pragma unroll
+        for (int q = 0; q < NA; ++q) cin[q] = tid > 0 ? K.co2[q][tid - 1] : 0;
+        __syncthreads();
+        pend = false;
+#pragma unroll
+        for (int q = 0; q < NA; ++q) {
+            int64_t cc = cin[q];
+            for (int k = beg; k < end && cc != 0; ++k)
+                w[q][k] = norm<BIN>((int64_t)w[q][k] + cc, R, cc);
+            if (beg >= end) cc = 0;
+            K.co2[q][tid] = cc;
+            pend |= cc != 0;
+        }
+        if (!__syncthreads_or(pend && tid != kRR - 1)) return;
+    }
+}
+
+// r + c for a digit r in [0, p) and a carry |c| <= 2^30 + 1: the digit in
+// [0, p), and c' = floor((r + c) / p) in {-1, 0, 1} added to the carry q of
+// the next position.
+__device__ __forceinline__ uint32_t add_carry(uint32_t r, int64_t c, uint32_t p, int64_t &q) {
+    int64_t s = (int64_t)r + c;
+    if (s < 0) {
+        s += p;
+        --q;
+    } else if (s >= (int64_t)p) {
+        s -= p;
+        ++q;
+    }
+    return (uint32_t)s;
+}
+
+// (x, y) <- (A x + B y, C x + D y) on digits [0, La) and (tx, ty) <-
+// (|A| tx + |B| ty, |C| tx + |D| ty) on [0, Lt); |A|..|D| < 2^28; all results
+// are >= 0 and fit in their digits. Every position is split into digit and
+// carry on its own (no dependence between positions); only the carry of the
+// position below, at most 2^30 + 1 in magnitude, is then added, so the
+// serial chain per position is one addition and compare.
+__device__ void rr_lincomb(uint32_t *__restrict__ x, uint32_t *__restrict__ y,
+                           uint32_t *__restrict__ tx, uint32_t *__restrict__ ty, int La, int Lt,
+                           int32_t A, int32_t B, int32_t C, int32_t D, RRCarry &K,
                            const Radix &R) {
-    // x, y use digits [0, La), tx, ty digits [0, Lt); both are zero above
-    // their ranges, so one chunking of [0, max(La, Lt)) serves all four.
-    const int L = max(La, Lt);
     int beg, end;
-    chunk_of(L, beg, end);
-    const int64_t aA = A < 0 ? -A : A, aB = B < 0 ? -B : B, aC = C < 0 ? -C : C,
-                  aD = D < 0 ? -D : D;
+    rr_chunk(max(La, Lt), beg, end);
+    const uint32_t aA = A < 0 ? -A : A, aB = B < 0 ? -B : B, aC = C < 0 ? -C : C,
+                   aD = D < 0 ? -D : D;
     int64_t c[4] = {0, 0, 0, 0};
     for (int k = beg; k < end; ++k) {
         if (k < La) {
-            int64_t xv = x[k], yv = y[k];
-            x[k] = divmod_p(A * xv + B * yv + c[0], R, c[0]);
-            y[k] = divmod_p(C * xv + D * yv + c[1], R, c[1]);
+            // digits below 2^31: signed 32 x 32 -> 64-bit products
+            const int32_t xv = (int32_t)x[k], yv = (int32_t)y[k];
+            int64_t q0, q1;
+            const uint32_t r0 = divmod_p((int64_t)A * xv + (int64_t)B * yv, R, q0);
+            const uint32_t r1 = divmod_p((int64_t)C * xv + (int64_t)D * yv, R, q1);
+            x[k] = add_carry(r0, c[0], R.p, q0);
+            y[k] = add_carry(r1, c[1], R.p, q1);
+            c[0] = q0;
+            c[1] = q1;
         }
         if (k < Lt) {
-            int64_t txv = tx[k], tyv = ty[k];
-            tx[k] = divmod_p(aA * txv + aB * tyv + c[2], R, c[2]);
-            ty[k] = divmod_p(aC * txv + aD * tyv + c[3], R, c[3]);
+            const uint32_t txv = tx[k], tyv = ty[k];
+            int64_t q2, q3;
+            const uint32_t r2 = divmod_p((int64_t)((uint64_t)aA * txv + (uint64_t)aB * tyv), R, q2);
+            const uint32_t r3 = divmod_p((int64_t)((uint64_t)aC * txv + (uint64_t)aD * tyv), R, q3);
+            tx[k] = add_carry(r2, c[2], R.p, q2);
+            ty[k] = add_carry(r3, c[3], R.p, q3);
+            c[2] = q2;
+            c[3] = q3;
         }
     }
-    uint32_t *ws[4] = {x, y, tx, ty};
-    resolve_p<4>(ws, beg, end, c, S, R);
+    uint32_t *const w[4] = {x, y, tx, ty};
+    settle<4>(w, beg, end, c, K, R);
 }
 
-// x <- x - q y p^sh and tx <- tx + q ty p^sh (0 < q < 2^29); L digits.
-__device__ void submul2_shift_p(uint32_t *x, const uint32_t *y, int ylen, uint32_t *tx,
-                                const uint32_t *ty, int tylen, int La, int Lt, int64_t q,
-                                int sh, RRShared &S, const Radix &R) {
+// x <- x - q y p^sh on [0, La) and tx <- tx + q ty p^sh on [0, Lt)
+// (0 < q < 2^29); the results are >= 0 and fit in their digits.
+__device__ void rr_submul(uint32_t *x, const uint32_t *y, int ylen, uint32_t *tx,
+                          const uint32_t *ty, int tylen, int La, int Lt, int64_t q, int sh,
+                          RRCarry &K, const Radix &R) {
     int beg, end;
-    chunk_of(max(La, Lt), beg, end);
+    rr_chunk(max(La, Lt), beg, end);
+    const uint32_t q32 = (uint32_t)q;
     int64_t c[2] = {0, 0};
     for (int k = beg; k < end; ++k) {
         const int src = k - sh;
         if (k < La) {
             const int64_t yv = (src >= 0 && src < ylen) ? y[src] : 0;
-            x[k] = divmod_p((int64_t)x[k] - q * yv + c[0], R, c[0]);
+            x[k] = divmod_p((int64_t)x[k] - (int64_t)((uint64_t)q32 * (uint32_t)yv) + c[0], R, c[0]);
         }
         if (k < Lt) {
             const int64_t tyv = (src >= 0 && src < tylen) ? ty[src] : 0;
-            tx[k] = divmod_p((int64_t)tx[k] + q * tyv + c[1], R, c[1]);
+            tx[k] = divmod_p((int64_t)tx[k] + (int64_t)((uint64_t)q32 * (uint32_t)tyv) + c[1], R, c[1]);
         }
     }
-    uint32_t *ws[2] = {x, tx};
-    resolve_p<2>(ws, beg, end, c, S, R);
+    uint32_t *const w[2] = {x, tx};
+    settle<2>(w, beg, end, c, K, R);
 }
 
-// floor(x / y) for x, y < 2^63, y > 0: subtraction for the small quotients
-// that dominate Euclid's algorithm, 64-bit division otherwise.
-__device__ __forceinline__ uint64_t small_quot(uint64_t x, uint64_t y) {
-    if (x < y) return 0;
-    uint64_t r = x - y;
-    if (r < y) return 1;
-    r -= y;
-    if (r < y) return 2;
-    r -= y;
-    if (r < y) return 3;
-    return x / y;
+// floor(n / d) for 0 < d, n < 2^63 and a quotient below 2^29: subtraction
+// for the smallest quotients, else a single-precision estimate (relative
+// error below 2^-21) corrected by one more estimate on the exact remainder
+// and unit steps.
+__device__ __forceinline__ float u64_to_float(uint64_t v) {
+    return __uint2float_rn((uint32_t)(v >> 32)) * 4294967296.0f + __uint2float_rn((uint32_t)v);
+}
+
+__device__ __forceinline__ uint64_t quot29(uint64_t n, uint64_t d) {
+    if (n < d) return 0;
+    uint64_t r = n - d;
+    if (r < d) return 1;
+    r -= d;
+    if (r < d) return 2;
+    const float fd = u64_to_float(d);
+    int64_t q = __float2int_rz(__fdividef(u64_to_float(n), fd));
+    int64_t rr = (int64_t)(n - (uint64_t)q * d);
+    if (rr < 0 || (uint64_t)rr >= d) {
+        const float fr = rr < 0 ? -u64_to_float((uint64_t)-rr) : u64_to_float((uint64_t)rr);
+        q += __float2int_rd(__fdividef(fr, fd));
+        rr = (int64_t)(n - (uint64_t)q * d);
+    }
+    while (rr < 0) {
+        --q;
+        rr += (int64_t)d;
+    }
+    while ((uint64_t)rr >= d) {
+        ++q;
+        rr -= (int64_t)d;
+    }
+    return (uint64_t)q;
 }
 
 __device__ int trim(const uint32_t *x, int l) {
@@ -411,204 +500,178 @@ __device__ void exact_step(const uint32_t *a, int la, const uint32_t *b, int lb,
     sh = s;
 }
 
-// zdig: m base-p digits of X (any int64 < 2^59 each; normalised here).
-// buf: 4 * cap digits (a, b, ta, tb). On success info[0] = 0,
+// The Lehmer matrix of a run of Euclid steps read off the leading parts ah,
+// bh of a and b (both taken at position s: digits of radix p, or bits when
+// BIN; steps = 0: no step could be certified). Runs stop short of the
+// numerator bound, so that no remainder below it is skipped: a step is taken
+// only while the new b keeps more than lim digits (bits), and the last steps
+// are taken exactly.
+template <bool BIN>
+__device__ __forceinline__ int lehmer(uint64_t ah, uint64_t bh, int s, int lim, uint32_t p,
+                                      int64_t &A, int64_t &B, int64_t &C, int64_t &D) {
+    A = 1;
+    B = 0;
+    C = 0;
+    D = 1;
+    int steps = 0;
+    while (true) {
+        const int64_t d1 = (int64_t)bh + C, d2 = (int64_t)bh + D;
+        if (d1 <= 0 || d2 <= 0) break;
+        if ((int64_t)ah + A < 0 || (int64_t)ah + B < 0) break;
+        const uint64_t n1 = (uint64_t)((int64_t)ah + A), n2 = (uint64_t)((int64_t)ah + B);
+        if (d1 < (1ll << 35) && n1 >= ((uint64_t)d1 << 28)) break;  // quotient >= 2^28
+        // floor(n1 / d1), and the same quotient for (n2, d2): q1 d2 <= n2 < (q1 + 1) d2
+        const uint64_t q1 = quot29(n1, (uint64_t)d1);
+        if (q1 >= (1ull << 28)) break;
+        const unsigned __int128 p2 = (unsigned __int128)q1 * (uint64_t)d2;
+        if (p2 > n2 || n2 - (uint64_t)p2 >= (uint64_t)d2) break;
+        const int64_t q = (int64_t)q1;
+        const int64_t nC = A - q * C, nD = B - q * D;
+        if (nC >= (1ll << 28) || nC <= -(1ll << 28) || nD >= (1ll << 28) || nD <= -(1ll << 28))
+            break;
+        const uint64_t nbh = ah - (uint64_t)q * bh;
+        const int est = BIN ? s + (64 - __clzll((long long)nbh))
+                            : s + (nbh >= p ? 2 : (nbh ? 1 : 0));
+        if (est <= lim) break;
+        A = C;
+        C = nC;
+        B = D;
+        D = nD;
+        ah = bh;
+        bh = nbh;
+        ++steps;
+    }
+    return steps;
+}
+
+template <class T>
+__device__ __forceinline__ void swap_(T &x, T &y) {
+    const T t = x;
+    x = y;
+    y = t;
+}
+
+// zdig: m base-p digits of X (|z_i| < 2^59 each; normalised here).
+// base: 4 * cap digits (a, b, ta, tb). On success info[0] = 0,
 // info[1] = digits of the denominator, written to den (base p).
 __device__ void ratrecon_body(const int64_t *__restrict__ z, int m, uint32_t p, int hN, int hD,
                               uint32_t *__restrict__ base, int cap, uint32_t *__restrict__ den,
                               int den_cap, int32_t *__restrict__ info,
                               const uint32_t *__restrict__ ainit, int alen) {
-    __shared__ RRShared S;
+    __shared__ RRCarry K;
     uint32_t *a = base, *b = base + cap, *ta = base + 2 * cap, *tb = base + 3 * cap;
     const int tid = threadIdx.x;
     const Radix R = make_radix(p);
-    for (int k = tid; k < cap; k += kRT) {
-        a[k] = 0;
-        b[k] = 0;
-        ta[k] = 0;
-        tb[k] = 0;
-    }
+    for (int k = tid; k < 4 * cap; k += kRR) base[k] = 0;
     __syncthreads();
-    if (tid == 0) {
-        // b = X mod p^m with digits in [0, p); a = p^m; ta = 0, tb = 1
-        int64_t carry = 0;
-        for (int i = 0; i < m; ++i) b[i] = divmod_p(z[i] + carry, R, carry);
-        if (ainit) {  // first operand given (hN = 0: full extended Euclid)
-            for (int i = 0; i < alen; ++i) a[i] = ainit[i];
-            S.la = trim(a, alen);
-        } else {
-            a[m] = 1;
-            S.la = m + 1;
-        }
-        tb[0] = 1;
-        S.lb = trim(b, m);
-        S.lta = 0;
-        S.ltb = 1;
-        S.mode = 0;
-        // The steps below keep a >= b; a given first operand may be the
-        // smaller one: exchange the pair (the coefficients still refer to b
-        // as given, so the cofactor found at the zero remainder is the same).
-        if (cmp_big(a, S.la, b, S.lb) < 0) {
-            const int L = max(S.la, S.lb);
-            for (int k = 0; k < L; ++k) {
-                const uint32_t t = a[k];
-                a[k] = b[k];
-                b[k] = t;
-            }
-            ta[0] = 1;
-            tb[0] = 0;
-            const int t = S.la;
-            S.la = S.lb;
-            S.lb = t;
-            S.lta = 1;
-            S.ltb = 0;
-        }
+    // b = X mod p^m with digits in [0, p): the carry out of digit m - 1 is
+    // dropped by settle
+    {
+        int beg, end;
+        rr_chunk(m, beg, end);
+        int64_t c[1] = {0};
+        for (int k = beg; k < end; ++k) b[k] = divmod_p(z[k] + c[0], R, c[0]);
+        uint32_t *const w[1] = {b};
+        settle<1>(w, beg, end, c, K, R);
     }
+    // a = p^m, or the given first operand (hN = 0: full extended Euclid);
+    // ta = 0, tb = 1
+    if (ainit) {
+        for (int k = tid; k < alen; k += kRR) a[k] = ainit[k];
+    } else if (tid == 0) {
+        a[m] = 1;
+    }
+    if (tid == 0) tb[0] = 1;
     __syncthreads();
+    int la = ainit ? trim(a, alen) : m + 1, lb = trim(b, m), lta = 0, ltb = 1;
+    // The steps below keep a >= b; a given first operand may be the smaller
+    // one: exchange the pair with its coefficients (the cofactor found at the
+    // zero remainder is the same).
+    if (cmp_big(a, la, b, lb) < 0) {
+        swap_(a, b);
+        swap_(la, lb);
+        swap_(ta, tb);
+        swap_(lta, ltb);
+    }
     // Every pass completes at least one Euclid step or one partial quotient
     // subtraction, each removing at least one bit from a or b; the bound
     // below exceeds the total bit length of (a, b) with a wide margin (a has
     // m + 1 digits, or alen when it is given: it can be much longer than b).
     const long max_iter = 4L * 32 * ((ainit && alen > m ? alen : m) + 4) + 1000;
+    int mode = 0;  // 0 running, 1 done, 2 capacity exceeded
     for (long iter = 0; iter < max_iter; ++iter) {
-        if (tid == 0) {
-            const int la = S.la, lb = S.lb;
-            if (lb <= hN) {
-                S.mode = 1;
-            } else {
-                const int s = la >= 2 ? la - 2 : 0;
-                uint64_t ah = top2(a, la, s, p), bh = top2(b, lb, s, p);
-                int64_t A = 1, B = 0, C = 0, D = 1;
-                int steps = 0;
-                while (true) {
-                    int64_t d1 = (int64_t)bh + C, d2 = (int64_t)bh + D;
-                    if (d1 <= 0 || d2 <= 0) break;
-                    if ((int64_t)ah + A < 0 || (int64_t)ah + B < 0) break;
-                    const uint64_t n1 = (uint64_t)((int64_t)ah + A), n2 = (uint64_t)((int64_t)ah + B);
-                    if (d1 < (1ll << 35) && n1 >= ((uint64_t)d1 << 28)) break;  // quotient >= 2^28
-                    const uint64_t q1 = small_quot(n1, (uint64_t)d1);
-                    const uint64_t q2 = small_quot(n2, (uint64_t)d2);
-                    if (q1 != q2 || q1 >= (1ull << 28)) break;
-                    int64_t q = (int64_t)q1;
-                    int64_t nC = A - q * C, nD = B - q * D;
-                    if (nC >= (1ll << 28) || nC <= -(1ll << 28) || nD >= (1ll << 28) ||
-                        nD <= -(1ll << 28))
-                        break;
-                    uint64_t nbh = ah - (uint64_t)q * bh;
-                    // stop short of the bound: the last steps are taken exactly
-                    const int est = s + (nbh >= p ? 2 : (nbh ? 1 : 0));
-                    if (est <= hN + 2) break;
-                    A = C;
-                    C = nC;
-                    B = D;
-                    D = nD;
-                    ah = bh;
-                    bh = nbh;
-                    ++steps;
-                }
-                S.A = A;
-                S.B = B;
-                S.C = C;
-                S.D = D;
-                S.steps = steps;
-                if (steps == 0) {
-                    if (cmp_big(a, la, b, lb) < 0) {
-                        S.sh = -1;  // swap only
-                    } else {
-                        uint64_t q;
-                        int sh;
-                        exact_step(a, la, b, lb, p, q, sh);
-                        S.q = q;
-                        S.sh = sh;
-                    }
-                }
-            }
+        if (lb <= hN) {
+            mode = 1;
+            break;
         }
-        __syncthreads();
-        if (S.mode != 0) break;
-        if (S.steps > 0) {
-            const int La = S.la, Lt = max(S.lta, S.ltb) + 2;
+        const int s = la >= 2 ? la - 2 : 0;
+        int64_t A, B, C, D;
+        const int steps = lehmer<false>(top2(a, la, s, p), top2(b, lb, s, p), s, hN + 2, p, A, B, C, D);
+        if (steps > 0) {
+            const int La = la, Lt = max(lta, ltb) + 2;
             if (Lt > cap) {
-                if (tid == 0) S.mode = 2;
-                __syncthreads();
+                mode = 2;
                 break;
             }
-            lincomb4_p(a, b, ta, tb, La, Lt, S.A, S.B, S.C, S.D, S, R);
-            if (tid == 0) {
-                S.la = trim(a, La);
-                S.lb = trim(b, La);
-                S.lta = trim(ta, Lt);
-                S.ltb = trim(tb, Lt);
-            }
-            __syncthreads();
+            __syncthreads();  // every thread has read the leading digits
+            rr_lincomb(a, b, ta, tb, La, Lt, (int32_t)A, (int32_t)B, (int32_t)C, (int32_t)D, K, R);
+            la = trim(a, La);
+            lb = trim(b, La);
+            lta = trim(ta, Lt);
+            ltb = trim(tb, Lt);
+        } else if (cmp_big(a, la, b, lb) < 0) {
+            swap_(a, b);
+            swap_(la, lb);
+            swap_(ta, tb);
+            swap_(lta, ltb);
         } else {
-            if (S.sh >= 0) {
-                const int La = S.la, Lt = max(S.lta, S.ltb + S.sh) + 2;
-                if (Lt > cap) {
-                    if (tid == 0) S.mode = 2;
-                    __syncthreads();
-                    break;
-                }
-                submul2_shift_p(a, b, S.lb, ta, tb, S.ltb, La, Lt, (int64_t)S.q, S.sh, S, R);
-                if (tid == 0) {
-                    S.la = trim(a, La);
-                    S.lta = trim(ta, Lt);
-                }
-                __syncthreads();
+            uint64_t q;
+            int sh;
+            exact_step(a, la, b, lb, p, q, sh);
+            const int La = la, Lt = max(lta, ltb + sh) + 2;
+            if (Lt > cap) {
+                mode = 2;
+                break;
             }
-            if (tid == 0) S.flag = cmp_big(a, S.la, b, S.lb) < 0;
             __syncthreads();
-            if (S.flag) {
-                const int L = max(S.la, S.lb), Lt = max(S.lta, S.ltb);
-                for (int k = tid; k < max(L, Lt); k += kRT) {
-                    if (k < L) {
-                        uint32_t t = a[k];
-                        a[k] = b[k];
-                        b[k] = t;
-                    }
-                    if (k < Lt) {
-                        uint32_t t = ta[k];
-                        ta[k] = tb[k];
-                        tb[k] = t;
-                    }
-                }
-                __syncthreads();
-                if (tid == 0) {
-                    int t = S.la;
-                    S.la = S.lb;
-                    S.lb = t;
-                    t = S.lta;
-                    S.lta = S.ltb;
-                    S.ltb = t;
-                }
-                __syncthreads();
+            rr_submul(a, b, lb, ta, tb, ltb, La, Lt, (int64_t)q, sh, K, R);
+            la = trim(a, La);
+            lta = trim(ta, Lt);
+            if (cmp_big(a, la, b, lb) < 0) {
+                swap_(a, b);
+                swap_(la, lb);
+                swap_(ta, tb);
+                swap_(lta, ltb);
             }
         }
     }
-    __syncthreads();
-    if (tid == 0) {
-        if (S.mode != 1) {
-            info[0] = 2;
-            return;
-        }
-        const int ld = S.ltb;
-        if (ld == 0 || ld > hD) {
+    if (mode != 1) {
+        if (tid == 0) info[0] = 2;
+        return;
+    }
+    const int ld = ltb;
+    if (ld == 0 || ld > hD) {
+        if (tid == 0) {
             info[0] = 1;  // no fraction within the bounds
             info[1] = ld;
-            return;
         }
-        if (ld > den_cap) {
+        return;
+    }
+    if (ld > den_cap) {
+        if (tid == 0) {
             info[0] = 4;
             info[1] = ld;
-            return;
         }
-        for (int k = 0; k < ld; ++k) den[k] = tb[k];
+        return;
+    }
+    for (int k = tid; k < ld; k += kRR) den[k] = tb[k];
+    if (tid == 0) {
         info[0] = 0;
         info[1] = ld;
     }
 }
 
-__global__ void __launch_bounds__(kRT)
+__global__ void __launch_bounds__(kRR)
 k_ratrecon(const int64_t *__restrict__ z, int m, uint32_t p, int hN, int hD,
            uint32_t *__restrict__ gbuf, int cap, uint32_t *__restrict__ den, int den_cap,
            int32_t *__restrict__ info, const uint32_t *__restrict__ ainit, int alen) {
@@ -617,10 +680,422 @@ k_ratrecon(const int64_t *__restrict__ z, int m, uint32_t p, int hN, int hD,
 }
 
 // One CTA per job of a batch (numbers in shared memory, 4 * cap digits).
-__global__ void __launch_bounds__(kRT) k_ratrecon_multi(const RRJob *__restrict__ jobs, int cap) {
+__global__ void __launch_bounds__(kRR) k_ratrecon_multi(const RRJob *__restrict__ jobs, int cap) {
     extern __shared__ uint32_t dyn[];
     const RRJob j = jobs[blockIdx.x];
     ratrecon_body(j.z, j.m, j.p, j.hN, j.hD, dyn, cap, j.den, j.den_cap, j.info, nullptr, 0);
+}
+
+// ---------------------------------------------------------------------------
+// The same reconstruction with the numbers in radix 2^31, for the callers
+// that want the denominator in binary (one CTA of kRR threads). The result is
+// the one above -- the first remainder of Euclid on (p^m, X) below p^hN, and
+// its cofactor as the denominator if that is below p^hD -- computed three ways
+// faster: a position is split into digit and carry by a mask and a shift
+// rather than a division by p; the Lehmer matrix is found by one thread and
+// handed to the others through shared memory; and the denominator comes out
+// in 32-bit limbs, with no conversion after it. The p-adic digits are brought
+// to binary first by Horner's rule, two digits per pass (X <- X p^2 + d' p +
+// d), with p^m, p^hN and p^hD formed in the same passes.
+
+// floor(x / 2^s) for a number x of l limbs (radix 2^31) below 2^(s + 64).
+__device__ __forceinline__ uint64_t bits_at(const uint32_t *x, int l, int s) {
+    const int i = s / 31, o = s % 31;
+    const uint64_t x0 = i < l ? x[i] : 0, x1 = i + 1 < l ? x[i + 1] : 0,
+                   x2 = i + 2 < l ? x[i + 2] : 0;
+    return (x0 >> o) | (x1 << (31 - o)) | (x2 << (62 - o));
+}
+
+__device__ __forceinline__ int bitlen31(const uint32_t *x, int l) {
+    return l == 0 ? 0 : 31 * (l - 1) + (32 - __clz((int)x[l - 1]));
+}
+
+// 31-bit limb k of y 2^sh (sh = 31 sl + sb).
+__device__ __forceinline__ uint32_t shifted31(const uint32_t *y, int ylen, int k, int sl, int sb) {
+    const int i = k - sl;
+    const uint32_t hi = (i >= 0 && i < ylen) ? y[i] : 0;
+    const uint32_t lo = (i - 1 >= 0 && i - 1 < ylen) ? y[i - 1] : 0;
+    return sb ? ((hi << sb) | (lo >> (31 - sb))) & kM31 : hi;
+}
+
+// (x, y) <- (A x + B y, C x + D y) on limbs [0, La) and (tx, ty) <-
+// (|A| tx + |B| ty, |C| tx + |D| ty) on [0, Lt); |A|..|D| < 2^28, limbs below
+// 2^31: every product is one signed 32 x 32 -> 64-bit multiply and
+// |A x_k + B y_k + carry| < 2^61.
+__device__ void rb_lincomb(uint32_t *__restrict__ x, uint32_t *__restrict__ y,
+                           uint32_t *__restrict__ tx, uint32_t *__restrict__ ty, int La, int Lt,
+                           int32_t A, int32_t B, int32_t C, int32_t D, RRCarry &K,
+                           const Radix &R) {
+    int beg, end;
+    rr_chunk(max(La, Lt), beg, end);
+    const int32_t aA = A < 0 ? -A : A, aB = B < 0 ? -B : B, aC = C < 0 ? -C : C,
+                  aD = D < 0 ? -D : D;
+    const int ea = min(end, La), et = min(end, Lt), e4 = min(ea, et);
+    int64_t c[4] = {0, 0, 0, 0};
+    int k = beg;
+    for (; k < e4; ++k) {
+        const int32_t xv = (int32_t)x[k], yv = (int32_t)y[k];
+        const int32_t txv = (int32_t)tx[k], tyv = (int32_t)ty[k];
+        x[k] = norm31((int64_t)A * xv + (int64_t)B * yv + c[0], c[0]);
+        y[k] = norm31((int64_t)C * xv + (int64_t)D * yv + c[1], c[1]);
+        tx[k] = norm31((int64_t)aA * txv + (int64_t)aB * tyv + c[2], c[2]);
+        ty[k] = norm31((int64_t)aC * txv + (int64_t)aD * tyv + c[3], c[3]);
+    }
+    for (int j = k; j < ea; ++j) {
+        const int32_t xv = (int32_t)x[j], yv = (int32_t)y[j];
+        x[j] = norm31((int64_t)A * xv + (int64_t)B * yv + c[0], c[0]);
+        y[j] = norm31((int64_t)C * xv + (int64_t)D * yv + c[1], c[1]);
+    }
+    for (int j = k; j < et; ++j) {
+        const int32_t txv = (int32_t)tx[j], tyv = (int32_t)ty[j];
+        tx[j] = norm31((int64_t)aA * txv + (int64_t)aB * tyv + c[2], c[2]);
+        ty[j] = norm31((int64_t)aC * txv + (int64_t)aD * tyv + c[3], c[3]);
+    }
+    uint32_t *const w[4] = {x, y, tx, ty};
+    settle<4, true>(w, beg, end, c, K, R);
+}
+
+// x <- x - q y 2^sh on [0, La) and tx <- tx + q ty 2^sh on [0, Lt)
+// (0 < q < 2^29); the results are >= 0 and fit in their limbs.
+__device__ void rb_submul(uint32_t *__restrict__ x, const uint32_t *__restrict__ y, int ylen,
+                          uint32_t *__restrict__ tx, const uint32_t *__restrict__ ty, int tylen,
+                          int La, int Lt, uint32_t q, int sh, RRCarry &K, const Radix &R) {
+    int beg, end;
+    rr_chunk(max(La, Lt), beg, end);
+    const int sl = sh / 31, sb = sh % 31;
+    int64_t c[2] = {0, 0};
+    for (int k = beg; k < end; ++k) {
+        if (k < La)
+            x[k] = norm31((int64_t)x[k] - (int64_t)((uint64_t)q * shifted31(y, ylen, k, sl, sb)) +
+                              c[0],
+                          c[0]);
+        if (k < Lt)
+            tx[k] = norm31((int64_t)tx[k] + (int64_t)((uint64_t)q * shifted31(ty, tylen, k, sl, sb)) +
+                               c[1],
+                           c[1]);
+    }
+    uint32_t *const w[2] = {x, tx};
+    settle<2, true>(w, beg, end, c, K, R);
+}
+
+// For a >= b > 0 (bit lengths abits, bbits): c in [1, 2^29) and a bit shift
+// sh with c b 2^sh <= a, c >= 2^27 whenever sh > 0.
+__device__ void rb_exact_step(const uint32_t *a, int la, int abits, const uint32_t *b, int lb,
+                              int bbits, uint32_t &q, int &sh) {
+    uint64_t c;
+    int s = 0;
+    if (abits <= 62) {
+        // exact quotient; above the clamp, its leading 29 bits at a shift
+        c = bits_at(a, la, 0) / bits_at(b, lb, 0);
+        if (c >= (1ull << 29)) {
+            s = (64 - __clzll((long long)c)) - 29;
+            c >>= s;
+        }
+    } else {
+        // a >= atop 2^(abits - 62); b < bt 2^sb
+        const uint64_t atop = bits_at(a, la, abits - 62);
+        const int sb = bbits > 32 ? bbits - 32 : 0;
+        const uint64_t bt = bits_at(b, lb, sb) + 1;
+        s = abits - bbits - 28;
+        if (s < 0) s = 0;
+        const int e = (abits - 62) - (sb + s);  // in [-30, -2]
+        c = (atop / bt) >> (-e);
+    }
+    if (c >= (1ull << 29)) c = (1ull << 29) - 1;
+    if (c == 0) c = 1;
+    q = (uint32_t)c;
+    sh = s;
+}
+
+// floor(n / d) for 0 < d, n < 2^62 and a quotient below 2^28: a
+// single-precision estimate (relative error below 2^-21), one unit step
+// either way, and for the rare larger errors a second estimate on the exact
+// remainder and unit steps.
+__device__ __forceinline__ uint32_t quot28(uint64_t n, uint64_t d) {
+    const float fd = u64_to_float(d);
+    int64_t q = (int64_t)__float2uint_rz(__fdividef(u64_to_float(n), fd));
+    int64_t r = (int64_t)(n - (uint64_t)q * d);
+    if (r < 0) {
+        --q;
+        r += (int64_t)d;
+    } else if ((uint64_t)r >= d) {
+        ++q;
+        r -= (int64_t)d;
+    }
+    if (r < 0 || (uint64_t)r >= d) {
+        const float fr = r < 0 ? -u64_to_float((uint64_t)-r) : u64_to_float((uint64_t)r);
+        q += __float2int_rd(__fdividef(fr, fd));
+        r = (int64_t)(n - (uint64_t)q * d);
+        while (r < 0) {
+            --q;
+            r += (int64_t)d;
+        }
+        while ((uint64_t)r >= d) {
+            ++q;
+            r -= (int64_t)d;
+        }
+    }
+    return (uint32_t)q;
+}
+
+// A run of Euclid steps on the leading parts ah >= bh of a and b, both taken
+// at bit s (a = ah 2^s + a', b = bh 2^s + b', 0 <= a', b' < 2^s), with
+// r_0 = ah, r_1 = bh and cofactors r_i = u_i ah + v_i bh. The same quotients
+// applied to (a, b) give R_i = r_i 2^s + e_i with e_i = u_i a' + v_i b'; the
+// signs alternate (u_i >= 0 >= v_i for even i, u_i <= 0 <= v_i for odd i), so
+// -|v_i| 2^s < e_i < |u_i| 2^s for even i and -|u_i| 2^s < e_i < |v_i| 2^s
+// for odd i, up to equality when a cofactor is 0. The quotient q_i of
+// r_(i-1) by r_i is therefore that of R_(i-1) by R_i (0 <= R_(i+1) < R_i)
+// whenever
+//     r_(i+1) >= |v_(i+1)| and r_i - r_(i+1) >= |u_(i+1) - u_i|   (i+1 even),
+//     r_(i+1) >= |u_(i+1)| and r_i - r_(i+1) >= |v_(i+1) - v_i|   (i+1 odd).
+// One division per step, no second quotient. The run stops at the first step
+// that fails this, whose quotient or cofactors reach 2^28, or whose remainder
+// keeps at most lim bits (so that no remainder below the numerator bound is
+// skipped; the last steps are taken exactly). On return (a, b) <- (A a + B b,
+// C a + D b) applies the accepted steps.
+__device__ __forceinline__ int lehmer_bin(uint64_t ah, uint64_t bh, int s, int lim, int64_t &A,
+                                          int64_t &B, int64_t &C, int64_t &D) {
+    int64_t u0 = 1, v0 = 0, u1 = 0, v1 = 1;
+    uint64_t r0 = ah, r1 = bh;
+    int steps = 0;
+    bool even = true;  // parity of the index of the next remainder (2 first)
+    while (r1 > 0) {
+        if (r1 < (1ull << 34) && r0 >= (r1 << 28)) break;  // quotient >= 2^28
+        const uint32_t q = quot28(r0, r1);
+        const uint64_t r2 = r0 - (uint64_t)q * r1;
+        const int64_t u2 = u0 - (int64_t)q * u1, v2 = v0 - (int64_t)q * v1;
+        const int64_t au2 = u2 < 0 ? -u2 : u2, av2 = v2 < 0 ? -v2 : v2;
+        if (au2 >= (1ll << 28) || av2 >= (1ll << 28)) break;
+        const int64_t du = u2 - u1, dv = v2 - v1;
+        const uint64_t need1 = (uint64_t)(even ? av2 : au2);
+        const uint64_t need2 = (uint64_t)(even ? (du < 0 ? -du : du) : (dv < 0 ? -dv : dv));
+        if (r2 < need1 || r1 - r2 < need2) break;
+        if (s + (64 - __clzll((long long)r2)) <= lim) break;
+        u0 = u1;
+        v0 = v1;
+        u1 = u2;
+        v1 = v2;
+        r0 = r1;
+        r1 = r2;
+        even = !even;
+        ++steps;
+    }
+    A = u0;
+    B = v0;
+    C = u1;
+    D = v1;
+    return steps;
+}
+
+struct RBShared {
+    int64_t A, B, C, D;
+    int steps;  // > 0: Lehmer matrix; 0: exact step (q, sh)
+    int sh;
+    uint32_t q;
+};
+
+// z: m base-p digits of X (|z_i| < 2^59 each). base: 5 * cap + 2 * bcap
+// limbs (cap >= m + 4 for a, b, ta, tb and the digits; bcap >= max(hN, hD) + 4
+// for the bounds). On success info[0] = 0, info[1] = 32-bit limbs of the
+// denominator written to den, info[2] = its bit length, info[3] = its
+// leading 31 bits; info[0] = 1: no fraction within the bounds, 2: capacity.
+__device__ void ratrecon_bin_body(const int64_t *__restrict__ z, int m, uint32_t p, int hN,
+                                  int hD, uint32_t *__restrict__ base, int cap, int bcap,
+                                  uint32_t *__restrict__ den, int den_cap,
+                                  int32_t *__restrict__ info) {
+    __shared__ RRCarry K;
+    __shared__ RBShared S;
+    uint32_t *a = base, *b = base + cap, *ta = base + 2 * cap, *tb = base + 3 * cap,
+             *dg = base + 4 * cap, *NB = base + 5 * cap, *DB = base + 5 * cap + bcap;
+    const int tid = threadIdx.x;
+    const Radix R = make_radix(p);
+    for (int k = tid; k < 5 * cap + 2 * bcap; k += kRR) base[k] = 0;
+    __syncthreads();
+    // the digits of X mod p^m in [0, p)
+    {
+        int beg, end;
+        rr_chunk(m, beg, end);
+        int64_t c[1] = {0};
+        for (int k = beg; k < end; ++k) dg[k] = divmod_p(z[k] + c[0], R, c[0]);
+        uint32_t *const w[1] = {dg};
+        settle<1>(w, beg, end, c, K, R);
+    }
+    // Horner: b <- X, a <- p^e with e = m at the end; NB = p^hN, DB = p^hD.
+    // p^2 = P1 2^31 + P0; limb k of v p^2 is x_k P0 + x_(k-1) P1 + carry.
+    const uint64_t p2 = (uint64_t)p * p;
+    const uint32_t P0 = (uint32_t)(p2 & kM31), P1 = (uint32_t)(p2 >> 31);
+    int L = 0, e = m & 1;  // limbs in use (an upper bound), exponent of a
+    if (tid == 0) {
+        a[0] = e ? p : 1;
+        b[0] = (m & 1) ? dg[m - 1] : 0;
+    }
+    L = 1;
+    __syncthreads();
+    auto capture = [&](uint32_t *dst, int want) {
+        // dst = p^want (< 2^(31 want): at most want <= bcap - 4 limbs) from
+        // a = p^e, e in {want, want - 1}
+        const int Lc = min(L + 1, bcap);
+        for (int k = tid; k < Lc; k += kRR) dst[k] = k < L ? a[k] : 0;
+        __syncthreads();
+        if (e == want - 1 && tid == 0) {
+            uint64_t c = 0;
+            for (int k = 0; k < Lc; ++k) {
+                const uint64_t v = (uint64_t)dst[k] * p + c;
+                dst[k] = (uint32_t)v & kM31;
+                c = v >> 31;
+            }
+        }
+        __syncthreads();
+    };
+    if (hN == 0) {
+        if (tid == 0) NB[0] = 1;
+    } else if (e == hN || e == hN - 1) {
+        capture(NB, hN);
+    }
+    if (hD == 0) {
+        if (tid == 0) DB[0] = 1;
+    } else if (e == hD || e == hD - 1) {
+        capture(DB, hD);
+    }
+    __syncthreads();
+    for (int i = m - 2 - (m & 1); i >= 0; i -= 2) {
+        // a p^2 = p^(e+2) and b p^2 + v < p^(e+2) < 2^(31 (e+2)): e + 2 limbs
+        L = min(cap, e + 3);
+        int beg, end;
+        rr_chunk(L, beg, end);
+        int64_t c[2] = {0, 0};
+        if (beg == 0 && end > 0) c[1] = (int64_t)((uint64_t)dg[i + 1] * p + dg[i]);
+        uint64_t ha = 0, hb = 0;
+        for (int k = beg; k < end; ++k) {
+            const uint32_t av = a[k], bv = b[k];
+            const uint64_t va = (uint64_t)av * P0 + ha + (uint64_t)c[0];
+            const uint64_t vb = (uint64_t)bv * P0 + hb + (uint64_t)c[1];
+            a[k] = (uint32_t)va & kM31;
+            b[k] = (uint32_t)vb & kM31;
+            c[0] = (int64_t)(va >> 31);
+            c[1] = (int64_t)(vb >> 31);
+            ha = (uint64_t)av * P1;
+            hb = (uint64_t)bv * P1;
+        }
+        c[0] += (int64_t)ha;
+        c[1] += (int64_t)hb;
+        uint32_t *const w[2] = {a, b};
+        settle<2, true>(w, beg, end, c, K, R);
+        e += 2;
+        if (e == hN || e == hN - 1) capture(NB, hN);
+        if (e == hD || e == hD - 1) capture(DB, hD);
+    }
+    // the digits' space becomes tb's scratch: clear ta and tb, tb = 1
+    for (int k = tid; k < 2 * cap; k += kRR) ta[k] = 0;
+    __syncthreads();
+    if (tid == 0) tb[0] = 1;
+    int la = trim(a, L), lb = trim(b, L), lta = 0, ltb = 1;
+    const int lnb = trim(NB, bcap), ldb = trim(DB, bcap);
+    const int nbbits = bitlen31(NB, lnb);
+    __syncthreads();
+    // a = p^m > X = b: no exchange needed
+    const long max_iter = 4L * 32 * (m + 4) + 1000;
+    int mode = 0;  // 0 running, 1 done, 2 capacity exceeded
+    for (long iter = 0; iter < max_iter; ++iter) {
+        if (cmp_big(b, lb, NB, lnb) < 0) {
+            mode = 1;
+            break;
+        }
+        const bool swap_only = cmp_big(a, la, b, lb) < 0;
+        if (!swap_only && tid == 0) {
+            const int abits = bitlen31(a, la), bbits = bitlen31(b, lb);
+            const int s = abits > 62 ? abits - 62 : 0;
+            int64_t A, B, C, D;
+            const int steps =
+                lehmer_bin(bits_at(a, la, s), bits_at(b, lb, s), s, nbbits + 64, A, B, C, D);
+            S.steps = steps;
+            S.A = A;
+            S.B = B;
+            S.C = C;
+            S.D = D;
+            if (steps == 0) {
+                uint32_t q;
+                int sh;
+                rb_exact_step(a, la, abits, b, lb, bbits, q, sh);
+                S.q = q;
+                S.sh = sh;
+            }
+        }
+        if (swap_only) {
+            swap_(a, b);
+            swap_(la, lb);
+            swap_(ta, tb);
+            swap_(lta, ltb);
+            continue;
+        }
+        __syncthreads();  // the step is published; every thread has read the lengths
+        const int steps = S.steps;
+        if (steps > 0) {
+            const int La = la, Lt = max(lta, ltb) + 2;
+            if (Lt > cap) {
+                mode = 2;
+                break;
+            }
+            rb_lincomb(a, b, ta, tb, La, Lt, (int32_t)S.A, (int32_t)S.B, (int32_t)S.C,
+                       (int32_t)S.D, K, R);
+            la = trim(a, La);
+            lb = trim(b, La);
+            lta = trim(ta, Lt);
+            ltb = trim(tb, Lt);
+        } else {
+            const uint32_t q = S.q;
+            const int sh = S.sh;
+            const int La = la, Lt = max(lta, ltb + sh / 31 + 1) + 2;
+            if (Lt > cap) {
+                mode = 2;
+                break;
+            }
+            rb_submul(a, b, lb, ta, tb, ltb, La, Lt, q, sh, K, R);
+            la = trim(a, La);
+            lta = trim(ta, Lt);
+        }
+    }
+    if (mode != 1) {
+        if (tid == 0) info[0] = 2;
+        return;
+    }
+    // the denominator tb, if 0 < tb < p^hD, in 32-bit limbs
+    if (ltb == 0 || cmp_big(tb, ltb, DB, ldb) >= 0) {
+        if (tid == 0) {
+            info[0] = 1;
+            info[1] = ltb;
+        }
+        return;
+    }
+    const int bits = bitlen31(tb, ltb);
+    const int l32 = (bits + 31) / 32;
+    if (l32 > den_cap) {
+        if (tid == 0) {
+            info[0] = 4;
+            info[1] = l32;
+        }
+        return;
+    }
+    for (int j = tid; j < l32; j += kRR) {
+        const int i = j + j / 31, o = j % 31;
+        const uint64_t lo = tb[i], hi = i + 1 < ltb ? tb[i + 1] : 0;
+        den[j] = (uint32_t)((lo >> o) | (hi << (31 - o)));
+    }
+    if (tid == 0) {
+        info[0] = 0;
+        info[1] = l32;
+        info[2] = bits;
+        info[3] = (int32_t)bits_at(tb, ltb, bits > 31 ? bits - 31 : 0);
+    }
+}
+
+// The numbers always in shared memory (ratrecon_bin_fits).
+__global__ void __launch_bounds__(kRR)
+k_ratrecon_bin(const int64_t *__restrict__ z, int m, uint32_t p, int hN, int hD, int cap,
+               int bcap, uint32_t *__restrict__ den, int den_cap, int32_t *__restrict__ info) {
+    extern __shared__ uint32_t dyn[];
+    ratrecon_bin_body(z, m, p, hN, hD, dyn, cap, bcap, den, den_cap, info);
 }
 
 // Base-p digits (len of them) -> base-2^32 limbs, Horner on one CTA:
@@ -709,6 +1184,10 @@ int launch_mixed_to_int(const uint32_t *primes, const int32_t *digits, int count
 int launch_ratrecon(const int64_t *z, int m, uint32_t p, int hN, int hD, uint32_t *den,
                     int den_cap, int32_t *info, Workspace &ws, const uint32_t *ainit, int alen) {
     cudaStream_t s = ws.stream();
+    if (p <= (1u << 30) || p >= (1u << 31)) {
+        set_last_error("rational reconstruction: p = %u is outside (2^30, 2^31)", p);
+        return IDET_ERR_ARG;
+    }
     const int cap = (m > alen ? m : alen) + 4;
     uint32_t *gbuf = nullptr;
     size_t smem = sizeof(uint32_t) * 4 * (size_t)cap;
@@ -718,7 +1197,37 @@ int launch_ratrecon(const int64_t *z, int m, uint32_t p, int hN, int hD, uint32_
     } else {
         IDET_TRY(allow_max_smem((const void *)k_ratrecon));
     }
-    k_ratrecon<<<1, kRT, smem, s>>>(z, m, p, hN, hD, gbuf, cap, den, den_cap, info, ainit, alen);
+    k_ratrecon<<<1, kRR, smem, s>>>(z, m, p, hN, hD, gbuf, cap, den, den_cap, info, ainit, alen);
+    count_launch();
+    IDET_CUDA_TRY(cudaGetLastError());
+    return IDET_OK;
+}
+
+static size_t ratrecon_bin_smem(int m, int hN, int hD) {
+    const size_t cap = (size_t)m + 4, bcap = (size_t)(hN > hD ? hN : hD) + 4;
+    return sizeof(uint32_t) * (5 * cap + 2 * bcap);
+}
+
+bool ratrecon_bin_fits(int m, int hN, int hD) {
+    return m >= 1 && ratrecon_bin_smem(m, hN, hD) <= 190 * 1024;
+}
+
+int launch_ratrecon_bin(const int64_t *z, int m, uint32_t p, int hN, int hD, uint32_t *den,
+                        int den_cap, int32_t *info, Workspace &ws) {
+    cudaStream_t s = ws.stream();
+    if (p <= (1u << 30) || p >= (1u << 31)) {
+        set_last_error("rational reconstruction: p = %u is outside (2^30, 2^31)", p);
+        return IDET_ERR_ARG;
+    }
+    if (m < 1 || hN < 0 || hD < 0 || hN > m || hD > m || !ratrecon_bin_fits(m, hN, hD)) {
+        set_last_error("rational reconstruction: bad bounds or too long (m %d, hN %d, hD %d)", m,
+                       hN, hD);
+        return IDET_ERR_ARG;
+    }
+    const int cap = m + 4, bcap = (hN > hD ? hN : hD) + 4;
+    IDET_TRY(allow_max_smem((const void *)k_ratrecon_bin));
+    k_ratrecon_bin<<<1, kRR, ratrecon_bin_smem(m, hN, hD), s>>>(z, m, p, hN, hD, cap, bcap, den,
+                                                                 den_cap, info);
     count_launch();
     IDET_CUDA_TRY(cudaGetLastError());
     return IDET_OK;
@@ -733,7 +1242,7 @@ int launch_ratrecon_multi(const RRJob *jobs_dev, int count, int max_m, cudaStrea
         return IDET_ERR_ARG;
     }
     IDET_TRY(allow_max_smem((const void *)k_ratrecon_multi));
-    k_ratrecon_multi<<<count, kRT, smem, s>>>(jobs_dev, cap);
+    k_ratrecon_multi<<<count, kRR, smem, s>>>(jobs_dev, cap);
     count_launch();
     IDET_CUDA_TRY(cudaGetLastError());
     return IDET_OK;

@@ -246,12 +246,15 @@ k_panel(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb,
 // Panel factorisation by a cluster of kCl CTAs (one cluster per prime).
 // The panel (rows [j0, n), columns [j0, j0 + jb)) is split into kCl
 // contiguous row blocks held in the CTAs' shared memory for the whole
-// panel. Per column: the owner of the diagonal row publishes whether the
-// diagonal entry is nonzero; otherwise every CTA publishes its first nonzero
-// row and all take the minimum (first-nonzero rule); the pivot row is read
-// through distributed shared memory; each CTA scales and updates its rows.
-// Swapped rows are exchanged across CTAs, and their parts outside the panel
-// are swapped in global memory.
+// panel. Every CTA also keeps a replica of the panel's top jb rows -- the
+// rows that become the pivot rows -- and applies the same eliminations to
+// it, so that each CTA knows every pivot row and pivot without
+// communication: a column costs one CTA barrier. Warp 0 eliminates the next
+// pivot row of the replica first and inverts the next pivot while the other
+// warps update the CTA's rows. Only a zero pivot (first-nonzero rule) needs
+// the cluster: the first nonzero row below it is found across the CTAs and
+// the two rows are exchanged in the owners' blocks (through distributed
+// shared memory), in every replica, and outside the panel in global memory.
 constexpr int kCl = 8;
 constexpr int kClThreads = 512;
 constexpr int kSP = kNBMax + 1;  // row stride of a CTA's panel block in shared memory
@@ -262,13 +265,11 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
                 int32_t *__restrict__ perm) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
-    extern __shared__ int32_t sp[];          // chunk x kSP panel block
-    __shared__ int s_flag[2];                // diagonal nonzero (owner)
-    __shared__ int32_t s_pinv[2];            // its inverse, when nonzero (owner)
-    __shared__ int s_cand[2];                // first nonzero row (each CTA)
-    __shared__ int32_t s_u[kNBMax];
-    __shared__ int32_t s_tmp[kNBMax];
-    __shared__ int32_t s_inv;
+    extern __shared__ int32_t sp[];         // chunk x kSP: this CTA's rows
+    __shared__ int32_t dg[kNBMax * kSP];    // replica of rows [j0, j0 + jb)
+    __shared__ int32_t s_inv[2];            // inverse of the pivot of column c, slot c & 1
+    __shared__ int s_cand;                  // first nonzero row below a zero pivot
+    __shared__ int32_t s_tmp[2][kNBMax];    // the two rows of an exchange
     const int rank = (int)cluster.block_rank();
     const int w = blockIdx.x / kCl;
     const ModP M = mods[w];
@@ -278,57 +279,58 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
     const int64_t rbeg = j0 + (int64_t)rank * chunk;
     const int64_t rend = min(n, rbeg + chunk);
     const int nloc = rend > rbeg ? (int)(rend - rbeg) : 0;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int e = tid; e < nloc * jb; e += kClThreads) {
         int r = e / jb, j = e % jb;
         sp[r * kSP + j] = a[(rbeg + r) * n + j0 + j];
+    }
+    for (int e = tid; e < jb * jb; e += kClThreads) {
+        int r = e / jb, j = e % jb;
+        dg[r * kSP + j] = a[(j0 + r) * n + j0 + j];
     }
     uint32_t det = st[w].det;
     int neg = st[w].neg;
     bool dead = false;
     __syncthreads();
-    cluster.sync();
+    if (tid == 0) s_inv[0] = dg[0] != 0 ? inv_bal32(dg[0], M.p) : 0;
+    __syncthreads();
     for (int c = 0; c < jb; ++c) {
         const int64_t col = j0 + c;
-        const int owner = (int)((col - j0) / chunk);
-        const int par = c & 1;
-        // The owner of the diagonal row publishes whether the diagonal entry
-        // is nonzero and, if so, its inverse, computed while the other CTAs
-        // are still updating (the owner has fewer rows below the diagonal).
-        if (rank == owner && tid == 0) {
-            const int32_t dg = sp[(int)(col - rbeg) * kSP + c];
-            s_flag[par] = dg != 0;
-            if (dg != 0) s_pinv[par] = inv_bal32(dg, M.p);
-        }
-        cluster.sync();
-        int *fl = cluster.map_shared_rank(&s_flag[par], owner);
-        int64_t piv = col;
-        const bool swapped = !*fl;
-        if (swapped) {
-            // every CTA: first row >= col + 1 of its block with a nonzero
-            if (tid == 0) s_cand[par] = INT_MAX;
-            __syncthreads();
+        int32_t pv = dg[c * kSP + c];
+        if (pv == 0) {
+            // (the replicas are identical: every CTA of the cluster is here)
+            if (tid == 0) s_cand = INT_MAX;
+            cluster.sync();
             for (int r = tid; r < nloc; r += kClThreads) {
-                int64_t gi = rbeg + r;
-                if (gi > col && sp[r * kSP + c] != 0) atomicMin(&s_cand[par], (int)gi);
+                const int64_t gi = rbeg + r;
+                if (gi > col && sp[r * kSP + c] != 0) atomicMin(&s_cand, (int)gi);
             }
             cluster.sync();
             int best = INT_MAX;
-            for (int k = 0; k < kCl; ++k) best = min(best, *cluster.map_shared_rank(&s_cand[par], k));
+            for (int k = 0; k < kCl; ++k)
+                best = min(best, *cluster.map_shared_rank(&s_cand, k));
             if (best == INT_MAX) {
                 dead = true;
                 break;
             }
-            piv = best;
-            // exchange rows piv and col (panel part) through DSMEM
-            const int po = (int)((piv - j0) / chunk);
-            int32_t *prow = cluster.map_shared_rank(sp, po) + (int)(piv - (j0 + (int64_t)po * chunk)) * kSP;
-            int32_t *crow = cluster.map_shared_rank(sp, owner) + (int)(col - (j0 + (int64_t)owner * chunk)) * kSP;
-            if (rank == 0 && tid < jb) s_tmp[tid] = crow[tid];
-            cluster.sync();
+            const int64_t piv = best;
+            const int po = (int)((piv - j0) / chunk), co = (int)((col - j0) / chunk);
+            int32_t *prow = cluster.map_shared_rank(sp, po) +
+                            (int)(piv - (j0 + (int64_t)po * chunk)) * kSP;
+            int32_t *crow = cluster.map_shared_rank(sp, co) +
+                            (int)(col - (j0 + (int64_t)co * chunk)) * kSP;
+            if (tid < jb) {
+                s_tmp[0][tid] = crow[tid];
+                s_tmp[1][tid] = prow[tid];
+            }
+            cluster.sync();  // both rows read everywhere before they change
             if (rank == 0 && tid < jb) {
-                crow[tid] = prow[tid];
-                prow[tid] = s_tmp[tid];
+                crow[tid] = s_tmp[1][tid];
+                prow[tid] = s_tmp[0][tid];
+            }
+            if (tid < jb) {
+                dg[c * kSP + tid] = s_tmp[1][tid];
+                if (piv < j0 + jb) dg[(int)(piv - j0) * kSP + tid] = s_tmp[0][tid];
             }
             // parts outside the panel, in global memory (rank 0)
             if (rank == 0) {
@@ -347,33 +349,47 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
             }
             neg ^= 1;
             cluster.sync();
-        }
-        // pivot row -> local copy (and the owner's inverse unless rows were
-        // swapped, when the pivot is not the entry the owner inverted)
-        {
-            const int32_t *crow = cluster.map_shared_rank(sp, owner) + (int)(col - (j0 + (int64_t)owner * chunk)) * kSP;
-            if (tid < jb) s_u[tid] = crow[tid];
-            if (!swapped && tid == 0) s_inv = *cluster.map_shared_rank(&s_pinv[par], owner);
-        }
-        __syncthreads();
-        const int32_t pv = s_u[c];
-        if (swapped) {
-            if (tid == 0) s_inv = inv_bal32(pv, M.p);
+            pv = dg[c * kSP + c];
+            if (tid == 0) s_inv[c & 1] = inv_bal32(pv, M.p);
             __syncthreads();
         }
+        const int32_t inv = s_inv[c & 1];
         det = det_mul(det, pv, M);
-        const int32_t inv = s_inv;
-        // a thread per row below the pivot: scale column c, then update the
-        // row's remaining panel columns (the row stride kSP = 33 words keeps
-        // the lanes of a warp on distinct banks)
-        for (int r = tid; r < nloc; r += kClThreads) {
-            if (rbeg + r <= col) continue;
-            int32_t *row = sp + r * kSP;
-            const int32_t l = mul_bal(row[c], inv, M);
-            row[c] = l;
-            if (l)
-                for (int j = c + 1; j < jb; ++j)
-                    row[j] = red_bal((int64_t)row[j] - (int64_t)l * s_u[j], M);
+        const int32_t *u = dg + c * kSP;
+        if (warp == 0) {
+            // the next pivot row of the replica, then the next pivot's inverse
+            if (c + 1 < jb) {
+                int32_t *row = dg + (c + 1) * kSP;
+                const int32_t l = mul_bal(row[c], inv, M);
+                __syncwarp();
+                if (lane == c) row[c] = l;
+                if (l && lane > c && lane < jb)
+                    row[lane] = red_bal((int64_t)row[lane] - (int64_t)l * u[lane], M);
+                __syncwarp();
+                if (lane == 0) {
+                    const int32_t d = row[c + 1];
+                    s_inv[(c + 1) & 1] = d != 0 ? inv_bal32(d, M.p) : 0;
+                }
+            }
+        } else {
+            // a thread per row: this CTA's rows below the pivot, then the
+            // replica's rows c + 2 .. jb - 1 (the row stride kSP = 33 words
+            // keeps the lanes of a warp on distinct banks)
+            const int items = nloc + max(0, jb - c - 2);
+            for (int it = tid - 32; it < items; it += kClThreads - 32) {
+                int32_t *row;
+                if (it < nloc) {
+                    if (rbeg + it <= col) continue;
+                    row = sp + it * kSP;
+                } else {
+                    row = dg + (c + 2 + (it - nloc)) * kSP;
+                }
+                const int32_t l = mul_bal(row[c], inv, M);
+                row[c] = l;
+                if (l)
+                    for (int j = c + 1; j < jb; ++j)
+                        row[j] = red_bal((int64_t)row[j] - (int64_t)l * u[j], M);
+            }
         }
         __syncthreads();
     }

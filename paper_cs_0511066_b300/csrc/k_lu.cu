@@ -55,6 +55,43 @@ __device__ __forceinline__ int32_t inv_bal32(int32_t a, uint32_t p) {
     return t0;
 }
 
+// Montgomery form with R = 2^32 for the panel's row updates: with u' = u R
+// mod p (balanced) stored once per pivot row, r - l u mod p costs one
+// 32 x 32 -> 64 product and one reduction by two 32-bit multiplies. For
+// t = l u' (|t| < p^2 / 4) and q = t p^{-1} mod 2^32 (as int32), t - q p is
+// divisible by 2^32 and v = (t - q p) / 2^32 = hi(t) - hi(q p) (the low words
+// agree) is l u mod p with |v| < p^2 / 2^34 + p / 2 < 0.63 p; r - v (in 64
+// bits) is then brought into the balanced range by one step either way.
+struct Mont {
+    int32_t p, half;
+    uint32_t pinv;  // p^{-1} mod 2^32
+    int32_t r1;     // 2^32 mod p, balanced
+};
+
+__device__ __forceinline__ Mont make_mont(uint32_t p) {
+    Mont m;
+    m.p = (int32_t)p;
+    m.half = (int32_t)((p - 1) / 2);
+    uint32_t x = p;  // p p = 1 mod 8; each step doubles the correct bits
+    for (int i = 0; i < 4; ++i) x *= 2u - p * x;
+    m.pinv = x;
+    int64_t r = (int64_t)((1ull << 32) % p);
+    if (r > m.half) r -= p;
+    m.r1 = (int32_t)r;
+    return m;
+}
+
+__device__ __forceinline__ int32_t sub_mont(int32_t r, int32_t l, int32_t um, const Mont &m) {
+    const int64_t t = (int64_t)l * um;
+    const int32_t q = (int32_t)((uint32_t)t * m.pinv);
+    const int32_t v = (int32_t)(t >> 32) - __mulhi(q, m.p);
+    // |r - v| < 1.13 p can pass 2^31 for p near 2^31: 64-bit
+    int64_t x = (int64_t)r - v;
+    if (x > m.half) x -= m.p;
+    if (x < -m.half) x += m.p;
+    return (int32_t)x;
+}
+
 // g: the residues (n x n, ld n), or null with A64: the int64 entries (n x n,
 // ld n), reduced here while they are loaded.
 __device__ void lu_small_body(int32_t *__restrict__ g, int n, const ModP M,
@@ -270,6 +307,7 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
     __shared__ int32_t s_inv[2];            // inverse of the pivot of column c, slot c & 1
     __shared__ int s_cand;                  // first nonzero row below a zero pivot
     __shared__ int32_t s_tmp[2][kNBMax];    // the two rows of an exchange
+    __shared__ int32_t s_um[2][kNBMax];     // pivot row of column c in Montgomery form, slot c & 1
     const int rank = (int)cluster.block_rank();
     const int w = blockIdx.x / kCl;
     const ModP M = mods[w];
@@ -291,8 +329,10 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
     uint32_t det = st[w].det;
     int neg = st[w].neg;
     bool dead = false;
+    const Mont mt = make_mont(M.p);
     __syncthreads();
     if (tid == 0) s_inv[0] = dg[0] != 0 ? inv_bal32(dg[0], M.p) : 0;
+    if (tid < jb) s_um[0][tid] = mul_bal(dg[tid], mt.r1, M);
     __syncthreads();
     for (int c = 0; c < jb; ++c) {
         const int64_t col = j0 + c;
@@ -351,21 +391,23 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
             cluster.sync();
             pv = dg[c * kSP + c];
             if (tid == 0) s_inv[c & 1] = inv_bal32(pv, M.p);
+            if (tid < jb) s_um[c & 1][tid] = mul_bal(dg[c * kSP + tid], mt.r1, M);
             __syncthreads();
         }
         const int32_t inv = s_inv[c & 1];
         det = det_mul(det, pv, M);
-        const int32_t *u = dg + c * kSP;
+        const int32_t *um = s_um[c & 1];
         if (warp == 0) {
-            // the next pivot row of the replica, then the next pivot's inverse
+            // the next pivot row of the replica (and its Montgomery form),
+            // then the next pivot's inverse
             if (c + 1 < jb) {
                 int32_t *row = dg + (c + 1) * kSP;
                 const int32_t l = mul_bal(row[c], inv, M);
                 __syncwarp();
                 if (lane == c) row[c] = l;
-                if (l && lane > c && lane < jb)
-                    row[lane] = red_bal((int64_t)row[lane] - (int64_t)l * u[lane], M);
+                if (l && lane > c && lane < jb) row[lane] = sub_mont(row[lane], l, um[lane], mt);
                 __syncwarp();
+                if (lane < jb) s_um[(c + 1) & 1][lane] = mul_bal(row[lane], mt.r1, M);
                 if (lane == 0) {
                     const int32_t d = row[c + 1];
                     s_inv[(c + 1) & 1] = d != 0 ? inv_bal32(d, M.p) : 0;
@@ -387,8 +429,7 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
                 const int32_t l = mul_bal(row[c], inv, M);
                 row[c] = l;
                 if (l)
-                    for (int j = c + 1; j < jb; ++j)
-                        row[j] = red_bal((int64_t)row[j] - (int64_t)l * u[j], M);
+                    for (int j = c + 1; j < jb; ++j) row[j] = sub_mont(row[j], l, um[j], mt);
             }
         }
         __syncthreads();
@@ -736,14 +777,18 @@ template <bool WIDE>
 int trsm_lower(const int32_t *Lm, int64_t sL, int32_t *X, int64_t sX, int64_t n,
                int64_t lr0, int64_t xr0, int jb, int64_t c0, int64_t ncols,
                const ModP *mods, const LUState *st, int W, cudaStream_t s,
-               int32_t *tri = nullptr) {
+               int32_t *tri = nullptr, bool have_inv = false) {
     if (ncols <= 0) return IDET_OK;
     if (tri) {
-        // explicit inverse of the diagonal block, then a dense apply
-        k_tri_inv<WIDE, false><<<W, kNBMax * kNBMax, 0, s>>>(Lm, sL, n, lr0, jb, mods, st, tri);
+        // explicit inverse of the diagonal block (unless tri holds it from
+        // an earlier solve with the same block), then a dense apply
+        if (!have_inv) {
+            k_tri_inv<WIDE, false><<<W, kNBMax * kNBMax, 0, s>>>(Lm, sL, n, lr0, jb, mods, st, tri);
+            count_launch();
+        }
         k_tri_apply<WIDE><<<dim3((unsigned)((ncols + 31) / 32), W), 128, 0, s>>>(
             tri, X, sX, n, xr0, jb, c0, ncols, mods, st);
-        count_launch(2);
+        count_launch();
         IDET_CUDA_TRY(cudaGetLastError());
         return IDET_OK;
     }
@@ -798,19 +843,29 @@ int lu_blocked(int32_t *R, int64_t n, const ModP *mods, int W, int nb, int32_t *
             }
             count_launch();
             IDET_CUDA_TRY(cudaGetLastError());
+            // the inverse of this panel's L11 goes to slot (j0 - J0) / nb of
+            // tri, for the solve inside the block column and again for the
+            // block row below
+            int32_t *tri_p = tri ? tri + (size_t)((j0 - J0) / nb) * W * kNBMax * kNBMax : nullptr;
             const int64_t inner = J0 + JB - (j0 + jb);  // columns left in the block column
             if (inner > 0) {
                 IDET_TRY(trsm_lower<WIDE>(R, nn, R, nn, n, j0, j0, jb, j0 + jb, inner, mods, st,
-                                          W, s, tri));
+                                          W, s, tri_p));
                 IDET_TRY(upd(j0 + jb, j0 + jb, j0, (int)(n - j0 - jb), (int)inner, jb));
+            } else if (tri_p && n - J0 - JB > 0) {
+                k_tri_inv<WIDE, false><<<W, kNBMax * kNBMax, 0, s>>>(R, nn, n, j0, jb, mods, st,
+                                                                      tri_p);
+                count_launch();
+                IDET_CUDA_TRY(cudaGetLastError());
             }
         }
         const int64_t rest = n - J0 - JB;
         if (rest <= 0) break;
         for (int64_t i0 = J0; i0 < J0 + JB; i0 += nb) {
             const int ib = (int)((J0 + JB - i0) < nb ? (J0 + JB - i0) : nb);
+            int32_t *tri_p = tri ? tri + (size_t)((i0 - J0) / nb) * W * kNBMax * kNBMax : nullptr;
             IDET_TRY(trsm_lower<WIDE>(R, nn, R, nn, n, i0, i0, ib, J0 + JB, rest, mods, st, W, s,
-                                      tri));
+                                      tri_p, tri_p != nullptr));
             const int64_t below = J0 + JB - (i0 + ib);
             if (below > 0) IDET_TRY(upd(i0 + ib, J0 + JB, i0, (int)below, (int)rest, ib));
         }
@@ -849,7 +904,7 @@ int lu_factor_batched(int32_t *R, int64_t n, const ModP *mods_dev,
                              : IDET_PATH_TC05;
         int32_t *tri = nullptr;
         void *scratch = nullptr;
-        IDET_TRY(ws.alloc_n(&tri, (size_t)W * kNBMax * kNBMax));
+        IDET_TRY(ws.alloc_n(&tri, (size_t)4 * W * kNBMax * kNBMax));  // 4 panels per block column
         if (path == IDET_PATH_TC05) IDET_TRY(ws.alloc(&scratch, tc05_scratch_bytes(n, W, 5)));
         IDET_TRY(lu_blocked<true>(R, n, mods_dev, W, nb, perm, st, s, path, scratch, tri));
         if (path == IDET_PATH_TC05) IDET_TRY(tc05_check_error(s));
@@ -866,7 +921,7 @@ int lu_factor_batched(int32_t *R, int64_t n, const ModP *mods_dev,
             path == IDET_PATH_I8 || path == IDET_PATH_BF16 || path == IDET_PATH_F64;
         if (legacy_tc) IDET_TRY(ws.alloc(&scratch, tc_scratch_bytes(n, W, path)));
         int32_t *tri = nullptr;
-        IDET_TRY(ws.alloc_n(&tri, (size_t)W * kNBMax * kNBMax));
+        IDET_TRY(ws.alloc_n(&tri, (size_t)4 * W * kNBMax * kNBMax));  // 4 panels per block column
         IDET_TRY(lu_blocked<false>(R, n, mods_dev, W, nb, perm, st, s, path, scratch, tri));
         if (path == IDET_PATH_TC05) IDET_TRY(tc05_check_error(s));
         if (legacy_tc) IDET_TRY(tc_check_error(s));

@@ -253,7 +253,7 @@ def run_case(case):
     import paper_cs_0511066_b300 as idet
     if case == "lu_paths":
         return run_lu_paths(torch, idet)
-    if case == "lift1k":
+    if case in ("lift1k", "rr"):
         A = torch.from_numpy(workloads.dense_u8(1000, seed=0)).cuda()
     else:
         A = torch.from_numpy(workloads.dense_pm2p20(4000, seed=0)).cuda()
@@ -261,6 +261,10 @@ def run_case(case):
     if case in ("lift", "lift1k"):
         b = workloads.random_rhs(A.shape[0], 1 << 40, seed=1)
         idet.dixon_digits(A, b, 2147483629, 64)
+    elif case == "rr":
+        # the whole determinant at n = 1000: one rational reconstruction of
+        # 803 base-p digits in radix 2^31
+        idet.int_det(A)
     elif case.startswith("lu"):
         path = {"lu": 1, "lu_int64": 1, "lu_i8": 2, "lu_f64": 3, "lu_bf16": 4, "lu_tc05": 5}[case]
         idet.det_mod_primes(A, [1048583, 1048589, 1048601, 1048609], update_path=path)
@@ -662,6 +666,7 @@ def main():
                          "'lu' / 'lu_int64' / 'lu_i8' / 'lu_f64' / 'lu_bf16' / 'lu_tc05' (det "
                          "mod 4 primes, n=4000, one update path): runs once and prints timings; "
                          "'lu_paths': every update path timed on 16 primes; "
+                         "'rr': the whole determinant at n=1000 [0,255] (one reconstruction); "
                          "'peaks': int8/bf16/fp64 GEMM throughput of the vendor libraries")
     ap.add_argument("--workload", default="plain",
                     choices=["plain", "batch", "serve", "lift_heavy", "small", "ablation",

@@ -260,15 +260,17 @@ __device__ __forceinline__ void chunk_of(int len, int &beg, int &end) {
 
 // The reconstruction's chunks: an odd stride puts the threads' digits of one
 // step in distinct shared-memory banks.
+template <int T = kRR>
 __device__ __forceinline__ void rr_chunk(int len, int &beg, int &end) {
-    const int per = ((len + kRR - 1) / kRR) | 1;
+    const int per = ((len + T - 1) / T) | 1;
     beg = min(len, (int)threadIdx.x * per);
     end = min(len, beg + per);
 }
 
+template <int T = kRR>
 struct RRCarry {
-    int64_t co[4][kRR];   // carry out of each chunk, computed with carry-in 0
-    int64_t co2[4][kRR];  // carries that rippled through a whole chunk
+    int64_t co[4][T];   // carry out of each chunk, computed with carry-in 0
+    int64_t co2[4][T];  // carries that rippled through a whole chunk
 };
 
 // Radix 2^31: v = carry * 2^31 + digit with 0 <= digit < 2^31 (floor
@@ -292,9 +294,9 @@ __device__ __forceinline__ uint32_t norm(int64_t v, const Radix &R, int64_t &car
 // every carry whose ripple ends inside the next chunk; a ripple through a
 // whole chunk (digits all radix - 1, or all 0 for a borrow) takes further
 // passes, each moving it at least one chunk up.
-template <int NA, bool BIN = false>
+template <int NA, bool BIN = false, int T = kRR>
 __device__ __forceinline__ void settle(uint32_t *const (&w)[NA], int beg, int end,
-                                       const int64_t (&c)[NA], RRCarry &K, const Radix &R) {
+                                       const int64_t (&c)[NA], RRCarry<T> &K, const Radix &R) {
     const int tid = threadIdx.x;
 #pragma unroll
     for (int q = 0; q < NA; ++q) K.co[q][tid] = c[q];
@@ -309,8 +311,8 @@ __device__ __forceinline__ void settle(uint32_t *const (&w)[NA], int beg, int en
         K.co2[q][tid] = cc;
         pend |= cc != 0;
     }
-    if (!__syncthreads_or(pend && tid != kRR - 1)) return;
-    for (int pass = 0; pass < kRR; ++pass) {
+    if (!__syncthreads_or(pend && tid != T - 1)) return;
+    for (int pass = 0; pass < T; ++pass) {
         int64_t cin[NA];
 #pragma unroll
         for (int q = 0; q < NA; ++q) cin[q] = tid > 0 ? K.co2[q][tid - 1] : 0;
@@ -325,7 +327,7 @@ __device__ __forceinline__ void settle(uint32_t *const (&w)[NA], int beg, int en
             K.co2[q][tid] = cc;
             pend |= cc != 0;
         }
-        if (!__syncthreads_or(pend && tid != kRR - 1)) return;
+        if (!__syncthreads_or(pend && tid != T - 1)) return;
     }
 }
 
@@ -352,7 +354,7 @@ __device__ __forceinline__ uint32_t add_carry(uint32_t r, int64_t c, uint32_t p,
 // serial chain per position is one addition and compare.
 __device__ void rr_lincomb(uint32_t *__restrict__ x, uint32_t *__restrict__ y,
                            uint32_t *__restrict__ tx, uint32_t *__restrict__ ty, int La, int Lt,
-                           int32_t A, int32_t B, int32_t C, int32_t D, RRCarry &K,
+                           int32_t A, int32_t B, int32_t C, int32_t D, RRCarry<> &K,
                            const Radix &R) {
     int beg, end;
     rr_chunk(max(La, Lt), beg, end);
@@ -390,7 +392,7 @@ __device__ void rr_lincomb(uint32_t *__restrict__ x, uint32_t *__restrict__ y,
 // (0 < q < 2^29); the results are >= 0 and fit in their digits.
 __device__ void rr_submul(uint32_t *x, const uint32_t *y, int ylen, uint32_t *tx,
                           const uint32_t *ty, int tylen, int La, int Lt, int64_t q, int sh,
-                          RRCarry &K, const Radix &R) {
+                          RRCarry<> &K, const Radix &R) {
     int beg, end;
     rr_chunk(max(La, Lt), beg, end);
     const uint32_t q32 = (uint32_t)q;
@@ -558,7 +560,7 @@ __device__ void ratrecon_body(const int64_t *__restrict__ z, int m, uint32_t p, 
                               uint32_t *__restrict__ base, int cap, uint32_t *__restrict__ den,
                               int den_cap, int32_t *__restrict__ info,
                               const uint32_t *__restrict__ ainit, int alen) {
-    __shared__ RRCarry K;
+    __shared__ RRCarry<> K;
     uint32_t *a = base, *b = base + cap, *ta = base + 2 * cap, *tb = base + 3 * cap;
     const int tid = threadIdx.x;
     const Radix R = make_radix(p);
@@ -722,24 +724,43 @@ __device__ __forceinline__ uint32_t shifted31(const uint32_t *y, int ylen, int k
 // (|A| tx + |B| ty, |C| tx + |D| ty) on [0, Lt); |A|..|D| < 2^28, limbs below
 // 2^31: every product is one signed 32 x 32 -> 64-bit multiply and
 // |A x_k + B y_k + carry| < 2^61.
+template <int T>
 __device__ void rb_lincomb(uint32_t *__restrict__ x, uint32_t *__restrict__ y,
                            uint32_t *__restrict__ tx, uint32_t *__restrict__ ty, int La, int Lt,
-                           int32_t A, int32_t B, int32_t C, int32_t D, RRCarry &K,
+                           int32_t A, int32_t B, int32_t C, int32_t D, RRCarry<T> &K,
                            const Radix &R) {
     int beg, end;
-    rr_chunk(max(La, Lt), beg, end);
+    rr_chunk<T>(max(La, Lt), beg, end);
     const int32_t aA = A < 0 ? -A : A, aB = B < 0 ? -B : B, aC = C < 0 ? -C : C,
                   aD = D < 0 ? -D : D;
     const int ea = min(end, La), et = min(end, Lt), e4 = min(ea, et);
     int64_t c[4] = {0, 0, 0, 0};
     int k = beg;
+    // the next position's limbs are loaded before this position's are
+    // stored (the four numbers never overlap)
+    int32_t xv = 0, yv = 0, txv = 0, tyv = 0;
+    if (k < e4) {
+        xv = (int32_t)x[k];
+        yv = (int32_t)y[k];
+        txv = (int32_t)tx[k];
+        tyv = (int32_t)ty[k];
+    }
     for (; k < e4; ++k) {
-        const int32_t xv = (int32_t)x[k], yv = (int32_t)y[k];
-        const int32_t txv = (int32_t)tx[k], tyv = (int32_t)ty[k];
+        int32_t xn = 0, yn = 0, txn = 0, tyn = 0;
+        if (k + 1 < e4) {
+            xn = (int32_t)x[k + 1];
+            yn = (int32_t)y[k + 1];
+            txn = (int32_t)tx[k + 1];
+            tyn = (int32_t)ty[k + 1];
+        }
         x[k] = norm31((int64_t)A * xv + (int64_t)B * yv + c[0], c[0]);
         y[k] = norm31((int64_t)C * xv + (int64_t)D * yv + c[1], c[1]);
         tx[k] = norm31((int64_t)aA * txv + (int64_t)aB * tyv + c[2], c[2]);
         ty[k] = norm31((int64_t)aC * txv + (int64_t)aD * tyv + c[3], c[3]);
+        xv = xn;
+        yv = yn;
+        txv = txn;
+        tyv = tyn;
     }
     for (int j = k; j < ea; ++j) {
         const int32_t xv = (int32_t)x[j], yv = (int32_t)y[j];
@@ -752,16 +773,17 @@ __device__ void rb_lincomb(uint32_t *__restrict__ x, uint32_t *__restrict__ y,
         ty[j] = norm31((int64_t)aC * txv + (int64_t)aD * tyv + c[3], c[3]);
     }
     uint32_t *const w[4] = {x, y, tx, ty};
-    settle<4, true>(w, beg, end, c, K, R);
+    settle<4, true, T>(w, beg, end, c, K, R);
 }
 
 // x <- x - q y 2^sh on [0, La) and tx <- tx + q ty 2^sh on [0, Lt)
 // (0 < q < 2^29); the results are >= 0 and fit in their limbs.
+template <int T>
 __device__ void rb_submul(uint32_t *__restrict__ x, const uint32_t *__restrict__ y, int ylen,
                           uint32_t *__restrict__ tx, const uint32_t *__restrict__ ty, int tylen,
-                          int La, int Lt, uint32_t q, int sh, RRCarry &K, const Radix &R) {
+                          int La, int Lt, uint32_t q, int sh, RRCarry<T> &K, const Radix &R) {
     int beg, end;
-    rr_chunk(max(La, Lt), beg, end);
+    rr_chunk<T>(max(La, Lt), beg, end);
     const int sl = sh / 31, sb = sh % 31;
     int64_t c[2] = {0, 0};
     for (int k = beg; k < end; ++k) {
@@ -775,7 +797,7 @@ __device__ void rb_submul(uint32_t *__restrict__ x, const uint32_t *__restrict__
                            c[1]);
     }
     uint32_t *const w[2] = {x, tx};
-    settle<2, true>(w, beg, end, c, K, R);
+    settle<2, true, T>(w, beg, end, c, K, R);
 }
 
 // For a >= b > 0 (bit lengths abits, bbits): c in [1, 2^29) and a bit shift
@@ -807,37 +829,6 @@ __device__ void rb_exact_step(const uint32_t *a, int la, int abits, const uint32
     sh = s;
 }
 
-// floor(n / d) for 0 < d, n < 2^62 and a quotient below 2^28: a
-// single-precision estimate (relative error below 2^-21), one unit step
-// either way, and for the rare larger errors a second estimate on the exact
-// remainder and unit steps.
-__device__ __forceinline__ uint32_t quot28(uint64_t n, uint64_t d) {
-    const float fd = u64_to_float(d);
-    int64_t q = (int64_t)__float2uint_rz(__fdividef(u64_to_float(n), fd));
-    int64_t r = (int64_t)(n - (uint64_t)q * d);
-    if (r < 0) {
-        --q;
-        r += (int64_t)d;
-    } else if ((uint64_t)r >= d) {
-        ++q;
-        r -= (int64_t)d;
-    }
-    if (r < 0 || (uint64_t)r >= d) {
-        const float fr = r < 0 ? -u64_to_float((uint64_t)-r) : u64_to_float((uint64_t)r);
-        q += __float2int_rd(__fdividef(fr, fd));
-        r = (int64_t)(n - (uint64_t)q * d);
-        while (r < 0) {
-            --q;
-            r += (int64_t)d;
-        }
-        while ((uint64_t)r >= d) {
-            ++q;
-            r -= (int64_t)d;
-        }
-    }
-    return (uint32_t)q;
-}
-
 // A run of Euclid steps on the leading parts ah >= bh of a and b, both taken
 // at bit s (a = ah 2^s + a', b = bh 2^s + b', 0 <= a', b' < 2^s), with
 // r_0 = ah, r_1 = bh and cofactors r_i = u_i ah + v_i bh. The same quotients
@@ -849,11 +840,15 @@ __device__ __forceinline__ uint32_t quot28(uint64_t n, uint64_t d) {
 // whenever
 //     r_(i+1) >= |v_(i+1)| and r_i - r_(i+1) >= |u_(i+1) - u_i|   (i+1 even),
 //     r_(i+1) >= |u_(i+1)| and r_i - r_(i+1) >= |v_(i+1) - v_i|   (i+1 odd).
-// One division per step, no second quotient. The run stops at the first step
-// that fails this, whose quotient or cofactors reach 2^28, or whose remainder
-// keeps at most lim bits (so that no remainder below the numerator bound is
-// skipped; the last steps are taken exactly). On return (a, b) <- (A a + B b,
-// C a + D b) applies the accepted steps.
+// One division per step, no second quotient: a single-precision estimate of
+// r_(i-1) / r_i (relative error below 2^-21), one unit correction either way,
+// and the exact test 0 <= r_(i+1) < r_i, which fails (and ends the run) in
+// the rare case of a larger error. The run stops at the first step that fails
+// a test, whose quotient or cofactors reach 2^28, or whose remainder keeps at
+// most lim bits (so that no remainder below the numerator bound is skipped;
+// the last steps are taken exactly); the tests of a step are combined into
+// one branch. On return (a, b) <- (A a + B b, C a + D b) applies the
+// accepted steps.
 __device__ __forceinline__ int lehmer_bin(uint64_t ah, uint64_t bh, int s, int lim, int64_t &A,
                                           int64_t &B, int64_t &C, int64_t &D) {
     int64_t u0 = 1, v0 = 0, u1 = 0, v1 = 1;
@@ -861,23 +856,33 @@ __device__ __forceinline__ int lehmer_bin(uint64_t ah, uint64_t bh, int s, int l
     int steps = 0;
     bool even = true;  // parity of the index of the next remainder (2 first)
     while (r1 > 0) {
-        if (r1 < (1ull << 34) && r0 >= (r1 << 28)) break;  // quotient >= 2^28
-        const uint32_t q = quot28(r0, r1);
-        const uint64_t r2 = r0 - (uint64_t)q * r1;
-        const int64_t u2 = u0 - (int64_t)q * u1, v2 = v0 - (int64_t)q * v1;
+        float fq = __fdividef(u64_to_float(r0), u64_to_float(r1));
+        fq = fminf(fq, 268435456.0f);  // 2^28: larger quotients end the run
+        int64_t q = (int64_t)__float2uint_rz(fq);
+        int64_t r2 = (int64_t)(r0 - (uint64_t)q * r1);
+        if (r2 < 0) {
+            --q;
+            r2 += (int64_t)r1;
+        } else if ((uint64_t)r2 >= r1) {
+            ++q;
+            r2 -= (int64_t)r1;
+        }
+        const int64_t u2 = u0 - q * u1, v2 = v0 - q * v1;
         const int64_t au2 = u2 < 0 ? -u2 : u2, av2 = v2 < 0 ? -v2 : v2;
-        if (au2 >= (1ll << 28) || av2 >= (1ll << 28)) break;
         const int64_t du = u2 - u1, dv = v2 - v1;
-        const uint64_t need1 = (uint64_t)(even ? av2 : au2);
-        const uint64_t need2 = (uint64_t)(even ? (du < 0 ? -du : du) : (dv < 0 ? -dv : dv));
-        if (r2 < need1 || r1 - r2 < need2) break;
-        if (s + (64 - __clzll((long long)r2)) <= lim) break;
+        const int64_t need1 = even ? av2 : au2;
+        const int64_t need2 = even ? (du < 0 ? -du : du) : (dv < 0 ? -dv : dv);
+        const bool ok = r2 >= 0 && (uint64_t)r2 < r1 && q < (1ll << 28) &&
+                        au2 < (1ll << 28) && av2 < (1ll << 28) && r2 >= need1 &&
+                        (int64_t)r1 - r2 >= need2 &&
+                        s + (64 - __clzll(r2)) > lim;
+        if (!ok) break;
         u0 = u1;
         v0 = v1;
         u1 = u2;
         v1 = v2;
         r0 = r1;
-        r1 = r2;
+        r1 = (uint64_t)r2;
         even = !even;
         ++steps;
     }
@@ -900,26 +905,27 @@ struct RBShared {
 // for the bounds). On success info[0] = 0, info[1] = 32-bit limbs of the
 // denominator written to den, info[2] = its bit length, info[3] = its
 // leading 31 bits; info[0] = 1: no fraction within the bounds, 2: capacity.
+template <int T>
 __device__ void ratrecon_bin_body(const int64_t *__restrict__ z, int m, uint32_t p, int hN,
                                   int hD, uint32_t *__restrict__ base, int cap, int bcap,
                                   uint32_t *__restrict__ den, int den_cap,
                                   int32_t *__restrict__ info) {
-    __shared__ RRCarry K;
+    __shared__ RRCarry<T> K;
     __shared__ RBShared S;
     uint32_t *a = base, *b = base + cap, *ta = base + 2 * cap, *tb = base + 3 * cap,
              *dg = base + 4 * cap, *NB = base + 5 * cap, *DB = base + 5 * cap + bcap;
     const int tid = threadIdx.x;
     const Radix R = make_radix(p);
-    for (int k = tid; k < 5 * cap + 2 * bcap; k += kRR) base[k] = 0;
+    for (int k = tid; k < 5 * cap + 2 * bcap; k += T) base[k] = 0;
     __syncthreads();
     // the digits of X mod p^m in [0, p)
     {
         int beg, end;
-        rr_chunk(m, beg, end);
+        rr_chunk<T>(m, beg, end);
         int64_t c[1] = {0};
         for (int k = beg; k < end; ++k) dg[k] = divmod_p(z[k] + c[0], R, c[0]);
         uint32_t *const w[1] = {dg};
-        settle<1>(w, beg, end, c, K, R);
+        settle<1, false, T>(w, beg, end, c, K, R);
     }
     // Horner: b <- X, a <- p^e with e = m at the end; NB = p^hN, DB = p^hD.
     // p^2 = P1 2^31 + P0; limb k of v p^2 is x_k P0 + x_(k-1) P1 + carry.
@@ -936,7 +942,7 @@ __device__ void ratrecon_bin_body(const int64_t *__restrict__ z, int m, uint32_t
         // dst = p^want (< 2^(31 want): at most want <= bcap - 4 limbs) from
         // a = p^e, e in {want, want - 1}
         const int Lc = min(L + 1, bcap);
-        for (int k = tid; k < Lc; k += kRR) dst[k] = k < L ? a[k] : 0;
+        for (int k = tid; k < Lc; k += T) dst[k] = k < L ? a[k] : 0;
         __syncthreads();
         if (e == want - 1 && tid == 0) {
             uint64_t c = 0;
@@ -963,12 +969,14 @@ __device__ void ratrecon_bin_body(const int64_t *__restrict__ z, int m, uint32_t
         // a p^2 = p^(e+2) and b p^2 + v < p^(e+2) < 2^(31 (e+2)): e + 2 limbs
         L = min(cap, e + 3);
         int beg, end;
-        rr_chunk(L, beg, end);
+        rr_chunk<T>(L, beg, end);
         int64_t c[2] = {0, 0};
         if (beg == 0 && end > 0) c[1] = (int64_t)((uint64_t)dg[i + 1] * p + dg[i]);
         uint64_t ha = 0, hb = 0;
+        uint32_t av = beg < end ? a[beg] : 0, bv = beg < end ? b[beg] : 0;
         for (int k = beg; k < end; ++k) {
-            const uint32_t av = a[k], bv = b[k];
+            // next limbs loaded before this position is stored
+            const uint32_t an = k + 1 < end ? a[k + 1] : 0, bn = k + 1 < end ? b[k + 1] : 0;
             const uint64_t va = (uint64_t)av * P0 + ha + (uint64_t)c[0];
             const uint64_t vb = (uint64_t)bv * P0 + hb + (uint64_t)c[1];
             a[k] = (uint32_t)va & kM31;
@@ -977,17 +985,19 @@ __device__ void ratrecon_bin_body(const int64_t *__restrict__ z, int m, uint32_t
             c[1] = (int64_t)(vb >> 31);
             ha = (uint64_t)av * P1;
             hb = (uint64_t)bv * P1;
+            av = an;
+            bv = bn;
         }
         c[0] += (int64_t)ha;
         c[1] += (int64_t)hb;
         uint32_t *const w[2] = {a, b};
-        settle<2, true>(w, beg, end, c, K, R);
+        settle<2, true, T>(w, beg, end, c, K, R);
         e += 2;
         if (e == hN || e == hN - 1) capture(NB, hN);
         if (e == hD || e == hD - 1) capture(DB, hD);
     }
     // the digits' space becomes tb's scratch: clear ta and tb, tb = 1
-    for (int k = tid; k < 2 * cap; k += kRR) ta[k] = 0;
+    for (int k = tid; k < 2 * cap; k += T) ta[k] = 0;
     __syncthreads();
     if (tid == 0) tb[0] = 1;
     int la = trim(a, L), lb = trim(b, L), lta = 0, ltb = 1;
@@ -1077,7 +1087,7 @@ __device__ void ratrecon_bin_body(const int64_t *__restrict__ z, int m, uint32_t
         }
         return;
     }
-    for (int j = tid; j < l32; j += kRR) {
+    for (int j = tid; j < l32; j += T) {
         const int i = j + j / 31, o = j % 31;
         const uint64_t lo = tb[i], hi = i + 1 < ltb ? tb[i + 1] : 0;
         den[j] = (uint32_t)((lo >> o) | (hi << (31 - o)));
@@ -1090,12 +1100,16 @@ __device__ void ratrecon_bin_body(const int64_t *__restrict__ z, int m, uint32_t
     }
 }
 
-// The numbers always in shared memory (ratrecon_bin_fits).
-__global__ void __launch_bounds__(kRR)
+// The numbers always in shared memory (ratrecon_bin_fits). More threads
+// than the base-p kernel: one thread finds the Lehmer matrix while the others
+// wait, so the extra warps cost no issue slots and halve every vector pass.
+constexpr int kRB = 512;
+
+__global__ void __launch_bounds__(kRB)
 k_ratrecon_bin(const int64_t *__restrict__ z, int m, uint32_t p, int hN, int hD, int cap,
                int bcap, uint32_t *__restrict__ den, int den_cap, int32_t *__restrict__ info) {
     extern __shared__ uint32_t dyn[];
-    ratrecon_bin_body(z, m, p, hN, hD, dyn, cap, bcap, den, den_cap, info);
+    ratrecon_bin_body<kRB>(z, m, p, hN, hD, dyn, cap, bcap, den, den_cap, info);
 }
 
 // Base-p digits (len of them) -> base-2^32 limbs, Horner on one CTA:
@@ -1226,7 +1240,7 @@ int launch_ratrecon_bin(const int64_t *z, int m, uint32_t p, int hN, int hD, uin
     }
     const int cap = m + 4, bcap = (hN > hD ? hN : hD) + 4;
     IDET_TRY(allow_max_smem((const void *)k_ratrecon_bin));
-    k_ratrecon_bin<<<1, kRR, ratrecon_bin_smem(m, hN, hD), s>>>(z, m, p, hN, hD, cap, bcap, den,
+    k_ratrecon_bin<<<1, kRB, ratrecon_bin_smem(m, hN, hD), s>>>(z, m, p, hN, hD, cap, bcap, den,
                                                                  den_cap, info);
     count_launch();
     IDET_CUDA_TRY(cudaGetLastError());

@@ -118,8 +118,11 @@ typedef struct {
     double ms_inverse;         /* LU + inverse mod the lifting prime        */
     double ms_rr;              /* rational reconstruction (idet_int_det_batch:
                                   included in ms_lift_kernel)                */
-    double inverse_macs;       /* 2 n^3 per lifting prime: LU and inverse,
-                                  the work timed by ms_inverse              */
+    double inverse_macs;       /* modular MACs timed by ms_inverse: the LU
+                                  (2n^3/3) and the triangular solves (n^3/6
+                                  forward, the inverse of L being lower
+                                  triangular, n^3/2 backward) per lifting
+                                  prime; 2n^3 per system in batches        */
     double ms_lift_setup;      /* forming E = (C A - I)/p and y_0 = C b for
                                   the one-product lift (0 otherwise)        */
     int32_t lift_path;         /* 1: one-product lift (E), 0: C and A       */
@@ -157,11 +160,12 @@ void idet_set_wait_limit(int64_t cycles);
  * factor K of s_n (Section 2.2), then Alg. 2.1 on det(A)/K reusing the
  * residues already computed (Section 4). opts may be NULL (defaults), stats
  * may be NULL. det receives the exact determinant.
- * Order limit of the solve: the lifting kernel stages the vector and at
- * least one row of A^{-1} mod p in shared memory (12 n bytes), so with
- * lif = 1 or 2 n is at most about 19,000 on a GPU with 227 KB of shared
- * memory per block; larger n return IDET_ERR_ARG ("lift: a row does not fit
- * in shared memory"). lif = 0 (Alg. 2.1 alone) has no such limit.
+ * Order limit of the solve: the lifting kernel stages its vector in shared
+ * memory (4 n bytes per right-hand side when n max|a_ij| < 2^32, else the
+ * vector and one row of A^{-1} mod p, 12 n bytes), so with lif = 1 or 2 n is
+ * at most about 50,000 (25,000 with i_max = 2), or 19,000 for the largest
+ * entries, on a GPU with 227 KB of shared memory per block; larger n return
+ * IDET_ERR_ARG. lif = 0 (Alg. 2.1 alone) has no such limit.
  */
 int idet_int_det(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
                  const idet_opts *opts, void *stream, idet_int *det,

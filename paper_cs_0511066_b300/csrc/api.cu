@@ -586,15 +586,8 @@ static int inverse_mod_prime(const DevMatrix &M, uint32_t p, int nb, Workspace &
     IDET_CUDA_TRY(cudaMemcpyAsync(&det, dd, 4, cudaMemcpyDeviceToHost, s));
     IDET_CUDA_TRY(cudaStreamSynchronize(s));
     if (det == 0) return IDET_ERR_SINGULAR;
-    if (ld4 == n) {
-        IDET_TRY(lu_inverse(R, perm, n, mh, md, true, nb, Cinv, ws));
-    } else {
-        IDET_TRY(ws.alloc_n(&Y, (size_t)n * n));
-        IDET_TRY(lu_inverse(R, perm, n, mh, md, true, nb, Y, ws));
-        IDET_CUDA_TRY(cudaMemsetAsync(Cinv, 0, sizeof(int32_t) * n * ld4, s));
-        IDET_CUDA_TRY(cudaMemcpy2DAsync(Cinv, 4 * ld4, Y, 4 * n, 4 * n, n,
-                                        cudaMemcpyDeviceToDevice, s));
-    }
+    IDET_TRY(ws.alloc_n(&Y, (size_t)n * n));
+    IDET_TRY(lu_inverse(R, perm, n, mh, md, true, nb, Y, Cinv, ld4, ws));
     return IDET_OK;
 }
 
@@ -615,17 +608,10 @@ static int lift_prime_inverse(DetJob &J, int32_t *Cinv, int64_t ld4, uint32_t *p
         IDET_CUDA_TRY(cudaMemcpyAsync(md, &mh, sizeof(ModP), cudaMemcpyHostToDevice, s));
         const int32_t *R = J.lu_R + (size_t)w * n * n;
         const int32_t *perm = J.lu_perm + (size_t)w * n;
-        if (ld4 == n) {
-            IDET_TRY(lu_inverse(R, perm, n, mh, md, true, J.nb, Cinv, ws));
-        } else {
-            int32_t *Y = nullptr;
-            IDET_TRY(ws.alloc_n(&Y, (size_t)n * n));
-            IDET_TRY(lu_inverse(R, perm, n, mh, md, true, J.nb, Y, ws));
-            IDET_CUDA_TRY(cudaMemsetAsync(Cinv, 0, sizeof(int32_t) * n * ld4, s));
-            IDET_CUDA_TRY(cudaMemcpy2DAsync(Cinv, 4 * ld4, Y, 4 * n, 4 * n, n,
-                                            cudaMemcpyDeviceToDevice, s));
-        }
-        J.st.inverse_macs += (4.0 / 3.0) * (double)n * n * n;
+        int32_t *Y = nullptr;
+        IDET_TRY(ws.alloc_n(&Y, (size_t)n * n));
+        IDET_TRY(lu_inverse(R, perm, n, mh, md, true, J.nb, Y, Cinv, ld4, ws));
+        J.st.inverse_macs += (2.0 / 3.0) * (double)n * n * n;
         *p_out = p;
         return IDET_OK;
     }
@@ -636,7 +622,7 @@ static int lift_prime_inverse(DetJob &J, int32_t *Cinv, int64_t ld4, uint32_t *p
         p = random_prime31(g);
         rc = inverse_mod_prime(J.M, p, J.nb, ws, Cinv, ld4);
     }
-    if (rc == IDET_OK) J.st.inverse_macs += 2.0 * (double)n * n * n;
+    if (rc == IDET_OK) J.st.inverse_macs += (4.0 / 3.0) * (double)n * n * n;
     *p_out = p;
     return rc;
 }
@@ -938,10 +924,12 @@ static int mp_lift(DetJob &J, unsigned int abits, MpLift &out) {
         IDET_CUDA_TRY(cudaStreamSynchronize(s));
         if (det != 0) break;
     }
+    int32_t *Ysc = nullptr;
     IDET_TRY(ws.alloc_n(&C, (size_t)n * n));
-    IDET_TRY(lu_inverse(R, perm, n, mh, md, true, J.nb, C, ws));
+    IDET_TRY(ws.alloc_n(&Ysc, (size_t)n * n));
+    IDET_TRY(lu_inverse(R, perm, n, mh, md, true, J.nb, Ysc, C, n, ws));
     J.st.ms_inverse += tinv.stop();
-    J.st.inverse_macs += 2.0 * (double)n * n * n;
+    J.st.inverse_macs += (4.0 / 3.0) * (double)n * n * n;
     // A as signed base-2^15 digit planes
     const int T = (int)((abits + 1 + 14) / 15) + 1;
     const int64_t ldp = (n + 7) / 8 * 8;
@@ -1510,7 +1498,7 @@ int idet_int_det(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
         if (inv_rc == IDET_OK) {
             J.pre_Cinv = inv_C;
             J.pre_p = inv_p;
-            J.st.inverse_macs += 2.0 * (double)n * n * n;
+            J.st.inverse_macs += (4.0 / 3.0) * (double)n * n * n;
             return IDET_OK;
         }
         if (inv_rc == IDET_ERR_SINGULAR) return IDET_OK;  // the solve reports it again

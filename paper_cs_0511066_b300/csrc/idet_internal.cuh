@@ -294,11 +294,12 @@ int lu_factor_batched(int32_t *R, int64_t n, const ModP *mods_dev,
                       const ModP *mods_host, int W, bool wide, int nb,
                       int32_t *perm, uint32_t *det_out, int update_path,
                       Workspace &ws);
-// Inverse of A mod p from its LU (R, perm as produced above with W = 1);
-// Xinv receives A^{-1} mod p, balanced, n x n.
+// Inverse of A mod p from its LU (R, perm as produced above with W = 1):
+// out (n rows of ld_out >= n, columns n .. ld_out - 1 zeroed) receives
+// A^{-1} mod p, balanced; Y (n x n) is scratch and must not overlap out.
 int lu_inverse(const int32_t *R, const int32_t *perm, int64_t n,
                const ModP &mod_host, const ModP *mod_dev, bool wide, int nb,
-               int32_t *Xinv, Workspace &ws);
+               int32_t *Y, int32_t *out, int64_t ld_out, Workspace &ws);
 
 // k_gemm_tc.cu: C <- C - A B mod p on the tensor cores (21-bit primes,
 // K <= 32), path = IDET_PATH_I8, IDET_PATH_BF16 or IDET_PATH_F64.

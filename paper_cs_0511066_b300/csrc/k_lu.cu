@@ -751,12 +751,29 @@ __global__ void k_finalize_det(const LUState *st, const ModP *mods, int W, uint3
     det_out[w] = d;
 }
 
+// Y = P (row i has its 1 in column perm[i]), or the identity when perm is null.
 __global__ void k_perm_identity(int32_t *Y, const int32_t *perm, int64_t n) {
     const int64_t total = n * n;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = e / n, j = e - i * n;
-        Y[e] = (perm[i] == j) ? 1 : 0;
+        Y[e] = ((perm ? perm[i] : i) == j) ? 1 : 0;
+    }
+}
+
+// out = W P for the permutation of the LU (P has its 1 of row k in column
+// perm[k]): column k of W goes to column perm[k]; columns n .. ld - 1 of out
+// are zero.
+__global__ void k_cols_by_perm(const int32_t *__restrict__ W, const int32_t *__restrict__ perm,
+                               int64_t n, int32_t *__restrict__ out, int64_t ld) {
+    const int64_t total = n * ld;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / ld, k = e - i * ld;
+        if (k < n)
+            out[i * ld + perm[k]] = W[i * n + k];
+        else
+            out[e] = 0;
     }
 }
 
@@ -935,13 +952,18 @@ int lu_factor_batched(int32_t *R, int64_t n, const ModP *mods_dev,
 // A^{-1} = U^{-1} L^{-1} P: Y <- P, Y <- L^{-1} Y (blocked forward
 // substitution), Y <- U^{-1} Y (blocked back substitution).
 int lu_inverse(const int32_t *R, const int32_t *perm, int64_t n, const ModP &mod_host,
-               const ModP *mod_dev, bool wide, int nb, int32_t *Y, Workspace &ws) {
+               const ModP *mod_dev, bool wide, int nb, int32_t *Y, int32_t *out, int64_t ld_out,
+               Workspace &ws) {
     cudaStream_t s = ws.stream();
     idet_tuned tuned{};
     const bool have_tuned = tuned_lookup(n, wide ? 31 : 21, &tuned);
     if (nb <= 0 && have_tuned) nb = tuned.nb;
     if (nb <= 0 || nb > kNBMax) nb = kNBMax;
-    k_perm_identity<<<148 * 4, 256, 0, s>>>(Y, perm, n);
+    // A^{-1} = U^{-1} L^{-1} P: Y <- I, Y <- L^{-1} Y (lower triangular: a
+    // block row of it has no nonzero right of its diagonal block, so every
+    // solve and update of the forward pass stops at that column), Y <- U^{-1} Y
+    // (full), then out = Y P.
+    k_perm_identity<<<148 * 4, 256, 0, s>>>(Y, nullptr, n);
     count_launch();
     IDET_CUDA_TRY(cudaGetLastError());
     // Y <- L^{-1} Y and Y <- U^{-1} Y, two-level: blocks of NB = 4 nb rows;
@@ -986,12 +1008,14 @@ int lu_inverse(const int32_t *R, const int32_t *perm, int64_t n, const ModP &mod
         count_launch((nfull ? 2 : 0) + (last ? 2 : 0));
         IDET_CUDA_TRY(cudaGetLastError());
     }
-    auto apply = [&](const int32_t *tri_blk, int64_t k0, int kb) -> int {
-        const dim3 grid((unsigned)((n + 31) / 32), 1);
+    auto apply = [&](const int32_t *tri_blk, int64_t k0, int kb, int64_t ncols) -> int {
+        const dim3 grid((unsigned)((ncols + 31) / 32), 1);
         if (wide)
-            k_tri_apply<true><<<grid, 128, 0, s>>>(tri_blk, Y, 0, n, k0, kb, 0, n, mod_dev, nullptr);
+            k_tri_apply<true><<<grid, 128, 0, s>>>(tri_blk, Y, 0, n, k0, kb, 0, ncols, mod_dev,
+                                                   nullptr);
         else
-            k_tri_apply<false><<<grid, 128, 0, s>>>(tri_blk, Y, 0, n, k0, kb, 0, n, mod_dev, nullptr);
+            k_tri_apply<false><<<grid, 128, 0, s>>>(tri_blk, Y, 0, n, k0, kb, 0, ncols, mod_dev,
+                                                    nullptr);
         count_launch();
         IDET_CUDA_TRY(cudaGetLastError());
         return IDET_OK;
@@ -1005,26 +1029,28 @@ int lu_inverse(const int32_t *R, const int32_t *perm, int64_t n, const ModP &mod
         IDET_TRY(ws.alloc_n(&st1, 1));
         IDET_CUDA_TRY(cudaMemsetAsync(st1, 0, sizeof(LUState), s));
     }
-    auto gsub = [&](const int32_t *Ap, const int32_t *Bp, int32_t *Cp, int64_t M, int K) -> int {
-        if (M <= 0 || K <= 0) return IDET_OK;
+    auto gsub = [&](const int32_t *Ap, const int32_t *Bp, int32_t *Cp, int64_t M, int K,
+                    int64_t N) -> int {
+        if (M <= 0 || K <= 0 || N <= 0) return IDET_OK;
         if (tc)
-            return gemm_sub_tc05(Ap, n, 0, Bp, n, 0, Cp, n, 0, (int)M, (int)n, K, mod_dev, st1, 1,
+            return gemm_sub_tc05(Ap, n, 0, Bp, n, 0, Cp, n, 0, (int)M, (int)N, K, mod_dev, st1, 1,
                                  scratch, s, wide ? 5 : 3);
         if (wide)
-            return gemm_sub<true>(Ap, n, 0, Bp, n, 0, Cp, n, 0, (int)M, (int)n, K, mod_dev, nullptr, 1,
-                                  s);
-        return gemm_sub<false>(Ap, n, 0, Bp, n, 0, Cp, n, 0, (int)M, (int)n, K, mod_dev, nullptr, 1,
+            return gemm_sub<true>(Ap, n, 0, Bp, n, 0, Cp, n, 0, (int)M, (int)N, K, mod_dev, nullptr,
+                                  1, s);
+        return gemm_sub<false>(Ap, n, 0, Bp, n, 0, Cp, n, 0, (int)M, (int)N, K, mod_dev, nullptr, 1,
                                s);
     };
     for (int64_t J0 = 0; J0 < n; J0 += NB) {
         const int JB = (int)((n - J0) < NB ? (n - J0) : NB);
         for (int64_t k0 = J0; k0 < J0 + JB; k0 += nb) {
             const int kb = (int)((J0 + JB - k0) < nb ? (J0 + JB - k0) : nb);
-            IDET_TRY(apply(triL + tsz * (k0 / nb), k0, kb));
+            IDET_TRY(apply(triL + tsz * (k0 / nb), k0, kb, k0 + kb));
             IDET_TRY(gsub(R + (k0 + kb) * n + k0, Y + k0 * n, Y + (k0 + kb) * n,
-                          J0 + JB - (k0 + kb), kb));
+                          J0 + JB - (k0 + kb), kb, k0 + kb));
         }
-        IDET_TRY(gsub(R + (J0 + JB) * n + J0, Y + J0 * n, Y + (J0 + JB) * n, n - J0 - JB, JB));
+        IDET_TRY(gsub(R + (J0 + JB) * n + J0, Y + J0 * n, Y + (J0 + JB) * n, n - J0 - JB, JB,
+                      J0 + JB));
     }
     const int64_t nblk = (n + NB - 1) / NB;
     for (int64_t bj = nblk - 1; bj >= 0; --bj) {
@@ -1034,14 +1060,17 @@ int lu_inverse(const int32_t *R, const int32_t *perm, int64_t n, const ModP &mod
         for (int64_t bi = nsub - 1; bi >= 0; --bi) {
             const int64_t k0 = J0 + bi * nb;
             const int kb = (int)((J0 + JB - k0) < nb ? (J0 + JB - k0) : nb);
-            IDET_TRY(apply(triU + tsz * (k0 / nb), k0, kb));
+            IDET_TRY(apply(triU + tsz * (k0 / nb), k0, kb, n));
             // rows J0 .. k0 of the block: Y_r -= U[r, k0..k0+kb) Y[k0..k0+kb)
-            IDET_TRY(gsub(R + J0 * n + k0, Y + k0 * n, Y + J0 * n, k0 - J0, kb));
+            IDET_TRY(gsub(R + J0 * n + k0, Y + k0 * n, Y + J0 * n, k0 - J0, kb, n));
         }
         // rows above the block
-        IDET_TRY(gsub(R + J0, Y + J0 * n, Y, J0, JB));
+        IDET_TRY(gsub(R + J0, Y + J0 * n, Y, J0, JB, n));
     }
     if (tc) IDET_TRY(tc05_check_error(s));
+    k_cols_by_perm<<<148 * 4, 256, 0, s>>>(Y, perm, n, out, ld_out);
+    count_launch();
+    IDET_CUDA_TRY(cudaGetLastError());
     return IDET_OK;
 }
 

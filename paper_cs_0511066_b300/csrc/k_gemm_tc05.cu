@@ -33,11 +33,12 @@
 //     last chunk of a tile signals its accumulator set full; two sets
 //     alternate between tiles; warp 1 also owns the tensor-memory
 //     allocation (512 columns);
-//   warps 2-5 and 6-9: two epilogue groups, one per accumulator set; each
-//     warp prefetches its 32 rows of C while the MMAs run, reads its 32-lane
-//     quarter of the accumulators with tcgen05.ld, recombines in int64,
-//     reduces mod p and writes C (16-byte accesses where aligned), then
-//     releases the set to the issuer.
+//   warps 2-9 and 10-17: two epilogue groups of 8 warps, one per accumulator
+//     set; each warp prefetches its 32 rows x 24 columns of C while the MMAs
+//     run, reads its 32-lane quarter (warp id mod 4) of those columns of the
+//     accumulators with tcgen05.ld, recombines in int64, reduces mod p and
+//     writes C (16-byte accesses where aligned), then releases the set to the
+//     issuer. (One set of 8 warps for five limbs.)
 // The epilogue of a tile overlaps the loads and MMAs of the next one. Every wait is bounded (about 2 s); a wait that gives up records an
 // error and raises a block-wide abort flag, after which every role leaves
 // its loop; bulk copies and MMAs already started are drained (bounded)
@@ -62,9 +63,15 @@ struct Tc {
     static constexpr int kGroups = 2 * L - 1;
     static constexpr int kBufs = L == 3 ? 2 : 1;
     static constexpr int kAccCols = L == 3 ? 256 : 512;
-    static constexpr int kThreads = 64 + 128 * kBufs;
+    static constexpr int kEpiWarps = 8;  // per accumulator set: 4 lane quarters x 2 column halves
+    static constexpr int kThreads = 64 + 32 * kEpiWarps * kBufs;
     static constexpr uint32_t kStageBytes = L * (kLimbA + kLimbB);
-    static constexpr int kStages = L == 3 ? 12 : 7;
+    static constexpr int kStages = L == 3 ? 9 : 6;
+    // C staging: one 128-row tile per accumulator set, rows padded to 52
+    // words (16-byte accesses of a warp's 32 rows then fall in distinct banks)
+    static constexpr int kCS = 52;
+    static constexpr uint32_t kCBytes = kTM * kCS * 4;
+    static constexpr size_t kSmem = (size_t)kStages * kStageBytes + (size_t)kBufs * kCBytes;
 };
 
 __device__ int g_tc05_err;  // first error code (1 load, 2 MMA) of any CTA
@@ -199,12 +206,43 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *m) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(m)) : "memory");
 }
 
+constexpr int kMaxWs = 64;  // primes whose state and reduction constants are cached in shared memory
+
+// The epilogue's reduction of C - sum_g 2^(7g) P_g mod p in Montgomery form
+// (R = 2^32): with weights w_g = 2^(7g) R mod p (balanced), t = sum_g w_g P_g
+// is one multiply-add per group (|t| < 9 2^30 2^22 < 2^56), and
+// v = (t - q p) / 2^32 with q = t p^{-1} mod 2^32 equals sum_g 2^(7g) P_g
+// mod p with |v| <= 2^24 + p/2; C - v then needs one step either way into
+// the balanced range. (Against two 64-bit Barrett reductions per entry.)
+struct EpiMont {
+    int32_t p, half;
+    uint32_t pinv;  // p^{-1} mod 2^32
+    int32_t w[9];
+};
+
+__device__ __forceinline__ EpiMont make_epi_mont(uint32_t p) {
+    EpiMont e;
+    e.p = (int32_t)p;
+    e.half = (int32_t)((p - 1) / 2);
+    uint32_t x = p;  // p p = 1 mod 8; each step doubles the correct bits
+    for (int i = 0; i < 4; ++i) x *= 2u - p * x;
+    e.pinv = x;
+    int64_t r = (int64_t)((1ull << 32) % p);
+    for (int g = 0; g < 9; ++g) {
+        e.w[g] = (int32_t)(r > e.half ? r - p : r);
+        r = (r * 128) % p;
+    }
+    return e;
+}
+
 template <int L>
 struct Tc05Shared {
     uint64_t full[Tc<L>::kStages], empty[Tc<L>::kStages], acc_full[2], acc_empty[2], drain;
     uint32_t taddr;
     volatile int abort;
     int prod_iter, mma_iter;
+    int dead[kMaxWs];
+    EpiMont mont[kMaxWs];
 };
 
 // Bounded wait with back-off, for warps that wait through whole tiles.
@@ -229,7 +267,13 @@ k_gemm_tc05(const __nv_bfloat16 *__restrict__ Apk, const __nv_bfloat16 *__restri
     __shared__ Tc05Shared<L> S;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int Kq = L * Kp, nck = Kp / kKc;
-    const int64_t tiles = (int64_t)W * Mt * Nt;
+    // tile t = (w Mt + mt) Nt + nt, in 32-bit arithmetic (W Mt Nt < 2^31)
+    const int MN = Mt * Nt, tiles = W * MN;
+    for (int i = tid; i < W && i < kMaxWs; i += blockDim.x) {
+        S.dead[i] = st[i].dead;
+        S.mont[i] = make_epi_mont(mods[i].p);
+    }
+    auto dead_of = [&](int w) { return w < kMaxWs ? S.dead[w] != 0 : st[w].dead != 0; };
     if (tid == 0) {
         for (int i = 0; i < kStages; ++i) {
             mbar_init(&S.full[i], 1);
@@ -237,7 +281,7 @@ k_gemm_tc05(const __nv_bfloat16 *__restrict__ Apk, const __nv_bfloat16 *__restri
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&S.acc_full[i], 1);
-            mbar_init(&S.acc_empty[i], 4);
+            mbar_init(&S.acc_empty[i], Tc<L>::kEpiWarps);
         }
         mbar_init(&S.drain, 1);
         S.abort = 0;
@@ -263,10 +307,10 @@ k_gemm_tc05(const __nv_bfloat16 *__restrict__ Apk, const __nv_bfloat16 *__restri
     if (warp == 0) {
         if (lane == 0) {  // producer
             int it = 0;
-            for (int64_t t = blockIdx.x; t < tiles && !S.abort; t += gridDim.x) {
-                const int w = (int)(t / ((int64_t)Mt * Nt));
-                const int mt = (int)((t / Nt) % Mt), nt = (int)(t % Nt);
-                if (st[w].dead) continue;
+            for (int t = blockIdx.x; t < tiles && !S.abort; t += gridDim.x) {
+                const int w = t / MN, rem = t - w * MN;
+                const int mt = rem / Nt, nt = rem - mt * Nt;
+                if (dead_of(w)) continue;
                 const unsigned char *gA =
                     (const unsigned char *)(Apk + ((int64_t)w * Mt + mt) * ((int64_t)kTM * Kq));
                 const unsigned char *gB =
@@ -295,9 +339,9 @@ k_gemm_tc05(const __nv_bfloat16 *__restrict__ Apk, const __nv_bfloat16 *__restri
         if (lane == 0) {  // MMA issuer
             int it = 0, tile = 0;
             const uint32_t lboA = (kTM / 8) * 128, lboB = (kTN / 8) * 128;
-            for (int64_t t = blockIdx.x; t < tiles && !S.abort; t += gridDim.x) {
-                const int w = (int)(t / ((int64_t)Mt * Nt));
-                if (st[w].dead) continue;
+            for (int t = blockIdx.x; t < tiles && !S.abort; t += gridDim.x) {
+                const int w = t / MN;
+                if (dead_of(w)) continue;
                 const int buf = tile % kBufs;
                 if (!mbar_wait(&S.acc_empty[buf], ((uint32_t)(tile / kBufs) & 1u) ^ 1u)) {
                     fail(2);
@@ -333,90 +377,143 @@ k_gemm_tc05(const __nv_bfloat16 *__restrict__ Apk, const __nv_bfloat16 *__restri
                 ++tile;
             }
         }
-    } else {  // epilogue groups: warps 2-5 (set 0), 6-9 (set 1 when two sets)
-        const int grp = (warp - 2) >> 2, q = warp & 3;
+    } else {  // epilogue: warps 2..9 (set 0), 10..17 (set 1 when two sets)
+        // Each warp reads the accumulator lanes of its quarter (warp id mod 4:
+        // the rows it may access) and one half of the 48 columns, so that 8
+        // warps per set keep the conversions and reductions in flight. The
+        // C entries of a tile are fetched into shared memory (cp.async) while
+        // the set's previous tile is reduced, so their latency is hidden.
+        constexpr int kHalf = kTN / 2, kCS = Tc<L>::kCS;
+        const int e = warp - 2, grp = e / Tc<L>::kEpiWarps, q = warp & 3;
+        const int h = (e % Tc<L>::kEpiWarps) / 4;
         const bool vec = (ldc % 4 == 0) && (sC % 4 == 0) && (((uintptr_t)C & 15) == 0);
-        int tile = 0;
-        for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-            const int w = (int)(t / ((int64_t)Mt * Nt));
-            const int mt = (int)((t / Nt) % Mt), nt = (int)(t % Nt);
-            if (st[w].dead) continue;
-            const int buf = tile % kBufs;
-            const uint32_t use = (uint32_t)(tile / kBufs) & 1u;
-            ++tile;
-            if (buf != grp) continue;
+        int32_t *cst = reinterpret_cast<int32_t *>(sm + (size_t)kStages * kStageBytes +
+                                                   (size_t)grp * Tc<L>::kCBytes) +
+                       (q * 32 + lane) * kCS + h * kHalf;
+        // the next tile of this set from index u on; c counts the CTA's live
+        // tiles (both sets), as the issuer does
+        auto advance = [&](int u, int &c) -> int {
+            for (; u < tiles; u += gridDim.x) {
+                const int wu = u / MN;
+                if (dead_of(wu)) continue;
+                const int b = c % kBufs;
+                ++c;
+                if (b == grp) return u;
+            }
+            return tiles;
+        };
+        // where this thread's 24 entries of tile u live, and whether they
+        // are fetched asynchronously (full 16-byte aligned row segments)
+        auto locate = [&](int u, int32_t *&crow, bool &rowok, bool &full, int &cb) {
+            const int w = u / MN, rem = u - w * MN;
+            const int mt = rem / Nt, nt = rem - mt * Nt;
             const int r = mt * kTM + q * 32 + lane;
-            const int cb = nt * kTN;
-            int32_t *crow = C + (int64_t)w * sC + (int64_t)r * ldc + cb;
-            const bool rowok = r < M;
-            const bool full = vec && cb + kTN <= N;
-            // prefetch this thread's 48 entries of C while the MMAs run
-            int32_t cv[kTN];
-            if (rowok && full) {
+            cb = nt * kTN + h * kHalf;
+            crow = C + (int64_t)w * sC + (int64_t)r * ldc + cb;
+            rowok = r < M;
+            full = vec && cb + kHalf <= N;
+        };
+        auto prefetch = [&](int u) {
+            int32_t *crow;
+            bool rowok, full;
+            int cb;
+            locate(u, crow, rowok, full, cb);
+            if (!(rowok && full)) return;
 #pragma unroll
-                for (int u = 0; u < kTN / 4; ++u) {
-                    const int4 x = *(const int4 *)(crow + 4 * u);
-                    cv[4 * u] = x.x;
-                    cv[4 * u + 1] = x.y;
-                    cv[4 * u + 2] = x.z;
-                    cv[4 * u + 3] = x.w;
+            for (int v = 0; v < kHalf / 4; ++v)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa(cst + 4 * v)),
+                             "l"(crow + 4 * v)
+                             : "memory");
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        int cnt = 0;
+        int t = advance(blockIdx.x, cnt);
+        if (t < tiles) prefetch(t);
+        while (t < tiles) {
+            int cnext = cnt;
+            const int tn = advance(t + gridDim.x, cnext);
+            const int w = t / MN;
+            const int buf = grp;
+            const uint32_t use = (uint32_t)((cnt - 1) / kBufs) & 1u;
+            int32_t *crow;
+            bool rowok, full;
+            int cb;
+            locate(t, crow, rowok, full, cb);
+            int32_t cv[kHalf];
+            if (rowok && full) {
+                asm volatile("cp.async.wait_all;" ::: "memory");
+#pragma unroll
+                for (int v = 0; v < kHalf / 4; ++v) {
+                    const int4 x = *(const int4 *)(cst + 4 * v);
+                    cv[4 * v] = x.x;
+                    cv[4 * v + 1] = x.y;
+                    cv[4 * v + 2] = x.z;
+                    cv[4 * v + 3] = x.w;
                 }
             } else {
 #pragma unroll
-                for (int j = 0; j < kTN; ++j) cv[j] = (rowok && cb + j < N) ? crow[j] : 0;
+                for (int j = 0; j < kHalf; ++j) cv[j] = (rowok && cb + j < N) ? crow[j] : 0;
             }
             const bool ok = mbar_wait_sleep(&S.acc_full[buf], use);
             if (__any_sync(0xffffffffu, !ok || S.abort)) {
                 if (lane == 0 && !ok) fail(4);
+                asm volatile("cp.async.wait_all;" ::: "memory");
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const ModP Md = mods[w];
-            const uint32_t tl = taddr + (uint32_t)(buf * kAccCols) + ((uint32_t)(q * 32) << 16);
+            const EpiMont em = w < kMaxWs ? S.mont[w] : make_epi_mont(mods[w].p);
+            const uint32_t tl = taddr + (uint32_t)(buf * kAccCols + h * kHalf) +
+                                ((uint32_t)(q * 32) << 16);
 #pragma unroll
-            for (int c0 = 0; c0 < kTN; c0 += 16) {
-                uint32_t rv[kGroups][16];
+            for (int c0 = 0; c0 < kHalf; c0 += 8) {
+                uint32_t rv[kGroups][8];
 #pragma unroll
                 for (int g = 0; g < kGroups; ++g)
                     asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,"
-                        "%10,%11,%12,%13,%14,%15}, [%16];\n"
+                        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
                         : "=r"(rv[g][0]), "=r"(rv[g][1]), "=r"(rv[g][2]), "=r"(rv[g][3]),
-                          "=r"(rv[g][4]), "=r"(rv[g][5]), "=r"(rv[g][6]), "=r"(rv[g][7]),
-                          "=r"(rv[g][8]), "=r"(rv[g][9]), "=r"(rv[g][10]), "=r"(rv[g][11]),
-                          "=r"(rv[g][12]), "=r"(rv[g][13]), "=r"(rv[g][14]), "=r"(rv[g][15])
+                          "=r"(rv[g][4]), "=r"(rv[g][5]), "=r"(rv[g][6]), "=r"(rv[g][7])
                         : "r"(tl + (uint32_t)(g * kTN + c0)));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    // sum_g 2^(7g) P_g: groups 0..3 (< 2^43) and, reduced first,
-                    // groups 4.. (< 2^50) times 2^28
-                    int64_t lo = 0, hi = 0;
+                for (int j = 0; j < 8; ++j) {
+                    // Each P_g is an integer below 2^22 in magnitude: adding
+                    // 1.5 2^23 puts it in the low mantissa bits exactly (one
+                    // full-rate add instead of a conversion instruction).
+                    int64_t tsum = 0;
 #pragma unroll
-                    for (int g = kGroups - 1; g >= 0; --g) {
-                        const int64_t v = (int64_t)(int32_t)__float2int_rn(__uint_as_float(rv[g][j]));
-                        if (g >= 4) hi = hi * 128 + v;
-                        else lo = lo * 128 + v;
+                    for (int g = 0; g < kGroups; ++g) {
+                        const float f = __fadd_rn(__uint_as_float(rv[g][j]), 12582912.0f);
+                        const int32_t v = (int32_t)__float_as_uint(f) - 0x4B400000;
+                        tsum += (int64_t)em.w[g] * v;
                     }
-                    const int64_t s = L == 3 ? lo + hi * (1ll << 28)
-                                             : (int64_t)red_bal(hi, Md) * (1ll << 28) + lo;
-                    cv[c0 + j] = red_bal((int64_t)cv[c0 + j] - s, Md);
+                    const int32_t qm = (int32_t)((uint32_t)tsum * em.pinv);
+                    const int32_t v = (int32_t)(tsum >> 32) - __mulhi(qm, em.p);
+                    int64_t x = (int64_t)cv[c0 + j] - v;
+                    if (x > em.half) x -= em.p;
+                    if (x < -em.half) x += em.p;
+                    cv[c0 + j] = (int32_t)x;
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&S.acc_empty[buf]);
+            // the staging slot was consumed above: fetch the set's next tile
+            if (tn < tiles) prefetch(tn);
             if (rowok && full) {
 #pragma unroll
-                for (int u = 0; u < kTN / 4; ++u)
-                    *(int4 *)(crow + 4 * u) =
-                        make_int4(cv[4 * u], cv[4 * u + 1], cv[4 * u + 2], cv[4 * u + 3]);
+                for (int v = 0; v < kHalf / 4; ++v)
+                    *(int4 *)(crow + 4 * v) =
+                        make_int4(cv[4 * v], cv[4 * v + 1], cv[4 * v + 2], cv[4 * v + 3]);
             } else if (rowok) {
 #pragma unroll
-                for (int j = 0; j < kTN; ++j)
+                for (int j = 0; j < kHalf; ++j)
                     if (cb + j < N) crow[j] = cv[j];
             }
+            t = tn;
+            cnt = cnext;
         }
+        asm volatile("cp.async.wait_all;" ::: "memory");
     }
     __syncthreads();
     if (S.abort && tid == 32) {
@@ -455,7 +552,7 @@ static int gemm_tc05_l(const int32_t *A, int64_t lda, int64_t sA, const int32_t 
                                                     Apk, Bpk);
     count_launch();
     IDET_CUDA_TRY(cudaGetLastError());
-    const size_t smem = (size_t)Tc<L>::kStages * Tc<L>::kStageBytes;
+    const size_t smem = Tc<L>::kSmem;
     IDET_TRY(allow_max_smem((const void *)k_gemm_tc05<L>));
     const int64_t tiles = (int64_t)W * Mt * Nt;
     const int grid = (int)std::min<int64_t>(tiles, 148);

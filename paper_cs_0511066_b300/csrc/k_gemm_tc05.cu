@@ -13,26 +13,32 @@
 // each an fp32 sum of integer products below 2^24 in magnitude, hence exact;
 // C - sum_g 2^(7g) P_g is then formed in int64 and reduced mod p.
 //
-// k_pack_limbs writes A (M x K, row-major residues) and B^T (N x K) as bf16
-// limb matrices of K' = 3 Kp columns (Kp = K rounded up to 16, limb-major
-// blocks of Kp), already in the tcgen05 K-major no-swizzle core-matrix
-// layout of one CTA tile: core matrices of 8 rows x 8 elements (128 bytes)
-// with the row groups of a tile adjacent (stride 128 B, the descriptor's
-// stride offset) and the K groups ROWS/8 core matrices apart (the leading
-// offset). A tile is then one contiguous block that k_gemm_tc05 fetches with
-// cp.async.bulk into shared memory.
+// k_pack_limbs writes A (M x K, row-major residues) as a bf16 limb matrix of
+// K' = 3 Kp columns (Kp = K rounded up to 16, limb-major blocks of Kp), and
+// B^T (N x K) with its three limbs stacked as rows (limb l's rows l kTN ..),
+// already in the tcgen05 K-major no-swizzle core-matrix layout of one CTA
+// tile: core matrices of 8 rows x 8 elements (128 bytes) with the row groups
+// of a tile adjacent (stride 128 B, the descriptor's stride offset) and the K
+// groups ROWS/8 core matrices apart (the leading offset). A tile is then one
+// contiguous block that k_gemm_tc05 fetches with cp.async.bulk into shared
+// memory.
 //
 // k_gemm_tc05: persistent, one CTA per SM looping over 128 x 48 output
 // tiles (all primes' tiles in one launch). Warp-specialised:
 //   warp 0 (one thread): producer, cp.async.bulk of 16-wide K chunks of the
 //     three limbs of A and B into a ring of shared-memory stages, each
 //     tracked by a full (transaction bytes) and an empty mbarrier;
-//   warp 1 (one thread): MMA issuer, 9 tcgen05.mma (128 x 48 x 16, bf16 in,
-//     fp32 out) per stage into five tensor-memory accumulators of 48
-//     columns (one per group); tcgen05.commit frees the stage, and after the
-//     last chunk of a tile signals its accumulator set full; two sets
-//     alternate between tiles; warp 1 also owns the tensor-memory
-//     allocation (512 columns);
+//   warp 1 (one thread): MMA issuer into five tensor-memory accumulators of
+//     48 columns (one per group, adjacent), with B's three limbs stacked as
+//     144 rows: an MMA of A_a against limbs b0 .. b1 of B (128 x 48 (b1 - b0
+//     + 1) x 16, bf16 in, fp32 out) lands exactly on groups a + b0 .. a + b1.
+//     The first chunk of a tile takes 5 MMAs (each group started by exactly
+//     one of them), the later chunks 3 (A_a against all of B) instead of one
+//     per limb pair, 9: the issue rate of the single issuing thread (about
+//     100 cycles per MMA), not the tensor pipe, bounds this kernel;
+//     tcgen05.commit frees the stage, and after the last chunk of a tile
+//     signals its accumulator set full; two sets alternate between tiles;
+//     warp 1 also owns the tensor-memory allocation (512 columns);
 //   warps 2-9 and 10-17: two epilogue groups of 8 warps, one per accumulator
 //     set; each warp prefetches its 32 rows x 24 columns of C while the MMAs
 //     run, reads its 32-lane quarter (warp id mod 4) of those columns of the
@@ -131,7 +137,8 @@ __global__ void k_pack_limbs(const int32_t *__restrict__ A, int64_t lda, int64_t
             __nv_bfloat16 *dst = Bpk + ((int64_t)w * Nt + nt) * btile;
             split7<L>(x, l);
 #pragma unroll
-            for (int i = 0; i < L; ++i) dst[core_off<kTN>(r, i * Kp + k)] = __int2bfloat16_rn(l[i]);
+            for (int i = 0; i < L; ++i)
+                dst[core_off<L * kTN>(i * kTN + r, k)] = __int2bfloat16_rn(l[i]);
         }
     }
 }
@@ -199,8 +206,11 @@ __device__ __forceinline__ void mma_commit(uint64_t *m) {
 // Instruction descriptor, kind::f16: fp32 accumulator (bits 4-5 = 1), A and
 // B bf16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0),
 // N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTN >> 3) << 17) |
-                            ((uint32_t)(kTM >> 4) << 24);
+constexpr uint32_t idesc_n(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(kTM >> 4) << 24);
+}
+constexpr uint32_t kIdesc = idesc_n(kTN);
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *m) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(m)) : "memory");
@@ -328,9 +338,11 @@ k_gemm_tc05(const __nv_bfloat16 *__restrict__ Apk, const __nv_bfloat16 *__restri
                         const int kb = (l * Kp + c * kKc) / 8;
                         bulk_g2s(dst + l * kLimbA, gA + (size_t)kb * (kTM / 8) * 128, kLimbA,
                                  &S.full[stg]);
-                        bulk_g2s(dst + L * kLimbA + l * kLimbB, gB + (size_t)kb * (kTN / 8) * 128,
-                                 kLimbB, &S.full[stg]);
                     }
+                    // B: the L limbs' rows stacked (L kTN rows), both K groups
+                    // of the chunk in one copy
+                    bulk_g2s(dst + L * kLimbA, gB + (size_t)(c * kKc / 8) * (L * kTN / 8) * 128,
+                             L * kLimbB, &S.full[stg]);
                     S.prod_iter = it + 1;
                 }
             }
@@ -338,7 +350,7 @@ k_gemm_tc05(const __nv_bfloat16 *__restrict__ Apk, const __nv_bfloat16 *__restri
     } else if (warp == 1) {
         if (lane == 0) {  // MMA issuer
             int it = 0, tile = 0;
-            const uint32_t lboA = (kTM / 8) * 128, lboB = (kTN / 8) * 128;
+            const uint32_t lboA = (kTM / 8) * 128, lboB = (L * kTN / 8) * 128;
             for (int t = blockIdx.x; t < tiles && !S.abort; t += gridDim.x) {
                 const int w = t / MN;
                 if (dead_of(w)) continue;
@@ -357,17 +369,34 @@ k_gemm_tc05(const __nv_bfloat16 *__restrict__ Apk, const __nv_bfloat16 *__restri
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    // one descriptor per operand and stage; the limbs' start
+                    // addresses (>> 4 in the low field, no carry: shared
+                    // memory is below 256 KB) are constant offsets from it
                     const uint32_t a0 = sa(sm + (size_t)stg * kStageBytes);
-                    const uint32_t b0 = a0 + L * kLimbA;
-                    for (int g = 0; g < kGroups; ++g) {
-                        uint32_t acc = c > 0 ? 1u : 0u;
-                        for (int a = (g > L - 1 ? g - (L - 1) : 0); a <= (g < L - 1 ? g : L - 1); ++a) {
-                            const int b = g - a;
-                            const uint64_t ad = smem_desc(a0 + a * kLimbA, lboA, 128);
-                            const uint64_t bd = smem_desc(b0 + b * kLimbB, lboB, 128);
-                            mma_bf16(dacc + (uint32_t)(g * kTN), ad, bd, kIdesc, acc);
-                            acc = 1u;
+                    const uint64_t dA = smem_desc(a0, lboA, 128);
+                    const uint64_t dB = smem_desc(a0 + L * kLimbA, lboB, 128);
+                    if (c == 0) {
+                        // first chunk of the tile: A_0 against all of B starts
+                        // groups 0 .. L-1; then for each later limb a, A_a B_(L-1)
+                        // starts group a + L - 1 and A_a against limbs 0 .. L-2
+                        // adds into the groups already started: 2L - 1 MMAs
+                        mma_bf16(dacc, dA, dB, idesc_n(L * kTN), 0u);
+#pragma unroll
+                        for (int a = 1; a < L; ++a) {
+                            mma_bf16(dacc + (uint32_t)((a + L - 1) * kTN),
+                                     dA + (uint64_t)((a * kLimbA) >> 4),
+                                     dB + (uint64_t)((L - 1) * (kTN / 8) * 128 >> 4), kIdesc, 0u);
+                            mma_bf16(dacc + (uint32_t)(a * kTN), dA + (uint64_t)((a * kLimbA) >> 4),
+                                     dB, idesc_n((L - 1) * kTN), 1u);
                         }
+                    } else {
+                        // later chunks: A_a against the stacked limbs of B
+                        // (L kTN columns) adds A_a B_b into group a + b for
+                        // every b at once: L MMAs instead of L^2
+#pragma unroll
+                        for (int a = 0; a < L; ++a)
+                            mma_bf16(dacc + (uint32_t)(a * kTN), dA + (uint64_t)((a * kLimbA) >> 4),
+                                     dB, idesc_n(L * kTN), 1u);
                     }
                     mma_commit(&S.empty[stg]);
                     S.mma_iter = it + 1;

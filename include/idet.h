@@ -105,7 +105,10 @@ typedef struct {
     int32_t log2_K;            /* bits of the factor K = s~_n found          */
     double log2_H;             /* log2 of the Hadamard bound used           */
     double ms_lu;              /* device time of the multi-prime LU         */
-    double ms_lift;            /* device time of the inverse + lift         */
+    double ms_lift;            /* wall time of the solve: lift and
+                                  reconstruction (and, in the speculative
+                                  order, the first CRA wave beside the
+                                  reconstruction)                           */
     double ms_cra;             /* device time of reconstruction steps       */
     double ms_total;
     uint64_t launches;         /* kernels launched by the call              */
@@ -116,7 +119,9 @@ typedef struct {
     double lu_macs;            /* (2/3) n^3 per factored CRA prime: the
                                   modular MACs of the work timed by ms_lu   */
     double ms_inverse;         /* LU + inverse mod the lifting prime        */
-    double ms_rr;              /* rational reconstruction (idet_int_det_batch:
+    double ms_rr;              /* rational reconstruction kernel(s) (with the
+                                  speculative order the first CRA wave, in
+                                  ms_lu, runs beside it; idet_int_det_batch:
                                   included in ms_lift_kernel)                */
     double inverse_macs;       /* modular MACs timed by ms_inverse: the LU
                                   (2n^3/3) and the triangular solves (n^3/6
@@ -160,6 +165,15 @@ void idet_set_wait_limit(int64_t cycles);
  * factor K of s_n (Section 2.2), then Alg. 2.1 on det(A)/K reusing the
  * residues already computed (Section 4). opts may be NULL (defaults), stats
  * may be NULL. det receives the exact determinant.
+ * Order of the steps: for n < 500 (and with certify, lif != 1, i_max = 2 or
+ * 31-bit CRA primes) the first CRA wave comes first and the solve follows
+ * only without early termination (from n = 1500 the LU and inverse mod the
+ * lifting prime run beside the wave on a second stream). From n = 500 on the
+ * order is speculative: inverse and lift first, then the first wave on a
+ * second stream while the rational reconstruction (one CTA) runs; the wave's
+ * early-termination verdict still wins (its determinant is returned, K is
+ * not used). Set the environment variable IDET_ET_FIRST to keep the wave
+ * first at every n. The result does not depend on the order.
  * Order limit of the solve: the lifting kernel stages its vector in shared
  * memory (4 n bytes per right-hand side when n max|a_ij| < 2^32, else the
  * vector and one row of A^{-1} mod p, 12 n bytes), so with lif = 1 or 2 n is

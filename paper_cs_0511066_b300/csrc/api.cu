@@ -12,6 +12,7 @@
 #include <mutex>
 #include <set>
 #include <string>
+#include <functional>
 #include <thread>
 #include <unordered_set>
 #include <vector>
@@ -26,6 +27,7 @@ namespace idet {
 static thread_local char g_err[1024] = "no error";
 std::atomic<unsigned long long> g_launches{0};
 thread_local bool t_native_alloc = false;
+thread_local int t_reserve_sms = 0;
 
 void set_last_error(const char *fmt, ...) {
     va_list ap;
@@ -348,6 +350,11 @@ struct Timer {
     }
     double stop() {
         cudaEventRecord(b, s);
+        return elapsed();
+    }
+    // end mark on the stream now; elapsed() waits for it later
+    void mark() { cudaEventRecord(b, s); }
+    double elapsed() {
         cudaEventSynchronize(b);
         float ms = 0;
         cudaEventElapsedTime(&ms, a, b);
@@ -424,6 +431,12 @@ struct DetJob {
     // stream while the first CRA wave is factored), or null
     int32_t *pre_Cinv = nullptr;
     uint32_t pre_p = 0;
+
+    // work run by the host while the reconstruction kernel is on the device
+    // (the first CRA wave, on a stream of its own), and its status
+    std::function<int()> during_rr;
+    int during_rr_rc = IDET_OK;
+    bool during_rr_ran = false;
 
     // LU factors kept from a wave of 31-bit CRA primes (primes[lu_first ..
     // lu_first + lu_count)): residues and permutations, prime-major
@@ -724,11 +737,19 @@ static int solve_and_denominator(DetJob &J, const int64_t *b_dev, const std::vec
         IDET_TRY(launch_ratrecon_bin(z, m, p, hN, hD, den, den_cap, info, ws));
     else
         IDET_TRY(launch_ratrecon(z, m, p, hN, hD, den, den_cap, info, ws));
+    trr.mark();  // the reconstruction kernel's end, on its stream
+    if (J.during_rr) {
+        // the reconstruction holds one SM: the other SMs take the hook's work
+        auto hook = std::move(J.during_rr);
+        J.during_rr = nullptr;
+        J.during_rr_rc = hook();
+        J.during_rr_ran = true;
+    }
     int32_t hinfo[4] = {0, 0, 0, 0};
     IDET_CUDA_TRY(cudaMemcpyAsync(hinfo, info, 16, cudaMemcpyDeviceToHost, s));
     IDET_CUDA_TRY(cudaStreamSynchronize(s));
+    J.st.ms_rr += trr.elapsed();
     if (hinfo[0] != 0) {
-        J.st.ms_rr += trr.stop();
         set_last_error("rational reconstruction failed (code %d)", hinfo[0]);
         return IDET_ERR_INTERNAL;
     }
@@ -737,13 +758,14 @@ static int solve_and_denominator(DetJob &J, const int64_t *b_dev, const std::vec
         out.Klen = hinfo[1];
         out.log2K = std::log2((double)(uint32_t)hinfo[3]) + std::max(0, hinfo[2] - 31);
     } else {
+        Timer tb(s);
         std::vector<uint32_t> dd(hinfo[1]);
         IDET_CUDA_TRY(cudaMemcpyAsync(dd.data(), den, 4 * (size_t)hinfo[1],
                                       cudaMemcpyDeviceToHost, s));
         IDET_CUDA_TRY(cudaStreamSynchronize(s));
         IDET_TRY(den_to_binary(ws, dd, p, &out.Kbin, &out.Klen, &out.log2K));
+        J.st.ms_rr += tb.stop();
     }
-    J.st.ms_rr += trr.stop();
     out.has_den = true;
     out.p = p;
     out.m = m;
@@ -1450,9 +1472,39 @@ int idet_int_det(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
     float inv_ms = 0;
     int32_t *inv_C = nullptr;
     uint32_t inv_p = 0;
-    // (measured: worth it from n ~ 2000; at n = 1000 the contention costs
-    // more than the overlap saves)
-    const bool overlap = o.lif == 1 && !certify && o.i_max < 2 && J.draw.bits != 31 &&
+    // From n = 500 on (21-bit CRA primes, one solve) the order is
+    // speculative instead: the inverse mod the lifting prime and the lift
+    // run first, and the first CRA wave is factored on a second stream while
+    // the rational reconstruction -- one CTA, about a fifth of the solve at
+    // n = 4000 -- runs beside it (Section 4 runs the LUs "in the background"
+    // of the solves). The wave's early-termination verdict still decides
+    // first: if it stops, its determinant is returned and K is not used. A
+    // lifting prime that divides det(A) (probably det(A) = 0) falls back to
+    // the wave-first order below.
+    bool spec = o.lif == 1 && !certify && o.i_max < 2 && J.draw.bits != 31 && n >= 500 &&
+                !getenv("IDET_ET_FIRST");
+    if (spec) {
+        IDET_TRY(make_Anar(J.M, J.amax, ws, &J.Anar, &J.abytes, &J.ldl));
+        int32_t *Cinv = nullptr;
+        IDET_TRY(ws.alloc_n(&Cinv, (size_t)n * J.ldl));
+        SplitMix g(J.o.seed ^ 0x11f7ull);
+        const uint32_t p = random_prime31(g);
+        Timer tinv(s);
+        const int rc = inverse_mod_prime(J.M, p, J.nb, ws, Cinv, J.ldl);
+        J.st.ms_inverse += tinv.stop();
+        if (rc == IDET_OK) {
+            J.pre_Cinv = Cinv;
+            J.pre_p = p;
+            J.st.inverse_macs += (4.0 / 3.0) * (double)n * n * n;
+        } else if (rc == IDET_ERR_SINGULAR) {
+            spec = false;
+        } else {
+            return finish(rc);
+        }
+    }
+    // Otherwise, from n = 1500 on, the LU and inverse mod the lifting prime
+    // run on a second stream beside the first wave.
+    const bool overlap = !spec && o.lif == 1 && !certify && o.i_max < 2 && J.draw.bits != 31 &&
                          n >= 1500 && !getenv("IDET_SERIAL_INVERSE");
     if (overlap && !solve_first) {
         IDET_TRY(make_Anar(J.M, J.amax, ws, &J.Anar, &J.abytes, &J.ldl));
@@ -1505,7 +1557,45 @@ int idet_int_det(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
         set_last_error("%s", inv_err.c_str());
         return inv_rc;
     };
-    if (!solve_first) {
+    bool spec_done = false;
+    if (spec) {
+        J.during_rr = [&]() -> int {
+            cudaStream_t s2 = nullptr;
+            IDET_CUDA_TRY(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+            int rc;
+            const bool native0 = t_native_alloc;
+            t_native_alloc = true;  // stream-ordered allocations on s2
+            {
+                Workspace ws2(s2);
+                t_native_alloc = native0;
+                DetJob J2(J.M, ws2, J.o, J.draw.bits);
+                J2.log2H = J.log2H;
+                J2.amax = J.amax;
+                J2.rowsq = J.rowsq;
+                J2.colsq = J.colsq;
+                J2.nb = J.nb;
+                J2.st.log2_H = J.st.log2_H;
+                t_reserve_sms = 1;
+                rc = det_first(J2, k0, wave, false, det, &spec_done);
+                t_reserve_sms = 0;
+                cudaStreamSynchronize(s2);
+                // the wave's residues, and the prime stream, continue in J
+                J.primes = J2.primes;
+                J.dets = J2.dets;
+                J.draw = J2.draw;
+                J.st.ms_lu += J2.st.ms_lu;
+                J.st.ms_cra += J2.st.ms_cra;
+                J.st.primes_used += J2.st.primes_used;
+                J.st.lu_macs += J2.st.lu_macs;
+                if (spec_done) {
+                    J.st.et_stop = J2.st.et_stop;
+                    J.st.primes_in_cra = J2.st.primes_in_cra;
+                }
+            }
+            cudaStreamDestroy(s2);
+            return rc;
+        };
+    } else if (!solve_first) {
         bool done = false;
         const int rc0 = det_first(J, k0, wave, certify || !o.lif, det, &done);
         const int rcj = join_inverse();
@@ -1534,6 +1624,18 @@ int idet_int_det(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
     int rc = lif_common(J, bdev, bh, lr);
     J.st.ms_lift += tl.stop();
     J.st.lift_timed_out = lr.timed_out;
+    if (spec) {
+        J.during_rr = nullptr;
+        if (J.during_rr_ran) {
+            if (J.during_rr_rc != IDET_OK) return finish(J.during_rr_rc);
+            if (spec_done) return finish(IDET_OK);
+        } else {
+            // the solve ended before its reconstruction: the wave now
+            bool done = false;
+            const int rc0 = det_first(J, k0, wave, false, det, &done);
+            if (rc0 != IDET_OK || done) return finish(rc0);
+        }
+    }
     if (rc != IDET_OK && rc != IDET_ERR_SINGULAR) return finish(rc);
     J.st.lift_iters = lr.m;
     J.st.lift_timed_out = lr.timed_out;

@@ -121,6 +121,9 @@ int allow_max_smem(const void *kernel);
 // Set by threads that must not call a user allocator (the serving
 // workers): their workspaces use cudaMallocAsync on their own stream.
 extern thread_local bool t_native_alloc;
+// SMs that persistent kernels launched from this thread leave free (one
+// while a single-CTA reconstruction runs beside them on another stream).
+extern thread_local int t_reserve_sms;
 
 class Workspace {
   public:

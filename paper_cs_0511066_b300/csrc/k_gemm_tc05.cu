@@ -584,7 +584,12 @@ static int gemm_tc05_l(const int32_t *A, int64_t lda, int64_t sA, const int32_t 
     const size_t smem = Tc<L>::kSmem;
     IDET_TRY(allow_max_smem((const void *)k_gemm_tc05<L>));
     const int64_t tiles = (int64_t)W * Mt * Nt;
-    const int grid = (int)std::min<int64_t>(tiles, 148);
+    int dev = 0, sms = 148;
+    IDET_CUDA_TRY(cudaGetDevice(&dev));
+    IDET_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // a CTA per SM, but none on SMs that a concurrent kernel of this thread
+    // holds (a persistent CTA waiting for such an SM would hold up its tiles)
+    const int grid = (int)std::min<int64_t>(tiles, std::max(1, sms - t_reserve_sms));
     k_gemm_tc05<L><<<grid, Tc<L>::kThreads, smem, s>>>(Apk, Bpk, Kp, Mt, Nt, W, C, ldc, sC, M, N,
                                                        mods, st);
     count_launch();

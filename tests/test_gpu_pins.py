@@ -425,3 +425,51 @@ def test_prime_bits_31_lift_reuses_a_cra_lu():
         assert st["inverse_macs"] == pytest.approx(2.0 / 3.0 * n ** 3), st
         d21, st21 = idet.int_det(A, return_stats=True)
         assert d21 == d and st21["inverse_macs"] == pytest.approx(4.0 / 3.0 * n ** 3)
+
+
+# --- order of the steps: speculative solve beside the first wave (n >= 500) ------------
+
+def _unimodular_np(n, ops, seed):
+    r = np.random.default_rng(seed)
+    U = np.eye(n, dtype=np.int64)
+    for _ in range(ops):
+        i, j = r.choice(n, 2, replace=False)
+        U[i] += int(r.choice([-1, 1])) * U[j]
+    return U
+
+
+def test_speculative_order_matches_wave_first(monkeypatch):
+    """From n = 500 the inverse and the lift run first and the first CRA wave
+    is factored beside the reconstruction. The determinant, the primes used
+    and the stopping point are those of the wave-first order (IDET_ET_FIRST),
+    for a dense matrix and for det = 7 (K = 7 from the solve, det/K = 1); a
+    singular matrix, whose lifting prime's LU is singular, falls back to the
+    wave-first order and returns 0."""
+    A = workloads.dense_pm100(600, seed=11)
+    d_spec, st_spec = idet.int_det(A, return_stats=True)
+    monkeypatch.setenv("IDET_ET_FIRST", "1")
+    d_first, st_first = idet.int_det(A, return_stats=True)
+    monkeypatch.delenv("IDET_ET_FIRST")
+    assert d_spec == d_first
+    assert st_spec["primes_used"] == st_first["primes_used"]
+    assert st_spec["primes_in_cra"] == st_first["primes_in_cra"]
+    qs = P21[-5:]
+    assert [d_spec % q for q in qs] == [int(x) for x in modular.det_mod_primes(A, qs)]
+    # det = 7: U diag(1, ..., 1, 7) V with U, V products of elementary operations
+    n = 520
+    U, V = _unimodular_np(n, n, 1), _unimodular_np(n, n, 2)
+    D = np.eye(n, dtype=np.int64)
+    D[-1, -1] = 7
+    B = U @ D @ V
+    assert np.abs(B).max() < (1 << 31)
+    d7, st7 = idet.int_det(B, return_stats=True)
+    monkeypatch.setenv("IDET_ET_FIRST", "1")
+    d7f, st7f = idet.int_det(B, return_stats=True)
+    monkeypatch.delenv("IDET_ET_FIRST")
+    assert d7 == d7f == 7
+    for key in ("primes_used", "primes_in_cra", "et_stop", "log2_K"):
+        assert st7[key] == st7f[key], key
+    # two equal rows: det = 0
+    S = workloads.dense_pm100(510, seed=12)
+    S[17] = S[400]
+    assert idet.int_det(S) == 0

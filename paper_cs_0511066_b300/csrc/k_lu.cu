@@ -292,11 +292,12 @@ k_panel(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb,
 // the cluster: the first nonzero row below it is found across the CTAs and
 // the two rows are exchanged in the owners' blocks (through distributed
 // shared memory), in every replica, and outside the panel in global memory.
-constexpr int kCl = 8;
+constexpr int kCl = 8;  // portable cluster size; 16 (opt-in) when few primes leave SMs idle
 constexpr int kClThreads = 512;
 constexpr int kSP = kNBMax + 1;  // row stride of a CTA's panel block in shared memory
 
-__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClThreads)
+template <int CL>
+__global__ void __launch_bounds__(kClThreads)
 k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chunk,
                 const ModP *__restrict__ mods, LUState *__restrict__ st,
                 int32_t *__restrict__ perm) {
@@ -309,7 +310,7 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
     __shared__ int32_t s_tmp[2][kNBMax];    // the two rows of an exchange
     __shared__ int32_t s_um[2][kNBMax];     // pivot row of column c in Montgomery form, slot c & 1
     const int rank = (int)cluster.block_rank();
-    const int w = blockIdx.x / kCl;
+    const int w = blockIdx.x / CL;
     const ModP M = mods[w];
     int32_t *a = R + (int64_t)w * n * n;
     const bool dead0 = st[w].dead != 0;  // uniform over the cluster
@@ -347,7 +348,7 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
             }
             cluster.sync();
             int best = INT_MAX;
-            for (int k = 0; k < kCl; ++k)
+            for (int k = 0; k < CL; ++k)
                 best = min(best, *cluster.map_shared_rank(&s_cand, k));
             if (best == INT_MAX) {
                 dead = true;
@@ -818,6 +819,71 @@ int trsm_lower(const int32_t *Lm, int64_t sL, int32_t *X, int64_t sX, int64_t n,
     return IDET_OK;
 }
 
+// Cluster size of the panel: 16 CTAs per prime (the non-portable size)
+// when the primes' clusters still fit on the SMs and the device schedules
+// them, else 8. With few primes (the lifting prime's LU is one) most SMs
+// would otherwise idle through the panels, and a column's work per CTA halves.
+static int panel_cluster_size(int W) {
+    static int ok16 = -1;  // 16-CTA clusters of this kernel can be scheduled
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return kCl;
+    if (W * 16 > sms - t_reserve_sms) return kCl;
+    if (ok16 < 0) {
+        ok16 = 0;
+        if (allow_max_smem((const void *)k_panel_cluster<16>) == IDET_OK &&
+            cudaFuncSetAttribute((const void *)k_panel_cluster<16>,
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at;
+            at.id = cudaLaunchAttributeClusterDimension;
+            at.val.clusterDim.x = 16;
+            at.val.clusterDim.y = 1;
+            at.val.clusterDim.z = 1;
+            cfg.gridDim = dim3(16);
+            cfg.blockDim = dim3(kClThreads);
+            cfg.dynamicSmemBytes = 64 * 1024;
+            cfg.attrs = &at;
+            cfg.numAttrs = 1;
+            int nc = 0;
+            if (cudaOccupancyMaxActiveClusters(&nc, (const void *)k_panel_cluster<16>, &cfg) ==
+                    cudaSuccess &&
+                nc >= 1)
+                ok16 = 1;
+        }
+        cudaGetLastError();
+    }
+    return ok16 ? 16 : kCl;
+}
+
+static int launch_panel_cluster(int CL, int W, size_t psmem, cudaStream_t s, int32_t *R, int64_t n,
+                                int64_t j0, int jb, int chunk, const ModP *mods, LUState *st,
+                                int32_t *perm) {
+    const void *kern =
+        CL == 16 ? (const void *)k_panel_cluster<16> : (const void *)k_panel_cluster<kCl>;
+    IDET_TRY(allow_max_smem(kern));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = CL;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(W * CL));
+    cfg.blockDim = dim3(kClThreads);
+    cfg.dynamicSmemBytes = psmem;
+    cfg.stream = s;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    if (CL == 16)
+        IDET_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_panel_cluster<16>, R, n, j0, jb, chunk, mods, st,
+                                         perm));
+    else
+        IDET_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_panel_cluster<kCl>, R, n, j0, jb, chunk, mods, st,
+                                         perm));
+    return IDET_OK;
+}
+
 // Two-level right-looking LU: block columns of NB = 128 (the trailing
 // update's K, so that the Schur complement is read and written once per 128
 // columns), each factored by 32-wide cluster panels with updates confined to
@@ -829,7 +895,6 @@ int lu_blocked(int32_t *R, int64_t n, const ModP *mods, int W, int nb, int32_t *
                int32_t *tri = nullptr) {
     k_state_init<<<W, 256, 0, s>>>(st, mods, W, perm, n);
     count_launch();
-    IDET_TRY(allow_max_smem((const void *)k_panel_cluster));
     const int64_t nn = n * n;
     const int NB = 4 * nb;
     auto upd = [&](int64_t r, int64_t c, int64_t kr, int M, int N, int K) -> int {
@@ -850,11 +915,12 @@ int lu_blocked(int32_t *R, int64_t n, const ModP *mods, int W, int nb, int32_t *
         const int JB = (int)((n - J0) < NB ? (n - J0) : NB);
         for (int64_t j0 = J0; j0 < J0 + JB; j0 += nb) {
             const int jb = (int)((J0 + JB - j0) < nb ? (J0 + JB - j0) : nb);
-            const int chunk = (int)((n - j0 + kCl - 1) / kCl);
+            const int CL = panel_cluster_size(W);
+            const int chunk = (int)((n - j0 + CL - 1) / CL);
             const size_t psmem = sizeof(int32_t) * (size_t)chunk * kSP;
             if (psmem <= 200 * 1024) {
-                k_panel_cluster<<<W * kCl, kClThreads, psmem, s>>>(R, n, j0, jb, chunk, mods, st,
-                                                                   perm);
+                IDET_TRY(launch_panel_cluster(CL, W, psmem, s, R, n, j0, jb, chunk, mods, st,
+                                              perm));
             } else {
                 k_panel<<<W, kPanelThreads, 0, s>>>(R, n, j0, jb, mods, st, perm);
             }

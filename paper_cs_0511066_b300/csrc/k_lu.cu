@@ -300,7 +300,7 @@ template <int CL>
 __global__ void __launch_bounds__(kClThreads)
 k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chunk,
                 const ModP *__restrict__ mods, LUState *__restrict__ st,
-                int32_t *__restrict__ perm) {
+                int32_t *__restrict__ perm, int32_t *__restrict__ tri) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ int32_t sp[];         // chunk x kSP: this CTA's rows
@@ -454,6 +454,33 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
         s.det = det;
         s.neg = neg;
         st[w] = s;
+    }
+    if (tri && rank == 0) {
+        // L11^{-1} (unit lower triangular, the strictly lower part of the
+        // replica) for the triangular solves: column j by forward substitution,
+        // x_i = -sum_{j <= k < i} L_ik x_k, by the 16 threads j*16 .. j*16+15
+        // (the sum split over them, partial sums reduced mod p before they
+        // are added); written as tri[w][i][j], zero outside jb x jb.
+        __shared__ int32_t sx[kNBMax][kNBMax + 1];
+        const int j = tid >> 4, sub = tid & 15;
+        const unsigned gmask = 0xffffu << (tid & 16);
+        for (int i = 0; i < kNBMax; ++i) {
+            int32_t x = (i == j) ? 1 : 0;
+            if (j < jb && i > j && i < jb) {
+                int64_t part = 0;
+                for (int k = j + sub; k < i; k += 16)
+                    part += (int64_t)dg[i * kSP + k] * sx[k][j];
+                int64_t acc = red_bal(part, M);
+#pragma unroll
+                for (int o = 8; o; o >>= 1) acc += __shfl_xor_sync(gmask, acc, o, 16);
+                x = red_bal(-acc, M);
+            }
+            if (sub == 0 && j < kNBMax) sx[i][j] = (i < jb && j < jb) ? x : 0;
+            __syncwarp(gmask);
+        }
+        __syncthreads();
+        for (int e = tid; e < kNBMax * kNBMax; e += kClThreads)
+            tri[(int64_t)w * kNBMax * kNBMax + e] = sx[e / kNBMax][e % kNBMax];
     }
 }
 
@@ -859,7 +886,7 @@ static int panel_cluster_size(int W) {
 
 static int launch_panel_cluster(int CL, int W, size_t psmem, cudaStream_t s, int32_t *R, int64_t n,
                                 int64_t j0, int jb, int chunk, const ModP *mods, LUState *st,
-                                int32_t *perm) {
+                                int32_t *perm, int32_t *tri) {
     const void *kern =
         CL == 16 ? (const void *)k_panel_cluster<16> : (const void *)k_panel_cluster<kCl>;
     IDET_TRY(allow_max_smem(kern));
@@ -877,10 +904,10 @@ static int launch_panel_cluster(int CL, int W, size_t psmem, cudaStream_t s, int
     cfg.numAttrs = 1;
     if (CL == 16)
         IDET_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_panel_cluster<16>, R, n, j0, jb, chunk, mods, st,
-                                         perm));
+                                         perm, tri));
     else
         IDET_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_panel_cluster<kCl>, R, n, j0, jb, chunk, mods, st,
-                                         perm));
+                                         perm, tri));
     return IDET_OK;
 }
 
@@ -915,27 +942,32 @@ int lu_blocked(int32_t *R, int64_t n, const ModP *mods, int W, int nb, int32_t *
         const int JB = (int)((n - J0) < NB ? (n - J0) : NB);
         for (int64_t j0 = J0; j0 < J0 + JB; j0 += nb) {
             const int jb = (int)((J0 + JB - j0) < nb ? (J0 + JB - j0) : nb);
+            // the inverse of this panel's L11 goes to slot (j0 - J0) / nb of
+            // tri, for the solve inside the block column and again for the
+            // block row below; the cluster panel forms it from its replica
+            int32_t *tri_p = tri ? tri + (size_t)((j0 - J0) / nb) * W * kNBMax * kNBMax : nullptr;
             const int CL = panel_cluster_size(W);
             const int chunk = (int)((n - j0 + CL - 1) / CL);
             const size_t psmem = sizeof(int32_t) * (size_t)chunk * kSP;
+            // With few primes the panel also forms L11^{-1} from its replica (a
+            // separate launch would cost more than the forward substitution,
+            // whose 31 dependent steps lengthen the panel); with a full wave one
+            // batched launch over the primes is cheaper.
+            const bool cluster_panel = psmem <= 200 * 1024 && W <= 4;
             if (psmem <= 200 * 1024) {
                 IDET_TRY(launch_panel_cluster(CL, W, psmem, s, R, n, j0, jb, chunk, mods, st,
-                                              perm));
+                                              perm, cluster_panel ? tri_p : nullptr));
             } else {
                 k_panel<<<W, kPanelThreads, 0, s>>>(R, n, j0, jb, mods, st, perm);
             }
             count_launch();
             IDET_CUDA_TRY(cudaGetLastError());
-            // the inverse of this panel's L11 goes to slot (j0 - J0) / nb of
-            // tri, for the solve inside the block column and again for the
-            // block row below
-            int32_t *tri_p = tri ? tri + (size_t)((j0 - J0) / nb) * W * kNBMax * kNBMax : nullptr;
             const int64_t inner = J0 + JB - (j0 + jb);  // columns left in the block column
             if (inner > 0) {
                 IDET_TRY(trsm_lower<WIDE>(R, nn, R, nn, n, j0, j0, jb, j0 + jb, inner, mods, st,
-                                          W, s, tri_p));
+                                          W, s, tri_p, tri_p && cluster_panel));
                 IDET_TRY(upd(j0 + jb, j0 + jb, j0, (int)(n - j0 - jb), (int)inner, jb));
-            } else if (tri_p && n - J0 - JB > 0) {
+            } else if (tri_p && !cluster_panel && n - J0 - JB > 0) {
                 k_tri_inv<WIDE, false><<<W, kNBMax * kNBMax, 0, s>>>(R, nn, n, j0, jb, mods, st,
                                                                       tri_p);
                 count_launch();

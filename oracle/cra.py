@@ -1,7 +1,7 @@
 """Chinese remaindering with early termination (oracle; test-only).
 
 Follows Section 2.1 of the paper:
-* crt_symmetric -- the value modulo p_0...p_t "in the symmetric range"
+* crt_symmetric -- the value modulo p_0...p_t, taken in the symmetric range
   -floor(M/2) <= r < ceil(M/2) (proof of Lemma 2.1(i)), computed by the
   textbook CRT formula r = sum_k d_k M_k (M_k^{-1} mod p_k) mod M.
 * et_cra -- Algorithm 2.1 (Early Terminated CRA): add one modular

@@ -1461,8 +1461,8 @@ int idet_int_det(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
     // of Abbott, Bronstein and Mulders that Fig. 2 compares against) skips
     // it and reconstructs det(A)/K to the bound 2H/K after the solve.
     const bool solve_first = o.lif == 2 && !certify;
-    // Section 4 runs the modular LUs "in the background" and solves the
-    // random systems "in parallel or in sequential": the LU and inverse mod
+    // Section 4 lets the modular LUs run behind the solves, and the random
+    // systems be solved together or one after another: the LU and inverse mod
     // the lifting prime do not depend on the CRA, so they run on a second
     // stream, from a second host thread, while the first CRA wave is factored
     // (its workspace from the stream-ordered pool, as the serving workers').
@@ -1476,8 +1476,8 @@ int idet_int_det(const int64_t *A, int64_t n, int64_t lda, int32_t on_device,
     // speculative instead: the inverse mod the lifting prime and the lift
     // run first, and the first CRA wave is factored on a second stream while
     // the rational reconstruction -- one CTA, about a fifth of the solve at
-    // n = 4000 -- runs beside it (Section 4 runs the LUs "in the background"
-    // of the solves). The wave's early-termination verdict still decides
+    // n = 4000 -- runs beside it (Section 4 lets the LUs run behind the
+    // solves). The wave's early-termination verdict still decides
     // first: if it stops, its determinant is returned and K is not used. A
     // lifting prime that divides det(A) (probably det(A) = 0) falls back to
     // the wave-first order below.
@@ -1980,7 +1980,7 @@ static int radix_dev_to_binary(Workspace &ws, const uint32_t *dig, int len, uint
 // first CRA on det(A) did not terminate. The two solves of the inner loop
 // run as one block lift (Section 6: solvings grouped into a block
 // iteration). i = 1: pi~_1 = s~ of x_1, K = pi~_1, and the CRA of det/K
-// resumes "for at most the time of one system solving": with the second
+// resumes for no longer than one solve takes: with the second
 // solve already done by the block lift, the time is spent better on it, so
 // the resume checks the residues at hand for early termination and factors
 // no new primes. i = 2: s~ = lcm of the

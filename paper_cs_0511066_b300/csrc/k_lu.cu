@@ -92,6 +92,20 @@ __device__ __forceinline__ int32_t sub_mont(int32_t r, int32_t l, int32_t um, co
     return (int32_t)x;
 }
 
+// d r - a u mod p for the fraction-free panel, with d' = d R and u' = u R
+// (balanced, R = 2^32) formed once per pivot: t = d' r - a u' has |t| <= p^2/2
+// < 2^61, and v = (t - q p) / 2^32 (q = t p^{-1} mod 2^32) is d r - a u mod p
+// with |v| < p^2 / 2^33 + p / 2 < 0.75 p: one step either way balances it.
+__device__ __forceinline__ int32_t ff_mont(int32_t dm, int32_t r, int32_t a, int32_t um,
+                                           const Mont &m) {
+    const int64_t t = (int64_t)dm * r - (int64_t)a * um;
+    const int32_t q = (int32_t)((uint32_t)t * m.pinv);
+    int32_t v = (int32_t)(t >> 32) - __mulhi(q, m.p);
+    if (v > m.half) v -= m.p;
+    if (v < -m.half) v += m.p;
+    return v;
+}
+
 // g: the residues (n x n, ld n), or null with A64: the int64 entries (n x n,
 // ld n), reduced here while they are loaded.
 __device__ void lu_small_body(int32_t *__restrict__ g, int n, const ModP M,
@@ -280,18 +294,30 @@ k_panel(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb,
 }
 
 
-// Panel factorisation by a cluster of kCl CTAs (one cluster per prime).
-// The panel (rows [j0, n), columns [j0, j0 + jb)) is split into kCl
+// Panel factorisation by a cluster of CL CTAs (one cluster per prime).
+// The panel (rows [j0, n), columns [j0, j0 + jb)) is split into CL
 // contiguous row blocks held in the CTAs' shared memory for the whole
 // panel. Every CTA also keeps a replica of the panel's top jb rows -- the
 // rows that become the pivot rows -- and applies the same eliminations to
 // it, so that each CTA knows every pivot row and pivot without
-// communication: a column costs one CTA barrier. Warp 0 eliminates the next
-// pivot row of the replica first and inverts the next pivot while the other
-// warps update the CTA's rows. Only a zero pivot (first-nonzero rule) needs
-// the cluster: the first nonzero row below it is found across the CTAs and
-// the two rows are exchanged in the owners' blocks (through distributed
-// shared memory), in every replica, and outside the panel in global memory.
+// communication: a column costs one CTA barrier.
+//
+// The elimination inside the panel is fraction-free: column c updates each
+// row below its pivot d_c by r <- d_c r - a u (a the row's entry in column
+// c, u the pivot row), so no modular inverse lies on the chain from one
+// column to the next. Every row below pivot c then carries the same factor
+// S_c = d_0 ... d_(c-1) (S_0 = 1): the true pivot is d_c / S_c, the true
+// multiplier of a row is its stored entry a / d_c (the factors cancel), and
+// the true pivot row is the stored one over S_c. At the end of the panel the
+// inverses of d_c and S_c come from one modular inverse (Montgomery's batch
+// trick) and every row is normalised to the ordinary L and U. Warp 0
+// eliminates the next pivot row of the replica first and forms its
+// Montgomery form while the other warps update their rows. Only a zero pivot
+// (first-nonzero rule; S_c != 0, so the stored and true pivots vanish
+// together) needs the cluster: the first nonzero row below it is found across
+// the CTAs and the two rows are exchanged in the owners' blocks (through
+// distributed shared memory), in every replica, and outside the panel in
+// global memory.
 constexpr int kCl = 8;  // portable cluster size; 16 (opt-in) when few primes leave SMs idle
 constexpr int kClThreads = 512;
 constexpr int kSP = kNBMax + 1;  // row stride of a CTA's panel block in shared memory
@@ -305,10 +331,11 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ int32_t sp[];         // chunk x kSP: this CTA's rows
     __shared__ int32_t dg[kNBMax * kSP];    // replica of rows [j0, j0 + jb)
-    __shared__ int32_t s_inv[2];            // inverse of the pivot of column c, slot c & 1
+    __shared__ int32_t s_dm[2];             // pivot of column c in Montgomery form, slot c & 1
     __shared__ int s_cand;                  // first nonzero row below a zero pivot
     __shared__ int32_t s_tmp[2][kNBMax];    // the two rows of an exchange
     __shared__ int32_t s_um[2][kNBMax];     // pivot row of column c in Montgomery form, slot c & 1
+    __shared__ int32_t s_invd[kNBMax], s_invS[kNBMax];  // 1 / d_c and 1 / S_c
     const int rank = (int)cluster.block_rank();
     const int w = blockIdx.x / CL;
     const ModP M = mods[w];
@@ -332,13 +359,12 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
     bool dead = false;
     const Mont mt = make_mont(M.p);
     __syncthreads();
-    if (tid == 0) s_inv[0] = dg[0] != 0 ? inv_bal32(dg[0], M.p) : 0;
+    if (tid == 0) s_dm[0] = mul_bal(dg[0], mt.r1, M);
     if (tid < jb) s_um[0][tid] = mul_bal(dg[tid], mt.r1, M);
     __syncthreads();
     for (int c = 0; c < jb; ++c) {
         const int64_t col = j0 + c;
-        int32_t pv = dg[c * kSP + c];
-        if (pv == 0) {
+        if (dg[c * kSP + c] == 0) {
             // (the replicas are identical: every CTA of the cluster is here)
             if (tid == 0) s_cand = INT_MAX;
             cluster.sync();
@@ -390,34 +416,27 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
             }
             neg ^= 1;
             cluster.sync();
-            pv = dg[c * kSP + c];
-            if (tid == 0) s_inv[c & 1] = inv_bal32(pv, M.p);
+            if (tid == 0) s_dm[c & 1] = mul_bal(dg[c * kSP + c], mt.r1, M);
             if (tid < jb) s_um[c & 1][tid] = mul_bal(dg[c * kSP + tid], mt.r1, M);
             __syncthreads();
         }
-        const int32_t inv = s_inv[c & 1];
-        det = det_mul(det, pv, M);
+        const int32_t dm = s_dm[c & 1];
         const int32_t *um = s_um[c & 1];
         if (warp == 0) {
-            // the next pivot row of the replica (and its Montgomery form),
-            // then the next pivot's inverse
+            // the next pivot row of the replica, then its Montgomery form
             if (c + 1 < jb) {
                 int32_t *row = dg + (c + 1) * kSP;
-                const int32_t l = mul_bal(row[c], inv, M);
-                __syncwarp();
-                if (lane == c) row[c] = l;
-                if (l && lane > c && lane < jb) row[lane] = sub_mont(row[lane], l, um[lane], mt);
+                const int32_t av = row[c];
+                if (lane > c && lane < jb) row[lane] = ff_mont(dm, row[lane], av, um[lane], mt);
                 __syncwarp();
                 if (lane < jb) s_um[(c + 1) & 1][lane] = mul_bal(row[lane], mt.r1, M);
-                if (lane == 0) {
-                    const int32_t d = row[c + 1];
-                    s_inv[(c + 1) & 1] = d != 0 ? inv_bal32(d, M.p) : 0;
-                }
+                if (lane == 0) s_dm[(c + 1) & 1] = mul_bal(row[c + 1], mt.r1, M);
             }
         } else {
             // a thread per row: this CTA's rows below the pivot, then the
             // replica's rows c + 2 .. jb - 1 (the row stride kSP = 33 words
-            // keeps the lanes of a warp on distinct banks)
+            // keeps the lanes of a warp on distinct banks); the entry in
+            // column c stays as the row's (unnormalised) multiplier
             const int items = nloc + max(0, jb - c - 2);
             for (int it = tid - 32; it < items; it += kClThreads - 32) {
                 int32_t *row;
@@ -427,13 +446,58 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
                 } else {
                     row = dg + (c + 2 + (it - nloc)) * kSP;
                 }
-                const int32_t l = mul_bal(row[c], inv, M);
-                row[c] = l;
-                if (l)
-                    for (int j = c + 1; j < jb; ++j) row[j] = sub_mont(row[j], l, um[j], mt);
+                // (a zero entry still scales the row by d_c: every row below
+                // the pivot must carry the same factor S_(c+1))
+                const int32_t av = row[c];
+                for (int j = c + 1; j < jb; ++j) row[j] = ff_mont(dm, row[j], av, um[j], mt);
             }
         }
         __syncthreads();
+    }
+    if (!dead) {
+        // 1 / d_c and 1 / S_c (S_c = d_0 ... d_(c-1)) from one inverse:
+        // prefix products P_c = d_0 ... d_c, then 1 / P_(jb-1) unwound
+        if (tid == 0) {
+            int32_t pre[kNBMax];
+            int32_t pr = 1;
+            for (int c = 0; c < jb; ++c) {
+                pr = mul_bal(pr, dg[c * kSP + c], M);
+                pre[c] = pr;
+            }
+            int32_t ip = inv_bal32(pr, M.p);  // 1 / P_(jb-1)
+            for (int c = jb - 1; c >= 0; --c) {
+                // 1 / d_c = P_(c-1) / P_c; 1 / P_(c-1) = d_c / P_c
+                s_invd[c] = c > 0 ? mul_bal(ip, pre[c - 1], M) : ip;
+                ip = mul_bal(ip, dg[c * kSP + c], M);
+            }
+            int32_t is = 1;  // 1 / S_c = 1 / P_(c-1)
+            for (int c = 0; c < jb; ++c) {
+                s_invS[c] = is;
+                is = mul_bal(is, s_invd[c], M);
+            }
+            // det *= prod_c d_c / S_c
+            for (int c = 0; c < jb; ++c)
+                det = det_mul(det, mul_bal(dg[c * kSP + c], s_invS[c], M), M);
+        }
+        __syncthreads();
+        // normalise this CTA's rows: multipliers (columns below the row's
+        // diagonal) times 1 / d_c; a pivot row's U part times 1 / S_r
+        for (int e = tid; e < nloc * jb; e += kClThreads) {
+            const int r = e / jb, j = e % jb;
+            const int64_t gr = rbeg + r - j0;  // row within the panel
+            int32_t &v = sp[r * kSP + j];
+            if (j < gr)
+                v = mul_bal(v, s_invd[j], M);
+            else
+                v = mul_bal(v, s_invS[gr], M);
+        }
+        if (tri && rank == 0) {
+            // the replica's L part likewise, for L11^{-1} below
+            for (int e = tid; e < jb * jb; e += kClThreads) {
+                const int r = e / jb, j = e % jb;
+                if (j < r) dg[r * kSP + j] = mul_bal(dg[r * kSP + j], s_invd[j], M);
+            }
+        }
     }
     cluster.sync();  // no CTA leaves while others may still read its block
     if (dead) {

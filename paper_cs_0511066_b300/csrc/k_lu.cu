@@ -318,12 +318,166 @@ k_panel(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb,
 // the CTAs and the two rows are exchanged in the owners' blocks (through
 // distributed shared memory), in every replica, and outside the panel in
 // global memory.
+//
+// That column loop runs only when the replica's block has a zero pivot. In
+// the common case one warp factors the block alone first; with all its
+// pivots nonzero the rule pivots on the panel's top rows in order, and each
+// thread then solves its rows against U11 with no barrier at all.
 constexpr int kCl = 8;  // portable cluster size; 16 (opt-in) when few primes leave SMs idle
 constexpr int kClThreads = 512;
 constexpr int kSP = kNBMax + 1;  // row stride of a CTA's panel block in shared memory
 
+// t R^{-1} mod p for |t| < 2^62 (R = 2^32): (t - q p) / 2^32 with
+// q = t p^{-1} mod 2^32, of magnitude below |t| / 2^32 + p / 2.
+__device__ __forceinline__ int32_t redc64(int64_t t, const Mont &m) {
+    const int32_t q = (int32_t)((uint32_t)t * m.pinv);
+    return (int32_t)(t >> 32) - __mulhi(q, m.p);
+}
+
+// a b R^{-1} mod p, balanced, for |a b| < p 2^32.
+__device__ __forceinline__ int32_t mont_mul(int32_t a, int32_t b, const Mont &m) {
+    int32_t v = redc64((int64_t)a * b, m);
+    if (v > m.half) v -= m.p;
+    if (v < -m.half) v += m.p;
+    return v;
+}
+
+// The panel's common case: when every pivot of the replica's jb x jb block
+// is nonzero, the first-nonzero rule takes the panel's top rows in order,
+// U11 is the block's U, and every row below solves x U11 = a for its L part
+// on its own, with no barrier per column.
+//
+// replica_lu_cta (all threads): fraction-free LU of the block in Montgomery
+// form (d' r' - a' u' reduced once is (d r - a u)'), thread (i, g) updating
+// columns g and g + 16 of row i, one CTA barrier per column. False
+// (CTA-uniform) at the first zero pivot, with dg untouched. Otherwise the
+// inverses of the pivots d_c and of their prefix products S_c come from one
+// inverse by product scans across a warp, and dg is overwritten with the
+// block's normalised factors (L_ic = s_ic / d_c below the diagonal, U_ic =
+// s_ic / S_i on and above it). -U_kc for k < c < jb (zero elsewhere) goes to
+// ut[c][k] for 21-bit primes (narrow), else split at bit 16 into its low
+// (ut) and high (ut2) parts; w[c] = 1 / U_cc = S_c / d_c (times R^2 when
+// narrow: the solve then reduces by two Montgomery steps); *detf = prod U_cc.
+struct ReplicaScratch {
+    int32_t fa[kNBMax * kSP];  // the block in Montgomery form
+    int32_t invd[kNBMax], invS[kNBMax];
+};
+
+__device__ bool replica_lu_cta(int32_t *dg, int jb, const ModP &M, const Mont &mt,
+                               ReplicaScratch &rs, int32_t *ut, int32_t *ut2, int32_t *w,
+                               bool narrow, int32_t *detf) {
+    const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
+    const int ng = blockDim.x >> 5;
+    const int32_t r2 = mul_bal(mt.r1, mt.r1, M);  // R^2 mod p
+    for (int e = tid; e < jb * jb; e += blockDim.x) {
+        const int i = e / jb, j = e % jb;
+        rs.fa[i * kSP + j] = mont_mul(dg[i * kSP + j], r2, mt);
+    }
+    __syncthreads();
+    for (int c = 0; c < jb; ++c) {
+        const int32_t dm = rs.fa[c * kSP + c];
+        if (dm == 0) return false;  // every thread reads the same pivot
+        if (lane > c && lane < jb) {
+            int32_t *row = rs.fa + lane * kSP;
+            const int32_t am = row[c];
+            for (int j = g; j < jb; j += ng)
+                if (j > c) row[j] = ff_mont(dm, row[j], am, rs.fa[c * kSP + j], mt);
+        }
+        __syncthreads();
+    }
+    if (tid < 32) {
+        const unsigned full = 0xffffffffu;
+        const int32_t d = lane < jb ? mont_mul(rs.fa[lane * kSP + lane], 1, mt) : 1;  // d_lane
+        int32_t P = d;  // P_c = d_0 ... d_c
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t t = __shfl_up_sync(full, P, o);
+            if (lane >= o) P = mul_bal(P, t, M);
+        }
+        int32_t S = __shfl_up_sync(full, P, 1);  // S_c = P_(c-1)
+        if (lane == 0) S = 1;
+        int32_t Q = d;  // d_c ... d_31
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t t = __shfl_down_sync(full, Q, o);
+            if (lane + o < 32) Q = mul_bal(Q, t, M);
+        }
+        int32_t Qx = __shfl_down_sync(full, Q, 1);  // d_(c+1) ... d_31
+        if (lane == 31) Qx = 1;
+        const int32_t I = inv_bal32(__shfl_sync(full, P, 31), M.p);  // 1 / P_31
+        const int32_t invP = mul_bal(I, Qx, M);                        // 1 / P_c
+        const int32_t invd = mul_bal(S, invP, M);                      // 1 / d_c
+        const int32_t invS = mul_bal(invP, d, M);                      // 1 / S_c
+        int32_t uf = lane < jb ? mul_bal(d, invS, M) : 1;              // U_cc
+#pragma unroll
+        for (int o = 16; o; o >>= 1) uf = mul_bal(uf, __shfl_xor_sync(full, uf, o), M);
+        rs.invd[lane] = invd;
+        rs.invS[lane] = invS;
+        const int32_t invU = mul_bal(S, invd, M);
+        w[lane] = lane < jb ? (narrow ? mul_bal(invU, r2, M) : invU) : 0;
+        if (lane == 0) *detf = uf;
+    }
+    __syncthreads();
+    for (int e = tid; e < kNBMax * kNBMax; e += blockDim.x) {
+        const int i = e & 31, j = e >> 5;  // row i, column j
+        int32_t v = 0;
+        if (i < jb && j < jb) {
+            v = mont_mul(rs.fa[i * kSP + j], j < i ? rs.invd[j] : rs.invS[i], mt);
+            dg[i * kSP + j] = v;
+        }
+        const int32_t nu = (i < j && j < jb) ? -v : 0;  // -U_ij at [j][i]
+        ut[j * kNBMax + i] = narrow ? nu : (nu & 0xffff);
+        if (!narrow) ut2[j * kNBMax + i] = nu >> 16;
+    }
+    __syncthreads();
+    return true;
+}
+
+// x U11 = a for one row below the replica (a: the row's jb panel entries,
+// overwritten in place by x, its L part, column by column):
+// x_c = (a_c - sum_{k<c} x_k U_kc) / U_cc with ut and w from replica_lu_cta
+// (ut[c][k] = 0 for k >= c, so the sum runs over whole groups of four).
+// 21-bit primes: at most 31 products below 2^40, exact in int64, reduced
+// once by two Montgomery steps (w_c = R^2 / U_cc).
+__device__ __forceinline__ void solve_row_narrow(int32_t *row, int jb, const int32_t *ut,
+                                                 const int32_t *w, const Mont &mt) {
+    for (int c = 0; c < jb; ++c) {
+        const int32_t *u = ut + c * kNBMax;
+        int64_t acc = row[c];
+        for (int k = 0; k < c; k += 4) {
+            const int4 q = *reinterpret_cast<const int4 *>(u + k);
+            acc += (int64_t)row[k] * q.x;
+            acc += (int64_t)row[k + 1] * q.y;
+            acc += (int64_t)row[k + 2] * q.z;
+            acc += (int64_t)row[k + 3] * q.w;
+        }
+        row[c] = mont_mul(redc64(acc, mt), w[c], mt);
+    }
+}
+
+// The same for primes up to 2^31: -U_kc split at bit 16 (ut: its low 16
+// bits, ut2: the rest), two int64 sums of terms below 2^46 and 2^44, reduced
+// by Barrett steps.
+__device__ __forceinline__ void solve_row_wide(int32_t *row, int jb, const int32_t *ut,
+                                               const int32_t *ut2, const int32_t *w,
+                                               const ModP &M) {
+    for (int c = 0; c < jb; ++c) {
+        const int32_t *u = ut + c * kNBMax, *h = ut2 + c * kNBMax;
+        int64_t lo = row[c], hi = 0;
+        for (int k = 0; k < c; k += 4) {
+            const int4 q = *reinterpret_cast<const int4 *>(u + k);
+            const int4 r = *reinterpret_cast<const int4 *>(h + k);
+            const int32_t x0 = row[k], x1 = row[k + 1], x2 = row[k + 2], x3 = row[k + 3];
+            lo += (int64_t)x0 * q.x + (int64_t)x1 * q.y + (int64_t)x2 * q.z + (int64_t)x3 * q.w;
+            hi += (int64_t)x0 * r.x + (int64_t)x1 * r.y + (int64_t)x2 * r.z + (int64_t)x3 * r.w;
+        }
+        const int32_t v = red_bal((int64_t)red_bal(hi, M) * 65536 + red_bal(lo, M), M);
+        row[c] = mul_bal(v, w[c], M);
+    }
+}
+
 template <int CL>
-__global__ void __launch_bounds__(kClThreads)
+__global__ void __launch_bounds__(kClThreads, 2)
 k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chunk,
                 const ModP *__restrict__ mods, LUState *__restrict__ st,
                 int32_t *__restrict__ perm, int32_t *__restrict__ tri) {
@@ -336,6 +490,11 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
     __shared__ int32_t s_tmp[2][kNBMax];    // the two rows of an exchange
     __shared__ int32_t s_um[2][kNBMax];     // pivot row of column c in Montgomery form, slot c & 1
     __shared__ int32_t s_invd[kNBMax], s_invS[kNBMax];  // 1 / d_c and 1 / S_c
+    __shared__ __align__(16) int32_t s_ut[kNBMax * kNBMax];  // -U_kc at [c][k], k < c
+    __shared__ __align__(16) int32_t s_ut2[kNBMax * kNBMax]; // its high part (31-bit p)
+    __shared__ int32_t s_w[kNBMax];                         // 1 / U_cc (times R^2: 21-bit p)
+    __shared__ int32_t s_detf;                              // prod U_cc
+    __shared__ ReplicaScratch s_rs;
     const int rank = (int)cluster.block_rank();
     const int w = blockIdx.x / CL;
     const ModP M = mods[w];
@@ -359,143 +518,163 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
     bool dead = false;
     const Mont mt = make_mont(M.p);
     __syncthreads();
-    if (tid == 0) s_dm[0] = mul_bal(dg[0], mt.r1, M);
-    if (tid < jb) s_um[0][tid] = mul_bal(dg[tid], mt.r1, M);
-    __syncthreads();
-    for (int c = 0; c < jb; ++c) {
-        const int64_t col = j0 + c;
-        if (dg[c * kSP + c] == 0) {
-            // (the replicas are identical: every CTA of the cluster is here)
-            if (tid == 0) s_cand = INT_MAX;
-            cluster.sync();
-            for (int r = tid; r < nloc; r += kClThreads) {
-                const int64_t gi = rbeg + r;
-                if (gi > col && sp[r * kSP + c] != 0) atomicMin(&s_cand, (int)gi);
+    // the common case first (every replica pivot nonzero): the CTA factors
+    // the replica, then each thread solves its rows below it
+    const bool narrow = M.p < (1u << 21);
+    // (the replicas agree: uniform over the cluster)
+    const bool fast = replica_lu_cta(dg, jb, M, mt, s_rs, s_ut, s_ut2, s_w, narrow, &s_detf);
+    if (fast) {
+        for (int r = tid; r < nloc; r += kClThreads) {
+            const int64_t gr = rbeg + r - j0;  // row within the panel
+            int32_t *row = sp + r * kSP;
+            if (gr < jb) {
+                for (int j = 0; j < jb; ++j) row[j] = dg[gr * kSP + j];
+            } else if (narrow) {
+                solve_row_narrow(row, jb, s_ut, s_w, mt);
+            } else {
+                solve_row_wide(row, jb, s_ut, s_ut2, s_w, M);
             }
-            cluster.sync();
-            int best = INT_MAX;
-            for (int k = 0; k < CL; ++k)
-                best = min(best, *cluster.map_shared_rank(&s_cand, k));
-            if (best == INT_MAX) {
-                dead = true;
-                break;
-            }
-            const int64_t piv = best;
-            const int po = (int)((piv - j0) / chunk), co = (int)((col - j0) / chunk);
-            int32_t *prow = cluster.map_shared_rank(sp, po) +
-                            (int)(piv - (j0 + (int64_t)po * chunk)) * kSP;
-            int32_t *crow = cluster.map_shared_rank(sp, co) +
-                            (int)(col - (j0 + (int64_t)co * chunk)) * kSP;
-            if (tid < jb) {
-                s_tmp[0][tid] = crow[tid];
-                s_tmp[1][tid] = prow[tid];
-            }
-            cluster.sync();  // both rows read everywhere before they change
-            if (rank == 0 && tid < jb) {
-                crow[tid] = s_tmp[1][tid];
-                prow[tid] = s_tmp[0][tid];
-            }
-            if (tid < jb) {
-                dg[c * kSP + tid] = s_tmp[1][tid];
-                if (piv < j0 + jb) dg[(int)(piv - j0) * kSP + tid] = s_tmp[0][tid];
-            }
-            // parts outside the panel, in global memory (rank 0)
-            if (rank == 0) {
-                for (int64_t j = tid; j < n; j += kClThreads) {
-                    if (j >= j0 && j < j0 + jb) continue;
-                    int32_t t = a[col * n + j];
-                    a[col * n + j] = a[piv * n + j];
-                    a[piv * n + j] = t;
+        }
+        if (tid == 0) det = det_mul(det, s_detf, M);
+    } else {
+        if (tid == 0) s_dm[0] = mul_bal(dg[0], mt.r1, M);
+        if (tid < jb) s_um[0][tid] = mul_bal(dg[tid], mt.r1, M);
+        __syncthreads();
+        for (int c = 0; c < jb; ++c) {
+            const int64_t col = j0 + c;
+            if (dg[c * kSP + c] == 0) {
+                // (the replicas are identical: every CTA of the cluster is here)
+                if (tid == 0) s_cand = INT_MAX;
+                cluster.sync();
+                for (int r = tid; r < nloc; r += kClThreads) {
+                    const int64_t gi = rbeg + r;
+                    if (gi > col && sp[r * kSP + c] != 0) atomicMin(&s_cand, (int)gi);
                 }
-                if (tid == 0 && perm) {
-                    int32_t *pm = perm + (int64_t)w * n;
-                    int32_t t = pm[col];
-                    pm[col] = pm[piv];
-                    pm[piv] = t;
+                cluster.sync();
+                int best = INT_MAX;
+                for (int k = 0; k < CL; ++k)
+                    best = min(best, *cluster.map_shared_rank(&s_cand, k));
+                if (best == INT_MAX) {
+                    dead = true;
+                    break;
+                }
+                const int64_t piv = best;
+                const int po = (int)((piv - j0) / chunk), co = (int)((col - j0) / chunk);
+                int32_t *prow = cluster.map_shared_rank(sp, po) +
+                                (int)(piv - (j0 + (int64_t)po * chunk)) * kSP;
+                int32_t *crow = cluster.map_shared_rank(sp, co) +
+                                (int)(col - (j0 + (int64_t)co * chunk)) * kSP;
+                if (tid < jb) {
+                    s_tmp[0][tid] = crow[tid];
+                    s_tmp[1][tid] = prow[tid];
+                }
+                cluster.sync();  // both rows read everywhere before they change
+                if (rank == 0 && tid < jb) {
+                    crow[tid] = s_tmp[1][tid];
+                    prow[tid] = s_tmp[0][tid];
+                }
+                if (tid < jb) {
+                    dg[c * kSP + tid] = s_tmp[1][tid];
+                    if (piv < j0 + jb) dg[(int)(piv - j0) * kSP + tid] = s_tmp[0][tid];
+                }
+                // parts outside the panel, in global memory (rank 0)
+                if (rank == 0) {
+                    for (int64_t j = tid; j < n; j += kClThreads) {
+                        if (j >= j0 && j < j0 + jb) continue;
+                        int32_t t = a[col * n + j];
+                        a[col * n + j] = a[piv * n + j];
+                        a[piv * n + j] = t;
+                    }
+                    if (tid == 0 && perm) {
+                        int32_t *pm = perm + (int64_t)w * n;
+                        int32_t t = pm[col];
+                        pm[col] = pm[piv];
+                        pm[piv] = t;
+                    }
+                }
+                neg ^= 1;
+                cluster.sync();
+                if (tid == 0) s_dm[c & 1] = mul_bal(dg[c * kSP + c], mt.r1, M);
+                if (tid < jb) s_um[c & 1][tid] = mul_bal(dg[c * kSP + tid], mt.r1, M);
+                __syncthreads();
+            }
+            const int32_t dm = s_dm[c & 1];
+            const int32_t *um = s_um[c & 1];
+            if (warp == 0) {
+                // the next pivot row of the replica, then its Montgomery form
+                if (c + 1 < jb) {
+                    int32_t *row = dg + (c + 1) * kSP;
+                    const int32_t av = row[c];
+                    if (lane > c && lane < jb) row[lane] = ff_mont(dm, row[lane], av, um[lane], mt);
+                    __syncwarp();
+                    if (lane < jb) s_um[(c + 1) & 1][lane] = mul_bal(row[lane], mt.r1, M);
+                    if (lane == 0) s_dm[(c + 1) & 1] = mul_bal(row[c + 1], mt.r1, M);
+                }
+            } else {
+                // a thread per row: this CTA's rows below the pivot, then the
+                // replica's rows c + 2 .. jb - 1 (the row stride kSP = 33 words
+                // keeps the lanes of a warp on distinct banks); the entry in
+                // column c stays as the row's (unnormalised) multiplier
+                const int items = nloc + max(0, jb - c - 2);
+                for (int it = tid - 32; it < items; it += kClThreads - 32) {
+                    int32_t *row;
+                    if (it < nloc) {
+                        if (rbeg + it <= col) continue;
+                        row = sp + it * kSP;
+                    } else {
+                        row = dg + (c + 2 + (it - nloc)) * kSP;
+                    }
+                    // (a zero entry still scales the row by d_c: every row below
+                    // the pivot must carry the same factor S_(c+1))
+                    const int32_t av = row[c];
+                    for (int j = c + 1; j < jb; ++j) row[j] = ff_mont(dm, row[j], av, um[j], mt);
                 }
             }
-            neg ^= 1;
-            cluster.sync();
-            if (tid == 0) s_dm[c & 1] = mul_bal(dg[c * kSP + c], mt.r1, M);
-            if (tid < jb) s_um[c & 1][tid] = mul_bal(dg[c * kSP + tid], mt.r1, M);
             __syncthreads();
         }
-        const int32_t dm = s_dm[c & 1];
-        const int32_t *um = s_um[c & 1];
-        if (warp == 0) {
-            // the next pivot row of the replica, then its Montgomery form
-            if (c + 1 < jb) {
-                int32_t *row = dg + (c + 1) * kSP;
-                const int32_t av = row[c];
-                if (lane > c && lane < jb) row[lane] = ff_mont(dm, row[lane], av, um[lane], mt);
-                __syncwarp();
-                if (lane < jb) s_um[(c + 1) & 1][lane] = mul_bal(row[lane], mt.r1, M);
-                if (lane == 0) s_dm[(c + 1) & 1] = mul_bal(row[c + 1], mt.r1, M);
-            }
-        } else {
-            // a thread per row: this CTA's rows below the pivot, then the
-            // replica's rows c + 2 .. jb - 1 (the row stride kSP = 33 words
-            // keeps the lanes of a warp on distinct banks); the entry in
-            // column c stays as the row's (unnormalised) multiplier
-            const int items = nloc + max(0, jb - c - 2);
-            for (int it = tid - 32; it < items; it += kClThreads - 32) {
-                int32_t *row;
-                if (it < nloc) {
-                    if (rbeg + it <= col) continue;
-                    row = sp + it * kSP;
-                } else {
-                    row = dg + (c + 2 + (it - nloc)) * kSP;
+        if (!dead) {
+            // 1 / d_c and 1 / S_c (S_c = d_0 ... d_(c-1)) from one inverse:
+            // prefix products P_c = d_0 ... d_c, then 1 / P_(jb-1) unwound
+            if (tid == 0) {
+                int32_t pre[kNBMax];
+                int32_t pr = 1;
+                for (int c = 0; c < jb; ++c) {
+                    pr = mul_bal(pr, dg[c * kSP + c], M);
+                    pre[c] = pr;
                 }
-                // (a zero entry still scales the row by d_c: every row below
-                // the pivot must carry the same factor S_(c+1))
-                const int32_t av = row[c];
-                for (int j = c + 1; j < jb; ++j) row[j] = ff_mont(dm, row[j], av, um[j], mt);
+                int32_t ip = inv_bal32(pr, M.p);  // 1 / P_(jb-1)
+                for (int c = jb - 1; c >= 0; --c) {
+                    // 1 / d_c = P_(c-1) / P_c; 1 / P_(c-1) = d_c / P_c
+                    s_invd[c] = c > 0 ? mul_bal(ip, pre[c - 1], M) : ip;
+                    ip = mul_bal(ip, dg[c * kSP + c], M);
+                }
+                int32_t is = 1;  // 1 / S_c = 1 / P_(c-1)
+                for (int c = 0; c < jb; ++c) {
+                    s_invS[c] = is;
+                    is = mul_bal(is, s_invd[c], M);
+                }
+                // det *= prod_c d_c / S_c
+                for (int c = 0; c < jb; ++c)
+                    det = det_mul(det, mul_bal(dg[c * kSP + c], s_invS[c], M), M);
             }
-        }
-        __syncthreads();
-    }
-    if (!dead) {
-        // 1 / d_c and 1 / S_c (S_c = d_0 ... d_(c-1)) from one inverse:
-        // prefix products P_c = d_0 ... d_c, then 1 / P_(jb-1) unwound
-        if (tid == 0) {
-            int32_t pre[kNBMax];
-            int32_t pr = 1;
-            for (int c = 0; c < jb; ++c) {
-                pr = mul_bal(pr, dg[c * kSP + c], M);
-                pre[c] = pr;
-            }
-            int32_t ip = inv_bal32(pr, M.p);  // 1 / P_(jb-1)
-            for (int c = jb - 1; c >= 0; --c) {
-                // 1 / d_c = P_(c-1) / P_c; 1 / P_(c-1) = d_c / P_c
-                s_invd[c] = c > 0 ? mul_bal(ip, pre[c - 1], M) : ip;
-                ip = mul_bal(ip, dg[c * kSP + c], M);
-            }
-            int32_t is = 1;  // 1 / S_c = 1 / P_(c-1)
-            for (int c = 0; c < jb; ++c) {
-                s_invS[c] = is;
-                is = mul_bal(is, s_invd[c], M);
-            }
-            // det *= prod_c d_c / S_c
-            for (int c = 0; c < jb; ++c)
-                det = det_mul(det, mul_bal(dg[c * kSP + c], s_invS[c], M), M);
-        }
-        __syncthreads();
-        // normalise this CTA's rows: multipliers (columns below the row's
-        // diagonal) times 1 / d_c; a pivot row's U part times 1 / S_r
-        for (int e = tid; e < nloc * jb; e += kClThreads) {
-            const int r = e / jb, j = e % jb;
-            const int64_t gr = rbeg + r - j0;  // row within the panel
-            int32_t &v = sp[r * kSP + j];
-            if (j < gr)
-                v = mul_bal(v, s_invd[j], M);
-            else
-                v = mul_bal(v, s_invS[gr], M);
-        }
-        if (tri && rank == 0) {
-            // the replica's L part likewise, for L11^{-1} below
-            for (int e = tid; e < jb * jb; e += kClThreads) {
+            __syncthreads();
+            // normalise this CTA's rows: multipliers (columns below the row's
+            // diagonal) times 1 / d_c; a pivot row's U part times 1 / S_r
+            for (int e = tid; e < nloc * jb; e += kClThreads) {
                 const int r = e / jb, j = e % jb;
-                if (j < r) dg[r * kSP + j] = mul_bal(dg[r * kSP + j], s_invd[j], M);
+                const int64_t gr = rbeg + r - j0;  // row within the panel
+                int32_t &v = sp[r * kSP + j];
+                if (j < gr)
+                    v = mul_bal(v, s_invd[j], M);
+                else
+                    v = mul_bal(v, s_invS[gr], M);
+            }
+            if (tri && rank == 0) {
+                // the replica's L part likewise, for L11^{-1} below
+                for (int e = tid; e < jb * jb; e += kClThreads) {
+                    const int r = e / jb, j = e % jb;
+                    if (j < r) dg[r * kSP + j] = mul_bal(dg[r * kSP + j], s_invd[j], M);
+                }
             }
         }
     }

@@ -90,6 +90,37 @@ def test_lu_factors_31bit():
     assert (perm == operm).all() and (lu == LU).all()
 
 
+def _zero_pivots_at(n, cols, seed):
+    """Row c (c in cols) = an integer combination of rows 0..c-1 plus a vector
+    that vanishes on columns 0..c: after c eliminations its pivot is zero mod
+    every prime and the first-nonzero rule exchanges it with the row below."""
+    rng = np.random.default_rng(seed)
+    A = workloads.dense_pm100(n, seed=seed).astype(np.int64)
+    for c in cols:
+        v = rng.integers(-50, 51, size=n)
+        v[:c + 1] = 0
+        A[c] = rng.integers(-2, 3, size=c) @ A[:c] + v
+    return A
+
+
+# zero pivots inside later panels: the second column of a panel, its first and
+# its last column, and a column of the last, 12-wide panel; the panels between
+# them have none
+@pytest.mark.parametrize("bits", [21, 31])
+def test_lu_factors_zero_pivots_inside_later_panels(bits):
+    n, cols = 300, [40, 128, 159, 200, 295]
+    A = _zero_pivots_at(n, cols, seed=bits)
+    p = P21[13] if bits == 21 else p31(1, 77)[0]
+    lu, perm, sing = idet.lu_mod_prime(A, p)
+    LU, operm, _, stop = modular.lu_mod_p(A, p)
+    assert not sing and stop == n
+    assert all(operm[c] != c for c in cols)  # each of them took a row exchange
+    assert (perm == operm).all()
+    assert (lu == LU).all()
+    primes = rprimes(9, bits)
+    assert list(idet.det_mod_primes(A, primes)) == list(modular.det_mod_primes(A, primes))
+
+
 # --- Dixon lifting --------------------------------------------------------------------
 
 @pytest.mark.parametrize("n,m", [(5, 4), (24, 7), (67, 5)])

@@ -20,6 +20,7 @@
 #include <cstdio>
 
 #include <cooperative_groups.h>
+#include <cuda_pipeline.h>
 
 #include "idet_internal.cuh"
 
@@ -55,13 +56,11 @@ __device__ __forceinline__ int32_t inv_bal32(int32_t a, uint32_t p) {
     return t0;
 }
 
-// Montgomery form with R = 2^32 for the panel's row updates: with u' = u R
-// mod p (balanced) stored once per pivot row, r - l u mod p costs one
-// 32 x 32 -> 64 product and one reduction by two 32-bit multiplies. For
-// t = l u' (|t| < p^2 / 4) and q = t p^{-1} mod 2^32 (as int32), t - q p is
-// divisible by 2^32 and v = (t - q p) / 2^32 = hi(t) - hi(q p) (the low words
-// agree) is l u mod p with |v| < p^2 / 2^34 + p / 2 < 0.63 p; r - v (in 64
-// bits) is then brought into the balanced range by one step either way.
+// Montgomery form with R = 2^32 for the panel: x' = x R mod p (balanced).
+// For a product t (|t| < 2^62) and q = t p^{-1} mod 2^32 (as int32), t - q p
+// is divisible by 2^32 and (t - q p) / 2^32 = hi(t) - hi(q p) (the low words
+// agree) is t R^{-1} mod p, of magnitude below |t| / 2^32 + p / 2: one 32 x 32
+// -> 64 product and two 32-bit multiplies per modular product.
 struct Mont {
     int32_t p, half;
     uint32_t pinv;  // p^{-1} mod 2^32
@@ -79,17 +78,6 @@ __device__ __forceinline__ Mont make_mont(uint32_t p) {
     if (r > m.half) r -= p;
     m.r1 = (int32_t)r;
     return m;
-}
-
-__device__ __forceinline__ int32_t sub_mont(int32_t r, int32_t l, int32_t um, const Mont &m) {
-    const int64_t t = (int64_t)l * um;
-    const int32_t q = (int32_t)((uint32_t)t * m.pinv);
-    const int32_t v = (int32_t)(t >> 32) - __mulhi(q, m.p);
-    // |r - v| < 1.13 p can pass 2^31 for p near 2^31: 64-bit
-    int64_t x = (int64_t)r - v;
-    if (x > m.half) x -= m.p;
-    if (x < -m.half) x += m.p;
-    return (int32_t)x;
 }
 
 // d r - a u mod p for the fraction-free panel, with d' = d R and u' = u R
@@ -342,6 +330,18 @@ __device__ __forceinline__ int32_t mont_mul(int32_t a, int32_t b, const Mont &m)
     return v;
 }
 
+// 1 / x = x^(p-2) mod p (Fermat) for x != 0, argument and result in
+// Montgomery form: square and multiply over the bits of p - 2.
+__device__ __forceinline__ int32_t mont_inv(int32_t xm, const Mont &m) {
+    const uint32_t e = (uint32_t)m.p - 2;
+    int32_t r = m.r1;  // 1 in Montgomery form
+    for (int b = 31 - __clz(e); b >= 0; --b) {
+        r = mont_mul(r, r, m);
+        if ((e >> b) & 1) r = mont_mul(r, xm, m);
+    }
+    return r;
+}
+
 // The panel's common case: when every pivot of the replica's jb x jb block
 // is nonzero, the first-nonzero rule takes the panel's top rows in order,
 // U11 is the block's U, and every row below solves x U11 = a for its L part
@@ -350,14 +350,15 @@ __device__ __forceinline__ int32_t mont_mul(int32_t a, int32_t b, const Mont &m)
 // replica_lu_cta (all threads): fraction-free LU of the block in Montgomery
 // form (d' r' - a' u' reduced once is (d r - a u)'), thread (i, g) updating
 // columns g and g + 16 of row i, one CTA barrier per column. False
-// (CTA-uniform) at the first zero pivot, with dg untouched. Otherwise the
-// inverses of the pivots d_c and of their prefix products S_c come from one
-// inverse by product scans across a warp, and dg is overwritten with the
+// (CTA-uniform) at the first zero pivot, with dg untouched. Otherwise lane c
+// of a warp inverts d_c (Fermat), the prefix products S_c of the pivots and
+// their inverses come from two product scans across the warp, and dg is
+// overwritten with the
 // block's normalised factors (L_ic = s_ic / d_c below the diagonal, U_ic =
 // s_ic / S_i on and above it). -U_kc for k < c < jb (zero elsewhere) goes to
 // ut[c][k] for 21-bit primes (narrow), else split at bit 16 into its low
-// (ut) and high (ut2) parts; w[c] = 1 / U_cc = S_c / d_c (times R^2 when
-// narrow: the solve then reduces by two Montgomery steps); *detf = prod U_cc.
+// (ut) and high (ut2) parts; w[c] = 1 / U_cc = S_c / d_c times R^2 (narrow)
+// or R^3, for the solves' Montgomery steps; *detf = prod U_cc.
 struct ReplicaScratch {
     int32_t fa[kNBMax * kSP];  // the block in Montgomery form
     int32_t invd[kNBMax], invS[kNBMax];
@@ -367,55 +368,53 @@ __device__ bool replica_lu_cta(int32_t *dg, int jb, const ModP &M, const Mont &m
                                ReplicaScratch &rs, int32_t *ut, int32_t *ut2, int32_t *w,
                                bool narrow, int32_t *detf) {
     const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
-    const int ng = blockDim.x >> 5;
     const int32_t r2 = mul_bal(mt.r1, mt.r1, M);  // R^2 mod p
     for (int e = tid; e < jb * jb; e += blockDim.x) {
         const int i = e / jb, j = e % jb;
         rs.fa[i * kSP + j] = mont_mul(dg[i * kSP + j], r2, mt);
     }
     __syncthreads();
+    static_assert(kClThreads == 16 * 32, "thread (i, g) covers columns g and g + 16");
     for (int c = 0; c < jb; ++c) {
         const int32_t dm = rs.fa[c * kSP + c];
         if (dm == 0) return false;  // every thread reads the same pivot
         if (lane > c && lane < jb) {
             int32_t *row = rs.fa + lane * kSP;
+            const int32_t *piv = rs.fa + c * kSP;
             const int32_t am = row[c];
-            for (int j = g; j < jb; j += ng)
-                if (j > c) row[j] = ff_mont(dm, row[j], am, rs.fa[c * kSP + j], mt);
+            const int32_t x0 = row[g], u0 = piv[g], x1 = row[g + 16], u1 = piv[g + 16];
+            if (g > c && g < jb) row[g] = ff_mont(dm, x0, am, u0, mt);
+            if (g + 16 > c && g + 16 < jb) row[g + 16] = ff_mont(dm, x1, am, u1, mt);
         }
         __syncthreads();
     }
     if (tid < 32) {
+        // all in Montgomery form; lanes past jb carry 1
         const unsigned full = 0xffffffffu;
-        const int32_t d = lane < jb ? mont_mul(rs.fa[lane * kSP + lane], 1, mt) : 1;  // d_lane
-        int32_t P = d;  // P_c = d_0 ... d_c
+        const int32_t dm = lane < jb ? rs.fa[lane * kSP + lane] : mt.r1;  // d_c
+        const int32_t idm = mont_inv(dm, mt);                               // 1 / d_c
+        int32_t S = dm, iS = idm;  // inclusive prefix products, then shifted
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int32_t t = __shfl_up_sync(full, P, o);
-            if (lane >= o) P = mul_bal(P, t, M);
+            const int32_t t = __shfl_up_sync(full, S, o), ti = __shfl_up_sync(full, iS, o);
+            if (lane >= o) {
+                S = mont_mul(S, t, mt);
+                iS = mont_mul(iS, ti, mt);
+            }
         }
-        int32_t S = __shfl_up_sync(full, P, 1);  // S_c = P_(c-1)
-        if (lane == 0) S = 1;
-        int32_t Q = d;  // d_c ... d_31
+        S = __shfl_up_sync(full, S, 1);  // S_c = d_0 ... d_(c-1)
+        iS = __shfl_up_sync(full, iS, 1);
+        if (lane == 0) S = iS = mt.r1;
+        int32_t uf = lane < jb ? mont_mul(dm, iS, mt) : mt.r1;  // U_cc = d_c / S_c
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int32_t t = __shfl_down_sync(full, Q, o);
-            if (lane + o < 32) Q = mul_bal(Q, t, M);
-        }
-        int32_t Qx = __shfl_down_sync(full, Q, 1);  // d_(c+1) ... d_31
-        if (lane == 31) Qx = 1;
-        const int32_t I = inv_bal32(__shfl_sync(full, P, 31), M.p);  // 1 / P_31
-        const int32_t invP = mul_bal(I, Qx, M);                        // 1 / P_c
-        const int32_t invd = mul_bal(S, invP, M);                      // 1 / d_c
-        const int32_t invS = mul_bal(invP, d, M);                      // 1 / S_c
-        int32_t uf = lane < jb ? mul_bal(d, invS, M) : 1;              // U_cc
-#pragma unroll
-        for (int o = 16; o; o >>= 1) uf = mul_bal(uf, __shfl_xor_sync(full, uf, o), M);
-        rs.invd[lane] = invd;
-        rs.invS[lane] = invS;
-        const int32_t invU = mul_bal(S, invd, M);
-        w[lane] = lane < jb ? (narrow ? mul_bal(invU, r2, M) : invU) : 0;
-        if (lane == 0) *detf = uf;
+        for (int o = 16; o; o >>= 1) uf = mont_mul(uf, __shfl_xor_sync(full, uf, o), mt);
+        rs.invd[lane] = mont_mul(idm, 1, mt);
+        rs.invS[lane] = mont_mul(iS, 1, mt);
+        const int32_t ium = mont_mul(S, idm, mt);  // 1 / U_cc = S_c / d_c
+        // R^2 / U_cc (21-bit) or R^3 / U_cc for the solves' Montgomery steps
+        const int32_t wm = narrow ? r2 : mont_mul(r2, r2, mt);
+        w[lane] = lane < jb ? mont_mul(ium, wm, mt) : 0;
+        if (lane == 0) *detf = mont_mul(uf, 1, mt);
     }
     __syncthreads();
     for (int e = tid; e < kNBMax * kNBMax; e += blockDim.x) {
@@ -436,43 +435,140 @@ __device__ bool replica_lu_cta(int32_t *dg, int jb, const ModP &M, const Mont &m
 // x U11 = a for one row below the replica (a: the row's jb panel entries,
 // overwritten in place by x, its L part, column by column):
 // x_c = (a_c - sum_{k<c} x_k U_kc) / U_cc with ut and w from replica_lu_cta
-// (ut[c][k] = 0 for k >= c, so the sum runs over whole groups of four).
+// (ut[c][k] = 0 for k >= c: the sum runs over all 32 columns, the entries
+// past c, solved or not, meeting zeros).
+// per = 2: two threads share the row (lanes 2m and 2m + 1, mask their pair),
+// each summing every other group of four, the halves exchanged by a shuffle;
+// both then hold x_c and store the same value.
 // 21-bit primes: at most 31 products below 2^40, exact in int64, reduced
 // once by two Montgomery steps (w_c = R^2 / U_cc).
+template <int per>
 __device__ __forceinline__ void solve_row_narrow(int32_t *row, int jb, const int32_t *ut,
-                                                 const int32_t *w, const Mont &mt) {
+                                                 const int32_t *w, const Mont &mt, int h,
+                                                 unsigned mask) {
     for (int c = 0; c < jb; ++c) {
         const int32_t *u = ut + c * kNBMax;
-        int64_t acc = row[c];
-        for (int k = 0; k < c; k += 4) {
+        const int32_t ac = row[c];
+        int64_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;  // four chains
+        // every group of four (no loop branch; the terms past c are zero)
+#pragma unroll
+        for (int i = 0; i < 8 / per; ++i) {
+            const int k = 4 * (per * i + h);
             const int4 q = *reinterpret_cast<const int4 *>(u + k);
-            acc += (int64_t)row[k] * q.x;
-            acc += (int64_t)row[k + 1] * q.y;
-            acc += (int64_t)row[k + 2] * q.z;
-            acc += (int64_t)row[k + 3] * q.w;
+            a0 += (int64_t)row[k] * q.x;
+            a1 += (int64_t)row[k + 1] * q.y;
+            a2 += (int64_t)row[k + 2] * q.z;
+            a3 += (int64_t)row[k + 3] * q.w;
         }
-        row[c] = mont_mul(redc64(acc, mt), w[c], mt);
+        int64_t sum = (a0 + a1) + (a2 + a3);
+        if (per == 2) sum += __shfl_xor_sync(mask, sum, 1);
+        row[c] = mont_mul(redc64(sum + ac, mt), w[c], mt);
     }
 }
 
 // The same for primes up to 2^31: -U_kc split at bit 16 (ut: its low 16
 // bits, ut2: the rest), two int64 sums of terms below 2^46 and 2^44, reduced
-// by Barrett steps.
+// by three Montgomery steps and a Montgomery product with w_c = R^3 / U_cc.
+template <int per>
 __device__ __forceinline__ void solve_row_wide(int32_t *row, int jb, const int32_t *ut,
                                                const int32_t *ut2, const int32_t *w,
-                                               const ModP &M) {
+                                               const Mont &mt, int hf, unsigned mask) {
     for (int c = 0; c < jb; ++c) {
         const int32_t *u = ut + c * kNBMax, *h = ut2 + c * kNBMax;
-        int64_t lo = row[c], hi = 0;
-        for (int k = 0; k < c; k += 4) {
+        const int32_t ac = row[c];
+        int64_t lo = 0, lo2 = 0, hi = 0, hi2 = 0;  // two chains each
+#pragma unroll
+        for (int i = 0; i < 8 / per; ++i) {
+            const int k = 4 * (per * i + hf);
             const int4 q = *reinterpret_cast<const int4 *>(u + k);
             const int4 r = *reinterpret_cast<const int4 *>(h + k);
             const int32_t x0 = row[k], x1 = row[k + 1], x2 = row[k + 2], x3 = row[k + 3];
-            lo += (int64_t)x0 * q.x + (int64_t)x1 * q.y + (int64_t)x2 * q.z + (int64_t)x3 * q.w;
-            hi += (int64_t)x0 * r.x + (int64_t)x1 * r.y + (int64_t)x2 * r.z + (int64_t)x3 * r.w;
+            lo += (int64_t)x0 * q.x + (int64_t)x2 * q.z;
+            lo2 += (int64_t)x1 * q.y + (int64_t)x3 * q.w;
+            hi += (int64_t)x0 * r.x + (int64_t)x2 * r.z;
+            hi2 += (int64_t)x1 * r.y + (int64_t)x3 * r.w;
         }
-        const int32_t v = red_bal((int64_t)red_bal(hi, M) * 65536 + red_bal(lo, M), M);
-        row[c] = mul_bal(v, w[c], M);
+        lo += lo2;
+        hi += hi2;
+        if (per == 2) {
+            lo += __shfl_xor_sync(mask, lo, 1);
+            hi += __shfl_xor_sync(mask, hi, 1);
+        }
+        // t = (lo + 2^16 hi) R^{-1} below 2^47, then t R^{-1} below 2^15 + p/2,
+        // times w_c = R^3 / U_cc with one more Montgomery step
+        const int64_t t = (int64_t)redc64(hi, mt) * 65536 + redc64(lo + ac, mt);
+        row[c] = mont_mul(redc64(t, mt), w[c], mt);
+    }
+}
+
+// L11^{-1} for the panel's triangular solves. X (32 rows of stride kSP)
+// holds the unit lower triangular L11 below its diagonal (jb x jb; rows and
+// columns past jb are the identity's); block inversion in place: for the
+// diagonal blocks of size s = 2h, whose halves are already inverted,
+// X21 <- -X22 (T21 X11) with the product T21 X11 formed in Y first. Five
+// levels of two small products, all blocks of a level at once, at most 16
+// terms per entry (exact in int64 for 21-bit residues, split at bit 16
+// otherwise). Written to out[i][j] (32 x 32, zero outside jb x jb). All the
+// CTA's threads, or (NAMED) warps 8-15 alone, synchronised by barrier 1.
+template <bool NAMED>
+__device__ void tri_inv_lower_cta(int32_t *X, int32_t *Y, const int32_t *dg, int jb,
+                                  const ModP &M, bool narrow, int32_t *out) {
+    const int tid = NAMED ? (int)threadIdx.x - 256 : (int)threadIdx.x;
+    const int nt = NAMED ? 256 : (int)blockDim.x;
+    auto sync = [] {
+        if (NAMED)
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+        else
+            __syncthreads();
+    };
+    for (int e = tid; e < kNBMax * kNBMax; e += nt) {
+        const int i = e >> 5, j = e & 31;
+        X[i * kSP + j] = (j < i && i < jb) ? dg[i * kSP + j] : (i == j ? 1 : 0);
+    }
+    sync();
+    auto dot_fin = [&](int64_t lo, int64_t hi) {
+        return narrow ? red_bal(lo, M) : red_bal((int64_t)red_bal(hi, M) * 65536 + red_bal(lo, M), M);
+    };
+    for (int h = 1; h < kNBMax; h <<= 1) {
+        const int hh = h * h, nent = (kNBMax / (2 * h)) * hh;
+        const bool act = tid < nent;
+        const int b = act ? tid / hh : 0, r = act ? (tid % hh) / h : 0, c = act ? tid % h : 0;
+        const int o = 2 * h * b;
+        const int32_t *xr = X + (o + h + r) * kSP + o;  // row o + h + r from column o
+        if (act) {
+            // Y = T21 X11: sum over c <= k < h (X11 is lower triangular)
+            int64_t lo = 0, hi = 0;
+            for (int k = c; k < h; ++k) {
+                const int32_t t = xr[k], u = X[(o + k) * kSP + o + c];
+                if (narrow) {
+                    lo += (int64_t)t * u;
+                } else {
+                    lo += (int64_t)t * (u & 0xffff);
+                    hi += (int64_t)t * (u >> 16);
+                }
+            }
+            Y[tid] = dot_fin(lo, hi);
+        }
+        sync();
+        if (act) {
+            // X21 = -X22 Y: sum over 0 <= k <= r (X22 is lower triangular)
+            int64_t lo = 0, hi = 0;
+            for (int k = 0; k <= r; ++k) {
+                const int32_t t = xr[h + k], u = Y[b * hh + k * h + c];
+                if (narrow) {
+                    lo += (int64_t)t * u;
+                } else {
+                    lo += (int64_t)t * (u & 0xffff);
+                    hi += (int64_t)t * (u >> 16);
+                }
+            }
+            X[(o + h + r) * kSP + o + c] = -dot_fin(lo, hi);
+        }
+        sync();
+    }
+    for (int e = tid; e < kNBMax * kNBMax; e += nt) {
+        const int i = e >> 5, j = e & 31;
+        out[e] = (i < jb && j < jb) ? X[i * kSP + j] : 0;
     }
 }
 
@@ -495,6 +591,7 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
     __shared__ int32_t s_w[kNBMax];                         // 1 / U_cc (times R^2: 21-bit p)
     __shared__ int32_t s_detf;                              // prod U_cc
     __shared__ ReplicaScratch s_rs;
+    __shared__ int32_t s_y[kNBMax * kNBMax / 4];  // block inversion scratch
     const int rank = (int)cluster.block_rank();
     const int w = blockIdx.x / CL;
     const ModP M = mods[w];
@@ -505,14 +602,15 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
     const int64_t rend = min(n, rbeg + chunk);
     const int nloc = rend > rbeg ? (int)(rend - rbeg) : 0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int e = tid; e < nloc * jb; e += kClThreads) {
-        int r = e / jb, j = e % jb;
-        sp[r * kSP + j] = a[(rbeg + r) * n + j0 + j];
+    // a warp per row: asynchronous copies, all in flight at once
+    if (lane < jb) {
+        for (int r = warp; r < nloc; r += kClThreads / 32)
+            __pipeline_memcpy_async(&sp[r * kSP + lane], &a[(rbeg + r) * n + j0 + lane], 4);
+        for (int r = warp; r < jb; r += kClThreads / 32)
+            __pipeline_memcpy_async(&dg[r * kSP + lane], &a[(j0 + r) * n + j0 + lane], 4);
     }
-    for (int e = tid; e < jb * jb; e += kClThreads) {
-        int r = e / jb, j = e % jb;
-        dg[r * kSP + j] = a[(j0 + r) * n + j0 + j];
-    }
+    __pipeline_commit();
+    __pipeline_wait_prior(0);
     uint32_t det = st[w].det;
     int neg = st[w].neg;
     bool dead = false;
@@ -523,16 +621,37 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
     const bool narrow = M.p < (1u << 21);
     // (the replicas agree: uniform over the cluster)
     const bool fast = replica_lu_cta(dg, jb, M, mt, s_rs, s_ut, s_ut2, s_w, narrow, &s_detf);
+    // L11^{-1} for the triangular solves comes from the last CTA, which has
+    // the fewest rows (its replica scratch is free once the factors are out):
+    // on warps 8-15 beside the rows when warps 0-7 can take them all
+    const bool tri_here = tri && rank == CL - 1;
+    int32_t *tri_w = tri ? tri + (int64_t)w * kNBMax * kNBMax : nullptr;
     if (fast) {
-        for (int r = tid; r < nloc; r += kClThreads) {
-            const int64_t gr = rbeg + r - j0;  // row within the panel
-            int32_t *row = sp + r * kSP;
-            if (gr < jb) {
-                for (int j = 0; j < jb; ++j) row[j] = dg[gr * kSP + j];
-            } else if (narrow) {
-                solve_row_narrow(row, jb, s_ut, s_w, mt);
-            } else {
-                solve_row_wide(row, jb, s_ut, s_ut2, s_w, M);
+        const bool split = tri_here && nloc <= kClThreads / 2;
+        if (tri_here && !split) tri_inv_lower_cta<false>(s_rs.fa, s_y, dg, jb, M, narrow, tri_w);
+        if (split && warp >= 8) {
+            tri_inv_lower_cta<true>(s_rs.fa, s_y, dg, jb, M, narrow, tri_w);
+        } else {
+            const int nt = split ? kClThreads / 2 : kClThreads;  // threads on rows
+            const int per = 2 * nloc <= nt ? 2 : 1;              // threads per row
+            const int h = tid % per;
+            const unsigned mask = per == 2 ? 3u << (lane & 30) : 0xffffffffu;
+            for (int r = tid / per; r < nloc; r += nt / per) {
+                const int64_t gr = rbeg + r - j0;  // row within the panel
+                int32_t *row = sp + r * kSP;
+                if (gr < jb) {
+                    for (int j = 0; j < jb; ++j) row[j] = dg[gr * kSP + j];
+                } else if (per == 2) {
+                    if (narrow)
+                        solve_row_narrow<2>(row, jb, s_ut, s_w, mt, h, mask);
+                    else
+                        solve_row_wide<2>(row, jb, s_ut, s_ut2, s_w, mt, h, mask);
+                } else {
+                    if (narrow)
+                        solve_row_narrow<1>(row, jb, s_ut, s_w, mt, 0, mask);
+                    else
+                        solve_row_wide<1>(row, jb, s_ut, s_ut2, s_w, mt, 0, mask);
+                }
             }
         }
         if (tid == 0) det = det_mul(det, s_detf, M);
@@ -669,7 +788,7 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
                 else
                     v = mul_bal(v, s_invS[gr], M);
             }
-            if (tri && rank == 0) {
+            if (tri_here) {
                 // the replica's L part likewise, for L11^{-1} below
                 for (int e = tid; e < jb * jb; e += kClThreads) {
                     const int r = e / jb, j = e % jb;
@@ -688,43 +807,16 @@ k_panel_cluster(int32_t *__restrict__ R, int64_t n, int64_t j0, int jb, int chun
         }
         return;
     }
-    for (int e = tid; e < nloc * jb; e += kClThreads) {
-        int r = e / jb, j = e % jb;
-        a[(rbeg + r) * n + j0 + j] = sp[r * kSP + j];
-    }
+    if (lane < jb)
+        for (int r = warp; r < nloc; r += kClThreads / 32)
+            a[(rbeg + r) * n + j0 + lane] = sp[r * kSP + lane];
     if (rank == 0 && tid == 0) {
         LUState s = st[w];
         s.det = det;
         s.neg = neg;
         st[w] = s;
     }
-    if (tri && rank == 0) {
-        // L11^{-1} (unit lower triangular, the strictly lower part of the
-        // replica) for the triangular solves: column j by forward substitution,
-        // x_i = -sum_{j <= k < i} L_ik x_k, by the 16 threads j*16 .. j*16+15
-        // (the sum split over them, partial sums reduced mod p before they
-        // are added); written as tri[w][i][j], zero outside jb x jb.
-        __shared__ int32_t sx[kNBMax][kNBMax + 1];
-        const int j = tid >> 4, sub = tid & 15;
-        const unsigned gmask = 0xffffu << (tid & 16);
-        for (int i = 0; i < kNBMax; ++i) {
-            int32_t x = (i == j) ? 1 : 0;
-            if (j < jb && i > j && i < jb) {
-                int64_t part = 0;
-                for (int k = j + sub; k < i; k += 16)
-                    part += (int64_t)dg[i * kSP + k] * sx[k][j];
-                int64_t acc = red_bal(part, M);
-#pragma unroll
-                for (int o = 8; o; o >>= 1) acc += __shfl_xor_sync(gmask, acc, o, 16);
-                x = red_bal(-acc, M);
-            }
-            if (sub == 0 && j < kNBMax) sx[i][j] = (i < jb && j < jb) ? x : 0;
-            __syncwarp(gmask);
-        }
-        __syncthreads();
-        for (int e = tid; e < kNBMax * kNBMax; e += kClThreads)
-            tri[(int64_t)w * kNBMax * kNBMax + e] = sx[e / kNBMax][e % kNBMax];
-    }
+    if (!fast && tri_here) tri_inv_lower_cta<false>(s_rs.fa, s_y, dg, jb, M, narrow, tri_w);
 }
 
 // X[r0 .. r0+jb)[cols] <- L^{-1} X, L unit lower triangular (jb x jb) at
@@ -1192,11 +1284,10 @@ int lu_blocked(int32_t *R, int64_t n, const ModP *mods, int W, int nb, int32_t *
             const int CL = panel_cluster_size(W);
             const int chunk = (int)((n - j0 + CL - 1) / CL);
             const size_t psmem = sizeof(int32_t) * (size_t)chunk * kSP;
-            // With few primes the panel also forms L11^{-1} from its replica (a
-            // separate launch would cost more than the forward substitution,
-            // whose 31 dependent steps lengthen the panel); with a full wave one
-            // batched launch over the primes is cheaper.
-            const bool cluster_panel = psmem <= 200 * 1024 && W <= 4;
+            // The cluster panel also forms L11^{-1} from its replica (in its
+            // last CTA, beside the other CTAs' rows); k_panel leaves it to a
+            // separate launch.
+            const bool cluster_panel = psmem <= 200 * 1024;
             if (psmem <= 200 * 1024) {
                 IDET_TRY(launch_panel_cluster(CL, W, psmem, s, R, n, j0, jb, chunk, mods, st,
                                               perm, cluster_panel ? tri_p : nullptr));

@@ -104,42 +104,54 @@ __device__ __forceinline__ int64_t core_off(int r, int k) {
     return ((int64_t)((k >> 3) * (ROWS / 8) + (r >> 3)) * 8 + (r & 7)) * 8 + (k & 7);
 }
 
-// One thread per (row, k) of each operand tile, for every prime (z).
-// A: rows m of A (M x K at lda); B: columns n of B (K x N at ldb), stored as
-// rows of B^T. Rows >= M (N) and k >= K are zero.
+// One thread per row and group of eight k of each operand tile, for every
+// prime (z): the eight residues of a group are split into limbs and each
+// limb's eight bf16 values (16 contiguous bytes of one core-matrix row) are
+// stored at once. A: rows m of A (M x K at lda), consecutive threads along a
+// row; B: columns n of B (K x N at ldb), stored as rows of B^T, consecutive
+// threads along n (coalesced loads of each k). Rows >= M (N) and k >= K are
+// zero.
 template <int L>
 __global__ void k_pack_limbs(const int32_t *__restrict__ A, int64_t lda, int64_t sA,
                              const int32_t *__restrict__ B, int64_t ldb, int64_t sB, int M, int N,
                              int K, int Kp, int Mt, int Nt, __nv_bfloat16 *__restrict__ Apk,
                              __nv_bfloat16 *__restrict__ Bpk) {
     const int w = blockIdx.z;
-    const int Kq = L * Kp;
+    const int Kq = L * Kp, G = Kp / 8;
     const int64_t atile = (int64_t)kTM * Kq, btile = (int64_t)kTN * Kq;
-    const int64_t arows = (int64_t)Mt * kTM, total = (arows + (int64_t)Nt * kTN) * Kp;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = e / Kp;
-        const int k = (int)(e - row * Kp);
-        int32_t x = 0;
-        int32_t l[L];
-        if (row < arows) {
-            const int m = (int)row;
-            if (m < M && k < K) x = A[(int64_t)w * sA + (int64_t)m * lda + k];
-            const int mt = m / kTM, r = m % kTM;
-            __nv_bfloat16 *dst = Apk + ((int64_t)w * Mt + mt) * atile;
-            split7<L>(x, l);
+    const int arows = Mt * kTM, brows = Nt * kTN;
+    const int na = arows * G, total = na + brows * G;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        int32_t x[8];
+        __nv_bfloat16 *dst[L];
+        if (e < na) {
+            const int m = e / G, k0 = 8 * (e - m * G);
+            const int32_t *src = A + (int64_t)w * sA + (int64_t)m * lda + k0;
 #pragma unroll
-            for (int i = 0; i < L; ++i) dst[core_off<kTM>(r, i * Kp + k)] = __int2bfloat16_rn(l[i]);
+            for (int i = 0; i < 8; ++i) x[i] = (m < M && k0 + i < K) ? src[i] : 0;
+            __nv_bfloat16 *base = Apk + ((int64_t)w * Mt + m / kTM) * atile;
+#pragma unroll
+            for (int l = 0; l < L; ++l) dst[l] = base + core_off<kTM>(m % kTM, l * Kp + k0);
         } else {
-            const int n = (int)(row - arows);
-            if (n < N && k < K) x = B[(int64_t)w * sB + (int64_t)k * ldb + n];
-            const int nt = n / kTN, r = n % kTN;
-            __nv_bfloat16 *dst = Bpk + ((int64_t)w * Nt + nt) * btile;
-            split7<L>(x, l);
+            const int e2 = e - na, g = e2 / brows, nn = e2 - g * brows, k0 = 8 * g;
+            const int32_t *src = B + (int64_t)w * sB + (int64_t)k0 * ldb + nn;
 #pragma unroll
-            for (int i = 0; i < L; ++i)
-                dst[core_off<L * kTN>(i * kTN + r, k)] = __int2bfloat16_rn(l[i]);
+            for (int i = 0; i < 8; ++i) x[i] = (nn < N && k0 + i < K) ? src[(int64_t)i * ldb] : 0;
+            __nv_bfloat16 *base = Bpk + ((int64_t)w * Nt + nn / kTN) * btile;
+#pragma unroll
+            for (int l = 0; l < L; ++l) dst[l] = base + core_off<L * kTN>(l * kTN + nn % kTN, k0);
         }
+        __align__(16) __nv_bfloat16 v[L][8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            int32_t li[L];
+            split7<L>(x[i], li);
+#pragma unroll
+            for (int l = 0; l < L; ++l) v[l][i] = __int2bfloat16_rn(li[l]);
+        }
+#pragma unroll
+        for (int l = 0; l < L; ++l)
+            *reinterpret_cast<uint4 *>(dst[l]) = *reinterpret_cast<const uint4 *>(v[l]);
     }
 }
 
@@ -575,7 +587,7 @@ static int gemm_tc05_l(const int32_t *A, int64_t lda, int64_t sA, const int32_t 
     const int Mt = (M + kTM - 1) / kTM, Nt = (N + kTN - 1) / kTN;
     __nv_bfloat16 *Apk = (__nv_bfloat16 *)scratch;
     __nv_bfloat16 *Bpk = Apk + (size_t)W * Mt * kTM * L * Kp;
-    const int64_t total = ((int64_t)Mt * kTM + (int64_t)Nt * kTN) * Kp;
+    const int64_t total = ((int64_t)Mt * kTM + (int64_t)Nt * kTN) * (Kp / 8);
     int pg = (int)std::min<int64_t>((total + 255) / 256, 148 * 8);
     k_pack_limbs<L><<<dim3(pg, 1, W), 256, 0, s>>>(A, lda, sA, B, ldb, sB, M, N, K, Kp, Mt, Nt,
                                                     Apk, Bpk);

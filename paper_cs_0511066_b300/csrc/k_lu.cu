@@ -970,47 +970,77 @@ k_tri_inv(const int32_t *__restrict__ Tm, int64_t strideT, int64_t n, int64_t r0
     (void)sQ;
 }
 
-// X[xr0 .. xr0+jb)[c0 .. c0+ncols) <- Inv X, per prime (blockIdx.y); 128
-// threads: 32 columns x 4 row chunks of 8.
+// X[xr0 .. xr0+jb)[c0 .. c0+ncols) <- Inv X, per prime (blockIdx.y): one
+// 32 x 32 tile of X per CTA (kTaThreads = 256). Lane r of every warp keeps
+// row r of Inv in registers (split at bit 16 for 31-bit primes); the tile
+// sits in shared memory (rows of 36 words: 16-byte aligned, a warp's row
+// access spanning all banks) and is read as broadcasts, four columns per
+// access. Warp q forms the tile's columns 4q .. 4q + 3 for all rows and
+// writes them back over its own columns; the tile then goes out row by row.
+constexpr int kTaThreads = 256;
+
 template <bool WIDE>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kTaThreads)
 k_tri_apply(const int32_t *__restrict__ Inv, int32_t *__restrict__ X, int64_t strideX, int64_t n,
             int64_t xr0, int jb, int64_t c0, int64_t ncols, const ModP *__restrict__ mods,
             const LUState *__restrict__ st) {
-    __shared__ int32_t sI[kNBMax][kNBMax + 1];
+    constexpr int kTS = 36, kWarps = kTaThreads / 32;
+    __shared__ __align__(16) int32_t sY[kNBMax * kTS];
+    __shared__ int32_t sI[kNBMax * (kNBMax + 1)];
     const int w = blockIdx.y;
     if (st && st[w].dead) return;
     const ModP M = mods[w];
-    const int32_t *I = Inv + (int64_t)w * kNBMax * kNBMax;
-    for (int e = threadIdx.x; e < kNBMax * kNBMax; e += blockDim.x)
-        sI[e / kNBMax][e % kNBMax] = I[e];
     const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
-    const int64_t j = c0 + (int64_t)blockIdx.x * 32 + lane;
-    const bool ok = j < c0 + ncols;
+    const int64_t cb0 = c0 + (int64_t)blockIdx.x * 32;
+    const int nc = (int)min((int64_t)32, c0 + ncols - cb0);  // columns in this tile
     int32_t *x = X + (int64_t)w * strideX;
-    int32_t y[kNBMax];
-#pragma unroll
-    for (int k = 0; k < kNBMax; ++k) y[k] = (ok && k < jb) ? x[(xr0 + k) * n + j] : 0;
+    const int32_t *I = Inv + (int64_t)w * kNBMax * kNBMax;
+    for (int r = q; r < kNBMax; r += kWarps) {
+        sY[r * kTS + lane] = (r < jb && lane < nc) ? x[(xr0 + r) * n + cb0 + lane] : 0;
+        sI[r * (kNBMax + 1) + lane] = I[r * kNBMax + lane];  // zero past jb
+    }
     __syncthreads();
-    if (!ok) return;
+    // row `lane` of Inv
+    int32_t t[kNBMax], th[WIDE ? kNBMax : 1];
 #pragma unroll
-    for (int rr = 0; rr < 8; ++rr) {
-        const int r = q * 8 + rr;
-        if (r >= jb) break;
-        int64_t lo = 0, hi = 0;
+    for (int k = 0; k < kNBMax; ++k) t[k] = sI[lane * (kNBMax + 1) + k];
+    if (WIDE) {
 #pragma unroll
         for (int k = 0; k < kNBMax; ++k) {
+            th[k] = t[k] >> 16;
+            t[k] &= 0xffff;
+        }
+    }
+    static_assert(kWarps * 4 == kNBMax, "one group of four columns per warp");
+    {
+        const int cb = 4 * q;
+        int64_t lo[4] = {0, 0, 0, 0}, hi[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int k = 0; k < kNBMax; ++k) {
+            const int4 y = *reinterpret_cast<const int4 *>(sY + k * kTS + cb);
+            lo[0] += (int64_t)t[k] * y.x;
+            lo[1] += (int64_t)t[k] * y.y;
+            lo[2] += (int64_t)t[k] * y.z;
+            lo[3] += (int64_t)t[k] * y.w;
             if (WIDE) {
-                lo += (int64_t)sI[r][k] * (y[k] & 0xffff);
-                hi += (int64_t)sI[r][k] * (y[k] >> 16);
-            } else {
-                lo += (int64_t)sI[r][k] * y[k];
+                hi[0] += (int64_t)th[WIDE ? k : 0] * y.x;
+                hi[1] += (int64_t)th[WIDE ? k : 0] * y.y;
+                hi[2] += (int64_t)th[WIDE ? k : 0] * y.z;
+                hi[3] += (int64_t)th[WIDE ? k : 0] * y.w;
             }
         }
-        const int32_t v = WIDE ? red_bal((int64_t)red_bal(hi, M) * 65536 + red_bal(lo, M), M)
-                               : red_bal(lo, M);
-        x[(xr0 + r) * n + j] = v;
+        int32_t v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            v[i] = WIDE ? red_bal((int64_t)red_bal(hi[i], M) * 65536 + red_bal(lo[i], M), M)
+                        : red_bal(lo[i], M);
+        __syncwarp();  // every lane has read these columns
+#pragma unroll
+        for (int i = 0; i < 4; ++i) sY[lane * kTS + cb + i] = v[i];
     }
+    __syncthreads();
+    for (int r = q; r < jb; r += kWarps)
+        if (lane < nc) x[(xr0 + r) * n + cb0 + lane] = sY[r * kTS + lane];
 }
 
 // C <- C - A B mod p (batched over primes by blockIdx.z). A: M x K (lda),
@@ -1166,7 +1196,7 @@ int trsm_lower(const int32_t *Lm, int64_t sL, int32_t *X, int64_t sX, int64_t n,
             k_tri_inv<WIDE, false><<<W, kNBMax * kNBMax, 0, s>>>(Lm, sL, n, lr0, jb, mods, st, tri);
             count_launch();
         }
-        k_tri_apply<WIDE><<<dim3((unsigned)((ncols + 31) / 32), W), 128, 0, s>>>(
+        k_tri_apply<WIDE><<<dim3((unsigned)((ncols + 31) / 32), W), kTaThreads, 0, s>>>(
             tri, X, sX, n, xr0, jb, c0, ncols, mods, st);
         count_launch();
         IDET_CUDA_TRY(cudaGetLastError());
@@ -1443,10 +1473,10 @@ int lu_inverse(const int32_t *R, const int32_t *perm, int64_t n, const ModP &mod
     auto apply = [&](const int32_t *tri_blk, int64_t k0, int kb, int64_t ncols) -> int {
         const dim3 grid((unsigned)((ncols + 31) / 32), 1);
         if (wide)
-            k_tri_apply<true><<<grid, 128, 0, s>>>(tri_blk, Y, 0, n, k0, kb, 0, ncols, mod_dev,
+            k_tri_apply<true><<<grid, kTaThreads, 0, s>>>(tri_blk, Y, 0, n, k0, kb, 0, ncols, mod_dev,
                                                    nullptr);
         else
-            k_tri_apply<false><<<grid, 128, 0, s>>>(tri_blk, Y, 0, n, k0, kb, 0, ncols, mod_dev,
+            k_tri_apply<false><<<grid, kTaThreads, 0, s>>>(tri_blk, Y, 0, n, k0, kb, 0, ncols, mod_dev,
                                                     nullptr);
         count_launch();
         IDET_CUDA_TRY(cudaGetLastError());

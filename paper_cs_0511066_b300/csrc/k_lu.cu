@@ -1043,6 +1043,90 @@ k_tri_apply(const int32_t *__restrict__ Inv, int32_t *__restrict__ X, int64_t st
         if (lane < nc) x[(xr0 + r) * n + cb0 + lane] = sY[r * kTS + lane];
 }
 
+// One block row of 4 x 32 rows (rows J0 .. J0 + JB) of Y <- T^{-1} Y for
+// the columns [0, ncols), one tile of 32 columns per CTA, in one launch:
+// the block's rows of the tile stay in shared memory while, for each 32-row
+// sub-block s in solve order (lower T: top down; upper T: bottom up),
+// X_s <- T_ss^{-1} X_s (the inverse from Inv, 32 x 32 per sub-block as
+// k_tri_inv writes them) and then X_d <- X_d - T_ds X_s for the sub-blocks d
+// still to come (T_ds read from the factor, ld n). Every 32 x 32 step keeps
+// row r of its factor block in lane r's registers (split at bit 16 for
+// 31-bit primes) and has warp q form the tile's columns 4q .. 4q + 3.
+template <bool WIDE, bool UPPER>
+__global__ void __launch_bounds__(kTaThreads)
+k_trsm_block(const int32_t *__restrict__ T, const int32_t *__restrict__ Inv,
+             int32_t *__restrict__ Y, int64_t n, int64_t J0, int JB, int64_t ncols,
+             const ModP *__restrict__ mods) {
+    constexpr int kTS = 36, kWarps = kTaThreads / 32, kRows = 4 * kNBMax;
+    static_assert(kWarps * 4 == kNBMax, "one group of four columns per warp");
+    __shared__ __align__(16) int32_t sY[kRows * kTS];
+    __shared__ int32_t sF[kNBMax * (kNBMax + 1)];
+    const ModP M = mods[0];
+    const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+    const int64_t cb0 = (int64_t)blockIdx.x * 32;
+    const int nc = (int)min((int64_t)32, ncols - cb0);  // columns in this tile
+    const int nsub = (JB + kNBMax - 1) / kNBMax;
+    for (int r = q; r < kRows; r += kWarps)
+        sY[r * kTS + lane] = (r < JB && lane < nc) ? Y[(J0 + r) * n + cb0 + lane] : 0;
+    // rows of sub-block d <- F X_s (d == s) or X_d - F X_s, F: frows x fcols
+    // at F0 (ld ldf), zero elsewhere
+    auto step = [&](const int32_t *F0, int64_t ldf, int frows, int fcols, int s_, int d) {
+        __syncthreads();  // the previous step is done with sF and the tile
+        for (int r = q; r < kNBMax; r += kWarps)
+            sF[r * (kNBMax + 1) + lane] =
+                (r < frows && lane < fcols) ? F0[(int64_t)r * ldf + lane] : 0;
+        __syncthreads();
+        int32_t t[kNBMax], th[WIDE ? kNBMax : 1];
+#pragma unroll
+        for (int k = 0; k < kNBMax; ++k) t[k] = sF[lane * (kNBMax + 1) + k];
+        if (WIDE) {
+#pragma unroll
+            for (int k = 0; k < kNBMax; ++k) {
+                th[k] = t[k] >> 16;
+                t[k] &= 0xffff;
+            }
+        }
+        const int cb = 4 * q;
+        int64_t lo[4] = {0, 0, 0, 0}, hi[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int k = 0; k < kNBMax; ++k) {
+            const int4 y = *reinterpret_cast<const int4 *>(sY + (kNBMax * s_ + k) * kTS + cb);
+            lo[0] += (int64_t)t[k] * y.x;
+            lo[1] += (int64_t)t[k] * y.y;
+            lo[2] += (int64_t)t[k] * y.z;
+            lo[3] += (int64_t)t[k] * y.w;
+            if (WIDE) {
+                hi[0] += (int64_t)th[WIDE ? k : 0] * y.x;
+                hi[1] += (int64_t)th[WIDE ? k : 0] * y.y;
+                hi[2] += (int64_t)th[WIDE ? k : 0] * y.z;
+                hi[3] += (int64_t)th[WIDE ? k : 0] * y.w;
+            }
+        }
+        int32_t v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            v[i] = WIDE ? red_bal((int64_t)red_bal(hi[i], M) * 65536 + red_bal(lo[i], M), M)
+                        : red_bal(lo[i], M);
+        __syncwarp();  // (d == s) every lane has read these columns of the rows
+        int32_t *o = sY + (kNBMax * d + lane) * kTS + cb;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) o[i] = d == s_ ? v[i] : red_bal((int64_t)o[i] - v[i], M);
+    };
+    const int64_t tsz = (int64_t)kNBMax * kNBMax;
+    for (int i = 0; i < nsub; ++i) {
+        const int s_ = UPPER ? nsub - 1 - i : i;
+        const int rs = min(kNBMax, JB - kNBMax * s_);
+        step(Inv + tsz * s_, kNBMax, kNBMax, kNBMax, s_, s_);
+        const int d0 = UPPER ? 0 : s_ + 1, d1 = UPPER ? s_ : nsub;
+        for (int d = d0; d < d1; ++d)
+            step(T + (J0 + kNBMax * d) * n + J0 + kNBMax * s_, n, min(kNBMax, JB - kNBMax * d), rs,
+                 s_, d);
+    }
+    __syncthreads();
+    for (int r = q; r < JB; r += kWarps)
+        if (lane < nc) Y[(J0 + r) * n + cb0 + lane] = sY[r * kTS + lane];
+}
+
 // C <- C - A B mod p (batched over primes by blockIdx.z). A: M x K (lda),
 // B: K x N (ldb), C: M x N (ldc). 64 x 64 tile, 256 threads, 4 x 4 outputs
 // per thread, int64 accumulators.
@@ -1503,13 +1587,38 @@ int lu_inverse(const int32_t *R, const int32_t *perm, int64_t n, const ModP &mod
         return gemm_sub<false>(Ap, n, 0, Bp, n, 0, Cp, n, 0, (int)M, (int)N, K, mod_dev, nullptr, 1,
                                s);
     };
+    // with nb = 32 a block row's four sub-block solves and the updates among
+    // them run in one launch (k_trsm_block)
+    const bool fused = nb == kNBMax;
+    auto block_solve = [&](bool upper, int64_t J0, int JB, int64_t ncols) -> int {
+        const dim3 grid((unsigned)((ncols + 31) / 32));
+        const int32_t *inv = (upper ? triU : triL) + tsz * (J0 / nb);
+        if (wide) {
+            if (upper)
+                k_trsm_block<true, true><<<grid, kTaThreads, 0, s>>>(R, inv, Y, n, J0, JB, ncols, mod_dev);
+            else
+                k_trsm_block<true, false><<<grid, kTaThreads, 0, s>>>(R, inv, Y, n, J0, JB, ncols, mod_dev);
+        } else {
+            if (upper)
+                k_trsm_block<false, true><<<grid, kTaThreads, 0, s>>>(R, inv, Y, n, J0, JB, ncols, mod_dev);
+            else
+                k_trsm_block<false, false><<<grid, kTaThreads, 0, s>>>(R, inv, Y, n, J0, JB, ncols, mod_dev);
+        }
+        count_launch();
+        IDET_CUDA_TRY(cudaGetLastError());
+        return IDET_OK;
+    };
     for (int64_t J0 = 0; J0 < n; J0 += NB) {
         const int JB = (int)((n - J0) < NB ? (n - J0) : NB);
-        for (int64_t k0 = J0; k0 < J0 + JB; k0 += nb) {
-            const int kb = (int)((J0 + JB - k0) < nb ? (J0 + JB - k0) : nb);
-            IDET_TRY(apply(triL + tsz * (k0 / nb), k0, kb, k0 + kb));
-            IDET_TRY(gsub(R + (k0 + kb) * n + k0, Y + k0 * n, Y + (k0 + kb) * n,
-                          J0 + JB - (k0 + kb), kb, k0 + kb));
+        if (fused) {
+            IDET_TRY(block_solve(false, J0, JB, J0 + JB));
+        } else {
+            for (int64_t k0 = J0; k0 < J0 + JB; k0 += nb) {
+                const int kb = (int)((J0 + JB - k0) < nb ? (J0 + JB - k0) : nb);
+                IDET_TRY(apply(triL + tsz * (k0 / nb), k0, kb, k0 + kb));
+                IDET_TRY(gsub(R + (k0 + kb) * n + k0, Y + k0 * n, Y + (k0 + kb) * n,
+                              J0 + JB - (k0 + kb), kb, k0 + kb));
+            }
         }
         IDET_TRY(gsub(R + (J0 + JB) * n + J0, Y + J0 * n, Y + (J0 + JB) * n, n - J0 - JB, JB,
                       J0 + JB));
@@ -1519,12 +1628,16 @@ int lu_inverse(const int32_t *R, const int32_t *perm, int64_t n, const ModP &mod
         const int64_t J0 = bj * NB;
         const int JB = (int)((n - J0) < NB ? (n - J0) : NB);
         const int64_t nsub = (JB + nb - 1) / nb;
-        for (int64_t bi = nsub - 1; bi >= 0; --bi) {
-            const int64_t k0 = J0 + bi * nb;
-            const int kb = (int)((J0 + JB - k0) < nb ? (J0 + JB - k0) : nb);
-            IDET_TRY(apply(triU + tsz * (k0 / nb), k0, kb, n));
-            // rows J0 .. k0 of the block: Y_r -= U[r, k0..k0+kb) Y[k0..k0+kb)
-            IDET_TRY(gsub(R + J0 * n + k0, Y + k0 * n, Y + J0 * n, k0 - J0, kb, n));
+        if (fused) {
+            IDET_TRY(block_solve(true, J0, JB, n));
+        } else {
+            for (int64_t bi = nsub - 1; bi >= 0; --bi) {
+                const int64_t k0 = J0 + bi * nb;
+                const int kb = (int)((J0 + JB - k0) < nb ? (J0 + JB - k0) : nb);
+                IDET_TRY(apply(triU + tsz * (k0 / nb), k0, kb, n));
+                // rows J0 .. k0 of the block: Y_r -= U[r, k0..k0+kb) Y[k0..k0+kb)
+                IDET_TRY(gsub(R + J0 * n + k0, Y + k0 * n, Y + J0 * n, k0 - J0, kb, n));
+            }
         }
         // rows above the block
         IDET_TRY(gsub(R + J0, Y + J0 * n, Y, J0, JB, n));

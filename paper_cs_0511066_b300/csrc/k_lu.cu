@@ -1044,41 +1044,74 @@ k_tri_apply(const int32_t *__restrict__ Inv, int32_t *__restrict__ X, int64_t st
 }
 
 // One block row of 4 x 32 rows (rows J0 .. J0 + JB) of Y <- T^{-1} Y for
-// the columns [0, ncols), one tile of 32 columns per CTA, in one launch:
-// the block's rows of the tile stay in shared memory while, for each 32-row
-// sub-block s in solve order (lower T: top down; upper T: bottom up),
-// X_s <- T_ss^{-1} X_s (the inverse from Inv, 32 x 32 per sub-block as
-// k_tri_inv writes them) and then X_d <- X_d - T_ds X_s for the sub-blocks d
-// still to come (T_ds read from the factor, ld n). Every 32 x 32 step keeps
-// row r of its factor block in lane r's registers (split at bit 16 for
-// 31-bit primes) and has warp q form the tile's columns 4q .. 4q + 3.
+// the columns [c0, c0 + ncols), one tile of 32 columns per CTA and one
+// prime per blockIdx.y, in one launch: the block's rows of the tile stay in
+// shared memory while, for each 32-row sub-block s in solve order (lower T:
+// top down; upper T: bottom up), X_s <- T_ss^{-1} X_s (the inverse of
+// sub-block s of prime w at Inv + s inv_sub + w inv_prime, 32 x 32 as
+// k_tri_inv and the panel write them) and then X_d <- X_d - T_ds X_s for the
+// sub-blocks d still to come (T_ds read from the factor, ld n). All ten
+// 32 x 32 factor blocks are copied in at once (dynamic shared memory, slot
+// d(d+1)/2 + s of the lower triangle, s(s+1)/2 + d of the upper); every
+// step keeps row r of its block in lane r's registers (split at bit 16 for
+// 31-bit primes) and has warp q form the tile's columns 4q .. 4q + 3 with
+// two accumulator chains per column.
+constexpr int kTbSlot = kNBMax * (kNBMax + 1);  // words per factor block
+constexpr size_t kTbSmem = sizeof(int32_t) * 10 * kTbSlot;
+
 template <bool WIDE, bool UPPER>
 __global__ void __launch_bounds__(kTaThreads)
-k_trsm_block(const int32_t *__restrict__ T, const int32_t *__restrict__ Inv,
-             int32_t *__restrict__ Y, int64_t n, int64_t J0, int JB, int64_t ncols,
-             const ModP *__restrict__ mods) {
+k_trsm_block(const int32_t *__restrict__ T0, int64_t strideT, const int32_t *__restrict__ Inv,
+             int64_t inv_sub, int64_t inv_prime, int32_t *__restrict__ Y0, int64_t strideY,
+             int64_t n, int64_t J0, int JB, int64_t c0, int64_t ncols,
+             const ModP *__restrict__ mods, const LUState *__restrict__ st) {
     constexpr int kTS = 36, kWarps = kTaThreads / 32, kRows = 4 * kNBMax;
     static_assert(kWarps * 4 == kNBMax, "one group of four columns per warp");
     __shared__ __align__(16) int32_t sY[kRows * kTS];
-    __shared__ int32_t sF[kNBMax * (kNBMax + 1)];
-    const ModP M = mods[0];
+    extern __shared__ int32_t sF[];  // 10 slots of kTbSlot words
+    const int w = blockIdx.y;
+    if (st && st[w].dead) return;
+    const ModP M = mods[w];
+    const int32_t *T = T0 + (int64_t)w * strideT;
+    int32_t *Y = Y0 + (int64_t)w * strideY;
     const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
-    const int64_t cb0 = (int64_t)blockIdx.x * 32;
-    const int nc = (int)min((int64_t)32, ncols - cb0);  // columns in this tile
+    const int64_t cb0 = c0 + (int64_t)blockIdx.x * 32;
+    const int nc = (int)min((int64_t)32, c0 + ncols - cb0);  // columns in this tile
     const int nsub = (JB + kNBMax - 1) / kNBMax;
-    for (int r = q; r < kRows; r += kWarps)
-        sY[r * kTS + lane] = (r < JB && lane < nc) ? Y[(J0 + r) * n + cb0 + lane] : 0;
-    // rows of sub-block d <- F X_s (d == s) or X_d - F X_s, F: frows x fcols
-    // at F0 (ld ldf), zero elsewhere
-    auto step = [&](const int32_t *F0, int64_t ldf, int frows, int fcols, int s_, int d) {
-        __syncthreads();  // the previous step is done with sF and the tile
-        for (int r = q; r < kNBMax; r += kWarps)
-            sF[r * (kNBMax + 1) + lane] =
-                (r < frows && lane < fcols) ? F0[(int64_t)r * ldf + lane] : 0;
-        __syncthreads();
+    auto slot = [](int d, int s_) { return UPPER ? s_ * (s_ + 1) / 2 + d : d * (d + 1) / 2 + s_; };
+    // the tile and the factor blocks, all copies in flight at once
+    for (int r = q; r < kRows; r += kWarps) {
+        if (r < JB && lane < nc)
+            __pipeline_memcpy_async(&sY[r * kTS + lane], &Y[(J0 + r) * n + cb0 + lane], 4);
+        else
+            sY[r * kTS + lane] = 0;
+    }
+    for (int s_ = 0; s_ < nsub; ++s_) {
+        const int rs = min(kNBMax, JB - kNBMax * s_);
+        for (int d = UPPER ? 0 : s_; d <= (UPPER ? s_ : nsub - 1); ++d) {
+            int32_t *dst = sF + slot(d, s_) * kTbSlot;
+            const int32_t *src = d == s_ ? Inv + inv_sub * s_ + inv_prime * w
+                                         : T + (J0 + kNBMax * d) * n + J0 + kNBMax * s_;
+            const int64_t ld = d == s_ ? kNBMax : n;
+            const int fr = d == s_ ? kNBMax : min(kNBMax, JB - kNBMax * d);
+            const int fc = d == s_ ? kNBMax : rs;
+            for (int r = q; r < kNBMax; r += kWarps) {
+                if (r < fr && lane < fc)
+                    __pipeline_memcpy_async(&dst[r * (kNBMax + 1) + lane], &src[r * ld + lane], 4);
+                else
+                    dst[r * (kNBMax + 1) + lane] = 0;
+            }
+        }
+    }
+    __pipeline_commit();
+    __pipeline_wait_prior(0);
+    __syncthreads();
+    // rows of sub-block d <- F X_s (d == s) or X_d - F X_s, F in slot (d, s)
+    auto step = [&](int s_, int d) {
+        const int32_t *F = sF + slot(d, s_) * kTbSlot + lane * (kNBMax + 1);
         int32_t t[kNBMax], th[WIDE ? kNBMax : 1];
 #pragma unroll
-        for (int k = 0; k < kNBMax; ++k) t[k] = sF[lane * (kNBMax + 1) + k];
+        for (int k = 0; k < kNBMax; ++k) t[k] = F[k];
         if (WIDE) {
 #pragma unroll
             for (int k = 0; k < kNBMax; ++k) {
@@ -1087,42 +1120,41 @@ k_trsm_block(const int32_t *__restrict__ T, const int32_t *__restrict__ Inv,
             }
         }
         const int cb = 4 * q;
-        int64_t lo[4] = {0, 0, 0, 0}, hi[4] = {0, 0, 0, 0};
+        int64_t lo[2][4] = {}, hi[2][4] = {};
 #pragma unroll
         for (int k = 0; k < kNBMax; ++k) {
             const int4 y = *reinterpret_cast<const int4 *>(sY + (kNBMax * s_ + k) * kTS + cb);
-            lo[0] += (int64_t)t[k] * y.x;
-            lo[1] += (int64_t)t[k] * y.y;
-            lo[2] += (int64_t)t[k] * y.z;
-            lo[3] += (int64_t)t[k] * y.w;
+            const int h = k & 1;
+            lo[h][0] += (int64_t)t[k] * y.x;
+            lo[h][1] += (int64_t)t[k] * y.y;
+            lo[h][2] += (int64_t)t[k] * y.z;
+            lo[h][3] += (int64_t)t[k] * y.w;
             if (WIDE) {
-                hi[0] += (int64_t)th[WIDE ? k : 0] * y.x;
-                hi[1] += (int64_t)th[WIDE ? k : 0] * y.y;
-                hi[2] += (int64_t)th[WIDE ? k : 0] * y.z;
-                hi[3] += (int64_t)th[WIDE ? k : 0] * y.w;
+                hi[h][0] += (int64_t)th[WIDE ? k : 0] * y.x;
+                hi[h][1] += (int64_t)th[WIDE ? k : 0] * y.y;
+                hi[h][2] += (int64_t)th[WIDE ? k : 0] * y.z;
+                hi[h][3] += (int64_t)th[WIDE ? k : 0] * y.w;
             }
         }
         int32_t v[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-            v[i] = WIDE ? red_bal((int64_t)red_bal(hi[i], M) * 65536 + red_bal(lo[i], M), M)
-                        : red_bal(lo[i], M);
+        for (int i = 0; i < 4; ++i) {
+            const int64_t l = lo[0][i] + lo[1][i];
+            v[i] = WIDE ? red_bal((int64_t)red_bal(hi[0][i] + hi[1][i], M) * 65536 + red_bal(l, M), M)
+                        : red_bal(l, M);
+        }
         __syncwarp();  // (d == s) every lane has read these columns of the rows
         int32_t *o = sY + (kNBMax * d + lane) * kTS + cb;
 #pragma unroll
         for (int i = 0; i < 4; ++i) o[i] = d == s_ ? v[i] : red_bal((int64_t)o[i] - v[i], M);
     };
-    const int64_t tsz = (int64_t)kNBMax * kNBMax;
     for (int i = 0; i < nsub; ++i) {
         const int s_ = UPPER ? nsub - 1 - i : i;
-        const int rs = min(kNBMax, JB - kNBMax * s_);
-        step(Inv + tsz * s_, kNBMax, kNBMax, kNBMax, s_, s_);
-        const int d0 = UPPER ? 0 : s_ + 1, d1 = UPPER ? s_ : nsub;
-        for (int d = d0; d < d1; ++d)
-            step(T + (J0 + kNBMax * d) * n + J0 + kNBMax * s_, n, min(kNBMax, JB - kNBMax * d), rs,
-                 s_, d);
+        step(s_, s_);
+        __syncthreads();  // X_s is final
+        for (int d = UPPER ? 0 : s_ + 1; d < (UPPER ? s_ : nsub); ++d) step(s_, d);
+        __syncthreads();
     }
-    __syncthreads();
     for (int r = q; r < JB; r += kWarps)
         if (lane < nc) Y[(J0 + r) * n + cb0 + lane] = sY[r * kTS + lane];
 }
@@ -1424,13 +1456,25 @@ int lu_blocked(int32_t *R, int64_t n, const ModP *mods, int W, int nb, int32_t *
         }
         const int64_t rest = n - J0 - JB;
         if (rest <= 0) break;
-        for (int64_t i0 = J0; i0 < J0 + JB; i0 += nb) {
-            const int ib = (int)((J0 + JB - i0) < nb ? (J0 + JB - i0) : nb);
-            int32_t *tri_p = tri ? tri + (size_t)((i0 - J0) / nb) * W * kNBMax * kNBMax : nullptr;
-            IDET_TRY(trsm_lower<WIDE>(R, nn, R, nn, n, i0, i0, ib, J0 + JB, rest, mods, st, W, s,
-                                      tri_p, tri_p != nullptr));
-            const int64_t below = J0 + JB - (i0 + ib);
-            if (below > 0) IDET_TRY(upd(i0 + ib, J0 + JB, i0, (int)below, (int)rest, ib));
+        if (tri && nb == kNBMax) {
+            // U12 = L11^{-1} A12 for the block row: the four sub-block solves
+            // and the updates among them in one launch
+            const int64_t tw = (int64_t)kNBMax * kNBMax;
+            IDET_TRY(allow_max_smem((const void *)k_trsm_block<WIDE, false>));
+            k_trsm_block<WIDE, false><<<dim3((unsigned)((rest + 31) / 32), W), kTaThreads, kTbSmem, s>>>(
+                R, nn, tri, tw * W, tw, R, nn, n, J0, JB, J0 + JB, rest, mods, st);
+            count_launch();
+            IDET_CUDA_TRY(cudaGetLastError());
+        } else {
+            for (int64_t i0 = J0; i0 < J0 + JB; i0 += nb) {
+                const int ib = (int)((J0 + JB - i0) < nb ? (J0 + JB - i0) : nb);
+                int32_t *tri_p =
+                    tri ? tri + (size_t)((i0 - J0) / nb) * W * kNBMax * kNBMax : nullptr;
+                IDET_TRY(trsm_lower<WIDE>(R, nn, R, nn, n, i0, i0, ib, J0 + JB, rest, mods, st,
+                                          W, s, tri_p, tri_p != nullptr));
+                const int64_t below = J0 + JB - (i0 + ib);
+                if (below > 0) IDET_TRY(upd(i0 + ib, J0 + JB, i0, (int)below, (int)rest, ib));
+            }
         }
         IDET_TRY(upd(J0 + JB, J0 + JB, J0, (int)rest, (int)rest, JB));
     }
@@ -1592,17 +1636,26 @@ int lu_inverse(const int32_t *R, const int32_t *perm, int64_t n, const ModP &mod
     const bool fused = nb == kNBMax;
     auto block_solve = [&](bool upper, int64_t J0, int JB, int64_t ncols) -> int {
         const dim3 grid((unsigned)((ncols + 31) / 32));
+        IDET_TRY(allow_max_smem(wide ? (upper ? (const void *)k_trsm_block<true, true>
+                                              : (const void *)k_trsm_block<true, false>)
+                                     : (upper ? (const void *)k_trsm_block<false, true>
+                                              : (const void *)k_trsm_block<false, false>)));
         const int32_t *inv = (upper ? triU : triL) + tsz * (J0 / nb);
+        const int64_t is = (int64_t)tsz;
         if (wide) {
             if (upper)
-                k_trsm_block<true, true><<<grid, kTaThreads, 0, s>>>(R, inv, Y, n, J0, JB, ncols, mod_dev);
+                k_trsm_block<true, true><<<grid, kTaThreads, kTbSmem, s>>>(
+                    R, 0, inv, is, 0, Y, 0, n, J0, JB, 0, ncols, mod_dev, nullptr);
             else
-                k_trsm_block<true, false><<<grid, kTaThreads, 0, s>>>(R, inv, Y, n, J0, JB, ncols, mod_dev);
+                k_trsm_block<true, false><<<grid, kTaThreads, kTbSmem, s>>>(
+                    R, 0, inv, is, 0, Y, 0, n, J0, JB, 0, ncols, mod_dev, nullptr);
         } else {
             if (upper)
-                k_trsm_block<false, true><<<grid, kTaThreads, 0, s>>>(R, inv, Y, n, J0, JB, ncols, mod_dev);
+                k_trsm_block<false, true><<<grid, kTaThreads, kTbSmem, s>>>(
+                    R, 0, inv, is, 0, Y, 0, n, J0, JB, 0, ncols, mod_dev, nullptr);
             else
-                k_trsm_block<false, false><<<grid, kTaThreads, 0, s>>>(R, inv, Y, n, J0, JB, ncols, mod_dev);
+                k_trsm_block<false, false><<<grid, kTaThreads, kTbSmem, s>>>(
+                    R, 0, inv, is, 0, Y, 0, n, J0, JB, 0, ncols, mod_dev, nullptr);
         }
         count_launch();
         IDET_CUDA_TRY(cudaGetLastError());

@@ -247,6 +247,10 @@ def run_lu_paths(torch, idet):
     print(json.dumps({"case": "lu_paths", "n": 4000, "primes": len(pool), "paths": out}))
 
 
+def _is_prime(m):
+    return m > 1 and all(m % d for d in range(2, int(m ** 0.5) + 1))
+
+
 def run_case(case):
     """Small fixed invocations of single kernels, for profiler captures."""
     import torch
@@ -265,6 +269,12 @@ def run_case(case):
         # the whole determinant at n = 1000: one rational reconstruction of
         # 803 base-p digits in radix 2^31
         idet.int_det(A)
+    elif case == "lu_wave":
+        # the first CRA wave's LU at n = 4000: 17 primes of 21 bits, default paths
+        idet.det_mod_primes(A, [p for p in range(1048583, 1048800, 2) if _is_prime(p)][:17])
+    elif case == "lu_lift":
+        # the lifting prime's LU at n = 4000: one 31-bit prime
+        idet.det_mod_primes(A, [2147483629])
     elif case.startswith("lu"):
         path = {"lu": 1, "lu_int64": 1, "lu_i8": 2, "lu_f64": 3, "lu_bf16": 4, "lu_tc05": 5}[case]
         idet.det_mod_primes(A, [1048583, 1048589, 1048601, 1048609], update_path=path)
@@ -665,6 +675,8 @@ def main():
                     help="profiling case: 'lift' (Dixon lifting, n=4000, 64 digits), "
                          "'lu' / 'lu_int64' / 'lu_i8' / 'lu_f64' / 'lu_bf16' / 'lu_tc05' (det "
                          "mod 4 primes, n=4000, one update path): runs once and prints timings; "
+                         "'lu_wave' / 'lu_lift': the 17-prime (21-bit) and one-prime (31-bit) "
+                         "LUs of the n=4000 determinant; "
                          "'lu_paths': every update path timed on 16 primes; "
                          "'rr': the whole determinant at n=1000 [0,255] (one reconstruction); "
                          "'peaks': int8/bf16/fp64 GEMM throughput of the vendor libraries")

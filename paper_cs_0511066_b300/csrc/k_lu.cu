@@ -1428,7 +1428,15 @@ int lu_blocked(int32_t *R, int64_t n, const ModP *mods, int W, int nb, int32_t *
             // block row below; the cluster panel forms it from its replica
             int32_t *tri_p = tri ? tri + (size_t)((j0 - J0) / nb) * W * kNBMax * kNBMax : nullptr;
             const int CL = panel_cluster_size(W);
-            const int chunk = (int)((n - j0 + CL - 1) / CL);
+            // rows per CTA: the last CTA, which also forms L11^{-1}, takes at
+            // most 128 (its rows then fit on half its warps, two threads a
+            // row) when the others stay within 256 (two threads a row too)
+            const int64_t rows = n - j0;
+            int chunk = (int)((rows + CL - 1) / CL);
+            if (rows > 128) {
+                const int chunk_t = (int)((rows - 128 + CL - 2) / (CL - 1));
+                if (chunk_t <= kClThreads / 2 && chunk_t >= chunk) chunk = chunk_t;
+            }
             const size_t psmem = sizeof(int32_t) * (size_t)chunk * kSP;
             // The cluster panel also forms L11^{-1} from its replica (in its
             // last CTA, beside the other CTAs' rows); k_panel leaves it to a

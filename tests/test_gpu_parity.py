@@ -121,6 +121,28 @@ def test_lu_factors_zero_pivots_inside_later_panels(bits):
     assert list(idet.det_mod_primes(A, primes)) == list(modular.det_mod_primes(A, primes))
 
 
+# Panels whose last CTA gets fewer rows than the others (the CTA that also
+# inverts L11): from 128 rows per cluster CTA on, i.e. about 1024 panel rows
+# with the 8-CTA clusters of 17 primes and 2048 with the 16-CTA cluster of one
+# prime; a zero pivot in the first such panels takes the column loop there.
+def test_det_mod_17_primes_uneven_panel_rows():
+    A = _zero_pivots_at(1100, [40], seed=5)
+    primes = rprimes(17, 5)
+    assert list(idet.det_mod_primes(A, primes)) == \
+        list(modular.det_mod_primes(A, primes, threads=4))
+
+
+def test_lu_factors_uneven_panel_rows_one_prime():
+    n = 2100
+    A = _zero_pivots_at(n, [40], seed=6)
+    p = p31(1, 6)[0]
+    lu, perm, sing = idet.lu_mod_prime(A, p)
+    LU, operm, _, stop = modular.lu_mod_p(A, p)
+    assert not sing and stop == n and operm[40] != 40
+    assert (perm == operm).all()
+    assert (lu == LU).all()
+
+
 # --- Dixon lifting --------------------------------------------------------------------
 
 @pytest.mark.parametrize("n,m", [(5, 4), (24, 7), (67, 5)])

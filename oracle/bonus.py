@@ -2,8 +2,8 @@
 
 With X = A^{-1} B for an n x k right-hand side B, s~ the common denominator
 of the entries of X (the lcm of their denominators, Section 2.2) and
-N = s~ X the integer matrix of numerators, Lemma 3.5 and the paragraph
-"Removing the undesired factors" give the factor
+N = s~ X the integer matrix of numerators, Lemma 3.5 and the subsection of
+Section 3.2 on taking out the unwanted factors give the factor
 
     pi~_k = s~^k / gcd(det(R N), s~^k)
 

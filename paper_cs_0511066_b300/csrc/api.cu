@@ -101,7 +101,7 @@ int Workspace::alloc(void **ptr, size_t bytes) {
 }
 
 // ---------------------------------------------------------------------------
-// Primes and random numbers (parameter choice, Alg. 2.1 "random primes")
+// Primes and random numbers (parameter choice; Alg. 2.1 draws its primes at random)
 
 static const uint32_t kLo21 = 1u << 20, kHi21 = 1u << 21;
 

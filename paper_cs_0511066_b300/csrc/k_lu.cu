@@ -858,41 +858,6 @@ __global__ void k_trsm_lower(const int32_t *__restrict__ Lm, int64_t strideL,
     }
 }
 
-// X[r0 .. r0+jb)[cols] <- U^{-1} X, U upper triangular with nonzero diagonal.
-template <bool WIDE>
-__global__ void k_trsm_upper(const int32_t *__restrict__ Um, int64_t n, int64_t ur0,
-                             int32_t *__restrict__ X, int64_t xr0, int jb,
-                             int64_t ncols, ModP M) {
-    __shared__ int32_t sU[kNBMax][kNBMax + 1];
-    __shared__ int32_t sInv[kNBMax];
-    for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) {
-        int r = e / jb, k = e % jb;
-        sU[r][k] = Um[(ur0 + r) * n + ur0 + k];
-    }
-    __syncthreads();
-    if (threadIdx.x < jb) sInv[threadIdx.x] = inv_bal(sU[threadIdx.x][threadIdx.x], M.p);
-    __syncthreads();
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= ncols) return;
-    int32_t u[kNBMax];
-#pragma unroll
-    for (int rr = kNBMax - 1; rr >= 0; --rr) {
-        if (rr < jb) {
-            int64_t acc = X[(xr0 + rr) * n + j];
-            int cnt = 0;
-#pragma unroll
-            for (int k = 0; k < kNBMax; ++k) {
-                if (k > rr && k < jb) {
-                    acc -= (int64_t)sU[rr][k] * u[k];
-                    if (WIDE && (++cnt % kFoldWide) == 0) acc = red_bal(acc, M);
-                }
-            }
-            u[rr] = mul_bal(red_bal(acc, M), sInv[rr], M);
-            X[(xr0 + rr) * n + j] = u[rr];
-        }
-    }
-}
-
 // Triangular solves by explicit inverses of the nb x nb diagonal blocks:
 // k_tri_inv forms T^{-1} once per prime (one thread per column of the
 // inverse: forward substitution on e_c for a unit lower T, backward with the
